@@ -1,0 +1,196 @@
+/*
+ * cm.h -- C ABI of the GB300 contrast-maximisation (CM) library, libcm.so.
+ *
+ * The library computes the self-supervised loss of arXiv 2412.06359 ("On-Device
+ * Self-Supervised Learning of Low-Latency Monocular Depth from Only Events")
+ * and its gradient on one GPU, every step in hand-written sm_103a kernels:
+ *
+ *   flow from inverse depth and ego-motion   (Sec. 3.2, Eq. 2; rigid motion field)
+ *   iterative warp of every event to the bin edges, bilinearly re-sampling
+ *     the flow at the current position        (Sec. 3.1; Sec. 3.3)
+ *   masking of events that leave the image at any point   (Sec. 3.1)
+ *   bilinear splat into polarity-split images of warped events (IWEs) of
+ *     counts and timestamp sums               (Sec. 3.1, kernel kappa in Eq. 1)
+ *   the average-timestamp focus loss, scaled by the number of non-empty
+ *     pixels and averaged over the reference times   (Eq. 1)
+ *   the analytic backward to flow, inverse depth and ego-motion (Sec. 3.3)
+ *
+ * Definitions used throughout (the paper leaves these open; the design notes
+ * of the repository list each reading with its reason):
+ *   tau = (t - t0) / (t1 - t0) is time normalised to the window [t0, t1];
+ *   B bins of equal length, edges tau_j = j / B; an event at tau lies in bin
+ *   b = min(floor(tau B), B - 1).
+ *   Reference times: CM_REF_END -> only the window end (R = 1);
+ *   CM_REF_ALL_EDGES -> all B + 1 bin edges (R = B + 1).
+ *   Average timestamp of an event at reference tau_r: 1 - |tau_r - tau|.
+ *   IWE of reference r, pixel x, polarity p: C_p(x) = sum of bilinear weights,
+ *   S_p(x) = sum of weight * average timestamp; T_p = S_p / (C_p + eps);
+ *   L_r = sum_x (T_+^2 + T_-^2) / (N_nz(r) + eps), N_nz(r) = number of pixels
+ *   with C_+ + C_- > 0;  loss L = (1/R) sum_r L_r.
+ *   Pixel centres lie at integer coordinates; the image is the closed box
+ *   [0, W-1] x [0, H-1]; an event any of whose computed trajectory points lies
+ *   outside it contributes to no IWE.
+ *   Flow is in pixels per window (per unit tau).
+ *
+ * Conventions for every entry point:
+ *   - Pointers named dev_* or documented as "device" are CUDA device memory the
+ *     caller owns (for example torch tensors' data_ptr()).  Host structs
+ *     (cm_camera, cm_events, cm_loss_cfg) are read during the call only.
+ *   - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *     stream.  Every call is asynchronous and stream-ordered: it enqueues work
+ *     and returns; results are valid once the stream reaches that point.
+ *   - The return value is a status code (CM_OK = 0).  Arguments are validated
+ *     on the host before anything is enqueued; nothing is enqueued on error.
+ *     No exception crosses the ABI.
+ *   - Events are structure-of-arrays in device memory: x, y int16 pixel column
+ *     and row, t float32 (ascending order is expected for performance, not for
+ *     correctness), p int8 polarity (> 0 positive, otherwise negative).  An
+ *     event whose (x, y) lies outside the sensor is treated as masked.
+ */
+#ifndef CM_H
+#define CM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define CM_OK 0
+#define CM_EINVAL 1     /* invalid argument (sizes, null pointers, nbins, t1 <= t0, ...) */
+#define CM_ENOMEM 2     /* workspace or server memory too small / allocation failed */
+#define CM_EBUSY 3      /* server: no slot or memory free for the request right now */
+#define CM_ETIMEOUT 4   /* a bounded wait gave up */
+#define CM_ECUDA 5      /* a CUDA runtime call failed (launch error, ...) */
+#define CM_ENOTFOUND 6  /* server: unknown ticket */
+#define CM_ESTATE 7     /* call out of order (backward without a forward, ...) */
+
+/* ---- reference-time modes ---- */
+#define CM_REF_END 0        /* one reference at the window end (the linear-warp variant, Sec. 4.2) */
+#define CM_REF_ALL_EDGES 1  /* every bin edge (supp. "Training": warp all events to all bin edges) */
+
+/* ---- splat strategies ---- */
+#define CM_SPLAT_AUTO 0     /* pick by the autotuner's cached choice (atomic until tuned) */
+#define CM_SPLAT_ATOMIC 1   /* FP32 vector atomics into the IWE (order of additions not fixed) */
+#define CM_SPLAT_SORT 2     /* deterministic: sort contributions by pixel, segmented sums */
+
+#define CM_MAX_BINS 32      /* largest supported number of bins B */
+
+/* Pinhole intrinsics of an undistorted, rectified sensor of width x height pixels. */
+typedef struct {
+    int32_t width, height;
+    float fx, fy, cx, cy;
+} cm_camera;
+
+/* One window of events (device SoA arrays of n entries) and its time span. */
+typedef struct {
+    const int16_t* x;
+    const int16_t* y;
+    const float* t;
+    const int8_t* p;
+    int64_t n;
+    float t0, t1;
+} cm_events;
+
+/* Loss configuration. */
+typedef struct {
+    int32_t nbins;        /* B, 1..CM_MAX_BINS */
+    int32_t ref_mode;     /* CM_REF_END or CM_REF_ALL_EDGES */
+    int32_t splat;        /* CM_SPLAT_* */
+    int32_t store_warps;  /* 0: the backward recomputes trajectories (default); 1: reserved */
+    float eps;            /* regulariser of both ratios; 1e-9 when <= 0 */
+} cm_loss_cfg;
+
+/* Opaque handle: the layout of a caller-provided device buffer (IWE, flow,
+ * reduction partials, statistics) plus the state the backward needs. */
+typedef struct cm_workspace cm_workspace;
+
+/* Human-readable name of a status code (static string). */
+const char* cm_status_string(int status);
+
+/* Library ABI version (incremented on incompatible changes). */
+int cm_abi_version(void);
+
+/*
+ * Device bytes a workspace needs for windows of this camera and configuration
+ * with up to max_events events and n_flow_bins flow fields (1 or nbins).
+ * Writes the size to *bytes.  Errors: CM_EINVAL.
+ */
+int cm_workspace_query(const cm_camera* cam, const cm_loss_cfg* cfg, int64_t max_events,
+                       int32_t n_flow_bins, size_t* bytes);
+
+/*
+ * Lay a workspace over caller-owned device memory dev_mem of `bytes` bytes
+ * (256-byte aligned, at least cm_workspace_query's size).  The library never
+ * allocates device memory for a workspace and never frees dev_mem; *ws is a
+ * small host object released by cm_workspace_destroy.  A workspace serves one
+ * stream at a time.  Errors: CM_EINVAL, CM_ENOMEM (buffer too small).
+ */
+int cm_workspace_create(void* dev_mem, size_t bytes, const cm_camera* cam, const cm_loss_cfg* cfg,
+                        int64_t max_events, int32_t n_flow_bins, cm_workspace** ws);
+int cm_workspace_destroy(cm_workspace* ws);
+
+/*
+ * S1 (Sec. 3.2, Eq. 2 in its instantaneous form): per-pixel flow of a static
+ * scene for a camera moving with linear velocity v and angular velocity w,
+ *   xn = (u - cx)/fx, yn = (v - cy)/fy, rho = inverse depth,
+ *   flow_x = dt fx [rho(-vx + xn vz) + xn yn wx - (1 + xn^2) wy + yn wz]
+ *   flow_y = dt fy [rho(-vy + yn vz) + (1 + yn^2) wx - xn yn wy - xn wz]
+ * inv_depth: device float [H][W]; ego6: device float (vx, vy, vz, wx, wy, wz);
+ * flow_out: device float [H][W][2].  dt_window: window length in the units of
+ * the velocities.  Errors: CM_EINVAL, CM_ECUDA.
+ */
+int cm_flow_from_depth(const cm_camera* cam, const float* inv_depth, const float* ego6, float dt_window,
+                       float* flow_out, void* stream);
+
+/*
+ * S2-S4 (Sec. 3.1, 3.3): warp every event along its trajectory and splat it
+ * into the IWEs.  flow: device float [n_flow_bins][H][W][2] (n_flow_bins 1 or
+ * cfg->nbins).  iwe_out: device float [R][H][W][4] holding (C+, S+, C-, S-) per
+ * pixel; it is zeroed and filled by the call.  If iwe_out is NULL the IWE is
+ * built in the workspace.  ws may be NULL when iwe_out is given.
+ * Errors: CM_EINVAL, CM_ECUDA.
+ */
+int cm_warp_splat(const cm_camera* cam, const cm_events* ev, const float* flow, int32_t n_flow_bins,
+                  const cm_loss_cfg* cfg, cm_workspace* ws, float* iwe_out, void* stream);
+
+/*
+ * S1-S5: the CM loss of one window, written to the device float *loss_out.
+ * Give either flow (device [n_flow_bins][H][W][2]) or, with flow NULL,
+ * inv_depth (device [H][W]) + ego6 (device [6]) + dt_window, from which the
+ * flow is computed into the workspace (n_flow_bins must then be 1).
+ * The workspace keeps what the backward needs; the per-reference losses and
+ * non-empty counts can be read with cm_workspace_stats.
+ * Errors: CM_EINVAL, CM_ENOMEM (workspace too small for n), CM_ECUDA.
+ */
+int cm_loss_forward(const cm_camera* cam, const cm_events* ev, const float* flow, int32_t n_flow_bins,
+                    const float* inv_depth, const float* ego6, float dt_window, const cm_loss_cfg* cfg,
+                    cm_workspace* ws, float* loss_out, void* stream);
+
+/*
+ * S6-S7 (Sec. 3.3 backward pass): gradient of dloss * L, where dloss is a device
+ * float scalar (the upstream gradient).  Must follow cm_loss_forward on the
+ * same workspace and stream with the same arguments.  Trajectories are
+ * recomputed, not stored.  Outputs (each may be NULL):
+ *   dflow       device float [n_flow_bins][H][W][2]   dL/dflow
+ *   dinv_depth  device float [H][W]                    dL/d(inverse depth)  (depth input only)
+ *   dego6       device float [6]                       dL/d(ego-motion)     (depth input only)
+ * Outputs are overwritten, not accumulated.  Errors: CM_EINVAL, CM_ESTATE, CM_ECUDA.
+ */
+int cm_loss_backward(const cm_camera* cam, const cm_events* ev, const float* flow, int32_t n_flow_bins,
+                     const float* inv_depth, const float* ego6, float dt_window, const cm_loss_cfg* cfg,
+                     cm_workspace* ws, const float* dloss, float* dflow, float* dinv_depth, float* dego6,
+                     void* stream);
+
+/*
+ * Device pointers to the per-reference statistics of the last forward on ws:
+ * loss_r -> float [R] (L_r), nnz_r -> int32 [R] (N_nz(r)).  Either may be NULL.
+ */
+int cm_workspace_stats(const cm_workspace* ws, const float** loss_r, const int32_t** nnz_r);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CM_H */

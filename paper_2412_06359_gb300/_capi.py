@@ -1,0 +1,146 @@
+"""ctypes binding of libcm.so with the names of include/cm.h.
+
+Argument marshalling only: every function takes plain integers for device
+pointers and streams and returns what the C call returns (raising CMError on a
+non-zero status).  Loading fails loudly when libcm.so is missing; there is no
+fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libcm.so")
+
+CM_OK, CM_EINVAL, CM_ENOMEM, CM_EBUSY, CM_ETIMEOUT, CM_ECUDA, CM_ENOTFOUND, CM_ESTATE = range(8)
+CM_REF_END, CM_REF_ALL_EDGES = 0, 1
+CM_SPLAT_AUTO, CM_SPLAT_ATOMIC, CM_SPLAT_SORT = 0, 1, 2
+CM_MAX_BINS = 32
+
+
+class CMError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = _lib_or_none().cm_status_string(status).decode() if _lib_or_none() else str(status)
+        super().__init__(f"{where}: {msg} (status {status})")
+
+
+class cm_camera(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("fx", ctypes.c_float),
+                ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float)]
+
+
+class cm_events(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("t", ctypes.c_void_p), ("p", ctypes.c_void_p),
+                ("n", ctypes.c_int64), ("t0", ctypes.c_float), ("t1", ctypes.c_float)]
+
+
+class cm_loss_cfg(ctypes.Structure):
+    _fields_ = [("nbins", ctypes.c_int32), ("ref_mode", ctypes.c_int32), ("splat", ctypes.c_int32),
+                ("store_warps", ctypes.c_int32), ("eps", ctypes.c_float)]
+
+
+_lib = None
+
+_vp, _i32, _i64, _f32, _sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_size_t
+_P = ctypes.POINTER
+
+# name -> (argtypes, restype); restype int means a status code
+SIGNATURES = {
+    "cm_status_string": ([ctypes.c_int], ctypes.c_char_p),
+    "cm_abi_version": ([], ctypes.c_int),
+    "cm_workspace_query": ([_P(cm_camera), _P(cm_loss_cfg), _i64, _i32, _P(_sz)], ctypes.c_int),
+    "cm_workspace_create": ([_vp, _sz, _P(cm_camera), _P(cm_loss_cfg), _i64, _i32, _P(_vp)], ctypes.c_int),
+    "cm_workspace_destroy": ([_vp], ctypes.c_int),
+    "cm_workspace_stats": ([_vp, _P(_vp), _P(_vp)], ctypes.c_int),
+    "cm_flow_from_depth": ([_P(cm_camera), _vp, _vp, _f32, _vp, _vp], ctypes.c_int),
+    "cm_warp_splat": ([_P(cm_camera), _P(cm_events), _vp, _i32, _P(cm_loss_cfg), _vp, _vp, _vp], ctypes.c_int),
+    "cm_loss_forward": ([_P(cm_camera), _P(cm_events), _vp, _i32, _vp, _vp, _f32, _P(cm_loss_cfg), _vp, _vp, _vp],
+                        ctypes.c_int),
+    "cm_loss_backward": ([_P(cm_camera), _P(cm_events), _vp, _i32, _vp, _vp, _f32, _P(cm_loss_cfg), _vp, _vp,
+                          _vp, _vp, _vp, _vp], ctypes.c_int),
+}
+
+
+def _lib_or_none():
+    return _lib
+
+
+def lib():
+    """Load libcm.so (raises when it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libcm.so is not built ({LIB_PATH}); run paper_2412_06359_gb300.build.build()")
+        l = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in SIGNATURES.items():
+            fn = getattr(l, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = l
+    return _lib
+
+
+def _check(status: int, where: str):
+    if status != CM_OK:
+        raise CMError(status, where)
+
+
+# ---------------------------------------------------------------------------
+# the entry points (same names as include/cm.h)
+
+
+def cm_status_string(status: int) -> str:
+    return lib().cm_status_string(status).decode()
+
+
+def cm_abi_version() -> int:
+    return lib().cm_abi_version()
+
+
+def cm_workspace_query(cam: cm_camera, cfg: cm_loss_cfg, max_events: int, n_flow_bins: int) -> int:
+    out = _sz(0)
+    _check(lib().cm_workspace_query(ctypes.byref(cam), ctypes.byref(cfg), max_events, n_flow_bins,
+                                    ctypes.byref(out)), "cm_workspace_query")
+    return out.value
+
+
+def cm_workspace_create(dev_mem: int, nbytes: int, cam: cm_camera, cfg: cm_loss_cfg, max_events: int,
+                        n_flow_bins: int) -> int:
+    h = _vp(0)
+    _check(lib().cm_workspace_create(dev_mem, nbytes, ctypes.byref(cam), ctypes.byref(cfg), max_events,
+                                     n_flow_bins, ctypes.byref(h)), "cm_workspace_create")
+    return h.value
+
+
+def cm_workspace_destroy(ws: int) -> None:
+    _check(lib().cm_workspace_destroy(ws), "cm_workspace_destroy")
+
+
+def cm_workspace_stats(ws: int) -> tuple[int, int]:
+    a, b = _vp(0), _vp(0)
+    _check(lib().cm_workspace_stats(ws, ctypes.byref(a), ctypes.byref(b)), "cm_workspace_stats")
+    return a.value, b.value
+
+
+def cm_flow_from_depth(cam, inv_depth: int, ego6: int, dt_window: float, flow_out: int, stream: int) -> None:
+    _check(lib().cm_flow_from_depth(ctypes.byref(cam), inv_depth, ego6, dt_window, flow_out, stream),
+           "cm_flow_from_depth")
+
+
+def cm_warp_splat(cam, ev, flow: int, n_flow_bins: int, cfg, ws: int | None, iwe_out: int | None, stream: int):
+    _check(lib().cm_warp_splat(ctypes.byref(cam), ctypes.byref(ev), flow, n_flow_bins, ctypes.byref(cfg), ws,
+                               iwe_out, stream), "cm_warp_splat")
+
+
+def cm_loss_forward(cam, ev, flow, n_flow_bins, inv_depth, ego6, dt_window, cfg, ws, loss_out, stream):
+    _check(lib().cm_loss_forward(ctypes.byref(cam), ctypes.byref(ev), flow, n_flow_bins, inv_depth, ego6,
+                                 dt_window, ctypes.byref(cfg), ws, loss_out, stream), "cm_loss_forward")
+
+
+def cm_loss_backward(cam, ev, flow, n_flow_bins, inv_depth, ego6, dt_window, cfg, ws, dloss, dflow, dinv_depth,
+                     dego6, stream):
+    _check(lib().cm_loss_backward(ctypes.byref(cam), ctypes.byref(ev), flow, n_flow_bins, inv_depth, ego6,
+                                  dt_window, ctypes.byref(cfg), ws, dloss, dflow, dinv_depth, dego6, stream),
+           "cm_loss_backward")

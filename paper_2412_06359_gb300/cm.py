@@ -1,0 +1,219 @@
+"""Torch-facing helpers over the C ABI: device buffers, streams and a
+torch.autograd.Function.
+
+PyTorch supplies device memory, the current stream and autograd plumbing;
+every step of the loss and its gradient runs in libcm.so's kernels.  The only
+work done here is allocating outputs with torch.empty and passing pointers.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+import torch
+
+from . import _capi as C
+
+REF_END = C.CM_REF_END
+REF_ALL = C.CM_REF_ALL_EDGES
+SPLAT_AUTO, SPLAT_ATOMIC, SPLAT_SORT = C.CM_SPLAT_AUTO, C.CM_SPLAT_ATOMIC, C.CM_SPLAT_SORT
+
+
+def _require_cuda(t: torch.Tensor, name: str, dtype=None):
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    return t.data_ptr()
+
+
+def camera(cam) -> C.cm_camera:
+    """cm_camera from anything with width, height, fx, fy, cx, cy."""
+    return C.cm_camera(int(cam.width), int(cam.height), float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy))
+
+
+def loss_cfg(nbins: int, ref_mode: int, splat: int = SPLAT_AUTO, eps: float = 1e-9) -> C.cm_loss_cfg:
+    return C.cm_loss_cfg(int(nbins), int(ref_mode), int(splat), 0, float(eps))
+
+
+def n_refs(cfg: C.cm_loss_cfg) -> int:
+    return 1 if cfg.ref_mode == REF_END else cfg.nbins + 1
+
+
+def stream_handle(device=None) -> int:
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+@dataclasses.dataclass
+class DeviceEvents:
+    """One window of events resident on the GPU (structure of arrays)."""
+    x: torch.Tensor  # int16
+    y: torch.Tensor  # int16
+    t: torch.Tensor  # float32
+    p: torch.Tensor  # int8
+    t0: float
+    t1: float
+
+    @property
+    def n(self) -> int:
+        return int(self.x.numel())
+
+    @staticmethod
+    def from_host(ev, device="cuda", pin: bool = False) -> "DeviceEvents":
+        def mv(a, dt):
+            t = torch.from_numpy(np.ascontiguousarray(a, dtype=dt))
+            if pin:
+                t = t.pin_memory()
+            return t.to(device, non_blocking=pin)
+        return DeviceEvents(mv(ev.x, np.int16), mv(ev.y, np.int16), mv(ev.t, np.float32), mv(ev.p, np.int8),
+                            float(ev.t0), float(ev.t1))
+
+    def c(self) -> C.cm_events:
+        if self.n:
+            ptrs = (_require_cuda(self.x, "x", torch.int16), _require_cuda(self.y, "y", torch.int16),
+                    _require_cuda(self.t, "t", torch.float32), _require_cuda(self.p, "p", torch.int8))
+        else:
+            ptrs = (None, None, None, None)
+        return C.cm_events(*ptrs, self.n, float(self.t0), float(self.t1))
+
+
+class Workspace:
+    """Device memory for one window shape, allocated through torch and laid out
+    by cm_workspace_create."""
+
+    def __init__(self, cam, cfg: C.cm_loss_cfg, max_events: int, n_flow_bins: int = 1, device="cuda"):
+        self.cam = camera(cam)
+        self.cfg = cfg
+        self.n_flow_bins = n_flow_bins
+        self.nbytes = C.cm_workspace_query(self.cam, cfg, int(max_events), n_flow_bins)
+        self.buf = torch.empty(self.nbytes + 256, dtype=torch.uint8, device=device)
+        base = self.buf.data_ptr()
+        self.ptr = (base + 255) // 256 * 256
+        self.handle = C.cm_workspace_create(self.ptr, self.nbytes, self.cam, cfg, int(max_events), n_flow_bins)
+
+    def stats(self):
+        """(loss_r [R] float32, nnz_r [R] int32) of the last forward, copied to host."""
+        R = n_refs(self.cfg)
+        lr, nz = C.cm_workspace_stats(self.handle)
+        off_l, off_n = lr - self.buf.data_ptr(), nz - self.buf.data_ptr()
+        loss_r = self.buf[off_l:off_l + 4 * R].view(torch.float32).cpu().numpy()
+        nnz_r = self.buf[off_n:off_n + 4 * R].view(torch.int32).cpu().numpy()
+        return loss_r, nnz_r
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            try:
+                C.cm_workspace_destroy(h)
+            except Exception:
+                pass
+            self.handle = None
+
+
+def flow_from_depth(cam, inv_depth: torch.Tensor, ego: torch.Tensor, dt: float) -> torch.Tensor:
+    c = camera(cam)
+    out = torch.empty((c.height, c.width, 2), dtype=torch.float32, device=inv_depth.device)
+    C.cm_flow_from_depth(c, _require_cuda(inv_depth, "inv_depth", torch.float32), _require_cuda(ego, "ego",
+                         torch.float32), float(dt), out.data_ptr(), stream_handle(inv_depth.device))
+    return out
+
+
+def warp_splat(cam, ev: DeviceEvents, flow: torch.Tensor, cfg: C.cm_loss_cfg) -> torch.Tensor:
+    """IWEs [R, H, W, 4] = (C+, S+, C-, S-) of one window."""
+    c = camera(cam)
+    nfb = 1 if flow.dim() == 3 else flow.shape[0]
+    out = torch.empty((n_refs(cfg), c.height, c.width, 4), dtype=torch.float32, device=flow.device)
+    C.cm_warp_splat(c, ev.c(), _require_cuda(flow, "flow", torch.float32), nfb, cfg, None, out.data_ptr(),
+                    stream_handle(flow.device))
+    return out
+
+
+def loss_forward(ws: Workspace, ev: DeviceEvents, *, flow=None, inv_depth=None, ego=None, dt: float = 0.01,
+                 out: torch.Tensor | None = None) -> torch.Tensor:
+    """CM loss of one window as a device float32 tensor of shape [1]."""
+    dev = (flow if flow is not None else inv_depth).device
+    loss = out if out is not None else torch.empty(1, dtype=torch.float32, device=dev)
+    nfb = 1 if flow is None or flow.dim() == 3 else flow.shape[0]
+    C.cm_loss_forward(ws.cam, ev.c(), None if flow is None else _require_cuda(flow, "flow", torch.float32), nfb,
+                      None if inv_depth is None else _require_cuda(inv_depth, "inv_depth", torch.float32),
+                      None if ego is None else _require_cuda(ego, "ego", torch.float32), float(dt), ws.cfg,
+                      ws.handle, loss.data_ptr(), stream_handle(dev))
+    return loss
+
+
+def loss_backward(ws: Workspace, ev: DeviceEvents, dloss: torch.Tensor, *, flow=None, inv_depth=None, ego=None,
+                  dt: float = 0.01, want_dflow: bool = True, out: dict | None = None) -> dict:
+    """Gradients of dloss * L: {"dflow"} for flow input, {"dinv_depth", "dego"}
+    (and "dflow" when want_dflow) for depth input."""
+    dev = dloss.device
+    res = {} if out is None else out
+    if flow is not None:
+        nfb = 1 if flow.dim() == 3 else flow.shape[0]
+        if "dflow" not in res:
+            res["dflow"] = torch.empty_like(flow)
+        C.cm_loss_backward(ws.cam, ev.c(), _require_cuda(flow, "flow", torch.float32), nfb, None, None, float(dt),
+                           ws.cfg, ws.handle, _require_cuda(dloss, "dloss", torch.float32), res["dflow"].data_ptr(),
+                           None, None, stream_handle(dev))
+        return res
+    H, W = inv_depth.shape
+    if want_dflow and "dflow" not in res:
+        res["dflow"] = torch.empty((H, W, 2), dtype=torch.float32, device=dev)
+    if "dinv_depth" not in res:
+        res["dinv_depth"] = torch.empty_like(inv_depth)
+    if "dego" not in res:
+        res["dego"] = torch.empty(6, dtype=torch.float32, device=dev)
+    C.cm_loss_backward(ws.cam, ev.c(), None, 1, _require_cuda(inv_depth, "inv_depth", torch.float32),
+                       _require_cuda(ego, "ego", torch.float32), float(dt), ws.cfg, ws.handle,
+                       _require_cuda(dloss, "dloss", torch.float32),
+                       res["dflow"].data_ptr() if want_dflow else None, res["dinv_depth"].data_ptr(),
+                       res["dego"].data_ptr(), stream_handle(dev))
+    return res
+
+
+class CMLossDepth(torch.autograd.Function):
+    """L_CM(inv_depth, ego) of one window with the hand-written adjoint as its
+    backward (Sec. 3.3); trajectories are recomputed in the backward."""
+
+    @staticmethod
+    def forward(ctx, inv_depth, ego, ev: DeviceEvents, ws: Workspace, dt: float):
+        inv_depth = inv_depth.contiguous()
+        ego = ego.contiguous()
+        loss = loss_forward(ws, ev, inv_depth=inv_depth, ego=ego, dt=dt)
+        ctx.save_for_backward(inv_depth, ego)
+        ctx.ev, ctx.ws, ctx.dt = ev, ws, dt
+        return loss[0]
+
+    @staticmethod
+    def backward(ctx, grad):
+        inv_depth, ego = ctx.saved_tensors
+        dloss = grad.reshape(1).to(torch.float32).contiguous()
+        g = loss_backward(ctx.ws, ctx.ev, dloss, inv_depth=inv_depth, ego=ego, dt=ctx.dt, want_dflow=False)
+        return g["dinv_depth"], g["dego"], None, None, None
+
+
+class CMLossFlow(torch.autograd.Function):
+    """L_CM(flow) of one window; backward gives dL/dflow."""
+
+    @staticmethod
+    def forward(ctx, flow, ev: DeviceEvents, ws: Workspace):
+        flow = flow.contiguous()
+        loss = loss_forward(ws, ev, flow=flow)
+        ctx.save_for_backward(flow)
+        ctx.ev, ctx.ws = ev, ws
+        return loss[0]
+
+    @staticmethod
+    def backward(ctx, grad):
+        (flow,) = ctx.saved_tensors
+        dloss = grad.reshape(1).to(torch.float32).contiguous()
+        g = loss_backward(ctx.ws, ctx.ev, dloss, flow=flow)
+        return g["dflow"], None, None
+
+
+def cm_loss(ev: DeviceEvents, ws: Workspace, *, flow=None, inv_depth=None, ego=None, dt: float = 0.01):
+    """Differentiable CM loss: pass flow, or inv_depth and ego."""
+    if flow is not None:
+        return CMLossFlow.apply(flow, ev, ws)
+    return CMLossDepth.apply(inv_depth, ego, ev, ws, dt)

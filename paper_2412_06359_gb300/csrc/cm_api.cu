@@ -1,0 +1,365 @@
+// cm_api.cu -- the C ABI of libcm.so (include/cm.h): argument validation,
+// workspace layout over caller-owned device memory, and the launch sequence
+// of each entry point.
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+
+#include "../../include/cm.h"
+#include "cm_launch.h"
+
+using cmk::Win;
+
+struct cm_workspace {
+    char* base;
+    size_t bytes;
+    cm_camera cam;
+    cm_loss_cfg cfg;
+    int64_t max_events;
+    int32_t nfb;
+    int32_t R;
+    int32_t loss_tiles, pix_tiles;
+    float4* iwe;
+    float2* flow;
+    float2* dflow;
+    float2* loss_part;
+    float* norm;
+    float* loss_r;
+    int32_t* nnz_r;
+    float* dego_part;
+    // state of the last forward on this workspace
+    int fwd_mode;            // 0 none, 1 flow input, 2 depth input
+    const void* fwd_events;  // event x pointer of the last forward
+    int64_t fwd_n;
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+int n_refs(const cm_loss_cfg& c) { return c.ref_mode == CM_REF_END ? 1 : c.nbins + 1; }
+
+int tiles_for(size_t hw, int cap)
+{
+    size_t t = (hw + 2047) / 2048;
+    if (t < 1) t = 1;
+    if (t > (size_t)cap) t = cap;
+    return (int)t;
+}
+
+struct Layout {
+    size_t iwe, flow, dflow, loss_part, norm, loss_r, nnz_r, dego_part, total;
+    int R, loss_tiles, pix_tiles;
+};
+
+bool finite_pos(float v) { return std::isfinite(v) && v > 0.0f; }
+
+int check_camera(const cm_camera* cam)
+{
+    if (!cam) return CM_EINVAL;
+    if (cam->width < 2 || cam->height < 2 || cam->width > 32767 || cam->height > 32767) return CM_EINVAL;
+    if (!finite_pos(cam->fx) || !finite_pos(cam->fy) || !std::isfinite(cam->cx) || !std::isfinite(cam->cy))
+        return CM_EINVAL;
+    return CM_OK;
+}
+
+int check_cfg(const cm_loss_cfg* cfg)
+{
+    if (!cfg) return CM_EINVAL;
+    if (cfg->nbins < 1 || cfg->nbins > CM_MAX_BINS) return CM_EINVAL;
+    if (cfg->ref_mode != CM_REF_END && cfg->ref_mode != CM_REF_ALL_EDGES) return CM_EINVAL;
+    if (cfg->splat != CM_SPLAT_AUTO && cfg->splat != CM_SPLAT_ATOMIC && cfg->splat != CM_SPLAT_SORT) return CM_EINVAL;
+    if (cfg->store_warps != 0) return CM_EINVAL;
+    if (!std::isfinite(cfg->eps)) return CM_EINVAL;
+    return CM_OK;
+}
+
+float eps_of(const cm_loss_cfg& c) { return c.eps > 0.0f ? c.eps : 1e-9f; }
+
+int check_events(const cm_events* ev)
+{
+    if (!ev || ev->n < 0) return CM_EINVAL;
+    if (ev->n > 0 && (!ev->x || !ev->y || !ev->t || !ev->p)) return CM_EINVAL;
+    if (!std::isfinite(ev->t0) || !std::isfinite(ev->t1) || !(ev->t1 > ev->t0)) return CM_EINVAL;
+    const float span = ev->t1 - ev->t0;
+    if (!(span > 0.0f) || !std::isfinite(span)) return CM_EINVAL;
+    return CM_OK;
+}
+
+Layout layout(const cm_camera& cam, const cm_loss_cfg& cfg, int32_t nfb)
+{
+    Layout L;
+    const size_t HW = (size_t)cam.width * cam.height;
+    L.R = n_refs(cfg);
+    L.loss_tiles = tiles_for(HW, 256);
+    L.pix_tiles = tiles_for(HW, 512);
+    size_t off = 0;
+    L.iwe = off;
+    off = align_up(off + (size_t)L.R * HW * sizeof(float4));
+    L.flow = off;
+    off = align_up(off + HW * sizeof(float2));
+    L.dflow = off;
+    off = align_up(off + (size_t)nfb * HW * sizeof(float2));
+    L.loss_part = off;
+    off = align_up(off + (size_t)L.R * L.loss_tiles * sizeof(float2));
+    L.norm = off;
+    off = align_up(off + (size_t)L.R * sizeof(float));
+    L.loss_r = off;
+    off = align_up(off + (size_t)L.R * sizeof(float));
+    L.nnz_r = off;
+    off = align_up(off + (size_t)L.R * sizeof(int32_t));
+    L.dego_part = off;
+    off = align_up(off + (size_t)L.pix_tiles * 6 * sizeof(float));
+    L.total = off;
+    return L;
+}
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? CM_OK : CM_ECUDA; }
+
+cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// descriptor of one window over the workspace buffers
+Win make_win(const cm_camera& cam, const cm_events* ev, const cm_loss_cfg& cfg, int32_t nfb)
+{
+    Win d;
+    std::memset(&d, 0, sizeof(d));
+    if (ev) {
+        d.x = ev->x;
+        d.y = ev->y;
+        d.t = ev->t;
+        d.p = ev->p;
+        d.n = ev->n;
+        d.t0 = ev->t0;
+        d.span = ev->t1 - ev->t0;
+    }
+    d.W = cam.width;
+    d.H = cam.height;
+    d.B = cfg.nbins;
+    d.R = n_refs(cfg);
+    d.ref_mode = cfg.ref_mode;
+    d.nfb = nfb;
+    d.eps = eps_of(cfg);
+    d.fx = cam.fx;
+    d.fy = cam.fy;
+    d.cx = cam.cx;
+    d.cy = cam.cy;
+    return d;
+}
+
+void attach_ws(Win& d, cm_workspace* ws)
+{
+    d.iwe = ws->iwe;
+    d.loss_part = ws->loss_part;
+    d.loss_tiles = ws->loss_tiles;
+    d.pix_tiles = ws->pix_tiles;
+    d.norm = ws->norm;
+    d.loss_r = ws->loss_r;
+    d.nnz_r = ws->nnz_r;
+    d.dego_part = ws->dego_part;
+}
+
+bool same_shape(const cm_workspace* ws, const cm_camera& cam, const cm_loss_cfg& cfg, int32_t nfb)
+{
+    return ws->cam.width == cam.width && ws->cam.height == cam.height && ws->cfg.nbins == cfg.nbins &&
+           ws->cfg.ref_mode == cfg.ref_mode && nfb <= ws->nfb;
+}
+
+}  // namespace
+
+namespace cmk {
+int sm_count_current()
+{
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 148;
+    if (dev < 64 && cache[dev] > 0) return cache[dev];
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+    if (dev < 64) cache[dev] = n;
+    return n;
+}
+}  // namespace cmk
+
+extern "C" {
+
+const char* cm_status_string(int s)
+{
+    switch (s) {
+    case CM_OK: return "ok";
+    case CM_EINVAL: return "invalid argument";
+    case CM_ENOMEM: return "out of memory (workspace or server budget too small)";
+    case CM_EBUSY: return "busy: no slot or memory free for the request";
+    case CM_ETIMEOUT: return "a bounded wait gave up";
+    case CM_ECUDA: return "CUDA runtime error";
+    case CM_ENOTFOUND: return "unknown ticket";
+    case CM_ESTATE: return "call out of order";
+    default: return "unknown status";
+    }
+}
+
+int cm_abi_version(void) { return 1; }
+
+int cm_workspace_query(const cm_camera* cam, const cm_loss_cfg* cfg, int64_t max_events, int32_t n_flow_bins,
+                       size_t* bytes)
+{
+    int st;
+    if ((st = check_camera(cam)) || (st = check_cfg(cfg))) return st;
+    if (!bytes || max_events < 0 || (n_flow_bins != 1 && n_flow_bins != cfg->nbins)) return CM_EINVAL;
+    *bytes = layout(*cam, *cfg, n_flow_bins).total;
+    return CM_OK;
+}
+
+int cm_workspace_create(void* dev_mem, size_t bytes, const cm_camera* cam, const cm_loss_cfg* cfg,
+                        int64_t max_events, int32_t n_flow_bins, cm_workspace** out)
+{
+    int st;
+    if ((st = check_camera(cam)) || (st = check_cfg(cfg))) return st;
+    if (!out || !dev_mem || max_events < 0 || (n_flow_bins != 1 && n_flow_bins != cfg->nbins)) return CM_EINVAL;
+    if (reinterpret_cast<uintptr_t>(dev_mem) % kAlign) return CM_EINVAL;
+    const Layout L = layout(*cam, *cfg, n_flow_bins);
+    if (bytes < L.total) return CM_ENOMEM;
+    cm_workspace* ws = new (std::nothrow) cm_workspace;
+    if (!ws) return CM_ENOMEM;
+    std::memset(ws, 0, sizeof(*ws));
+    char* b = static_cast<char*>(dev_mem);
+    ws->base = b;
+    ws->bytes = bytes;
+    ws->cam = *cam;
+    ws->cfg = *cfg;
+    ws->max_events = max_events;
+    ws->nfb = n_flow_bins;
+    ws->R = L.R;
+    ws->loss_tiles = L.loss_tiles;
+    ws->pix_tiles = L.pix_tiles;
+    ws->iwe = reinterpret_cast<float4*>(b + L.iwe);
+    ws->flow = reinterpret_cast<float2*>(b + L.flow);
+    ws->dflow = reinterpret_cast<float2*>(b + L.dflow);
+    ws->loss_part = reinterpret_cast<float2*>(b + L.loss_part);
+    ws->norm = reinterpret_cast<float*>(b + L.norm);
+    ws->loss_r = reinterpret_cast<float*>(b + L.loss_r);
+    ws->nnz_r = reinterpret_cast<int32_t*>(b + L.nnz_r);
+    ws->dego_part = reinterpret_cast<float*>(b + L.dego_part);
+    *out = ws;
+    return CM_OK;
+}
+
+int cm_workspace_destroy(cm_workspace* ws)
+{
+    delete ws;
+    return CM_OK;
+}
+
+int cm_workspace_stats(const cm_workspace* ws, const float** loss_r, const int32_t** nnz_r)
+{
+    if (!ws) return CM_EINVAL;
+    if (loss_r) *loss_r = ws->loss_r;
+    if (nnz_r) *nnz_r = ws->nnz_r;
+    return CM_OK;
+}
+
+int cm_flow_from_depth(const cm_camera* cam, const float* inv_depth, const float* ego6, float dt_window,
+                       float* flow_out, void* stream)
+{
+    int st;
+    if ((st = check_camera(cam))) return st;
+    if (!inv_depth || !ego6 || !flow_out || !std::isfinite(dt_window)) return CM_EINVAL;
+    cm_loss_cfg c{1, CM_REF_END, CM_SPLAT_AUTO, 0, 0.0f};
+    Win d = make_win(*cam, nullptr, c, 1);
+    d.rho = inv_depth;
+    d.ego = ego6;
+    d.dt = dt_window;
+    d.flow = reinterpret_cast<const float2*>(flow_out);
+    return cuda_status(cmk::launch_flow(d, as_stream(stream)));
+}
+
+int cm_warp_splat(const cm_camera* cam, const cm_events* ev, const float* flow, int32_t n_flow_bins,
+                  const cm_loss_cfg* cfg, cm_workspace* ws, float* iwe_out, void* stream)
+{
+    int st;
+    if ((st = check_camera(cam)) || (st = check_cfg(cfg)) || (st = check_events(ev))) return st;
+    if (!flow || (n_flow_bins != 1 && n_flow_bins != cfg->nbins)) return CM_EINVAL;
+    if (!iwe_out && !ws) return CM_EINVAL;
+    if (ws && !iwe_out && !same_shape(ws, *cam, *cfg, n_flow_bins)) return CM_EINVAL;
+    Win d = make_win(*cam, ev, *cfg, n_flow_bins);
+    d.flow = reinterpret_cast<const float2*>(flow);
+    d.iwe = iwe_out ? reinterpret_cast<float4*>(iwe_out) : ws->iwe;
+    cudaStream_t s = as_stream(stream);
+    const size_t bytes = (size_t)d.R * d.W * d.H * sizeof(float4);
+    if ((st = cuda_status(cudaMemsetAsync(d.iwe, 0, bytes, s)))) return st;
+    return cuda_status(cmk::launch_splat(d, cmk::sm_count_current(), s));
+}
+
+int cm_loss_forward(const cm_camera* cam, const cm_events* ev, const float* flow, int32_t n_flow_bins,
+                    const float* inv_depth, const float* ego6, float dt_window, const cm_loss_cfg* cfg,
+                    cm_workspace* ws, float* loss_out, void* stream)
+{
+    int st;
+    if ((st = check_camera(cam)) || (st = check_cfg(cfg)) || (st = check_events(ev))) return st;
+    if (!ws || !loss_out) return CM_EINVAL;
+    if (n_flow_bins != 1 && n_flow_bins != cfg->nbins) return CM_EINVAL;
+    const bool depth = flow == nullptr;
+    if (depth && (!inv_depth || !ego6 || n_flow_bins != 1 || !std::isfinite(dt_window))) return CM_EINVAL;
+    if (!same_shape(ws, *cam, *cfg, n_flow_bins)) return CM_EINVAL;
+    if (ev->n > ws->max_events) return CM_ENOMEM;
+    cudaStream_t s = as_stream(stream);
+    Win d = make_win(*cam, ev, *cfg, n_flow_bins);
+    attach_ws(d, ws);
+    d.loss = loss_out;
+    if (depth) {
+        d.rho = inv_depth;
+        d.ego = ego6;
+        d.dt = dt_window;
+        d.flow = ws->flow;
+        if ((st = cuda_status(cmk::launch_flow(d, s)))) return st;
+    } else {
+        d.flow = reinterpret_cast<const float2*>(flow);
+    }
+    const size_t bytes = (size_t)d.R * d.W * d.H * sizeof(float4);
+    if ((st = cuda_status(cudaMemsetAsync(d.iwe, 0, bytes, s)))) return st;
+    if ((st = cuda_status(cmk::launch_splat(d, cmk::sm_count_current(), s)))) return st;
+    if ((st = cuda_status(cmk::launch_loss(d, s)))) return st;
+    ws->fwd_mode = depth ? 2 : 1;
+    ws->fwd_events = ev->x;
+    ws->fwd_n = ev->n;
+    return CM_OK;
+}
+
+int cm_loss_backward(const cm_camera* cam, const cm_events* ev, const float* flow, int32_t n_flow_bins,
+                     const float* inv_depth, const float* ego6, float dt_window, const cm_loss_cfg* cfg,
+                     cm_workspace* ws, const float* dloss, float* dflow, float* dinv_depth, float* dego6,
+                     void* stream)
+{
+    int st;
+    if ((st = check_camera(cam)) || (st = check_cfg(cfg)) || (st = check_events(ev))) return st;
+    if (!ws || !dloss) return CM_EINVAL;
+    if (n_flow_bins != 1 && n_flow_bins != cfg->nbins) return CM_EINVAL;
+    const bool depth = flow == nullptr;
+    if (depth && (!inv_depth || !ego6 || n_flow_bins != 1 || !std::isfinite(dt_window))) return CM_EINVAL;
+    if (!same_shape(ws, *cam, *cfg, n_flow_bins)) return CM_EINVAL;
+    if (ws->fwd_mode != (depth ? 2 : 1) || ws->fwd_events != ev->x || ws->fwd_n != ev->n) return CM_ESTATE;
+    if (!depth && (dinv_depth || dego6)) return CM_EINVAL;
+    cudaStream_t s = as_stream(stream);
+    Win d = make_win(*cam, ev, *cfg, n_flow_bins);
+    attach_ws(d, ws);
+    d.dloss = dloss;
+    d.flow = depth ? ws->flow : reinterpret_cast<const float2*>(flow);
+    d.dflow = dflow ? reinterpret_cast<float2*>(dflow) : ws->dflow;
+    if (!depth && !dflow) return CM_OK;
+    const size_t gbytes = (size_t)n_flow_bins * d.W * d.H * sizeof(float2);
+    if ((st = cuda_status(cudaMemsetAsync(d.dflow, 0, gbytes, s)))) return st;
+    if ((st = cuda_status(cmk::launch_adjoint(d, cmk::sm_count_current(), s)))) return st;
+    if (depth && (dinv_depth || dego6)) {
+        d.rho = inv_depth;
+        d.ego = ego6;
+        d.dt = dt_window;
+        d.drho = dinv_depth;
+        d.dego = dego6;
+        if ((st = cuda_status(cmk::launch_depth_ego(d, s)))) return st;
+    }
+    return CM_OK;
+}
+
+}  // extern "C"

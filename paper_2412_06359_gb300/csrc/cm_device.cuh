@@ -1,0 +1,387 @@
+// cm_device.cuh -- device-side building blocks of the contrast-maximisation
+// kernels: the window descriptor, the FP32 trajectory arithmetic and the
+// bilinear sample / splat primitives.
+//
+// FP32 arithmetic contract.  The floor of a trajectory position decides the
+// flow cell that is sampled, the pixels a splat touches, whether a corner has a
+// nonzero weight and whether the event stays inside the image; the
+// eps-regularised ratio of Eq. 1 makes the loss sensitive to those decisions.
+// Every operation that produces a position is therefore written as an explicit
+// correctly rounded single-precision intrinsic (__fadd_rn, __fmul_rn,
+// __fmaf_rn, __fdiv_rn), so that the compiler cannot contract or reorder it
+// and the positions are a fixed function of the inputs:
+//   tau     = (t - t0) / span                      span = t1 - t0
+//   b       = clamp(floor(tau * B), 0, B - 1)
+//   tau_j   = j / B,  h = 1 / B
+//   forward:  x_{b+1} = fma(tau_{b+1} - tau, u_b[x_k], x_k),   x_{j+1} = fma(h, u_j(x_j), x_j)
+//   backward: x_b     = fma(-(tau - tau_b), u_b[x_k], x_k),    x_{j-1} = fma(-h, u_{j-1}(x_j), x_j)
+//   sample u(x): a = x - floor(x), c = 1 - a (per axis),
+//                w00 = cx*cy, w10 = ax*cy, w01 = cx*ay, w11 = ax*ay,
+//                u = w00*u00;  u = fma(w10, u10, u);  u = fma(w01, u01, u);  u = fma(w11, u11, u)
+// (Sec. 3.1 iterative warp with bilinearly sampled flow; Sec. 3.3.)
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace cmk {
+
+constexpr int kRefEnd = 0;
+constexpr int kRefAll = 1;
+constexpr int kEventThreads = 256;
+
+// One window: events, flow, IWE and gradient buffers, statistics.
+struct Win {
+    const int16_t* x;
+    const int16_t* y;
+    const float* t;
+    const int8_t* p;
+    int64_t n;
+    int32_t W, H, B, R;
+    int32_t ref_mode, nfb;
+    float t0, span, eps;
+    float dt;                // window length (depth input)
+    float fx, fy, cx, cy;    // intrinsics (depth input)
+    const float2* flow;      // [nfb][H][W]
+    float4* iwe;             // [R][H][W]: (C+, S+, C-, S-); after the loss (A+, T+, A-, T-)
+    float2* dflow;           // [nfb][H][W]
+    float* norm;             // [R]: 1 / (R (N_nz(r) + eps))
+    float* loss_r;           // [R]
+    int32_t* nnz_r;          // [R]
+    float* loss;             // [1]
+    const float* dloss;      // [1]
+    float2* loss_part;       // [R][loss_tiles]: (sum of T^2, non-empty count)
+    int32_t loss_tiles;
+    int32_t pix_tiles;
+    const float* rho;        // [H][W] inverse depth
+    const float* ego;        // [6]
+    float* drho;             // [H][W]
+    float* dego;             // [6]
+    float* dego_part;        // [pix_tiles][6]
+};
+
+__device__ __forceinline__ size_t plane_size(const Win& d) { return (size_t)d.W * (size_t)d.H; }
+
+__device__ __forceinline__ const float2* field(const Win& d, int j)
+{
+    return d.flow + (d.nfb == 1 ? (size_t)0 : (size_t)j * plane_size(d));
+}
+
+__device__ __forceinline__ float2* field_grad(const Win& d, int j)
+{
+    return d.dflow + (d.nfb == 1 ? (size_t)0 : (size_t)j * plane_size(d));
+}
+
+__device__ __forceinline__ float tau_of(float t, float t0, float span)
+{
+    return __fdiv_rn(__fsub_rn(t, t0), span);
+}
+
+__device__ __forceinline__ int bin_of(float tau, int B)
+{
+    float q = floorf(__fmul_rn(tau, (float)B));
+    q = fminf(fmaxf(q, 0.0f), (float)(B - 1));
+    return (int)q;
+}
+
+__device__ __forceinline__ float edge_tau(int j, int B) { return __fdiv_rn((float)j, (float)B); }
+
+// average timestamp of an event at normalised time tau for reference edge j
+__device__ __forceinline__ float tbar_of(int j, int B, float tau)
+{
+    return __fsub_rn(1.0f, fabsf(__fsub_rn(edge_tau(j, B), tau)));
+}
+
+__device__ __forceinline__ bool inside(float px, float py, float W1, float H1)
+{
+    return px >= 0.0f && px <= W1 && py >= 0.0f && py <= H1;
+}
+
+// Bilinear cell, fractional parts and the four weights of a point.
+struct Bil {
+    int ix, iy;
+    float ax, ay, bx, by;
+    float w00, w10, w01, w11;
+};
+
+__device__ __forceinline__ Bil bil(float px, float py)
+{
+    Bil s;
+    const float fx0 = floorf(px), fy0 = floorf(py);
+    s.ix = (int)fx0;
+    s.iy = (int)fy0;
+    s.ax = __fsub_rn(px, fx0);
+    s.ay = __fsub_rn(py, fy0);
+    s.bx = __fsub_rn(1.0f, s.ax);
+    s.by = __fsub_rn(1.0f, s.ay);
+    s.w00 = __fmul_rn(s.bx, s.by);
+    s.w10 = __fmul_rn(s.ax, s.by);
+    s.w01 = __fmul_rn(s.bx, s.ay);
+    s.w11 = __fmul_rn(s.ax, s.ay);
+    return s;
+}
+
+// The four flow values around a cell (corner indices clamped to the image).
+struct Quad {
+    float2 u00, u10, u01, u11;
+};
+
+__device__ __forceinline__ Quad load_quad(const float2* __restrict__ U, int W, int H, const Bil& s)
+{
+    const int ix1 = min(s.ix + 1, W - 1), iy1 = min(s.iy + 1, H - 1);
+    Quad q;
+    q.u00 = __ldg(U + (size_t)s.iy * W + s.ix);
+    q.u10 = __ldg(U + (size_t)s.iy * W + ix1);
+    q.u01 = __ldg(U + (size_t)iy1 * W + s.ix);
+    q.u11 = __ldg(U + (size_t)iy1 * W + ix1);
+    return q;
+}
+
+__device__ __forceinline__ float2 interp(const Bil& s, const Quad& q)
+{
+    float ux = __fmul_rn(s.w00, q.u00.x);
+    ux = __fmaf_rn(s.w10, q.u10.x, ux);
+    ux = __fmaf_rn(s.w01, q.u01.x, ux);
+    ux = __fmaf_rn(s.w11, q.u11.x, ux);
+    float uy = __fmul_rn(s.w00, q.u00.y);
+    uy = __fmaf_rn(s.w10, q.u10.y, uy);
+    uy = __fmaf_rn(s.w01, q.u01.y, uy);
+    uy = __fmaf_rn(s.w11, q.u11.y, uy);
+    return make_float2(ux, uy);
+}
+
+// Trajectory points at the computed edges (registers; indices are compile-time
+// after unrolling).
+template <int MAXB>
+struct Traj {
+    float x[MAXB + 1];
+    float y[MAXB + 1];
+    float ex, ey;  // the point at the window end (edge B), kept in scalars so that
+                   // selecting it never needs a run-time array index
+};
+
+// Per-event quantities shared by the forward and backward kernels.
+struct EventAt {
+    int xk, yk, b, pol2;
+    float tau;
+};
+
+__device__ __forceinline__ bool load_event(const Win& d, int64_t k, EventAt& e)
+{
+    e.xk = d.x[k];
+    e.yk = d.y[k];
+    if ((unsigned)e.xk >= (unsigned)d.W || (unsigned)e.yk >= (unsigned)d.H) return false;
+    e.tau = tau_of(__ldg(d.t + k), d.t0, d.span);
+    e.b = bin_of(e.tau, d.B);
+    e.pol2 = d.p[k] > 0 ? 0 : 2;
+    return true;
+}
+
+// S2 + S3: the trajectory of one event through all computed edges (forward
+// chain b+1..B; with all edges as references also the backward chain b..0)
+// and the global mask.  Returns false when any computed point leaves the image.
+template <int MAXB>
+__device__ __forceinline__ bool trajectory(const Win& d, const EventAt& e, Traj<MAXB>& P)
+{
+    const int W = d.W, H = d.H, B = d.B, b = e.b;
+    const float W1 = (float)(W - 1), H1 = (float)(H - 1);
+    const float h = __fdiv_rn(1.0f, (float)B);
+    const float2 u0 = __ldg(field(d, b) + (size_t)e.yk * W + e.xk);
+    const float fxk = (float)e.xk, fyk = (float)e.yk;
+    bool ok = true;
+    const float dtf = __fsub_rn(edge_tau(b + 1, B), e.tau);
+#pragma unroll
+    for (int j = 1; j <= MAXB; ++j) {
+        if (j <= B && j > b) {
+            if (j == b + 1) {
+                P.x[j] = __fmaf_rn(dtf, u0.x, fxk);
+                P.y[j] = __fmaf_rn(dtf, u0.y, fyk);
+            } else if (ok) {
+                const Bil s = bil(P.x[j - 1], P.y[j - 1]);
+                const float2 u = interp(s, load_quad(field(d, j - 1), W, H, s));
+                P.x[j] = __fmaf_rn(h, u.x, P.x[j - 1]);
+                P.y[j] = __fmaf_rn(h, u.y, P.y[j - 1]);
+            } else {
+                P.x[j] = P.x[j - 1];
+                P.y[j] = P.y[j - 1];
+            }
+            ok = ok && inside(P.x[j], P.y[j], W1, H1);
+            P.ex = P.x[j];
+            P.ey = P.y[j];
+        }
+    }
+    if (d.ref_mode == kRefAll) {
+        const float dtb = __fsub_rn(e.tau, edge_tau(b, B));
+#pragma unroll
+        for (int j = MAXB - 1; j >= 0; --j) {
+            if (j <= b) {
+                if (j == b) {
+                    P.x[j] = __fmaf_rn(-dtb, u0.x, fxk);
+                    P.y[j] = __fmaf_rn(-dtb, u0.y, fyk);
+                } else if (ok) {
+                    const Bil s = bil(P.x[j + 1], P.y[j + 1]);
+                    const float2 u = interp(s, load_quad(field(d, j), W, H, s));
+                    P.x[j] = __fmaf_rn(-h, u.x, P.x[j + 1]);
+                    P.y[j] = __fmaf_rn(-h, u.y, P.y[j + 1]);
+                } else {
+                    P.x[j] = P.x[j + 1];
+                    P.y[j] = P.y[j + 1];
+                }
+                ok = ok && inside(P.x[j], P.y[j], W1, H1);
+            }
+        }
+    }
+    return ok;
+}
+
+// 8-byte vector reduction (no return value) into global memory.
+__device__ __forceinline__ void red_add_v2(float* addr, float a, float b)
+{
+    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(addr), "f"(a), "f"(b) : "memory");
+}
+
+// S4: bilinear splat of one point (weight w to C_p, w * tbar to S_p) into one
+// IWE plane; corners with a zero weight are skipped (they lie outside the
+// image or carry nothing).
+__device__ __forceinline__ void splat_point(float4* plane, int W, float px, float py, float tbar, int pol2)
+{
+    const Bil s = bil(px, py);
+    float* q = reinterpret_cast<float*>(plane + (size_t)s.iy * W + s.ix) + pol2;
+    red_add_v2(q, s.w00, __fmul_rn(s.w00, tbar));
+    if (s.ax > 0.0f) red_add_v2(q + 4, s.w10, __fmul_rn(s.w10, tbar));
+    if (s.ay > 0.0f) red_add_v2(q + 4 * (size_t)W, s.w01, __fmul_rn(s.w01, tbar));
+    if (s.ax > 0.0f && s.ay > 0.0f) red_add_v2(q + 4 * (size_t)W + 4, s.w11, __fmul_rn(s.w11, tbar));
+}
+
+template <int MAXB>
+__device__ __forceinline__ void splat_event(const Win& d, int64_t k)
+{
+    EventAt e;
+    if (!load_event(d, k, e)) return;
+    Traj<MAXB> P;
+    if (!trajectory<MAXB>(d, e, P)) return;
+    const size_t HW = plane_size(d);
+    if (d.ref_mode == kRefAll) {
+#pragma unroll
+        for (int j = 0; j <= MAXB; ++j)
+            if (j <= d.B) splat_point(d.iwe + (size_t)j * HW, d.W, P.x[j], P.y[j], tbar_of(j, d.B, e.tau), e.pol2);
+    } else {
+        splat_point(d.iwe, d.W, P.ex, P.ey, tbar_of(d.B, d.B, e.tau), e.pol2);
+    }
+}
+
+// dL/dw for one corner from the loss-transformed image (A, T) = (2T/(C+eps), T):
+// phi = kappa * A * (tbar - T)
+__device__ __forceinline__ float phi_at(const float4* G, size_t i, int pol2, float kap, float tbar)
+{
+    const float2 g = __ldg(reinterpret_cast<const float2*>(G + i) + (pol2 >> 1));
+    return kap * g.x * (tbar - g.y);
+}
+
+// position adjoint a = sum_c grad(w_c) phi_c at reference r, edge j
+__device__ __forceinline__ float2 ref_adjoint(const Win& d, int r, int j, float px, float py, float tau, int pol2,
+                                              float dl)
+{
+    const size_t HW = plane_size(d);
+    const int W = d.W, H = d.H;
+    const float kap = dl * __ldg(d.norm + r);
+    const float tb = tbar_of(j, d.B, tau);
+    const Bil s = bil(px, py);
+    const float4* G = d.iwe + (size_t)r * HW;
+    const size_t i00 = (size_t)s.iy * W + s.ix;
+    const bool inx = s.ix + 1 <= W - 1, iny = s.iy + 1 <= H - 1;
+    const float p00 = phi_at(G, i00, pol2, kap, tb);
+    const float p10 = inx ? phi_at(G, i00 + 1, pol2, kap, tb) : 0.0f;
+    const float p01 = iny ? phi_at(G, i00 + W, pol2, kap, tb) : 0.0f;
+    const float p11 = (inx && iny) ? phi_at(G, i00 + W + 1, pol2, kap, tb) : 0.0f;
+    float2 a;
+    a.x = s.by * (p10 - p00) + s.ay * (p11 - p01);
+    a.y = s.bx * (p01 - p00) + s.ax * (p11 - p10);
+    return a;
+}
+
+// One push of the adjoint back across a step x' = x + hs u(x) sampled at x
+// (hs = +h forward chain, -h backward chain): scatter hs w_c lambda into the
+// flow gradient and return lambda + hs J(x)^T lambda.
+__device__ __forceinline__ float2 push_back(float2* Gf, const float2* U, int W, int H, float px, float py, float hs,
+                                            float2 lam)
+{
+    const Bil s = bil(px, py);
+    const Quad q = load_quad(U, W, H, s);
+    const float hx = hs * lam.x, hy = hs * lam.y;
+    float* g = reinterpret_cast<float*>(Gf + (size_t)s.iy * W + s.ix);
+    red_add_v2(g, s.w00 * hx, s.w00 * hy);
+    if (s.ax > 0.0f) red_add_v2(g + 2, s.w10 * hx, s.w10 * hy);
+    if (s.ay > 0.0f) red_add_v2(g + 2 * (size_t)W, s.w01 * hx, s.w01 * hy);
+    if (s.ax > 0.0f && s.ay > 0.0f) red_add_v2(g + 2 * (size_t)W + 2, s.w11 * hx, s.w11 * hy);
+    const float jxx = s.by * (q.u10.x - q.u00.x) + s.ay * (q.u11.x - q.u01.x);
+    const float jxy = s.bx * (q.u01.x - q.u00.x) + s.ax * (q.u11.x - q.u10.x);
+    const float jyx = s.by * (q.u10.y - q.u00.y) + s.ay * (q.u11.y - q.u01.y);
+    const float jyy = s.bx * (q.u01.y - q.u00.y) + s.ax * (q.u11.y - q.u10.y);
+    float2 out;
+    out.x = lam.x + hs * (jxx * lam.x + jyx * lam.y);
+    out.y = lam.y + hs * (jxy * lam.x + jyy * lam.y);
+    return out;
+}
+
+// S6: per-event adjoint.  The trajectory is recomputed; the position adjoint of
+// each reference point is gathered from the loss-transformed IWE, and the
+// adjoint is carried back along both chains of pushes, scattering dL/dflow.
+template <int MAXB>
+__device__ __forceinline__ void adjoint_event(const Win& d, int64_t k, float dl)
+{
+    EventAt e;
+    if (!load_event(d, k, e)) return;
+    Traj<MAXB> P;
+    if (!trajectory<MAXB>(d, e, P)) return;
+    const int W = d.W, H = d.H, B = d.B, b = e.b;
+    const float h = __fdiv_rn(1.0f, (float)B);
+    const bool all = d.ref_mode == kRefAll;
+    const size_t ik = (size_t)e.yk * W + e.xk;
+    // forward chain: edges B .. b+1
+    float2 lam = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int j = MAXB; j >= 1; --j) {
+        if (j <= B && j > b) {
+            if (all || j == B) {
+                const float2 a = ref_adjoint(d, all ? j : 0, j, P.x[j], P.y[j], e.tau, e.pol2, dl);
+                lam.x += a.x;
+                lam.y += a.y;
+            }
+            if (j > b + 1) {
+                lam = push_back(field_grad(d, j - 1), field(d, j - 1), W, H, P.x[j - 1], P.y[j - 1], h, lam);
+            } else {
+                const float dtf = __fsub_rn(edge_tau(b + 1, B), e.tau);
+                red_add_v2(reinterpret_cast<float*>(field_grad(d, b) + ik), dtf * lam.x, dtf * lam.y);
+            }
+        }
+    }
+    if (!all) return;
+    // backward chain: edges 0 .. b
+    lam = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int j = 0; j <= MAXB - 1; ++j) {
+        if (j <= b) {
+            const float2 a = ref_adjoint(d, j, j, P.x[j], P.y[j], e.tau, e.pol2, dl);
+            lam.x += a.x;
+            lam.y += a.y;
+            if (j < b) {
+                lam = push_back(field_grad(d, j), field(d, j), W, H, P.x[j + 1], P.y[j + 1], -h, lam);
+            } else {
+                const float dtb = __fsub_rn(e.tau, edge_tau(b, B));
+                red_add_v2(reinterpret_cast<float*>(field_grad(d, b) + ik), -dtb * lam.x, -dtb * lam.y);
+            }
+        }
+    }
+}
+
+// warp-level sum (fixed shuffle tree: deterministic)
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+}  // namespace cmk

@@ -1,0 +1,168 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle, on the
+same seeded inputs, element by element where the output is an image and on
+the loss / gradients with the stated tolerances (loss 1e-5 relative, every
+gradient 1e-4 relative L2, integer decisions exact)."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2412_06359_gb300 import synth
+from tests.gpu_util import assert_parity, gpu_lib, rel_l2, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+END, ALL = synth.REF_END, synth.REF_ALL
+
+
+def small_flow_window(W, H, n, B, ref_mode, nfb=1, seed=0, mag=4.0):
+    rng = np.random.default_rng(seed)
+    ev = synth.uniform_events(rng, W, H, n)
+    flow = np.stack([synth.sinusoid_flow(rng, W, H, mag) for _ in range(nfb)])
+    return synth.Window(synth.Camera(W, H, 0.7 * W, 0.7 * W, W / 2, H / 2), ev, B, ref_mode, flow=flow)
+
+
+def small_depth_window(W, H, n, B, ref_mode=ALL, seed=0):
+    return synth.depth_window(np.random.default_rng(seed), W, H, n, nbins=B, ref_mode=ref_mode)
+
+
+def test_flow_from_depth_is_bit_exact():
+    import torch
+    cm = gpu_lib()
+    w = synth.davis_window(n=10)
+    rho = torch.from_numpy(w.inv_depth).cuda()
+    ego = torch.from_numpy(w.ego).cuda()
+    f = cm.flow_from_depth(w.cam, rho, ego, w.dt).cpu().numpy()
+    f32 = O.flow_from_depth_f32(w.cam, w.inv_depth, w.ego, w.dt)
+    assert np.array_equal(f, f32)
+    f64 = O.flow_from_depth(w.cam, w.inv_depth, w.ego, w.dt)
+    assert np.abs(f - f64).max() <= 2e-6 * np.abs(f64).max()
+
+
+@pytest.mark.parametrize("wl", ["flow", "depth"])
+def test_iwe_elementwise(wl):
+    if wl == "flow":
+        win = small_flow_window(96, 80, 7000, 6, ALL, seed=3)
+    else:
+        win = small_depth_window(120, 90, 9000, 10, seed=4)
+    g = run_gpu(win, grad=False, want_iwe=True)
+    o = run_oracle(win, grad=False, want_iwe=True)
+    if wl == "depth":
+        assert np.array_equal(g["flow"], O.flow_from_depth_f32(win.cam, win.inv_depth, win.ego, win.dt))
+    gi, oi = g["iwe"], o["iwe"]
+    assert gi.shape == oi.shape
+    # support is identical (decisions in the same precision); values within FP32 accumulation error
+    assert np.array_equal(gi != 0, oi != 0)
+    np.testing.assert_allclose(gi, oi, rtol=1e-5, atol=2e-6)
+
+
+def test_flow_window_128():
+    # 128x128 sensor, 20,000 events, sinusoid flow, one bin, window-end reference
+    win = synth.flow_window()
+    assert_parity(run_gpu(win), run_oracle(win))
+
+
+def test_davis_window_346():
+    # 346x260 DAVIS sensor, 100,000 gradient-sampled events, depth + ego, 10 bins, 11 references
+    win = synth.davis_window()
+    assert_parity(run_gpu(win), run_oracle(win))
+
+
+@pytest.mark.parametrize("B,ref_mode,nfb", [(4, ALL, 4), (5, END, 1), (5, END, 5), (3, ALL, 1), (2, ALL, 2)])
+def test_bins_refs_and_per_bin_flows(B, ref_mode, nfb):
+    win = small_flow_window(70, 50, 5000, B, ref_mode, nfb=nfb, seed=B * 10 + nfb)
+    assert_parity(run_gpu(win), run_oracle(win))
+
+
+@pytest.mark.parametrize("B", [20, 32])
+def test_many_bins(B):
+    win = small_depth_window(160, 120, 6000, B, seed=B)
+    assert_parity(run_gpu(win), run_oracle(win))
+
+
+@pytest.mark.parametrize("n", [1, 31, 255, 257, 1023])
+def test_ragged_event_counts(n):
+    # loss at the default eps; gradients at eps = 1e-2: with a handful of events
+    # nearly every pixel is reached by one event only, where the gradient term is
+    # proportional to eps (t-bar - T = t-bar eps / (w + eps)) and FP32 rounding of
+    # S = w * t-bar (2^-24 relative) changes it by a factor ~ w 2^-24 / eps
+    win = small_depth_window(64, 48, n, 10, seed=n)
+    assert_parity(run_gpu(win, grad=False), run_oracle(win, grad=False), grad=False)
+    assert_parity(run_gpu(win, eps=1e-2), run_oracle(win, eps=1e-2))
+
+
+def test_empty_window():
+    win = small_flow_window(32, 24, 0, 4, ALL)
+    g = run_gpu(win)
+    assert g["loss"] == 0.0 and not np.any(g["dflow"]) and not np.any(g["nnz_r"])
+
+
+def test_all_events_masked():
+    # a flow of 100 px per window pushes every event out of a 40x30 image
+    win = small_flow_window(40, 30, 2000, 4, ALL)
+    win.flow = np.full_like(win.flow, 100.0)
+    g = run_gpu(win)
+    o = run_oracle(win)
+    assert o["valid"].sum() == 0
+    assert g["loss"] == 0.0 and not np.any(g["nnz_r"]) and not np.any(g["dflow"])
+
+
+def test_zero_flow_window():
+    win = small_flow_window(50, 40, 3000, 5, ALL)
+    win.flow = np.zeros_like(win.flow)
+    assert_parity(run_gpu(win), run_oracle(win))
+
+
+def test_out_of_range_events_are_masked():
+    win = small_flow_window(48, 32, 1000, 3, ALL, seed=8)
+    win.events.x[:10] = 48       # one past the last column
+    win.events.y[10:20] = -1     # above the first row
+    win.events.x[20:30] = 32767
+    g, o = run_gpu(win), run_oracle(win)
+    assert not o["valid"][:30].any()
+    assert_parity(g, o)
+
+
+def test_smallest_sensor():
+    win = small_flow_window(2, 2, 50, 2, ALL, mag=0.3)
+    assert_parity(run_gpu(win), run_oracle(win))
+
+
+def test_events_on_window_edges():
+    win = small_flow_window(64, 48, 600, 8, ALL, seed=12)
+    t = win.events.t.copy()
+    t[:100] = win.events.t0
+    t[-100:] = win.events.t1
+    t[200:300] = np.float32(0.005)  # an interior bin edge (tau = 0.5 for 8 bins)
+    win.events.t = np.sort(t)
+    assert_parity(run_gpu(win), run_oracle(win))
+
+
+def test_dloss_scales_gradient():
+    win = small_depth_window(80, 60, 4000, 10, seed=5)
+    g1 = run_gpu(win, dloss=1.0)
+    g2 = run_gpu(win, dloss=-2.5)
+    assert g1["loss"] == g2["loss"]
+    assert rel_l2(g2["dinv_depth"], -2.5 * g1["dinv_depth"]) < 1e-6
+    assert rel_l2(g2["dego"], -2.5 * g1["dego"]) < 1e-6
+
+
+def test_eps_is_used():
+    win = small_flow_window(60, 45, 3000, 4, ALL, seed=6)
+    assert_parity(run_gpu(win, eps=1e-3), run_oracle(win, eps=1e-3))
+
+
+def test_autograd_function_matches_backward():
+    import torch
+    cm = gpu_lib()
+    win = small_depth_window(100, 80, 5000, 10, seed=7)
+    cfg = cm.loss_cfg(win.nbins, win.ref_mode, cm.SPLAT_ATOMIC)
+    ws = cm.Workspace(win.cam, cfg, win.events.n)
+    ev = cm.DeviceEvents.from_host(win.events)
+    rho = torch.from_numpy(win.inv_depth).cuda().requires_grad_(True)
+    ego = torch.from_numpy(win.ego).cuda().requires_grad_(True)
+    loss = cm.cm_loss(ev, ws, inv_depth=rho, ego=ego, dt=win.dt)
+    (3.0 * loss).backward()
+    o = run_oracle(win, dloss=3.0)
+    assert abs(loss.item() - o["loss"]) <= 1e-5 * o["loss"]
+    assert rel_l2(rho.grad.cpu().numpy(), o["dinv_depth"]) < 1e-4
+    assert rel_l2(ego.grad.cpu().numpy(), o["dego"]) < 1e-4
