@@ -1,0 +1,442 @@
+#!/usr/bin/env python
+"""Throughput of the contrast-maximisation loss + gradient on one GB300.
+
+Workload: the uneven 64-window batch (640x480 sensor, fx = fy = 450, event
+counts log-uniform in [5k, 500k] per window, each window with its own
+inverse-depth map and ego-motion, 10 bins, all 11 bin edges as references).
+A step is one full forward + backward (loss, dL/d inverse depth, dL/d
+ego-motion) of every window of the batch; the metric is input events of such
+evaluations per second (Mev/s).  Inputs are seeded synthetic windows resident
+in HBM before the timed region.
+
+Printed as one JSON line (rank 0).  --impl reference times the CPU oracle on
+the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CM loss+grad Mevents/s batched vs plain per-window at ≤1e-5 rel err; p50/p99 latency"
+WORKLOAD = "batch64_640x480_b10"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--windows", type=int, default=64, help="windows per step (64 for the headline workload)")
+    ap.add_argument("--no-plain", action="store_true", help="skip the per-window plain comparison")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="bound of the CPU oracle sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+# ---------------------------------------------------------------------------
+# GPU clocks during the timed region
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9:
+                    rows.append(f)
+        except Exception:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except Exception:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic bytes per kernel launch (strict model: events read by the forward
+# splat and by the adjoint, 9 B each; inverse depth read by the flow kernel and
+# its gradient written by the depth/ego kernel, 4 B per pixel each; the IWE is
+# intermediate state).  The materialised-IWE model adds the dense IWE traffic
+# of this design: 16 B per pixel and reference written by the splat, read and
+# rewritten by the loss pass, gathered by the adjoint.
+
+
+def kernel_bytes(name: str, n: int, hw: int, R: int, model: str) -> float:
+    iwe = model == "iwe"
+    if name == "k_splat":
+        return 9.0 * n + (16.0 * R * hw if iwe else 0.0)
+    if name == "k_adjoint":
+        return 9.0 * n + (16.0 * R * hw if iwe else 0.0)
+    if name == "k_flow":
+        return 4.0 * hw + (8.0 * hw if iwe else 0.0)
+    if name == "k_depth_ego":
+        return 4.0 * hw + (8.0 * hw if iwe else 0.0)
+    if name == "k_loss_partial":
+        return 32.0 * R * hw if iwe else 0.0
+    return 0.0
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2412_06359_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None
+    when the kernels changed since the counters were taken."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(p))
+    except Exception:
+        return None
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    k = d.get("kernels", {}).get(kernel)
+    return None if k is None else float(k["dram_bytes_per_launch_at_bench"])
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle baseline
+
+
+def oracle_sample(windows, seconds: float):
+    """Time the FP64 oracle (single thread) on windows of the workload until
+    `seconds` of CPU work are done; returns (events, seconds, windows used)."""
+    from oracle import oracle as O
+    O.build()
+    ev = 0
+    t_total = 0.0
+    used = 0
+    for w in windows:
+        t0 = time.perf_counter()
+        O.cm_window(w, grad=True, positions="f32")
+        t_total += time.perf_counter() - t0
+        ev += w.events.n
+        used += 1
+        if t_total >= seconds:
+            break
+    return ev, t_total, used
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2412_06359_gb300 import synth
+    wins = synth.batch_windows(args.windows)
+    from oracle import oracle as O
+    O.build()
+    # each step: the oracle on one window of the batch (rotating), a bounded sample
+    for i in range(args.warmup):
+        O.cm_window(wins[i % len(wins)], grad=True, positions="f32")
+    ev = 0
+    t0 = time.perf_counter()
+    times = []
+    for i in range(args.steps):
+        w = wins[i % len(wins)]
+        s = time.perf_counter()
+        O.cm_window(w, grad=True, positions="f32")
+        times.append(time.perf_counter() - s)
+        ev += w.events.n
+    el = time.perf_counter() - t0
+    v = ev / el / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "Mev/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "windows": args.windows, "sample": "one window of the batch per step"},
+        "cpu_baseline": {"value": v, "unit": "Mev/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} windows of the 64-window batch, one per step, loss + gradient"},
+        "e2e": {"value": v, "unit": "Mev/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "p50_ms": 1e3 * float(np.percentile(times, 50)), "p99_ms": 1e3 * float(np.percentile(times, 99)),
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our path
+
+
+class Batch:
+    """The windows of one step, resident on the device, with one workspace per
+    window (the plain per-window path through the C ABI)."""
+
+    def __init__(self, wins, device):
+        import torch
+
+        from paper_2412_06359_gb300 import cm
+        self.cm = cm
+        self.wins = wins
+        self.dev = device
+        self.items = []
+        for w in wins:
+            cfg = cm.loss_cfg(w.nbins, w.ref_mode, cm.SPLAT_ATOMIC)
+            ws = cm.Workspace(w.cam, cfg, w.events.n, 1, device)
+            ev = cm.DeviceEvents.from_host(w.events, device)
+            rho = torch.from_numpy(w.inv_depth).to(device)
+            ego = torch.from_numpy(w.ego).to(device)
+            out = {"dinv_depth": torch.empty_like(rho), "dego": torch.empty(6, device=device)}
+            loss = torch.empty(1, device=device)
+            self.items.append((w, ws, ev, rho, ego, out, loss))
+        self.dloss = torch.ones(1, device=device)
+        self.events = sum(w.events.n for w in wins)
+
+    def step(self):
+        cm = self.cm
+        for w, ws, ev, rho, ego, out, loss in self.items:
+            cm.loss_forward(ws, ev, inv_depth=rho, ego=ego, dt=w.dt, out=loss)
+            cm.loss_backward(ws, ev, self.dloss, inv_depth=rho, ego=ego, dt=w.dt, want_dflow=False, out=out)
+
+    def plain_window(self, i):
+        import torch
+        w, ws, ev, rho, ego, out, loss = self.items[i]
+        self.cm.loss_forward(ws, ev, inv_depth=rho, ego=ego, dt=w.dt, out=loss)
+        self.cm.loss_backward(ws, ev, self.dloss, inv_depth=rho, ego=ego, dt=w.dt, want_dflow=False, out=out)
+        torch.cuda.current_stream().synchronize()
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2412_06359_gb300 import _capi as C
+    from paper_2412_06359_gb300 import build, synth
+    build.build()
+    C.lib()
+
+    # weak scaling: every rank evaluates its own 64 windows
+    wins = synth.batch_windows(args.windows, first=rank * args.windows)
+    batch = Batch(wins, dev)
+    hw = wins[0].cam.width * wins[0].cam.height
+    R = wins[0].nbins + 1
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        batch.step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, CUDA events on the launching stream ----
+    ev_steps = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    C.cm_profile_reset()
+    launches0 = C.cm_launch_count()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        C.cm_profile_enable(True)
+        ev_steps[0].record(stream)
+        for k in range(args.steps):
+            batch.step()
+            ev_steps[k + 1].record(stream)
+        torch.cuda.synchronize()
+        C.cm_profile_enable(False)
+    launches = C.cm_launch_count() - launches0
+    step_ms = [ev_steps[k].elapsed_time(ev_steps[k + 1]) for k in range(args.steps)]
+    total_ms = ev_steps[0].elapsed_time(ev_steps[-1])
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    clocks = clk.summary()
+    prof = C.cm_profile_collect()
+    ms_per_step = total_ms / args.steps
+    value = world * batch.events / (ms_per_step * 1e-3) / 1e6
+
+    # ---- roofline of the dominant kernel ----
+    peak, peak_kind = measured_peak()
+    dom = max(prof.items(), key=lambda kv: kv[1][1])[0] if prof else None
+    roof = None
+    roof_iwe = None
+    if dom:
+        nl, ms = prof[dom]
+        per_launch_ms = ms / nl
+        nwin = len(wins)
+        avg_n = batch.events / nwin
+        for model in ("strict", "iwe"):
+            b = kernel_bytes(dom, avg_n, hw, R, model)
+            ach = b / (per_launch_ms * 1e-3) / 1e9
+            obj = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                   "traffic": recorded_traffic(dom) if model == "strict" else None, "kernel": dom,
+                   "launch_ms": per_launch_ms, "bytes_per_launch": b, "peak_kind": f"{peak_kind} hbm_gbs"}
+            if model == "strict":
+                roof = obj
+            else:
+                roof_iwe = obj
+
+    # ---- plain per-window comparison (a stream sync after every window) ----
+    plain = None
+    if not args.no_plain:
+        for i in range(min(3, len(wins))):
+            batch.plain_window(i)
+        lat = []
+        t0 = time.perf_counter()
+        for i in range(len(wins)):
+            s = time.perf_counter()
+            batch.plain_window(i)
+            lat.append(1e3 * (time.perf_counter() - s))
+        el = time.perf_counter() - t0
+        plain = {"value": batch.events / el / 1e6, "unit": "Mev/s", "p50_ms": float(np.percentile(lat, 50)),
+                 "p99_ms": float(np.percentile(lat, 99)), "windows": len(wins)}
+
+    # ---- end to end through the public API with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(batch, args, stream)
+
+    # ---- CPU oracle baseline (rank 0 at N = 1 only) ----
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        n, sec, used = oracle_sample(wins, args.cpu_seconds)
+        cpu = {"value": n / sec / 1e6, "unit": "Mev/s", "cores": 1, "kind": "oracle",
+               "sample": f"first {used} windows of the batch ({n} events), loss + gradient, FP64, one thread"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "Mev/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "windows": len(wins), "events_per_step": batch.events,
+                       "sensor": "640x480", "bins": wins[0].nbins, "refs": R, "splat": "atomic",
+                       "path": "per-window launches, one stream, no host sync",
+                       "l2": "per-step IWE working set %.2f GB > L2 (no flush needed)" % (len(wins) * R * hw * 16 / 1e9)},
+            "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
+            "plain": plain, "roofline": roof, "roofline_iwe": roof_iwe, "cpu_baseline": cpu, "e2e": e2e,
+            "clocks": clocks, "gpu_launches": int(launches),
+            "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])},
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_e2e(batch, args, stream):
+    """Same metric through the C ABI with host buffers: every step copies each
+    window's events, inverse depth and ego-motion from pinned host memory to the
+    device, evaluates loss + gradient, and copies the loss and both gradients
+    back to pinned host memory."""
+    import torch
+    host_in, host_out = [], []
+    h2d = d2h = 0
+    for w, ws, ev, rho, ego, out, loss in batch.items:
+        hin = [torch.from_numpy(a).pin_memory() for a in (w.events.x, w.events.y, w.events.t, w.events.p,
+                                                          w.inv_depth, w.ego)]
+        hout = [torch.empty(1).pin_memory(), torch.empty_like(rho, device="cpu").pin_memory(),
+                torch.empty(6).pin_memory()]
+        host_in.append(hin)
+        host_out.append(hout)
+        h2d += sum(a.numel() * a.element_size() for a in hin)
+        d2h += sum(a.numel() * a.element_size() for a in hout)
+
+    def step():
+        for (w, ws, ev, rho, ego, out, loss), hin, hout in zip(batch.items, host_in, host_out):
+            for dst, src in zip((ev.x, ev.y, ev.t, ev.p, rho, ego), hin):
+                dst.copy_(src, non_blocking=True)
+            batch.cm.loss_forward(ws, ev, inv_depth=rho, ego=ego, dt=w.dt, out=loss)
+            batch.cm.loss_backward(ws, ev, batch.dloss, inv_depth=rho, ego=ego, dt=w.dt, want_dflow=False, out=out)
+            hout[0].copy_(loss, non_blocking=True)
+            hout[1].copy_(out["dinv_depth"], non_blocking=True)
+            hout[2].copy_(out["dego"], non_blocking=True)
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    K = max(3, args.steps // 3)
+    a.record(stream)
+    for _ in range(K):
+        step()
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / K
+    return {"value": batch.events / (ms * 1e-3) / 1e6, "unit": "Mev/s", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": ms}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -190,6 +190,27 @@ int cm_loss_backward(const cm_camera* cam, const cm_events* ev, const float* flo
  */
 int cm_workspace_stats(const cm_workspace* ws, const float** loss_r, const int32_t** nnz_r);
 
+/* ---- tracing ----
+ * Per-kernel timing with CUDA events recorded on each kernel's own launch
+ * stream (no counterpart in the paper, which reports phase runtimes in its
+ * Fig. 2).  While enabled, every library kernel launch is bracketed by two
+ * events; cm_profile_collect waits for the recorded events and returns, per
+ * kernel name, the number of launches and the summed elapsed milliseconds since
+ * the last cm_profile_reset.  Launches captured into a CUDA graph are not timed. */
+typedef struct {
+    char name[48];
+    int64_t launches;
+    double total_ms;
+} cm_kernel_stat;
+
+int cm_profile_enable(int on);
+/* Fills out[0 .. min(cap, *count) - 1]; *count receives the number of kernel names. */
+int cm_profile_collect(cm_kernel_stat* out, int32_t cap, int32_t* count);
+int cm_profile_reset(void);
+/* Number of kernels the library has enqueued since it was loaded (graph replays
+ * count each kernel node). */
+int64_t cm_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

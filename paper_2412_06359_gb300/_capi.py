@@ -41,6 +41,10 @@ class cm_loss_cfg(ctypes.Structure):
                 ("store_warps", ctypes.c_int32), ("eps", ctypes.c_float)]
 
 
+class cm_kernel_stat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
+
+
 _lib = None
 
 _vp, _i32, _i64, _f32, _sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_size_t
@@ -60,6 +64,10 @@ SIGNATURES = {
                         ctypes.c_int),
     "cm_loss_backward": ([_P(cm_camera), _P(cm_events), _vp, _i32, _vp, _vp, _f32, _P(cm_loss_cfg), _vp, _vp,
                           _vp, _vp, _vp, _vp], ctypes.c_int),
+    "cm_profile_enable": ([ctypes.c_int], ctypes.c_int),
+    "cm_profile_collect": ([_P(cm_kernel_stat), _i32, _P(_i32)], ctypes.c_int),
+    "cm_profile_reset": ([], ctypes.c_int),
+    "cm_launch_count": ([], ctypes.c_int64),
 }
 
 
@@ -144,3 +152,24 @@ def cm_loss_backward(cam, ev, flow, n_flow_bins, inv_depth, ego6, dt_window, cfg
     _check(lib().cm_loss_backward(ctypes.byref(cam), ctypes.byref(ev), flow, n_flow_bins, inv_depth, ego6,
                                   dt_window, ctypes.byref(cfg), ws, dloss, dflow, dinv_depth, dego6, stream),
            "cm_loss_backward")
+
+
+def cm_profile_enable(on: bool) -> None:
+    _check(lib().cm_profile_enable(1 if on else 0), "cm_profile_enable")
+
+
+def cm_profile_collect() -> dict:
+    """{kernel name: (launches, total milliseconds)} since the last reset."""
+    n = _i32(0)
+    _check(lib().cm_profile_collect(None, 0, ctypes.byref(n)), "cm_profile_collect")
+    arr = (cm_kernel_stat * max(n.value, 1))()
+    _check(lib().cm_profile_collect(arr, n.value, ctypes.byref(n)), "cm_profile_collect")
+    return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(n.value)}
+
+
+def cm_profile_reset() -> None:
+    _check(lib().cm_profile_reset(), "cm_profile_reset")
+
+
+def cm_launch_count() -> int:
+    return int(lib().cm_launch_count())

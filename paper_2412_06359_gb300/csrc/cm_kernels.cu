@@ -197,6 +197,7 @@ cudaError_t launch_flow(const Win& d, cudaStream_t st)
 {
     const size_t HW = (size_t)d.W * d.H;
     const int grid = (int)((HW + 255) / 256 < 4096 ? (HW + 255) / 256 : 4096);
+    KernelScope ks("k_flow", st);
     k_flow<<<grid, 256, 0, st>>>(d.W, d.H, d.rho, d.ego, d.fx, d.fy, d.cx, d.cy, d.dt, const_cast<float2*>(d.flow));
     return cudaGetLastError();
 }
@@ -205,6 +206,7 @@ cudaError_t launch_splat(const Win& d, int sm_count, cudaStream_t st)
 {
     if (d.n == 0) return cudaSuccess;
     const int g = event_grid(d.n, sm_count);
+    KernelScope ks("k_splat", st);
     if (d.B <= 1) k_splat<1><<<g, kEventThreads, 0, st>>>(d);
     else if (d.B <= 10) k_splat<10><<<g, kEventThreads, 0, st>>>(d);
     else if (d.B <= 20) k_splat<20><<<g, kEventThreads, 0, st>>>(d);
@@ -216,6 +218,7 @@ cudaError_t launch_adjoint(const Win& d, int sm_count, cudaStream_t st)
 {
     if (d.n == 0) return cudaSuccess;
     const int g = event_grid(d.n, sm_count);
+    KernelScope ks("k_adjoint", st);
     if (d.B <= 1) k_adjoint<1><<<g, kEventThreads, 0, st>>>(d);
     else if (d.B <= 10) k_adjoint<10><<<g, kEventThreads, 0, st>>>(d);
     else if (d.B <= 20) k_adjoint<20><<<g, kEventThreads, 0, st>>>(d);
@@ -225,15 +228,27 @@ cudaError_t launch_adjoint(const Win& d, int sm_count, cudaStream_t st)
 
 cudaError_t launch_loss(const Win& d, cudaStream_t st)
 {
-    k_loss_partial<<<dim3(d.loss_tiles, d.R), 256, 0, st>>>(d);
-    k_loss_final<<<1, 1024, 0, st>>>(d);
+    {
+        KernelScope ks("k_loss_partial", st);
+        k_loss_partial<<<dim3(d.loss_tiles, d.R), 256, 0, st>>>(d);
+    }
+    {
+        KernelScope ks("k_loss_final", st);
+        k_loss_final<<<1, 1024, 0, st>>>(d);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_depth_ego(const Win& d, cudaStream_t st)
 {
-    k_depth_ego<<<d.pix_tiles, 256, 0, st>>>(d);
-    k_depth_ego_final<<<1, 192, 0, st>>>(d);
+    {
+        KernelScope ks("k_depth_ego", st);
+        k_depth_ego<<<d.pix_tiles, 256, 0, st>>>(d);
+    }
+    {
+        KernelScope ks("k_depth_ego_final", st);
+        k_depth_ego_final<<<1, 192, 0, st>>>(d);
+    }
     return cudaGetLastError();
 }
 

@@ -17,4 +17,23 @@ cudaError_t launch_depth_ego(const Win& d, cudaStream_t st);
 // number of SMs of the current device (cached per device)
 int sm_count_current();
 
+// Tracing scope around one kernel launch: counts the launch and, when
+// profiling is on and the stream is not being captured, brackets it with CUDA
+// events on the launch stream (cm_profile.cu).
+class KernelScope {
+public:
+    KernelScope(const char* name, cudaStream_t s, int launches = 1);
+    ~KernelScope();
+    KernelScope(const KernelScope&) = delete;
+    KernelScope& operator=(const KernelScope&) = delete;
+
+private:
+    const char* name_;
+    cudaStream_t s_;
+    cudaEvent_t a_;
+};
+
+// add kernel launches made outside KernelScope (graph replays)
+void count_launches(long long n);
+
 }  // namespace cmk

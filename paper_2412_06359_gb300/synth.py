@@ -241,11 +241,12 @@ def davis_window(n: int = 100_000) -> Window:
 
 
 def batch_windows(count: int = 64, width: int = 640, height: int = 480,
-                  lo: float = 5e3, hi: float = 5e5) -> list[Window]:
+                  lo: float = 5e3, hi: float = 5e5, first: int = 0) -> list[Window]:
     """Uneven batch: `count` 640x480 windows with log-uniform event counts in
-    [5k, 500k], each with its own depth map and ego-motion, 10 bins."""
+    [5k, 500k], each with its own depth map and ego-motion, 10 bins.  Windows
+    first .. first+count-1 of the seeded sequence."""
     out = []
-    for i in range(count):
+    for i in range(first, first + count):
         rng = rng_for(3, i)
         n = log_uniform_count(rng, lo, hi)
         out.append(depth_window(rng, width, height, n))
