@@ -190,6 +190,40 @@ int cm_loss_backward(const cm_camera* cam, const cm_events* ev, const float* flo
  */
 int cm_workspace_stats(const cm_workspace* ws, const float** loss_r, const int32_t** nnz_r);
 
+/* ---- loss and flow gradient without any allocation ----
+ * The paper has no counterpart of this entry point; it exists for callers that
+ * cannot allocate device memory where they evaluate the loss: a real-time
+ * control or on-board learning loop that must not pay an allocator's latency or
+ * risk an out-of-memory failure mid-cycle, a plug-in inside a framework that
+ * owns all device memory through its own pool, code whose memory was budgeted
+ * up front.  It computes what cm_loss_forward followed by cm_loss_backward
+ * compute for a flow input, but keeps every intermediate buffer in one fixed
+ * device array inside the library instead of a caller workspace.
+ *
+ *   flow       device float [n_flow_bins][H][W][2] (input)
+ *   dloss      device float scalar, the upstream gradient (input)
+ *   loss_out   device float scalar (output)
+ *   dflow_out  device float [n_flow_bins][H][W][2], overwritten with dL/dflow scaled by dloss (output)
+ *
+ * Limits and behaviour:
+ *   - The fixed array holds CM_STATIC_SCRATCH_BYTES; a window whose images of
+ *     warped events and reduction buffers need more (about R x W x H x 16 bytes,
+ *     e.g. 346x260 with 11 references fits, 640x480 with 11 does not) is rejected
+ *     with CM_ENOMEM before anything is enqueued.  Every GPU that loads the
+ *     library's module keeps the array reserved until the process exits.
+ *   - The call makes no cudaMalloc, cudaFree or other allocating call.  The
+ *     first call on each device looks up the array's device address (once, with
+ *     that device current); make that first call before any stream capture.
+ *   - All calls share the array and it keeps the last call's contents; each
+ *     call clears what must start at zero.  Calls whose work overlaps on the
+ *     GPU race on the array: order them on one stream or synchronise between them.
+ *   - cfg->splat must be CM_SPLAT_AUTO or CM_SPLAT_ATOMIC.
+ * Errors: CM_EINVAL, CM_ENOMEM (window too large for the array), CM_ECUDA. */
+#define CM_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
+int cm_loss_grad_static(const cm_camera* cam, const cm_events* ev, const float* flow, int32_t n_flow_bins,
+                        const cm_loss_cfg* cfg, const float* dloss, float* loss_out, float* dflow_out,
+                        void* stream);
+
 /* ---- tracing ----
  * Per-kernel timing with CUDA events recorded on each kernel's own launch
  * stream (no counterpart in the paper, which reports phase runtimes in its

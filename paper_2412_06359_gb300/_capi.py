@@ -17,6 +17,7 @@ CM_OK, CM_EINVAL, CM_ENOMEM, CM_EBUSY, CM_ETIMEOUT, CM_ECUDA, CM_ENOTFOUND, CM_E
 CM_REF_END, CM_REF_ALL_EDGES = 0, 1
 CM_SPLAT_AUTO, CM_SPLAT_ATOMIC, CM_SPLAT_SORT = 0, 1, 2
 CM_MAX_BINS = 32
+CM_STATIC_SCRATCH_BYTES = 32 * 1024 * 1024
 
 
 class CMError(RuntimeError):
@@ -64,6 +65,8 @@ SIGNATURES = {
                         ctypes.c_int),
     "cm_loss_backward": ([_P(cm_camera), _P(cm_events), _vp, _i32, _vp, _vp, _f32, _P(cm_loss_cfg), _vp, _vp,
                           _vp, _vp, _vp, _vp], ctypes.c_int),
+    "cm_loss_grad_static": ([_P(cm_camera), _P(cm_events), _vp, _i32, _P(cm_loss_cfg), _vp, _vp, _vp, _vp],
+                            ctypes.c_int),
     "cm_profile_enable": ([ctypes.c_int], ctypes.c_int),
     "cm_profile_collect": ([_P(cm_kernel_stat), _i32, _P(_i32)], ctypes.c_int),
     "cm_profile_reset": ([], ctypes.c_int),
@@ -152,6 +155,14 @@ def cm_loss_backward(cam, ev, flow, n_flow_bins, inv_depth, ego6, dt_window, cfg
     _check(lib().cm_loss_backward(ctypes.byref(cam), ctypes.byref(ev), flow, n_flow_bins, inv_depth, ego6,
                                   dt_window, ctypes.byref(cfg), ws, dloss, dflow, dinv_depth, dego6, stream),
            "cm_loss_backward")
+
+
+def cm_loss_grad_static(cam, ev, flow: int, n_flow_bins: int, cfg, dloss: int, loss_out: int, dflow_out: int,
+                        stream: int) -> None:
+    """Loss and dL/dflow of one window with no workspace and no allocation
+    (the library's fixed internal array; see include/cm.h for the limits)."""
+    _check(lib().cm_loss_grad_static(ctypes.byref(cam), ctypes.byref(ev), flow, n_flow_bins, ctypes.byref(cfg),
+                                     dloss, loss_out, dflow_out, stream), "cm_loss_grad_static")
 
 
 def cm_profile_enable(on: bool) -> None:
