@@ -120,17 +120,18 @@ class ClockSampler:
 
 
 def kernel_bytes(name: str, n: int, hw: int, R: int, model: str) -> float:
+    """Algorithmic bytes of one launch of `name` that processes n events over
+    hw pixels (summed over the windows the launch covers) with R references."""
     iwe = model == "iwe"
-    if name == "k_splat":
+    base = name.replace("_batch", "")
+    if base in ("k_splat", "k_adjoint"):
         return 9.0 * n + (16.0 * R * hw if iwe else 0.0)
-    if name == "k_adjoint":
-        return 9.0 * n + (16.0 * R * hw if iwe else 0.0)
-    if name == "k_flow":
+    if base in ("k_flow", "k_depth_ego"):
         return 4.0 * hw + (8.0 * hw if iwe else 0.0)
-    if name == "k_depth_ego":
-        return 4.0 * hw + (8.0 * hw if iwe else 0.0)
-    if name == "k_loss_partial":
+    if base == "k_loss_partial":
         return 32.0 * R * hw if iwe else 0.0
+    if base == "k_zero":
+        return 16.0 * R * hw if iwe else 0.0
     return 0.0
 
 
@@ -229,8 +230,9 @@ def run_reference(args):
 
 
 class Batch:
-    """The windows of one step, resident on the device, with one workspace per
-    window (the plain per-window path through the C ABI)."""
+    """The windows of one step resident on the device: a batched plan over all
+    of them (the timed path) and one workspace per window for the plain
+    per-window comparison through the single-window entry points."""
 
     def __init__(self, wins, device):
         import torch
@@ -240,6 +242,7 @@ class Batch:
         self.wins = wins
         self.dev = device
         self.items = []
+        dev_wins = []
         for w in wins:
             cfg = cm.loss_cfg(w.nbins, w.ref_mode, cm.SPLAT_ATOMIC)
             ws = cm.Workspace(w.cam, cfg, w.events.n, 1, device)
@@ -249,14 +252,13 @@ class Batch:
             out = {"dinv_depth": torch.empty_like(rho), "dego": torch.empty(6, device=device)}
             loss = torch.empty(1, device=device)
             self.items.append((w, ws, ev, rho, ego, out, loss))
+            dev_wins.append({"cam": w.cam, "ev": ev, "inv_depth": rho, "ego": ego, "dt": w.dt})
         self.dloss = torch.ones(1, device=device)
+        self.plan = cm.BatchPlan(dev_wins, cm.loss_cfg(wins[0].nbins, wins[0].ref_mode, cm.SPLAT_ATOMIC), device)
         self.events = sum(w.events.n for w in wins)
 
     def step(self):
-        cm = self.cm
-        for w, ws, ev, rho, ego, out, loss in self.items:
-            cm.loss_forward(ws, ev, inv_depth=rho, ego=ego, dt=w.dt, out=loss)
-            cm.loss_backward(ws, ev, self.dloss, inv_depth=rho, ego=ego, dt=w.dt, want_dflow=False, out=out)
+        self.plan.run()
 
     def plain_window(self, i):
         import torch
@@ -288,6 +290,7 @@ def run_ours(args):
     R = wins[0].nbins + 1
     stream = torch.cuda.current_stream()
 
+    schedule = batch.plan.autotune()  # picks chains / windows per kernel for this batch (cached per shape)
     for _ in range(args.warmup):
         batch.step()
     torch.cuda.synchronize()
@@ -328,14 +331,18 @@ def run_ours(args):
     if dom:
         nl, ms = prof[dom]
         per_launch_ms = ms / nl
-        nwin = len(wins)
-        avg_n = batch.events / nwin
+        launches_per_step = nl / args.steps
+        # kernel time summed over the chains per step / step time: above 1 when
+        # kernels of concurrent chains overlap (each launch's duration then includes
+        # the time it shares the GPU)
+        overlap = sum(v[1] for v in prof.values()) / args.steps / ms_per_step
         for model in ("strict", "iwe"):
-            b = kernel_bytes(dom, avg_n, hw, R, model)
+            b = kernel_bytes(dom, batch.events, hw * len(wins), R, model) / launches_per_step
             ach = b / (per_launch_ms * 1e-3) / 1e9
             obj = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                    "traffic": recorded_traffic(dom) if model == "strict" else None, "kernel": dom,
-                   "launch_ms": per_launch_ms, "bytes_per_launch": b, "peak_kind": f"{peak_kind} hbm_gbs"}
+                   "launch_ms": per_launch_ms, "bytes_per_launch": b, "launches_per_step": launches_per_step,
+                   "overlap": overlap, "peak_kind": f"{peak_kind} hbm_gbs"}
             if model == "strict":
                 roof = obj
             else:
@@ -375,7 +382,8 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "windows": len(wins), "events_per_step": batch.events,
                        "sensor": "640x480", "bins": wins[0].nbins, "refs": R, "splat": "atomic",
-                       "path": "per-window launches, one stream, no host sync",
+                       "path": "batched plan replayed from a CUDA graph",
+                       "schedule": {"chains": schedule[0], "windows_per_kernel": schedule[1]},
                        "l2": "per-step IWE working set %.2f GB > L2 (no flush needed)" % (len(wins) * R * hw * 16 / 1e9)},
             "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
             "plain": plain, "roofline": roof, "roofline_iwe": roof_iwe, "cpu_baseline": cpu, "e2e": e2e,
@@ -389,31 +397,34 @@ def run_ours(args):
 
 def run_e2e(batch, args, stream):
     """Same metric through the C ABI with host buffers: every step copies each
-    window's events, inverse depth and ego-motion from pinned host memory to the
-    device, evaluates loss + gradient, and copies the loss and both gradients
-    back to pinned host memory."""
+    window's events, inverse depth and ego-motion from pinned host memory into
+    the device buffers the batch plan is bound to, runs the plan, and copies
+    every loss and both gradients of every window back to pinned host memory."""
     import torch
+    plan = batch.plan
     host_in, host_out = [], []
     h2d = d2h = 0
-    for w, ws, ev, rho, ego, out, loss in batch.items:
+    for (w, ws, ev, rho, ego, out, loss) in batch.items:
         hin = [torch.from_numpy(a).pin_memory() for a in (w.events.x, w.events.y, w.events.t, w.events.p,
                                                           w.inv_depth, w.ego)]
-        hout = [torch.empty(1).pin_memory(), torch.empty_like(rho, device="cpu").pin_memory(),
-                torch.empty(6).pin_memory()]
         host_in.append(hin)
-        host_out.append(hout)
         h2d += sum(a.numel() * a.element_size() for a in hin)
+    for o in plan.outputs:
+        hout = [torch.empty_like(o["dinv_depth"], device="cpu").pin_memory(), torch.empty(6).pin_memory()]
+        host_out.append(hout)
         d2h += sum(a.numel() * a.element_size() for a in hout)
+    loss_host = torch.empty(plan.loss.numel()).pin_memory()
+    d2h += loss_host.numel() * 4
 
     def step():
-        for (w, ws, ev, rho, ego, out, loss), hin, hout in zip(batch.items, host_in, host_out):
+        for (w, ws, ev, rho, ego, out, loss), hin in zip(batch.items, host_in):
             for dst, src in zip((ev.x, ev.y, ev.t, ev.p, rho, ego), hin):
                 dst.copy_(src, non_blocking=True)
-            batch.cm.loss_forward(ws, ev, inv_depth=rho, ego=ego, dt=w.dt, out=loss)
-            batch.cm.loss_backward(ws, ev, batch.dloss, inv_depth=rho, ego=ego, dt=w.dt, want_dflow=False, out=out)
-            hout[0].copy_(loss, non_blocking=True)
-            hout[1].copy_(out["dinv_depth"], non_blocking=True)
-            hout[2].copy_(out["dego"], non_blocking=True)
+        plan.run()
+        loss_host.copy_(plan.loss, non_blocking=True)
+        for o, hout in zip(plan.outputs, host_out):
+            hout[0].copy_(o["dinv_depth"], non_blocking=True)
+            hout[1].copy_(o["dego"], non_blocking=True)
 
     for _ in range(2):
         step()

@@ -190,6 +190,76 @@ int cm_loss_backward(const cm_camera* cam, const cm_events* ev, const float* flo
  */
 int cm_workspace_stats(const cm_workspace* ws, const float** loss_r, const int32_t** nnz_r);
 
+/* ---- batched evaluation ----
+ * Loss and gradient of many windows at once (the batched training step of the
+ * paper, supp. "Training": batches of 4-8 event windows on one GPU), with
+ * windows of different sizes and event counts in one launch per phase:
+ * events are split into chunks of 256 and handed out in window order, pixel
+ * passes into per-window tiles, with device-side prefix tables mapping a chunk
+ * or tile to its window, so no window is padded.  The phases (zero, flow from
+ * depth, warp + splat, loss pass 1 and 2, adjoint, depth / ego gradient and its
+ * reduction) run as one CUDA graph, captured at the first cm_batch_run and
+ * replayed afterwards.
+ *
+ * One window of a batch (all pointers are device memory; nbins, reference mode
+ * and eps come from the batch's cm_loss_cfg and are shared by all windows). */
+typedef struct {
+    cm_camera cam;
+    cm_events ev;
+    const float* flow;      /* [H][W][2] flow input, or NULL: flow from inv_depth + ego6 */
+    const float* inv_depth; /* [H][W] (depth input) */
+    const float* ego6;      /* [6]    (depth input) */
+    float dt_window;        /* window length for the motion field (depth input) */
+    const float* dloss;     /* scalar: upstream gradient of this window's loss (required) */
+    float* loss_out;        /* scalar: this window's loss (required) */
+    float* dflow;           /* [H][W][2] dL/dflow, or NULL (then kept in the plan's memory) */
+    float* dinv_depth;      /* [H][W] dL/d(inverse depth), or NULL (depth input only) */
+    float* dego6;           /* [6] dL/d(ego-motion), or NULL (depth input only) */
+} cm_window;
+
+typedef struct cm_batch cm_batch;
+
+/* Device bytes of a batch plan for these windows (they also fix its
+ * capacities: the number of windows and the image sizes it can hold). */
+int cm_batch_query(const cm_window* wins, int32_t nwin, const cm_loss_cfg* cfg, size_t* bytes);
+/* Lay a plan over caller-owned device memory (256-byte aligned, at least
+ * cm_batch_query's size) and point it at `wins`.  The plan owns a small pinned
+ * host staging buffer, a capture stream and a few events (host-side); it never
+ * allocates device memory.  cfg->splat must be AUTO or ATOMIC.
+ * Errors: CM_EINVAL, CM_ENOMEM, CM_ECUDA. */
+int cm_batch_create(void* dev_mem, size_t bytes, const cm_window* wins, int32_t nwin, const cm_loss_cfg* cfg,
+                    cm_batch** plan);
+/* Point the plan at another set of windows.  They must fit its capacities
+ * (window count and the per-window image memory, summed); CM_ENOMEM otherwise.
+ * Takes effect at the next cm_batch_run, which uploads the new table first. */
+int cm_batch_set_windows(cm_batch* plan, const cm_window* wins, int32_t nwin);
+/* Forward and backward of every window of the plan, stream-ordered on
+ * `stream`: writes each loss_out and the requested gradients. */
+int cm_batch_run(cm_batch* plan, void* stream);
+
+/* Schedule of a plan: windows are taken `group` at a time (each kernel of the
+ * graph covers one group) and the groups run on `chains` concurrent chains of
+ * the graph, each chain one group after another; group 0 (with chains 1) puts
+ * every window in each kernel.  Few windows in flight keep their images of
+ * warped events in L2; several chains overlap each other's tails.  Default:
+ * chains 2, group 1. */
+typedef struct {
+    int32_t chains;  /* 1..8 */
+    int32_t group;   /* windows per kernel; 0 = all */
+} cm_batch_schedule;
+int cm_batch_set_schedule(cm_batch* plan, const cm_batch_schedule* schedule);
+int cm_batch_get_schedule(const cm_batch* plan, cm_batch_schedule* schedule);
+/* Autotuner: times each candidate schedule on the plan's own windows (three
+ * replays each, CUDA events on `stream`), keeps the fastest and remembers it
+ * for plans of the same shape (window count, first window size, references,
+ * event count to a power of two) for the life of the process.  Runs the plan
+ * several times (outputs are overwritten); synchronises `stream`. */
+int cm_batch_autotune(cm_batch* plan, void* stream, cm_batch_schedule* chosen);
+/* Device pointers to window `window`'s per-reference losses (float [R]) and
+ * non-empty counts (int32 [R]) of the last run. */
+int cm_batch_stats(const cm_batch* plan, int32_t window, const float** loss_r, const int32_t** nnz_r);
+int cm_batch_destroy(cm_batch* plan);
+
 /* ---- loss and flow gradient without any allocation ----
  * The paper has no counterpart of this entry point; it exists for callers that
  * cannot allocate device memory where they evaluate the loss: a real-time

@@ -42,6 +42,17 @@ class cm_loss_cfg(ctypes.Structure):
                 ("store_warps", ctypes.c_int32), ("eps", ctypes.c_float)]
 
 
+class cm_window(ctypes.Structure):
+    _fields_ = [("cam", cm_camera), ("ev", cm_events), ("flow", ctypes.c_void_p), ("inv_depth", ctypes.c_void_p),
+                ("ego6", ctypes.c_void_p), ("dt_window", ctypes.c_float), ("dloss", ctypes.c_void_p),
+                ("loss_out", ctypes.c_void_p), ("dflow", ctypes.c_void_p), ("dinv_depth", ctypes.c_void_p),
+                ("dego6", ctypes.c_void_p)]
+
+
+class cm_batch_schedule(ctypes.Structure):
+    _fields_ = [("chains", ctypes.c_int32), ("group", ctypes.c_int32)]
+
+
 class cm_kernel_stat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
 
@@ -65,6 +76,15 @@ SIGNATURES = {
                         ctypes.c_int),
     "cm_loss_backward": ([_P(cm_camera), _P(cm_events), _vp, _i32, _vp, _vp, _f32, _P(cm_loss_cfg), _vp, _vp,
                           _vp, _vp, _vp, _vp], ctypes.c_int),
+    "cm_batch_query": ([_P(cm_window), _i32, _P(cm_loss_cfg), _P(_sz)], ctypes.c_int),
+    "cm_batch_create": ([_vp, _sz, _P(cm_window), _i32, _P(cm_loss_cfg), _P(_vp)], ctypes.c_int),
+    "cm_batch_set_windows": ([_vp, _P(cm_window), _i32], ctypes.c_int),
+    "cm_batch_run": ([_vp, _vp], ctypes.c_int),
+    "cm_batch_set_schedule": ([_vp, _P(cm_batch_schedule)], ctypes.c_int),
+    "cm_batch_get_schedule": ([_vp, _P(cm_batch_schedule)], ctypes.c_int),
+    "cm_batch_autotune": ([_vp, _vp, _P(cm_batch_schedule)], ctypes.c_int),
+    "cm_batch_stats": ([_vp, _i32, _P(_vp), _P(_vp)], ctypes.c_int),
+    "cm_batch_destroy": ([_vp], ctypes.c_int),
     "cm_loss_grad_static": ([_P(cm_camera), _P(cm_events), _vp, _i32, _P(cm_loss_cfg), _vp, _vp, _vp, _vp],
                             ctypes.c_int),
     "cm_profile_enable": ([ctypes.c_int], ctypes.c_int),
@@ -155,6 +175,59 @@ def cm_loss_backward(cam, ev, flow, n_flow_bins, inv_depth, ego6, dt_window, cfg
     _check(lib().cm_loss_backward(ctypes.byref(cam), ctypes.byref(ev), flow, n_flow_bins, inv_depth, ego6,
                                   dt_window, ctypes.byref(cfg), ws, dloss, dflow, dinv_depth, dego6, stream),
            "cm_loss_backward")
+
+
+def _win_array(wins):
+    arr = (cm_window * len(wins))(*wins)
+    return arr
+
+
+def cm_batch_query(wins, cfg) -> int:
+    out = _sz(0)
+    _check(lib().cm_batch_query(_win_array(wins), len(wins), ctypes.byref(cfg), ctypes.byref(out)), "cm_batch_query")
+    return out.value
+
+
+def cm_batch_create(dev_mem: int, nbytes: int, wins, cfg) -> int:
+    h = _vp(0)
+    _check(lib().cm_batch_create(dev_mem, nbytes, _win_array(wins), len(wins), ctypes.byref(cfg), ctypes.byref(h)),
+           "cm_batch_create")
+    return h.value
+
+
+def cm_batch_set_windows(plan: int, wins) -> None:
+    _check(lib().cm_batch_set_windows(plan, _win_array(wins), len(wins)), "cm_batch_set_windows")
+
+
+def cm_batch_run(plan: int, stream: int) -> None:
+    _check(lib().cm_batch_run(plan, stream), "cm_batch_run")
+
+
+def cm_batch_set_schedule(plan: int, chains: int, group: int) -> None:
+    s = cm_batch_schedule(chains, group)
+    _check(lib().cm_batch_set_schedule(plan, ctypes.byref(s)), "cm_batch_set_schedule")
+
+
+def cm_batch_get_schedule(plan: int) -> tuple[int, int]:
+    s = cm_batch_schedule()
+    _check(lib().cm_batch_get_schedule(plan, ctypes.byref(s)), "cm_batch_get_schedule")
+    return s.chains, s.group
+
+
+def cm_batch_autotune(plan: int, stream: int) -> tuple[int, int]:
+    s = cm_batch_schedule()
+    _check(lib().cm_batch_autotune(plan, stream, ctypes.byref(s)), "cm_batch_autotune")
+    return s.chains, s.group
+
+
+def cm_batch_stats(plan: int, window: int) -> tuple[int, int]:
+    a, b = _vp(0), _vp(0)
+    _check(lib().cm_batch_stats(plan, window, ctypes.byref(a), ctypes.byref(b)), "cm_batch_stats")
+    return a.value, b.value
+
+
+def cm_batch_destroy(plan: int) -> None:
+    _check(lib().cm_batch_destroy(plan), "cm_batch_destroy")
 
 
 def cm_loss_grad_static(cam, ev, flow: int, n_flow_bins: int, cfg, dloss: int, loss_out: int, dflow_out: int,

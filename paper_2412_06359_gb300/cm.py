@@ -217,3 +217,92 @@ def cm_loss(ev: DeviceEvents, ws: Workspace, *, flow=None, inv_depth=None, ego=N
     if flow is not None:
         return CMLossFlow.apply(flow, ev, ws)
     return CMLossDepth.apply(inv_depth, ego, ev, ws, dt)
+
+
+class BatchPlan:
+    """A batch of windows evaluated by cm_batch_run (one persistent launch per
+    phase, replayed from a CUDA graph).  Each entry of `windows` is a dict with
+    cam, ev (DeviceEvents) and either flow or inv_depth + ego (+ dt).  Outputs
+    are allocated here: loss [nwin] and, per window, dflow (flow input) or
+    dinv_depth and dego (depth input)."""
+
+    def __init__(self, windows: list, cfg: C.cm_loss_cfg, device="cuda", dloss: torch.Tensor | None = None,
+                 want_dflow: bool = False):
+        self.cfg = cfg
+        self.device = device
+        self.loss = torch.empty(len(windows), dtype=torch.float32, device=device)
+        self.dloss = dloss if dloss is not None else torch.ones(len(windows), dtype=torch.float32, device=device)
+        self.want_dflow = want_dflow
+        self.keep = []
+        self.structs = self._structs(windows)
+        self.nbytes = C.cm_batch_query(self.structs, cfg)
+        self.buf = torch.empty(self.nbytes + 256, dtype=torch.uint8, device=device)
+        self.ptr = (self.buf.data_ptr() + 255) // 256 * 256
+        self.handle = C.cm_batch_create(self.ptr, self.nbytes, self.structs, cfg)
+
+    def _structs(self, windows):
+        out = []
+        self.outputs = []
+        self.keep = [windows]
+        for i, w in enumerate(windows):
+            cam = camera(w["cam"])
+            s = C.cm_window()
+            s.cam = cam
+            s.ev = w["ev"].c()
+            s.dloss = self.dloss.data_ptr() + 4 * i
+            s.loss_out = self.loss.data_ptr() + 4 * i
+            o = {}
+            if w.get("flow") is not None:
+                s.flow = _require_cuda(w["flow"], "flow", torch.float32)
+                o["dflow"] = torch.empty_like(w["flow"])
+                s.dflow = o["dflow"].data_ptr()
+            else:
+                s.inv_depth = _require_cuda(w["inv_depth"], "inv_depth", torch.float32)
+                s.ego6 = _require_cuda(w["ego"], "ego", torch.float32)
+                s.dt_window = float(w.get("dt", 0.01))
+                o["dinv_depth"] = torch.empty_like(w["inv_depth"])
+                o["dego"] = torch.empty(6, dtype=torch.float32, device=self.device)
+                s.dinv_depth = o["dinv_depth"].data_ptr()
+                s.dego6 = o["dego"].data_ptr()
+                if self.want_dflow:
+                    o["dflow"] = torch.empty((cam.height, cam.width, 2), dtype=torch.float32, device=self.device)
+                    s.dflow = o["dflow"].data_ptr()
+            self.outputs.append(o)
+            out.append(s)
+        return out
+
+    def set_windows(self, windows: list):
+        if len(windows) > self.loss.numel():
+            raise ValueError("more windows than the plan holds")
+        self.structs = self._structs(windows)
+        C.cm_batch_set_windows(self.handle, self.structs)
+
+    def run(self):
+        C.cm_batch_run(self.handle, stream_handle(self.buf.device))
+
+    def set_schedule(self, chains: int, group: int):
+        C.cm_batch_set_schedule(self.handle, chains, group)
+
+    def schedule(self) -> tuple[int, int]:
+        return C.cm_batch_get_schedule(self.handle)
+
+    def autotune(self) -> tuple[int, int]:
+        """Pick the fastest schedule for these windows (runs the plan several times)."""
+        return C.cm_batch_autotune(self.handle, stream_handle(self.buf.device))
+
+    def stats(self, i: int):
+        R = n_refs(self.cfg)
+        lr, nz = C.cm_batch_stats(self.handle, i)
+        base = self.buf.data_ptr()
+        loss_r = self.buf[lr - base:lr - base + 4 * R].view(torch.float32).cpu().numpy()
+        nnz_r = self.buf[nz - base:nz - base + 4 * R].view(torch.int32).cpu().numpy()
+        return loss_r, nnz_r
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            try:
+                C.cm_batch_destroy(h)
+            except Exception:
+                pass
+            self.handle = None

@@ -1,0 +1,815 @@
+// cm_batch.cu -- the batched path: the loss and gradient of many windows,
+// replayed from one CUDA graph.
+//
+// Work decomposition.  The events of window w form ceil(n_w / 256) chunks and
+// its pixel passes form per-window tiles; device prefix tables map a chunk or
+// tile to its window (binary search), so windows of very different sizes share
+// a launch with no padding.  Every kernel covers a range of windows.
+//
+// Schedule.  A window's images of warped events (R x H x W x 16 bytes, 54 MB at
+// 640x480 with 11 references) are written by the splat, read and rewritten by
+// the loss pass and gathered by the adjoint; when the windows in flight exceed
+// the 129 MB L2 those passes go to DRAM.  The schedule therefore groups
+// windows (group = windows per kernel) and runs the groups on a few concurrent
+// chains of the graph, each chain taking its groups one after another: a few
+// windows are in flight, their images stay in L2, and the chains overlap each
+// other's tails and launch gaps.  group 0 puts every window in each kernel on
+// one chain.  cm_batch_autotune times the candidates on the plan's own windows.
+//
+// The window table, the prefix tables and the totals live in device memory;
+// cm_batch_set_windows rewrites the staging copy and the next cm_batch_run
+// uploads it before the replay.  With group 0 the graph stays valid for any
+// windows that fit the plan; otherwise it is captured again for the new set.
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/cm.h"
+#include "cm_launch.h"
+
+namespace cmk {
+
+struct BatchHdr {
+    int32_t nwin;
+    int32_t pad;
+    long long total_chunks;  // event chunks of kEventThreads events
+    int32_t total_ltiles;    // loss tiles (R x loss_tiles per window)
+    int32_t total_ptiles;    // pixel tiles (pix_tiles per window)
+    long long iwe_f4;        // float4 elements of the IWE slab in use
+};
+
+// largest w in [lo, hi) with s[w] <= c (s non-decreasing; empty windows skipped)
+__device__ __forceinline__ int find_ll(const long long* s, int lo, int hi, long long c)
+{
+    hi -= 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(s + mid) <= c) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int find_i(const int* s, int lo, int hi, int c)
+{
+    hi -= 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(s + mid) <= c) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int clamp_end(const BatchHdr* h, int w1) { return w1 < h->nwin ? w1 : h->nwin; }
+
+// Each kernel covers windows [w0, w1) of the table (clamped to the windows in
+// use).  Pixel passes walk per-window tiles, event passes chunks of 256 events.
+
+// zero the images of warped events and the flow-gradient target, compute the
+// flow of depth-input windows, reset the completion counters
+__global__ void __launch_bounds__(256) k_prep_batch(const BatchHdr* h, const Win* tab, const int* pstart, int w0,
+                                                    int w1)
+{
+    w1 = clamp_end(h, w1);
+    if (w0 >= w1) return;
+    const int tb = pstart[w0], te = pstart[w1];
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int tile = tb + blockIdx.x; tile < te; tile += gridDim.x) {
+        const int w = find_i(pstart, w0, w1, tile);
+        const Win d = tab[w];
+        const int ti = tile - pstart[w];
+        if (ti == 0 && threadIdx.x < 2) d.sync[threadIdx.x] = 0;
+        const size_t HW = plane_size(d);
+        float2* flow = const_cast<float2*>(d.flow);
+        for (size_t i = (size_t)ti * blockDim.x + threadIdx.x; i < HW; i += (size_t)d.pix_tiles * blockDim.x) {
+            for (int r = 0; r < d.R; ++r) d.iwe[(size_t)r * HW + i] = z4;
+            d.dflow[i] = make_float2(0.f, 0.f);
+            if (d.rho) {
+                const int v = (int)(i / d.W), u = (int)(i - (size_t)v * d.W);
+                flow[i] = motion_field(u, v, __ldg(d.rho + i), d.ego, d.fx, d.fy, d.cx, d.cy, d.dt);
+            }
+        }
+    }
+}
+
+template <int MAXB>
+__global__ void __launch_bounds__(kEventThreads) k_splat_batch(const BatchHdr* h, const Win* tab,
+                                                                const long long* cstart, int w0, int w1)
+{
+    w1 = clamp_end(h, w1);
+    if (w0 >= w1) return;
+    const long long cb = cstart[w0], ce = cstart[w1];
+    for (long long c = cb + blockIdx.x; c < ce; c += gridDim.x) {
+        const int w = find_ll(cstart, w0, w1, c);
+        const Win d = tab[w];
+        const long long k = (c - cstart[w]) * kEventThreads + threadIdx.x;
+        if (k < d.n) splat_event<MAXB>(d, k);
+    }
+}
+
+template <int MAXB>
+__global__ void __launch_bounds__(kEventThreads) k_adjoint_batch(const BatchHdr* h, const Win* tab,
+                                                                  const long long* cstart, int w0, int w1)
+{
+    w1 = clamp_end(h, w1);
+    if (w0 >= w1) return;
+    const long long cb = cstart[w0], ce = cstart[w1];
+    for (long long c = cb + blockIdx.x; c < ce; c += gridDim.x) {
+        const int w = find_ll(cstart, w0, w1, c);
+        const Win d = tab[w];
+        const long long k = (c - cstart[w]) * kEventThreads + threadIdx.x;
+        if (k < d.n) adjoint_event<MAXB>(d, k, __ldg(d.dloss));
+    }
+}
+
+// loss pass 1 per tile; the block completing a window's last tile runs pass 2
+__global__ void __launch_bounds__(256) k_loss_batch(const BatchHdr* h, const Win* tab, const int* lstart, int w0,
+                                                    int w1)
+{
+    w1 = clamp_end(h, w1);
+    if (w0 >= w1) return;
+    const int tb = lstart[w0], te = lstart[w1];
+    for (int tile = tb + blockIdx.x; tile < te; tile += gridDim.x) {
+        const int w = find_i(lstart, w0, w1, tile);
+        const Win d = tab[w];
+        const int local = tile - lstart[w];
+        const int r = local / d.loss_tiles, ti = local - r * d.loss_tiles;
+        loss_tile(d, r, ti, d.loss_tiles, d.loss_part + (size_t)r * d.loss_tiles + ti);
+        if (last_tile_done(d.sync + 0, d.R * d.loss_tiles)) loss_final_window(d);
+    }
+}
+
+// depth / ego gradient per tile; the block completing a window's last tile
+// reduces the six ego sums
+__global__ void __launch_bounds__(256) k_grad_batch(const BatchHdr* h, const Win* tab, const int* pstart, int w0,
+                                                    int w1)
+{
+    w1 = clamp_end(h, w1);
+    if (w0 >= w1) return;
+    const int tb = pstart[w0], te = pstart[w1];
+    for (int tile = tb + blockIdx.x; tile < te; tile += gridDim.x) {
+        const int w = find_i(pstart, w0, w1, tile);
+        const Win d = tab[w];
+        if (!d.rho) continue;
+        depth_ego_tile(d, tile - pstart[w], d.pix_tiles);
+        if (last_tile_done(d.sync + 1, d.pix_tiles)) {
+            __syncthreads();
+            depth_ego_final_window(d);
+        }
+    }
+}
+
+
+}  // namespace cmk
+
+using cmk::BatchHdr;
+using cmk::Win;
+
+namespace {
+
+constexpr int kPhases = 5;
+const char* const kPhaseName[kPhases] = {"k_prep_batch", "k_splat_batch", "k_loss_batch", "k_adjoint_batch",
+                                         "k_grad_batch"};
+constexpr int kMaxChains = 8;
+
+size_t up256(size_t v) { return (v + 255) / 256 * 256; }
+
+int tiles_for(size_t hw, int cap)
+{
+    size_t t = (hw + 2047) / 2048;
+    if (t < 1) t = 1;
+    if (t > (size_t)cap) t = cap;
+    return (int)t;
+}
+
+int refs_of(const cm_loss_cfg& c) { return c.ref_mode == CM_REF_END ? 1 : c.nbins + 1; }
+
+// device bytes of the per-window slabs for a list of windows
+struct Need {
+    size_t iwe, flow, dflow, part, stat, dego;
+};
+
+bool window_ok(const cm_window& w)
+{
+    const cm_camera& c = w.cam;
+    if (c.width < 2 || c.height < 2 || c.width > 32767 || c.height > 32767) return false;
+    if (!(c.fx > 0.0f) || !(c.fy > 0.0f) || !std::isfinite(c.fx) || !std::isfinite(c.fy)) return false;
+    if (!std::isfinite(c.cx) || !std::isfinite(c.cy)) return false;
+    const cm_events& e = w.ev;
+    if (e.n < 0 || (e.n > 0 && (!e.x || !e.y || !e.t || !e.p))) return false;
+    if (!std::isfinite(e.t0) || !std::isfinite(e.t1) || !(e.t1 - e.t0 > 0.0f)) return false;
+    if (!w.dloss || !w.loss_out) return false;
+    if (!w.flow && (!w.inv_depth || !w.ego6 || !std::isfinite(w.dt_window))) return false;
+    if (w.flow && (w.dinv_depth || w.dego6)) return false;
+    return true;
+}
+
+bool cfg_ok(const cm_loss_cfg* cfg)
+{
+    if (!cfg || cfg->nbins < 1 || cfg->nbins > CM_MAX_BINS) return false;
+    if (cfg->ref_mode != CM_REF_END && cfg->ref_mode != CM_REF_ALL_EDGES) return false;
+    if (cfg->splat != CM_SPLAT_AUTO && cfg->splat != CM_SPLAT_ATOMIC) return false;
+    return cfg->store_warps == 0 && std::isfinite(cfg->eps);
+}
+
+Need need_of(const cm_window* wins, int32_t nwin, const cm_loss_cfg& cfg)
+{
+    Need n{};
+    const int R = refs_of(cfg);
+    for (int i = 0; i < nwin; ++i) {
+        const size_t HW = (size_t)wins[i].cam.width * wins[i].cam.height;
+        n.iwe += (size_t)R * HW * sizeof(float4);
+        if (!wins[i].flow) n.flow += HW * sizeof(float2);
+        if (!wins[i].dflow) n.dflow += HW * sizeof(float2);
+        n.part += (size_t)R * tiles_for(HW, 256) * sizeof(float2);
+        n.stat += (size_t)R;
+        n.dego += (size_t)tiles_for(HW, 512) * 6 * sizeof(float);
+    }
+    return n;
+}
+
+struct Layout {
+    size_t hdr, tab, cstart, lstart, pstart, table_end;  // the uploaded region [0, table_end)
+    size_t iwe, flow, dflow, part, norm, lr, nnz, dego, sync, total;
+};
+
+Layout layout_of(int cap, const Need& n)
+{
+    Layout L;
+    size_t o = 0;
+    L.hdr = o;
+    o = up256(o + sizeof(BatchHdr));
+    L.tab = o;
+    o += (size_t)cap * sizeof(Win);
+    L.cstart = o = (o + 15) / 16 * 16;
+    o += (size_t)(cap + 1) * sizeof(long long);
+    L.lstart = o;
+    o += (size_t)(cap + 1) * sizeof(int);
+    L.pstart = o;
+    o += (size_t)(cap + 1) * sizeof(int);
+    L.table_end = o = up256(o);
+    L.iwe = o;
+    o = up256(o + n.iwe);
+    L.flow = o;
+    o = up256(o + n.flow);
+    L.dflow = o;
+    o = up256(o + n.dflow);
+    L.part = o;
+    o = up256(o + n.part);
+    L.norm = o;
+    o = up256(o + n.stat * sizeof(float));
+    L.lr = o;
+    o = up256(o + n.stat * sizeof(float));
+    L.nnz = o;
+    o = up256(o + n.stat * sizeof(int32_t));
+    L.dego = o;
+    o = up256(o + n.dego);
+    L.sync = o;
+    o = up256(o + (size_t)cap * 2 * sizeof(int32_t));
+    L.total = o;
+    return L;
+}
+
+// one kernel node of the graph and the event-record nodes around it
+struct ProfNode {
+    int phase;
+    cudaEvent_t ea, eb;           // the plan's own events (recorded when timing is off)
+    cudaGraphNode_t na, nb;
+};
+
+struct Group {
+    int w0, w1, chain;
+    long long chunks;
+    int ltiles, ptiles;
+};
+
+}  // namespace
+
+struct cm_batch {
+    char* base = nullptr;
+    size_t bytes = 0;
+    cm_loss_cfg cfg{};
+    int cap = 0;
+    Need capn{};
+    Layout L{};
+    unsigned char* staging = nullptr;  // pinned host copy of [0, table_end)
+    bool dirty = false;
+    cudaEvent_t staged = nullptr;      // recorded after the last upload of the staging copy
+    int nwin = 0;
+    std::vector<long long> chunks;     // per window, host copy
+    std::vector<int> ltiles, ptiles;   // per window, host copy
+    int grid_events = 0, grid_tiles = 0;
+    cm_batch_schedule sched{2, 1};
+    bool stale = true;                 // the graph must be (re)captured before the next replay
+    cudaStream_t streams[kMaxChains] = {};
+    cudaEvent_t fork = nullptr;
+    cudaEvent_t join[kMaxChains] = {};
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<ProfNode> prof;
+    bool swapped = false;
+};
+
+namespace {
+
+// fill the staging copy of the table for these windows; checks the capacities
+int stage_windows(cm_batch* b, const cm_window* wins, int32_t nwin)
+{
+    if (nwin < 1 || nwin > b->cap) return CM_EINVAL;
+    for (int i = 0; i < nwin; ++i)
+        if (!window_ok(wins[i])) return CM_EINVAL;
+    const Need n = need_of(wins, nwin, b->cfg);
+    const Need& c = b->capn;
+    if (n.iwe > c.iwe || n.flow > c.flow || n.dflow > c.dflow || n.part > c.part || n.stat > c.stat ||
+        n.dego > c.dego)
+        return CM_ENOMEM;
+    // the previous upload must have left the staging buffer before it is rewritten
+    if (cudaEventSynchronize(b->staged) != cudaSuccess) return CM_ECUDA;
+    unsigned char* s = b->staging;
+    std::memset(s, 0, b->L.table_end);
+    BatchHdr* h = reinterpret_cast<BatchHdr*>(s + b->L.hdr);
+    Win* tab = reinterpret_cast<Win*>(s + b->L.tab);
+    long long* cs = reinterpret_cast<long long*>(s + b->L.cstart);
+    int* ls = reinterpret_cast<int*>(s + b->L.lstart);
+    int* ps = reinterpret_cast<int*>(s + b->L.pstart);
+    const int R = refs_of(b->cfg);
+    const float eps = b->cfg.eps > 0.0f ? b->cfg.eps : 1e-9f;
+    size_t o_iwe = 0, o_flow = 0, o_dflow = 0, o_part = 0, o_stat = 0, o_dego = 0;
+    long long chunks = 0;
+    int lt_total = 0, pt_total = 0;
+    char* base = b->base;
+    b->chunks.assign(nwin, 0);
+    b->ltiles.assign(nwin, 0);
+    b->ptiles.assign(nwin, 0);
+    for (int i = 0; i < nwin; ++i) {
+        const cm_window& w = wins[i];
+        const size_t HW = (size_t)w.cam.width * w.cam.height;
+        Win& d = tab[i];
+        d.x = w.ev.x;
+        d.y = w.ev.y;
+        d.t = w.ev.t;
+        d.p = w.ev.p;
+        d.n = w.ev.n;
+        d.W = w.cam.width;
+        d.H = w.cam.height;
+        d.B = b->cfg.nbins;
+        d.R = R;
+        d.ref_mode = b->cfg.ref_mode;
+        d.nfb = 1;
+        d.t0 = w.ev.t0;
+        d.span = w.ev.t1 - w.ev.t0;
+        d.eps = eps;
+        d.dt = w.dt_window;
+        d.fx = w.cam.fx;
+        d.fy = w.cam.fy;
+        d.cx = w.cam.cx;
+        d.cy = w.cam.cy;
+        d.iwe = reinterpret_cast<float4*>(base + b->L.iwe + o_iwe);
+        o_iwe += (size_t)R * HW * sizeof(float4);
+        if (w.flow) {
+            d.flow = reinterpret_cast<const float2*>(w.flow);
+        } else {
+            d.flow = reinterpret_cast<const float2*>(base + b->L.flow + o_flow);
+            o_flow += HW * sizeof(float2);
+            d.rho = w.inv_depth;
+            d.ego = w.ego6;
+            d.drho = w.dinv_depth;
+            d.dego = w.dego6;
+        }
+        if (w.dflow) {
+            d.dflow = reinterpret_cast<float2*>(w.dflow);
+        } else {
+            d.dflow = reinterpret_cast<float2*>(base + b->L.dflow + o_dflow);
+            o_dflow += HW * sizeof(float2);
+        }
+        d.loss_tiles = tiles_for(HW, 256);
+        d.pix_tiles = tiles_for(HW, 512);
+        d.loss_part = reinterpret_cast<float2*>(base + b->L.part + o_part);
+        o_part += (size_t)R * d.loss_tiles * sizeof(float2);
+        d.norm = reinterpret_cast<float*>(base + b->L.norm) + o_stat;
+        d.loss_r = reinterpret_cast<float*>(base + b->L.lr) + o_stat;
+        d.nnz_r = reinterpret_cast<int32_t*>(base + b->L.nnz) + o_stat;
+        o_stat += R;
+        d.dego_part = reinterpret_cast<float*>(base + b->L.dego + o_dego);
+        o_dego += (size_t)d.pix_tiles * 6 * sizeof(float);
+        d.sync = reinterpret_cast<int32_t*>(base + b->L.sync) + 2 * i;
+        d.loss = w.loss_out;
+        d.dloss = w.dloss;
+        cs[i] = chunks;
+        ls[i] = lt_total;
+        ps[i] = pt_total;
+        b->chunks[i] = (w.ev.n + cmk::kEventThreads - 1) / cmk::kEventThreads;
+        b->ltiles[i] = R * d.loss_tiles;
+        b->ptiles[i] = d.pix_tiles;
+        chunks += b->chunks[i];
+        lt_total += b->ltiles[i];
+        pt_total += b->ptiles[i];
+    }
+    cs[nwin] = chunks;
+    ls[nwin] = lt_total;
+    ps[nwin] = pt_total;
+    h->nwin = nwin;
+    h->total_chunks = chunks;
+    h->total_ltiles = lt_total;
+    h->total_ptiles = pt_total;
+    h->iwe_f4 = (long long)(o_iwe / sizeof(float4));
+    b->nwin = nwin;
+    b->dirty = true;
+    if (b->sched.group > 0) b->stale = true;  // the graph's window groups depend on the windows
+    return CM_OK;
+}
+
+// Window groups and their chains.  group <= 0: one group over every slot of the
+// table on one chain (the kernels clamp to the windows in use, so the graph
+// stays valid when the windows change).  Otherwise consecutive groups of
+// `group` windows, each assigned to the chain with the least work so far.
+std::vector<Group> make_groups(const cm_batch* b)
+{
+    std::vector<Group> g;
+    if (b->sched.group <= 0) {
+        long long c = 0;
+        int lt = 0, pt = 0;
+        for (int i = 0; i < b->nwin; ++i) {
+            c += b->chunks[i];
+            lt += b->ltiles[i];
+            pt += b->ptiles[i];
+        }
+        g.push_back({0, b->cap, 0, c, lt, pt});
+        return g;
+    }
+    const int chains = b->sched.chains < 1 ? 1 : (b->sched.chains > kMaxChains ? kMaxChains : b->sched.chains);
+    std::vector<double> load(chains, 0.0);
+    for (int w = 0; w < b->nwin; w += b->sched.group) {
+        Group x{w, w + b->sched.group < b->nwin ? w + b->sched.group : b->nwin, 0, 0, 0, 0};
+        double work = 0.0;
+        for (int i = x.w0; i < x.w1; ++i) {
+            x.chunks += b->chunks[i];
+            x.ltiles += b->ltiles[i];
+            x.ptiles += b->ptiles[i];
+            work += (double)b->chunks[i] + 0.5 * b->ltiles[i];
+        }
+        int best = 0;
+        for (int c = 1; c < chains; ++c)
+            if (load[c] < load[best]) best = c;
+        x.chain = best;
+        load[best] += work;
+        g.push_back(x);
+    }
+    return g;
+}
+
+template <int MAXB>
+void enqueue_event_kernel(cm_batch* b, cudaStream_t s, int which, int grid, int w0, int w1)
+{
+    const BatchHdr* h = reinterpret_cast<const BatchHdr*>(b->base + b->L.hdr);
+    const Win* tab = reinterpret_cast<const Win*>(b->base + b->L.tab);
+    const long long* cs = reinterpret_cast<const long long*>(b->base + b->L.cstart);
+    if (which == 0) cmk::k_splat_batch<MAXB><<<grid, cmk::kEventThreads, 0, s>>>(h, tab, cs, w0, w1);
+    else cmk::k_adjoint_batch<MAXB><<<grid, cmk::kEventThreads, 0, s>>>(h, tab, cs, w0, w1);
+}
+
+void enqueue_event(cm_batch* b, cudaStream_t s, int which, int grid, int w0, int w1)
+{
+    const int B = b->cfg.nbins;
+    if (B <= 1) enqueue_event_kernel<1>(b, s, which, grid, w0, w1);
+    else if (B <= 10) enqueue_event_kernel<10>(b, s, which, grid, w0, w1);
+    else if (B <= 20) enqueue_event_kernel<20>(b, s, which, grid, w0, w1);
+    else enqueue_event_kernel<32>(b, s, which, grid, w0, w1);
+}
+
+void release_graph(cm_batch* b)
+{
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    for (ProfNode& p : b->prof) {
+        cudaEventDestroy(p.ea);
+        cudaEventDestroy(p.eb);
+    }
+    b->prof.clear();
+    b->swapped = false;
+}
+
+int clampi(long long v, int lo, int hi) { return (int)(v < lo ? lo : (v > hi ? hi : v)); }
+
+// Capture the five phases of every group on its chain's stream, each kernel
+// bracketed by event-record nodes (used for per-kernel timing).
+int capture(cm_batch* b)
+{
+    release_graph(b);
+    const std::vector<Group> groups = make_groups(b);
+    int chains = 1;
+    for (const Group& g : groups) chains = g.chain + 1 > chains ? g.chain + 1 : chains;
+    for (int c = 0; c < chains; ++c)
+        if (!b->streams[c] && cudaStreamCreateWithFlags(&b->streams[c], cudaStreamNonBlocking) != cudaSuccess)
+            return CM_ECUDA;
+    if (!b->fork && cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) return CM_ECUDA;
+    for (int c = 0; c < chains; ++c)
+        if (!b->join[c] && cudaEventCreateWithFlags(&b->join[c], cudaEventDisableTiming) != cudaSuccess)
+            return CM_ECUDA;
+    const BatchHdr* h = reinterpret_cast<const BatchHdr*>(b->base + b->L.hdr);
+    const Win* tab = reinterpret_cast<const Win*>(b->base + b->L.tab);
+    const int* ls = reinterpret_cast<const int*>(b->base + b->L.lstart);
+    const int* ps = reinterpret_cast<const int*>(b->base + b->L.pstart);
+    cudaStream_t s0 = b->streams[0];
+    if (cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return CM_ECUDA;
+    bool ok = true;
+    if (chains > 1) {
+        ok = ok && cudaEventRecord(b->fork, s0) == cudaSuccess;
+        for (int c = 1; c < chains; ++c) ok = ok && cudaStreamWaitEvent(b->streams[c], b->fork, 0) == cudaSuccess;
+    }
+    const bool wide = b->sched.group <= 0;
+    for (const Group& g : groups) {
+        cudaStream_t s = b->streams[g.chain];
+        for (int ph = 0; ph < kPhases && ok; ++ph) {
+            ProfNode p{ph, nullptr, nullptr, nullptr, nullptr};
+            ok = cudaEventCreate(&p.ea) == cudaSuccess && cudaEventCreate(&p.eb) == cudaSuccess;
+            if (!ok) break;
+            b->prof.push_back(p);
+            cudaEventRecordWithFlags(p.ea, s, cudaEventRecordExternal);
+            const int gt = wide ? b->grid_tiles : clampi(g.ptiles, 1, b->grid_tiles);
+            const int gl = wide ? b->grid_tiles : clampi(g.ltiles, 1, b->grid_tiles);
+            const int ge = wide ? b->grid_events : clampi(g.chunks, 1, b->grid_events);
+            switch (ph) {
+            case 0: cmk::k_prep_batch<<<gt, 256, 0, s>>>(h, tab, ps, g.w0, g.w1); break;
+            case 1: enqueue_event(b, s, 0, ge, g.w0, g.w1); break;
+            case 2: cmk::k_loss_batch<<<gl, 256, 0, s>>>(h, tab, ls, g.w0, g.w1); break;
+            case 3: enqueue_event(b, s, 1, ge, g.w0, g.w1); break;
+            case 4: cmk::k_grad_batch<<<gt, 256, 0, s>>>(h, tab, ps, g.w0, g.w1); break;
+            }
+            cudaEventRecordWithFlags(p.eb, s, cudaEventRecordExternal);
+        }
+    }
+    for (int c = 1; c < chains && ok; ++c) {
+        ok = cudaEventRecord(b->join[c], b->streams[c]) == cudaSuccess;
+        ok = ok && cudaStreamWaitEvent(s0, b->join[c], 0) == cudaSuccess;
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(s0, &g);
+    if (!ok || e != cudaSuccess || !g) {
+        cudaGetLastError();
+        if (g) cudaGraphDestroy(g);
+        return CM_ECUDA;
+    }
+    b->graph = g;
+    if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) return CM_ECUDA;
+    size_t nn = 0;
+    cudaGraphGetNodes(g, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    cudaGraphGetNodes(g, nodes.data(), &nn);
+    for (cudaGraphNode_t n : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(n, &t) != cudaSuccess || t != cudaGraphNodeTypeEventRecord) continue;
+        cudaEvent_t ev = nullptr;
+        cudaGraphEventRecordNodeGetEvent(n, &ev);
+        for (ProfNode& p : b->prof) {
+            if (ev == p.ea) p.na = n;
+            if (ev == p.eb) p.nb = n;
+        }
+    }
+    for (const ProfNode& p : b->prof)
+        if (!p.na || !p.nb) return CM_ECUDA;
+    b->stale = false;
+    return CM_OK;
+}
+
+void destroy_batch(cm_batch* b)
+{
+    if (!b) return;
+    release_graph(b);
+    for (int c = 0; c < kMaxChains; ++c) {
+        if (b->streams[c]) cudaStreamDestroy(b->streams[c]);
+        if (b->join[c]) cudaEventDestroy(b->join[c]);
+    }
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->staged) {
+        cudaEventSynchronize(b->staged);
+        cudaEventDestroy(b->staged);
+    }
+    if (b->staging) cudaFreeHost(b->staging);
+    delete b;
+}
+
+template <int MAXB>
+int occupancy_blocks()
+{
+    int a = 0, c = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, cmk::k_splat_batch<MAXB>, cmk::kEventThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, cmk::k_adjoint_batch<MAXB>, cmk::kEventThreads, 0);
+    const int m = a < c ? a : c;
+    return m < 1 ? 1 : m;
+}
+
+int run_plan(cm_batch* b, cudaStream_t s)
+{
+    if (b->dirty) {
+        if (cudaMemcpyAsync(b->base, b->staging, b->L.table_end, cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return CM_ECUDA;
+        if (cudaEventRecord(b->staged, s) != cudaSuccess) return CM_ECUDA;
+        b->dirty = false;
+    }
+    if (b->stale || !b->exec) {
+        const int st = capture(b);
+        if (st) return st;
+    }
+    // per-kernel timing: point the event-record nodes at fresh events from the
+    // profiler's pool for this replay; otherwise back at the plan's own events
+    const bool prof = cmk::profiling_on();
+    std::vector<cudaEvent_t> ev;
+    if (prof) {
+        ev.resize(2 * b->prof.size());
+        for (size_t i = 0; i < b->prof.size(); ++i) {
+            ev[2 * i] = cmk::profile_take_event();
+            ev[2 * i + 1] = cmk::profile_take_event();
+            if (!ev[2 * i] || !ev[2 * i + 1] ||
+                cudaGraphExecEventRecordNodeSetEvent(b->exec, b->prof[i].na, ev[2 * i]) != cudaSuccess ||
+                cudaGraphExecEventRecordNodeSetEvent(b->exec, b->prof[i].nb, ev[2 * i + 1]) != cudaSuccess)
+                return CM_ECUDA;
+        }
+        b->swapped = true;
+    } else if (b->swapped) {
+        for (const ProfNode& p : b->prof)
+            if (cudaGraphExecEventRecordNodeSetEvent(b->exec, p.na, p.ea) != cudaSuccess ||
+                cudaGraphExecEventRecordNodeSetEvent(b->exec, p.nb, p.eb) != cudaSuccess)
+                return CM_ECUDA;
+        b->swapped = false;
+    }
+    if (cudaGraphLaunch(b->exec, s) != cudaSuccess) return CM_ECUDA;
+    cmk::count_launches((long long)b->prof.size());
+    if (prof)
+        for (size_t i = 0; i < b->prof.size(); ++i)
+            cmk::profile_push(kPhaseName[b->prof[i].phase], ev[2 * i], ev[2 * i + 1]);
+    return CM_OK;
+}
+
+// autotuner cache: (window count, first window's size, references, events
+// bucket) -> schedule, for the life of the process
+struct TuneKey {
+    int nwin, W, H, R, ebucket;
+};
+std::vector<std::pair<TuneKey, cm_batch_schedule>> g_tuned;
+
+TuneKey key_of(const cm_batch* b)
+{
+    long long c = 0;
+    for (long long v : b->chunks) c += v;
+    int e = 0;
+    while ((1LL << e) < c + 1) ++e;
+    const Win* tab = reinterpret_cast<const Win*>(b->staging + b->L.tab);
+    return {b->nwin, tab[0].W, tab[0].H, refs_of(b->cfg), e};
+}
+
+}  // namespace
+
+extern "C" {
+
+int cm_batch_query(const cm_window* wins, int32_t nwin, const cm_loss_cfg* cfg, size_t* bytes)
+{
+    if (!wins || nwin < 1 || !bytes || !cfg_ok(cfg)) return CM_EINVAL;
+    for (int i = 0; i < nwin; ++i)
+        if (!window_ok(wins[i])) return CM_EINVAL;
+    *bytes = layout_of(nwin, need_of(wins, nwin, *cfg)).total;
+    return CM_OK;
+}
+
+int cm_batch_create(void* dev_mem, size_t bytes, const cm_window* wins, int32_t nwin, const cm_loss_cfg* cfg,
+                    cm_batch** out)
+{
+    if (!dev_mem || !wins || nwin < 1 || !out || !cfg_ok(cfg)) return CM_EINVAL;
+    if (reinterpret_cast<uintptr_t>(dev_mem) % 256) return CM_EINVAL;
+    for (int i = 0; i < nwin; ++i)
+        if (!window_ok(wins[i])) return CM_EINVAL;
+    const Need n = need_of(wins, nwin, *cfg);
+    const Layout L = layout_of(nwin, n);
+    if (bytes < L.total) return CM_ENOMEM;
+    cm_batch* b = new (std::nothrow) cm_batch;
+    if (!b) return CM_ENOMEM;
+    b->base = static_cast<char*>(dev_mem);
+    b->bytes = bytes;
+    b->cfg = *cfg;
+    b->cap = nwin;
+    b->capn = n;
+    b->L = L;
+    b->sched = nwin > 1 ? cm_batch_schedule{2, 1} : cm_batch_schedule{1, 0};
+    int st = CM_OK;
+    if (cudaMallocHost(reinterpret_cast<void**>(&b->staging), L.table_end) != cudaSuccess) st = CM_ENOMEM;
+    if (!st && cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming) != cudaSuccess) st = CM_ECUDA;
+    if (!st) {
+        const int sms = cmk::sm_count_current();
+        int occ = 1;
+        const int B = cfg->nbins;
+        if (B <= 1) occ = occupancy_blocks<1>();
+        else if (B <= 10) occ = occupancy_blocks<10>();
+        else if (B <= 20) occ = occupancy_blocks<20>();
+        else occ = occupancy_blocks<32>();
+        b->grid_events = sms * occ;
+        b->grid_tiles = sms * 4;
+        st = stage_windows(b, wins, nwin);
+    }
+    // the completion counters start at zero (the prep kernel also resets them)
+    if (!st && cudaMemset(b->base + L.sync, 0, (size_t)nwin * 2 * sizeof(int32_t)) != cudaSuccess) st = CM_ECUDA;
+    if (st) {
+        destroy_batch(b);
+        return st;
+    }
+    *out = b;
+    return CM_OK;
+}
+
+int cm_batch_set_windows(cm_batch* b, const cm_window* wins, int32_t nwin)
+{
+    if (!b || !wins) return CM_EINVAL;
+    return stage_windows(b, wins, nwin);
+}
+
+int cm_batch_set_schedule(cm_batch* b, const cm_batch_schedule* s)
+{
+    if (!b || !s || s->chains < 1 || s->chains > kMaxChains || s->group < 0) return CM_EINVAL;
+    if (s->group == 0 && s->chains != 1) return CM_EINVAL;
+    b->sched = *s;
+    b->stale = true;
+    return CM_OK;
+}
+
+int cm_batch_get_schedule(const cm_batch* b, cm_batch_schedule* s)
+{
+    if (!b || !s) return CM_EINVAL;
+    *s = b->sched;
+    return CM_OK;
+}
+
+int cm_batch_run(cm_batch* b, void* stream)
+{
+    if (!b) return CM_EINVAL;
+    return run_plan(b, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int cm_batch_autotune(cm_batch* b, void* stream, cm_batch_schedule* chosen)
+{
+    if (!b) return CM_EINVAL;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const TuneKey k = key_of(b);
+    for (const auto& e : g_tuned) {
+        const TuneKey& q = e.first;
+        if (q.nwin == k.nwin && q.W == k.W && q.H == k.H && q.R == k.R && q.ebucket == k.ebucket) {
+            b->sched = e.second;
+            b->stale = true;
+            if (chosen) *chosen = b->sched;
+            return CM_OK;
+        }
+    }
+    std::vector<cm_batch_schedule> cand = {{1, 0}, {1, 1}, {2, 1}, {3, 1}, {4, 1}, {2, 2}, {4, 2}};
+    if (b->nwin == 1) cand = {{1, 0}};
+    cudaEvent_t a = nullptr, z = nullptr;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&z) != cudaSuccess) return CM_ECUDA;
+    float best = 1e30f;
+    cm_batch_schedule pick = b->sched;
+    int st = CM_OK;
+    for (const cm_batch_schedule& c : cand) {
+        b->sched = c;
+        b->stale = true;
+        if ((st = run_plan(b, s))) break;  // capture + warm-up
+        cudaEventRecord(a, s);
+        for (int r = 0; r < 3 && !st; ++r) st = run_plan(b, s);
+        cudaEventRecord(z, s);
+        if (st || cudaEventSynchronize(z) != cudaSuccess) {
+            st = st ? st : CM_ECUDA;
+            break;
+        }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, a, z);
+        if (ms < best) {
+            best = ms;
+            pick = c;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(z);
+    if (st) return st;
+    b->sched = pick;
+    b->stale = true;
+    g_tuned.push_back({k, pick});
+    if (chosen) *chosen = pick;
+    return CM_OK;
+}
+
+int cm_batch_stats(const cm_batch* b, int32_t window, const float** loss_r, const int32_t** nnz_r)
+{
+    if (!b || window < 0 || window >= b->nwin) return CM_EINVAL;
+    const int R = refs_of(b->cfg);
+    if (loss_r) *loss_r = reinterpret_cast<const float*>(b->base + b->L.lr) + (size_t)window * R;
+    if (nnz_r) *nnz_r = reinterpret_cast<const int32_t*>(b->base + b->L.nnz) + (size_t)window * R;
+    return CM_OK;
+}
+
+int cm_batch_destroy(cm_batch* b)
+{
+    destroy_batch(b);
+    return CM_OK;
+}
+
+}  // extern "C"

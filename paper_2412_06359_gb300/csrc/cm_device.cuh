@@ -58,6 +58,7 @@ struct Win {
     float* drho;             // [H][W]
     float* dego;             // [6]
     float* dego_part;        // [pix_tiles][6]
+    int32_t* sync;           // [2] tile-completion counters of the loss and gradient reductions (batched path)
 };
 
 __device__ __forceinline__ size_t plane_size(const Win& d) { return (size_t)d.W * (size_t)d.H; }
@@ -234,10 +235,12 @@ __device__ __forceinline__ bool trajectory(const Win& d, const EventAt& e, Traj<
     return ok;
 }
 
-// 8-byte vector reduction (no return value) into global memory.
+// 8-byte vector reduction (no return value) into global memory.  No memory
+// clobber: a kernel never reads the buffer it reduces into, so the reductions
+// need no ordering against its other loads.
 __device__ __forceinline__ void red_add_v2(float* addr, float a, float b)
 {
-    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(addr), "f"(a), "f"(b) : "memory");
+    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(addr), "f"(a), "f"(b));
 }
 
 // S4: bilinear splat of one point (weight w to C_p, w * tbar to S_p) into one
@@ -382,6 +385,194 @@ __device__ __forceinline__ T warp_sum(T v)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
+}
+
+// True in exactly one block: the last of `total` tile completions counted on
+// `counter`.  Every thread fences its own writes before the block's arrival is
+// counted, and the last block fences again before reading the others' writes;
+// it then resets the counter for the next use.  The caller's reduction over
+// the tiles runs in a fixed order, so the result does not depend on which
+// block arrives last.
+__device__ __forceinline__ bool last_tile_done(int32_t* counter, int total)
+{
+    __shared__ int is_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int prev = atomicAdd(counter, 1);
+        is_last = prev == total - 1;
+        if (is_last) atomicExch(counter, 0);
+    }
+    __syncthreads();
+    if (is_last) __threadfence();
+    return is_last != 0;
+}
+
+// ---------------------------------------------------------------------------
+// Per-pixel passes, written once for the single-window and the batched
+// kernels.  A pass over one image is split into `ntiles` tiles; tile `tile`
+// covers pixels tile*blockDim + threadIdx.x, stepping by ntiles*blockDim.
+
+// S1: rigid motion field (Sec. 3.2, Eq. 2 in its instantaneous form), FP32
+// with the operation order of the trajectory contract:
+//   xn = (u - cx) * (1/fx),  yn = (v - cy) * (1/fy),  xy = xn*yn
+//   xd = rho * fma(xn, vz, -vx); xd = fma(xy, wx, xd); xd = fma(-fma(xn, xn, 1), wy, xd); xd = fma(yn, wz, xd)
+//   yd = rho * fma(yn, vz, -vy); yd = fma(fma(yn, yn, 1), wx, yd); yd = fma(-xy, wy, yd); yd = fma(-xn, wz, yd)
+//   flow = ((dt*fx) * xd, (dt*fy) * yd)
+__device__ __forceinline__ float2 motion_field(int u, int v, float rho, const float* __restrict__ ego, float fx,
+                                               float fy, float cx, float cy, float dt)
+{
+    const float vx = __ldg(ego + 0), vy = __ldg(ego + 1), vz = __ldg(ego + 2);
+    const float wx = __ldg(ego + 3), wy = __ldg(ego + 4), wz = __ldg(ego + 5);
+    const float ifx = __fdiv_rn(1.0f, fx), ify = __fdiv_rn(1.0f, fy);
+    const float sx = __fmul_rn(dt, fx), sy = __fmul_rn(dt, fy);
+    const float xn = __fmul_rn(__fsub_rn((float)u, cx), ifx);
+    const float yn = __fmul_rn(__fsub_rn((float)v, cy), ify);
+    const float xy = __fmul_rn(xn, yn);
+    float xd = __fmul_rn(rho, __fmaf_rn(xn, vz, -vx));
+    xd = __fmaf_rn(xy, wx, xd);
+    xd = __fmaf_rn(-__fmaf_rn(xn, xn, 1.0f), wy, xd);
+    xd = __fmaf_rn(yn, wz, xd);
+    float yd = __fmul_rn(rho, __fmaf_rn(yn, vz, -vy));
+    yd = __fmaf_rn(__fmaf_rn(yn, yn, 1.0f), wx, yd);
+    yd = __fmaf_rn(-xy, wy, yd);
+    yd = __fmaf_rn(-xn, wz, yd);
+    return make_float2(__fmul_rn(sx, xd), __fmul_rn(sy, yd));
+}
+
+__device__ __forceinline__ void flow_tile(const Win& d, int tile, int ntiles)
+{
+    const int W = d.W;
+    const size_t HW = plane_size(d);
+    float2* flow = const_cast<float2*>(d.flow);
+    for (size_t i = (size_t)tile * blockDim.x + threadIdx.x; i < HW; i += (size_t)ntiles * blockDim.x) {
+        const int v = (int)(i / W), u = (int)(i - (size_t)v * W);
+        flow[i] = motion_field(u, v, __ldg(d.rho + i), d.ego, d.fx, d.fy, d.cx, d.cy, d.dt);
+    }
+}
+
+// S5 pass 1 over one tile of plane r: T = S/(C+eps) for both polarities, the
+// sum of T^2 and the non-empty count go to out[0]; the plane is rewritten in
+// place as (A+, T+, A-, T-) with A = 2T/(C+eps), all that the adjoint needs.
+// Ends with __syncthreads (the caller may loop).
+__device__ __forceinline__ void loss_tile(const Win& d, int r, int tile, int ntiles, float2* out)
+{
+    const size_t HW = plane_size(d);
+    float4* plane = d.iwe + (size_t)r * HW;
+    const float eps = d.eps;
+    float s = 0.0f;
+    int cnt = 0;
+    for (size_t i = (size_t)tile * blockDim.x + threadIdx.x; i < HW; i += (size_t)ntiles * blockDim.x) {
+        const float4 q = plane[i];
+        const float cp = q.x + eps, cm = q.z + eps;
+        const float tp = q.y / cp, tm = q.w / cm;
+        s = fmaf(tp, tp, s);
+        s = fmaf(tm, tm, s);
+        cnt += (q.x > 0.0f || q.z > 0.0f) ? 1 : 0;
+        plane[i] = make_float4(2.0f * tp / cp, tp, 2.0f * tm / cm, tm);
+    }
+    __shared__ float ss[32];
+    __shared__ int sc[32];
+    s = warp_sum(s);
+    cnt = warp_sum(cnt);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) {
+        ss[w] = s;
+        sc[w] = cnt;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float a = 0.0f;
+        int c = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+            a += ss[i];
+            c += sc[i];
+        }
+        *out = make_float2(a, (float)c);
+    }
+    __syncthreads();
+}
+
+// S5 pass 2 for one window (one block): fixed-order reduction of the tiles,
+// L_r, N_nz(r), 1/(R(N_nz + eps)) and the loss.
+__device__ __forceinline__ void loss_final_window(const Win& d)
+{
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    __shared__ double lr[64];
+    for (int r = w; r < d.R; r += nw) {
+        double s = 0.0, c = 0.0;
+        for (int i = l; i < d.loss_tiles; i += 32) {
+            const float2 q = d.loss_part[(size_t)r * d.loss_tiles + i];
+            s += (double)q.x;
+            c += (double)q.y;
+        }
+        s = warp_sum(s);
+        c = warp_sum(c);
+        if (l == 0) {
+            const double L = s / (c + (double)d.eps);
+            lr[r] = L;
+            d.loss_r[r] = (float)L;
+            d.nnz_r[r] = (int32_t)c;
+            d.norm[r] = (float)(1.0 / ((double)d.R * (c + (double)d.eps)));
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double L = 0.0;
+        for (int r = 0; r < d.R; ++r) L += lr[r];
+        d.loss[0] = (float)(L / d.R);
+    }
+}
+
+// S7 over one tile: dL/d(rho) per pixel and the tile's six dL/d(ego) sums
+// (to d.dego_part[tile][6]).  Ends with __syncthreads.
+__device__ __forceinline__ void depth_ego_tile(const Win& d, int tile, int ntiles)
+{
+    const int W = d.W;
+    const size_t HW = plane_size(d);
+    const float vx = __ldg(d.ego + 0), vy = __ldg(d.ego + 1), vz = __ldg(d.ego + 2);
+    const float ifx = 1.0f / d.fx, ify = 1.0f / d.fy;
+    const float sx = d.dt * d.fx, sy = d.dt * d.fy;
+    float g[6] = {0, 0, 0, 0, 0, 0};
+    for (size_t i = (size_t)tile * blockDim.x + threadIdx.x; i < HW; i += (size_t)ntiles * blockDim.x) {
+        const int v = (int)(i / W), u = (int)(i - (size_t)v * W);
+        const float xn = ((float)u - d.cx) * ifx, yn = ((float)v - d.cy) * ify;
+        const float r = __ldg(d.rho + i);
+        const float2 df = d.dflow[i];
+        const float Gx = sx * df.x, Gy = sy * df.y;
+        if (d.drho) d.drho[i] = Gx * (xn * vz - vx) + Gy * (yn * vz - vy);
+        g[0] -= r * Gx;
+        g[1] -= r * Gy;
+        g[2] += r * (xn * Gx + yn * Gy);
+        g[3] += xn * yn * Gx + (1.0f + yn * yn) * Gy;
+        g[4] -= (1.0f + xn * xn) * Gx + xn * yn * Gy;
+        g[5] += yn * Gx - xn * Gy;
+    }
+    __shared__ float sg[32][6];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        const float v = warp_sum(g[c]);
+        if (l == 0) sg[w][c] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        float a = 0.0f;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) a += sg[i][threadIdx.x];
+        d.dego_part[(size_t)tile * 6 + threadIdx.x] = a;
+    }
+    __syncthreads();
+}
+
+// S7 final for one window: warps 0..5 reduce the tiles of one component each.
+__device__ __forceinline__ void depth_ego_final_window(const Win& d)
+{
+    const int c = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (c >= 6) return;
+    double s = 0.0;
+    for (int i = l; i < d.pix_tiles; i += 32) s += (double)d.dego_part[(size_t)i * 6 + c];
+    s = warp_sum(s);
+    if (l == 0 && d.dego) d.dego[c] = (float)s;
 }
 
 }  // namespace cmk

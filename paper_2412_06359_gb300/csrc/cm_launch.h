@@ -36,4 +36,10 @@ private:
 // add kernel launches made outside KernelScope (graph replays)
 void count_launches(long long n);
 
+// for CUDA-graph replays: whether per-kernel timing is on, an event from the
+// profiler's pool, and a recorded (start, stop) pair to be collected
+bool profiling_on();
+cudaEvent_t profile_take_event();
+void profile_push(const char* name, cudaEvent_t a, cudaEvent_t b);
+
 }  // namespace cmk

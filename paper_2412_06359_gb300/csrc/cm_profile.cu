@@ -86,6 +86,24 @@ void count_launches(long long n)
     g_launches += n;
 }
 
+bool profiling_on()
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    return g_on;
+}
+
+cudaEvent_t profile_take_event()
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    return take_event();
+}
+
+void profile_push(const char* name, cudaEvent_t a, cudaEvent_t b)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_pending.push_back({name, a, b});
+}
+
 }  // namespace cmk
 
 using namespace cmk;

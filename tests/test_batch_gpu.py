@@ -1,0 +1,166 @@
+"""The batched path (cm_batch_*): every window of an uneven batch in one
+persistent launch per phase, replayed from a CUDA graph, against the oracle
+and against the plain single-window path."""
+import numpy as np
+import pytest
+
+from paper_2412_06359_gb300 import synth
+from tests.gpu_util import GRAD_RTOL_L2, LOSS_RTOL, assert_parity, gpu_lib, rel_l2, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+def _dev_windows(cm, wins):
+    import torch
+    out = []
+    for w in wins:
+        d = {"cam": w.cam, "ev": cm.DeviceEvents.from_host(w.events)}
+        if w.flow is not None:
+            d["flow"] = torch.from_numpy(np.ascontiguousarray(w.flow[0])).cuda()
+        else:
+            d["inv_depth"] = torch.from_numpy(w.inv_depth).cuda()
+            d["ego"] = torch.from_numpy(w.ego).cuda()
+            d["dt"] = w.dt
+        out.append(d)
+    return out
+
+
+def _batch_result(plan, i):
+    import torch
+    torch.cuda.synchronize()
+    r = {"loss": float(plan.loss[i].item())}
+    r["loss_r"], r["nnz_r"] = plan.stats(i)
+    for k, v in plan.outputs[i].items():
+        r[k] = v.cpu().numpy()
+    return r
+
+
+def _mixed_windows(count, seed):
+    rng = np.random.default_rng(seed)
+    wins = []
+    for i in range(count):
+        W, H = [(96, 72), (120, 90), (64, 48), (160, 100)][i % 4]
+        n = int(rng.integers(0, 6000)) if i % 5 else 0  # some empty windows
+        wins.append(synth.depth_window(np.random.default_rng(seed * 100 + i), W, H, n, nbins=10))
+    return wins
+
+
+def test_batch_of_mixed_windows_matches_oracle():
+    cm = gpu_lib()
+    wins = _mixed_windows(9, 1)
+    plan = cm.BatchPlan(_dev_windows(cm, wins), cm.loss_cfg(10, cm.REF_ALL, cm.SPLAT_ATOMIC))
+    for rep in range(2):  # capture, then replay
+        plan.run()
+        for i, w in enumerate(wins):
+            g = _batch_result(plan, i)
+            if w.events.n == 0:
+                assert g["loss"] == 0.0 and not np.any(g["dinv_depth"]) and not np.any(g["dego"])
+                continue
+            assert_parity(g, run_oracle(w))
+
+
+def test_batch_flow_windows_end_reference():
+    cm = gpu_lib()
+    rng = np.random.default_rng(4)
+    wins = []
+    for i in range(5):
+        W, H = 80 + 8 * i, 60
+        ev = synth.uniform_events(rng, W, H, 3000 + 500 * i)
+        flow = synth.sinusoid_flow(rng, W, H, 4.0)[None]
+        wins.append(synth.Window(synth.Camera(W, H, 50.0, 50.0, W / 2, H / 2), ev, 4, synth.REF_END, flow=flow))
+    plan = cm.BatchPlan(_dev_windows(cm, wins), cm.loss_cfg(4, cm.REF_END, cm.SPLAT_ATOMIC))
+    plan.run()
+    for i, w in enumerate(wins):
+        g = _batch_result(plan, i)
+        g["dflow"] = g["dflow"][None]
+        assert_parity(g, run_oracle(w))
+
+
+def test_batch_equals_plain_path_on_the_640x480_windows():
+    # four windows of the 64-window workload: each batched result equals the plain
+    # single-window result within the parity tolerances
+    cm = gpu_lib()
+    wins = synth.batch_windows(4)
+    plan = cm.BatchPlan(_dev_windows(cm, wins), cm.loss_cfg(10, cm.REF_ALL, cm.SPLAT_ATOMIC))
+    plan.run()
+    for i, w in enumerate(wins):
+        g = _batch_result(plan, i)
+        p = run_gpu(w)
+        assert np.array_equal(g["nnz_r"], p["nnz_r"])
+        assert abs(g["loss"] - p["loss"]) <= LOSS_RTOL * abs(p["loss"])
+        assert rel_l2(g["dinv_depth"], p["dinv_depth"]) <= GRAD_RTOL_L2
+        assert rel_l2(g["dego"], p["dego"]) <= GRAD_RTOL_L2
+
+
+def test_batch_set_windows_reuses_the_graph():
+    import torch
+    cm = gpu_lib()
+    first = _mixed_windows(6, 7)
+    plan = cm.BatchPlan(_dev_windows(cm, first), cm.loss_cfg(10, cm.REF_ALL, cm.SPLAT_ATOMIC))
+    plan.run()
+    # a smaller set of windows that fits the plan: reversed order, fewer windows
+    second = list(reversed(first))[:4]
+    plan.set_windows(_dev_windows(cm, second))
+    plan.run()
+    for i, w in enumerate(second):
+        g = _batch_result(plan, i)
+        if w.events.n:
+            assert_parity(g, run_oracle(w))
+    # windows larger than the plan's image memory are refused
+    big = [synth.depth_window(np.random.default_rng(3), 640, 480, 100, nbins=10)] * 6
+    from paper_2412_06359_gb300 import _capi as C
+    with pytest.raises(C.CMError) as e:
+        plan.set_windows(_dev_windows(cm, big))
+    assert e.value.status == C.CM_ENOMEM
+    torch.cuda.synchronize()
+
+
+def test_batch_profiling_records_every_phase():
+    from paper_2412_06359_gb300 import _capi as C
+    cm = gpu_lib()
+    wins = _mixed_windows(4, 11)
+    plan = cm.BatchPlan(_dev_windows(cm, wins), cm.loss_cfg(10, cm.REF_ALL, cm.SPLAT_ATOMIC))
+    plan.set_schedule(2, 1)
+    plan.run()
+    C.cm_profile_reset()
+    n0 = C.cm_launch_count()
+    C.cm_profile_enable(True)
+    for _ in range(3):
+        plan.run()
+    C.cm_profile_enable(False)
+    plan.run()
+    prof = C.cm_profile_collect()
+    per_run = 5 * len(wins)  # five kernels per window group, one window per group
+    assert C.cm_launch_count() - n0 == 4 * per_run
+    assert set(prof) == {"k_prep_batch", "k_splat_batch", "k_loss_batch", "k_adjoint_batch", "k_grad_batch"}
+    assert all(v[0] == 3 * len(wins) and v[1] > 0 for v in prof.values())
+    # results still right after switching the timing events back
+    g = _batch_result(plan, 1)
+    if wins[1].events.n:
+        assert_parity(g, run_oracle(wins[1]))
+
+
+@pytest.mark.parametrize("chains,group", [(1, 0), (1, 1), (2, 1), (3, 2), (4, 1)])
+def test_every_schedule_gives_the_same_results(chains, group):
+    cm = gpu_lib()
+    wins = _mixed_windows(7, 21)
+    plan = cm.BatchPlan(_dev_windows(cm, wins), cm.loss_cfg(10, cm.REF_ALL, cm.SPLAT_ATOMIC))
+    plan.set_schedule(chains, group)
+    assert plan.schedule() == (chains, group)
+    plan.run()
+    plan.run()
+    for i, w in enumerate(wins):
+        if w.events.n:
+            assert_parity(_batch_result(plan, i), run_oracle(w))
+
+
+def test_autotune_picks_a_schedule_and_stays_correct():
+    cm = gpu_lib()
+    wins = synth.batch_windows(6)
+    plan = cm.BatchPlan(_dev_windows(cm, wins), cm.loss_cfg(10, cm.REF_ALL, cm.SPLAT_ATOMIC))
+    chains, group = plan.autotune()
+    assert 1 <= chains <= 8 and group >= 0
+    assert plan.autotune() == (chains, group)  # cached for this shape
+    plan.run()
+    for i in (0, 3):
+        assert_parity(_batch_result(plan, i), run_oracle(wins[i]))
