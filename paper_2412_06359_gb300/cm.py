@@ -120,13 +120,15 @@ def flow_from_depth(cam, inv_depth: torch.Tensor, ego: torch.Tensor, dt: float) 
     return out
 
 
-def warp_splat(cam, ev: DeviceEvents, flow: torch.Tensor, cfg: C.cm_loss_cfg) -> torch.Tensor:
-    """IWEs [R, H, W, 4] = (C+, S+, C-, S-) of one window."""
+def warp_splat(cam, ev: DeviceEvents, flow: torch.Tensor, cfg: C.cm_loss_cfg,
+               ws: "Workspace | None" = None) -> torch.Tensor:
+    """IWEs [R, H, W, 4] = (C+, S+, C-, S-) of one window (the sort path needs
+    a workspace created with the same configuration)."""
     c = camera(cam)
     nfb = 1 if flow.dim() == 3 else flow.shape[0]
     out = torch.empty((n_refs(cfg), c.height, c.width, 4), dtype=torch.float32, device=flow.device)
-    C.cm_warp_splat(c, ev.c(), _require_cuda(flow, "flow", torch.float32), nfb, cfg, None, out.data_ptr(),
-                    stream_handle(flow.device))
+    C.cm_warp_splat(c, ev.c(), _require_cuda(flow, "flow", torch.float32), nfb, cfg,
+                    None if ws is None else ws.handle, out.data_ptr(), stream_handle(flow.device))
     return out
 
 

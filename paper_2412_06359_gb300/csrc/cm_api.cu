@@ -8,6 +8,7 @@
 
 #include "../../include/cm.h"
 #include "cm_launch.h"
+#include "cm_sort.h"
 
 using cmk::Win;
 
@@ -28,6 +29,8 @@ struct cm_workspace {
     float* loss_r;
     int32_t* nnz_r;
     float* dego_part;
+    bool has_sort;           // buffers of the deterministic sort path are laid out
+    cmk::SortBufs sb;
     // state of the last forward on this workspace
     int fwd_mode;            // 0 none, 1 flow input, 2 depth input
     const void* fwd_events;  // event x pointer of the last forward
@@ -52,7 +55,9 @@ int tiles_for(size_t hw, int cap)
 
 struct Layout {
     size_t iwe, flow, dflow, loss_part, norm, loss_r, nnz_r, dego_part, total;
+    size_t ka, kb, va, vb, pay, hist, part, start;  // sort path (CM_SPLAT_SORT only)
     int R, loss_tiles, pix_tiles;
+    bool sort;
 };
 
 bool finite_pos(float v) { return std::isfinite(v) && v > 0.0f; }
@@ -89,7 +94,7 @@ int check_events(const cm_events* ev)
     return CM_OK;
 }
 
-Layout layout(const cm_camera& cam, const cm_loss_cfg& cfg, int32_t nfb)
+Layout layout(const cm_camera& cam, const cm_loss_cfg& cfg, int32_t nfb, int64_t max_events)
 {
     Layout L;
     const size_t HW = (size_t)cam.width * cam.height;
@@ -113,6 +118,26 @@ Layout layout(const cm_camera& cam, const cm_loss_cfg& cfg, int32_t nfb)
     off = align_up(off + (size_t)L.R * sizeof(int32_t));
     L.dego_part = off;
     off = align_up(off + (size_t)L.pix_tiles * 6 * sizeof(float));
+    L.sort = cfg.splat == CM_SPLAT_SORT;
+    if (L.sort) {
+        const cmk::SortSizes z = cmk::sort_sizes(max_events, L.R, cfg.nbins, nfb, HW);
+        L.ka = off;
+        off = align_up(off + z.entries * 4);
+        L.kb = off;
+        off = align_up(off + z.entries * 4);
+        L.va = off;
+        off = align_up(off + z.entries * 4);
+        L.vb = off;
+        off = align_up(off + z.entries * 4);
+        L.pay = off;
+        off = align_up(off + z.entries * 16);
+        L.hist = off;
+        off = align_up(off + z.hist * 4);
+        L.part = off;
+        off = align_up(off + z.part * 4);
+        L.start = off;
+        off = align_up(off + z.start * 4);
+    }
     L.total = off;
     return L;
 }
@@ -208,7 +233,7 @@ int cm_workspace_query(const cm_camera* cam, const cm_loss_cfg* cfg, int64_t max
     int st;
     if ((st = check_camera(cam)) || (st = check_cfg(cfg))) return st;
     if (!bytes || max_events < 0 || (n_flow_bins != 1 && n_flow_bins != cfg->nbins)) return CM_EINVAL;
-    *bytes = layout(*cam, *cfg, n_flow_bins).total;
+    *bytes = layout(*cam, *cfg, n_flow_bins, max_events).total;
     return CM_OK;
 }
 
@@ -219,7 +244,7 @@ int cm_workspace_create(void* dev_mem, size_t bytes, const cm_camera* cam, const
     if ((st = check_camera(cam)) || (st = check_cfg(cfg))) return st;
     if (!out || !dev_mem || max_events < 0 || (n_flow_bins != 1 && n_flow_bins != cfg->nbins)) return CM_EINVAL;
     if (reinterpret_cast<uintptr_t>(dev_mem) % kAlign) return CM_EINVAL;
-    const Layout L = layout(*cam, *cfg, n_flow_bins);
+    const Layout L = layout(*cam, *cfg, n_flow_bins, max_events);
     if (bytes < L.total) return CM_ENOMEM;
     cm_workspace* ws = new (std::nothrow) cm_workspace;
     if (!ws) return CM_ENOMEM;
@@ -242,6 +267,17 @@ int cm_workspace_create(void* dev_mem, size_t bytes, const cm_camera* cam, const
     ws->loss_r = reinterpret_cast<float*>(b + L.loss_r);
     ws->nnz_r = reinterpret_cast<int32_t*>(b + L.nnz_r);
     ws->dego_part = reinterpret_cast<float*>(b + L.dego_part);
+    ws->has_sort = L.sort;
+    if (L.sort) {
+        ws->sb.ka = reinterpret_cast<uint32_t*>(b + L.ka);
+        ws->sb.kb = reinterpret_cast<uint32_t*>(b + L.kb);
+        ws->sb.va = reinterpret_cast<uint32_t*>(b + L.va);
+        ws->sb.vb = reinterpret_cast<uint32_t*>(b + L.vb);
+        ws->sb.pay = reinterpret_cast<float4*>(b + L.pay);
+        ws->sb.hist = reinterpret_cast<uint32_t*>(b + L.hist);
+        ws->sb.part = reinterpret_cast<uint32_t*>(b + L.part);
+        ws->sb.start = reinterpret_cast<uint32_t*>(b + L.start);
+    }
     *out = ws;
     return CM_OK;
 }
@@ -287,6 +323,12 @@ int cm_warp_splat(const cm_camera* cam, const cm_events* ev, const float* flow, 
     d.flow = reinterpret_cast<const float2*>(flow);
     d.iwe = iwe_out ? reinterpret_cast<float4*>(iwe_out) : ws->iwe;
     cudaStream_t s = as_stream(stream);
+    if (cfg->splat == CM_SPLAT_SORT) {
+        // the sort path needs a workspace laid out for it and for this shape
+        if (!ws || !ws->has_sort || !same_shape(ws, *cam, *cfg, n_flow_bins)) return CM_EINVAL;
+        if (ev->n > ws->max_events) return CM_ENOMEM;
+        return cuda_status(cmk::sort_splat(d, ws->sb, cmk::sm_count_current(), s));
+    }
     const size_t bytes = (size_t)d.R * d.W * d.H * sizeof(float4);
     if ((st = cuda_status(cudaMemsetAsync(d.iwe, 0, bytes, s)))) return st;
     return cuda_status(cmk::launch_splat(d, cmk::sm_count_current(), s));
@@ -317,9 +359,14 @@ int cm_loss_forward(const cm_camera* cam, const cm_events* ev, const float* flow
     } else {
         d.flow = reinterpret_cast<const float2*>(flow);
     }
-    const size_t bytes = (size_t)d.R * d.W * d.H * sizeof(float4);
-    if ((st = cuda_status(cudaMemsetAsync(d.iwe, 0, bytes, s)))) return st;
-    if ((st = cuda_status(cmk::launch_splat(d, cmk::sm_count_current(), s)))) return st;
+    if (cfg->splat == CM_SPLAT_SORT) {
+        if (!ws->has_sort) return CM_EINVAL;
+        if ((st = cuda_status(cmk::sort_splat(d, ws->sb, cmk::sm_count_current(), s)))) return st;
+    } else {
+        const size_t bytes = (size_t)d.R * d.W * d.H * sizeof(float4);
+        if ((st = cuda_status(cudaMemsetAsync(d.iwe, 0, bytes, s)))) return st;
+        if ((st = cuda_status(cmk::launch_splat(d, cmk::sm_count_current(), s)))) return st;
+    }
     if ((st = cuda_status(cmk::launch_loss(d, s)))) return st;
     ws->fwd_mode = depth ? 2 : 1;
     ws->fwd_events = ev->x;
@@ -348,9 +395,14 @@ int cm_loss_backward(const cm_camera* cam, const cm_events* ev, const float* flo
     d.flow = depth ? ws->flow : reinterpret_cast<const float2*>(flow);
     d.dflow = dflow ? reinterpret_cast<float2*>(dflow) : ws->dflow;
     if (!depth && !dflow) return CM_OK;
-    const size_t gbytes = (size_t)n_flow_bins * d.W * d.H * sizeof(float2);
-    if ((st = cuda_status(cudaMemsetAsync(d.dflow, 0, gbytes, s)))) return st;
-    if ((st = cuda_status(cmk::launch_adjoint(d, cmk::sm_count_current(), s)))) return st;
+    if (cfg->splat == CM_SPLAT_SORT) {
+        if (!ws->has_sort) return CM_EINVAL;
+        if ((st = cuda_status(cmk::sort_adjoint(d, ws->sb, cmk::sm_count_current(), s)))) return st;
+    } else {
+        const size_t gbytes = (size_t)n_flow_bins * d.W * d.H * sizeof(float2);
+        if ((st = cuda_status(cudaMemsetAsync(d.dflow, 0, gbytes, s)))) return st;
+        if ((st = cuda_status(cmk::launch_adjoint(d, cmk::sm_count_current(), s)))) return st;
+    }
     if (depth && (dinv_depth || dego6)) {
         d.rho = inv_depth;
         d.ego = ego6;

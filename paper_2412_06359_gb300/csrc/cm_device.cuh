@@ -68,6 +68,11 @@ __device__ __forceinline__ const float2* field(const Win& d, int j)
     return d.flow + (d.nfb == 1 ? (size_t)0 : (size_t)j * plane_size(d));
 }
 
+__device__ __forceinline__ const float2* field_ptr(const Win& d, int j) { return field(d, j); }
+
+// flow-field plane used by the push across bin j (one field for all bins, or one per bin)
+__device__ __forceinline__ size_t plane_of(const Win& d, int j) { return d.nfb == 1 ? (size_t)0 : (size_t)j; }
+
 __device__ __forceinline__ float2* field_grad(const Win& d, int j)
 {
     return d.dflow + (d.nfb == 1 ? (size_t)0 : (size_t)j * plane_size(d));
@@ -256,20 +261,81 @@ __device__ __forceinline__ void splat_point(float4* plane, int W, float px, floa
     if (s.ax > 0.0f && s.ay > 0.0f) red_add_v2(q + 4 * (size_t)W + 4, s.w11, __fmul_rn(s.w11, tbar));
 }
 
-template <int MAXB>
-__device__ __forceinline__ void splat_event(const Win& d, int64_t k)
+// Where the splat (S4) and the flow-gradient scatter (S6) go.
+//
+// RedSink adds into the IWE / dL/dflow with 8-byte vector reductions (the order
+// of the additions is not fixed).  EmitSink writes one entry per splat point or
+// push instead: a key (plane * HW + the cell of the point's top-left corner) and
+// the payload (x, y, a, b); entry k * stride + slot belongs to event k, so the
+// entries have a fixed order.  The sort path orders them by key (stable) and a
+// per-pixel gather sums each pixel's entries in that order: bit-reproducible.
+struct RedSink {
+    __device__ __forceinline__ void splat(const Win& d, int r, float px, float py, float tbar, int pol2,
+                                          int64_t) const
+    {
+        splat_point(d.iwe + (size_t)r * plane_size(d), d.W, px, py, tbar, pol2);
+    }
+    // a push sampled at (px, py) in cell s: hs * w_c * lambda to the four corners
+    __device__ __forceinline__ void scatter(const Win& d, int field, int, const Bil& s, float, float, float hx,
+                                            float hy, int64_t) const
+    {
+        const int W = d.W;
+        float* g = reinterpret_cast<float*>(field_grad(d, field) + (size_t)s.iy * W + s.ix);
+        red_add_v2(g, s.w00 * hx, s.w00 * hy);
+        if (s.ax > 0.0f) red_add_v2(g + 2, s.w10 * hx, s.w10 * hy);
+        if (s.ay > 0.0f) red_add_v2(g + 2 * (size_t)W, s.w01 * hx, s.w01 * hy);
+        if (s.ax > 0.0f && s.ay > 0.0f) red_add_v2(g + 2 * (size_t)W + 2, s.w11 * hx, s.w11 * hy);
+    }
+    // the first push of a chain, sampled at the event's own pixel
+    __device__ __forceinline__ void point(const Win& d, int field, int, int xk, int yk, float vx, float vy,
+                                          int64_t) const
+    {
+        red_add_v2(reinterpret_cast<float*>(field_grad(d, field) + (size_t)yk * d.W + xk), vx, vy);
+    }
+};
+
+struct EmitSink {
+    uint32_t* key;
+    float4* pay;
+    int32_t stride;  // entries per event: R for the splat, B + 1 for the adjoint (one per edge)
+
+    __device__ __forceinline__ void splat(const Win& d, int r, float px, float py, float tbar, int pol2,
+                                          int64_t k) const
+    {
+        const Bil s = bil(px, py);
+        const int64_t e = k * stride + r;
+        key[e] = (uint32_t)((size_t)(2 * r + (pol2 >> 1)) * plane_size(d) + (size_t)s.iy * d.W + s.ix);
+        pay[e] = make_float4(px, py, 1.0f, tbar);
+    }
+    __device__ __forceinline__ void scatter(const Win& d, int field, int edge, const Bil& s, float px, float py,
+                                            float hx, float hy, int64_t k) const
+    {
+        const int64_t e = k * stride + edge;
+        key[e] = (uint32_t)(plane_of(d, field) * plane_size(d) + (size_t)s.iy * d.W + s.ix);
+        pay[e] = make_float4(px, py, hx, hy);
+    }
+    __device__ __forceinline__ void point(const Win& d, int field, int edge, int xk, int yk, float vx, float vy,
+                                          int64_t k) const
+    {
+        const int64_t e = k * stride + edge;
+        key[e] = (uint32_t)(plane_of(d, field) * plane_size(d) + (size_t)yk * d.W + xk);
+        pay[e] = make_float4((float)xk, (float)yk, vx, vy);
+    }
+};
+
+template <int MAXB, class Sink = RedSink>
+__device__ __forceinline__ void splat_event(const Win& d, int64_t k, const Sink& sink = Sink())
 {
     EventAt e;
     if (!load_event(d, k, e)) return;
     Traj<MAXB> P;
     if (!trajectory<MAXB>(d, e, P)) return;
-    const size_t HW = plane_size(d);
     if (d.ref_mode == kRefAll) {
 #pragma unroll
         for (int j = 0; j <= MAXB; ++j)
-            if (j <= d.B) splat_point(d.iwe + (size_t)j * HW, d.W, P.x[j], P.y[j], tbar_of(j, d.B, e.tau), e.pol2);
+            if (j <= d.B) sink.splat(d, j, P.x[j], P.y[j], tbar_of(j, d.B, e.tau), e.pol2, k);
     } else {
-        splat_point(d.iwe, d.W, P.ex, P.ey, tbar_of(d.B, d.B, e.tau), e.pol2);
+        sink.splat(d, 0, P.ex, P.ey, tbar_of(d.B, d.B, e.tau), e.pol2, k);
     }
 }
 
@@ -305,18 +371,16 @@ __device__ __forceinline__ float2 ref_adjoint(const Win& d, int r, int j, float 
 
 // One push of the adjoint back across a step x' = x + hs u(x) sampled at x
 // (hs = +h forward chain, -h backward chain): scatter hs w_c lambda into the
-// flow gradient and return lambda + hs J(x)^T lambda.
-__device__ __forceinline__ float2 push_back(float2* Gf, const float2* U, int W, int H, float px, float py, float hs,
-                                            float2 lam)
+// gradient of field `field` and return lambda + hs J(x)^T lambda.
+template <class Sink>
+__device__ __forceinline__ float2 push_back(const Win& d, const Sink& sink, int field, int edge, float px, float py,
+                                            float hs, float2 lam, int64_t k)
 {
+    const int W = d.W, H = d.H;
     const Bil s = bil(px, py);
-    const Quad q = load_quad(U, W, H, s);
+    const Quad q = load_quad(field_ptr(d, field), W, H, s);
     const float hx = hs * lam.x, hy = hs * lam.y;
-    float* g = reinterpret_cast<float*>(Gf + (size_t)s.iy * W + s.ix);
-    red_add_v2(g, s.w00 * hx, s.w00 * hy);
-    if (s.ax > 0.0f) red_add_v2(g + 2, s.w10 * hx, s.w10 * hy);
-    if (s.ay > 0.0f) red_add_v2(g + 2 * (size_t)W, s.w01 * hx, s.w01 * hy);
-    if (s.ax > 0.0f && s.ay > 0.0f) red_add_v2(g + 2 * (size_t)W + 2, s.w11 * hx, s.w11 * hy);
+    sink.scatter(d, field, edge, s, px, py, hx, hy, k);
     const float jxx = s.by * (q.u10.x - q.u00.x) + s.ay * (q.u11.x - q.u01.x);
     const float jxy = s.bx * (q.u01.x - q.u00.x) + s.ax * (q.u11.x - q.u10.x);
     const float jyx = s.by * (q.u10.y - q.u00.y) + s.ay * (q.u11.y - q.u01.y);
@@ -330,17 +394,16 @@ __device__ __forceinline__ float2 push_back(float2* Gf, const float2* U, int W, 
 // S6: per-event adjoint.  The trajectory is recomputed; the position adjoint of
 // each reference point is gathered from the loss-transformed IWE, and the
 // adjoint is carried back along both chains of pushes, scattering dL/dflow.
-template <int MAXB>
-__device__ __forceinline__ void adjoint_event(const Win& d, int64_t k, float dl)
+template <int MAXB, class Sink = RedSink>
+__device__ __forceinline__ void adjoint_event(const Win& d, int64_t k, float dl, const Sink& sink = Sink())
 {
     EventAt e;
     if (!load_event(d, k, e)) return;
     Traj<MAXB> P;
     if (!trajectory<MAXB>(d, e, P)) return;
-    const int W = d.W, H = d.H, B = d.B, b = e.b;
+    const int B = d.B, b = e.b;
     const float h = __fdiv_rn(1.0f, (float)B);
     const bool all = d.ref_mode == kRefAll;
-    const size_t ik = (size_t)e.yk * W + e.xk;
     // forward chain: edges B .. b+1
     float2 lam = make_float2(0.0f, 0.0f);
 #pragma unroll
@@ -352,10 +415,10 @@ __device__ __forceinline__ void adjoint_event(const Win& d, int64_t k, float dl)
                 lam.y += a.y;
             }
             if (j > b + 1) {
-                lam = push_back(field_grad(d, j - 1), field(d, j - 1), W, H, P.x[j - 1], P.y[j - 1], h, lam);
+                lam = push_back(d, sink, j - 1, j, P.x[j - 1], P.y[j - 1], h, lam, k);
             } else {
                 const float dtf = __fsub_rn(edge_tau(b + 1, B), e.tau);
-                red_add_v2(reinterpret_cast<float*>(field_grad(d, b) + ik), dtf * lam.x, dtf * lam.y);
+                sink.point(d, b, j, e.xk, e.yk, dtf * lam.x, dtf * lam.y, k);
             }
         }
     }
@@ -369,10 +432,10 @@ __device__ __forceinline__ void adjoint_event(const Win& d, int64_t k, float dl)
             lam.x += a.x;
             lam.y += a.y;
             if (j < b) {
-                lam = push_back(field_grad(d, j), field(d, j), W, H, P.x[j + 1], P.y[j + 1], -h, lam);
+                lam = push_back(d, sink, j, j, P.x[j + 1], P.y[j + 1], -h, lam, k);
             } else {
                 const float dtb = __fsub_rn(e.tau, edge_tau(b, B));
-                red_add_v2(reinterpret_cast<float*>(field_grad(d, b) + ik), -dtb * lam.x, -dtb * lam.y);
+                sink.point(d, b, j, e.xk, e.yk, -dtb * lam.x, -dtb * lam.y, k);
             }
         }
     }

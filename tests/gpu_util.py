@@ -44,7 +44,7 @@ def run_gpu(win: synth.Window, *, splat=None, grad=True, dloss=1.0, eps=1e-9, wa
             g = cm.loss_backward(ws, ev, dl, flow=flow)
             out["dflow"] = g["dflow"].cpu().numpy().reshape(nfb, win.cam.height, win.cam.width, 2)
         if want_iwe:
-            out["iwe"] = cm.warp_splat(win.cam, ev, flow, cfg).cpu().numpy()
+            out["iwe"] = cm.warp_splat(win.cam, ev, flow, cfg, ws).cpu().numpy()
     else:
         rho = torch.from_numpy(np.ascontiguousarray(win.inv_depth, np.float32)).to(dev)
         ego = torch.from_numpy(np.ascontiguousarray(win.ego, np.float32)).to(dev)
@@ -57,7 +57,7 @@ def run_gpu(win: synth.Window, *, splat=None, grad=True, dloss=1.0, eps=1e-9, wa
         if want_iwe:
             flow = cm.flow_from_depth(win.cam, rho, ego, win.dt)
             out["flow"] = flow.cpu().numpy()
-            out["iwe"] = cm.warp_splat(win.cam, ev, flow, cfg).cpu().numpy()
+            out["iwe"] = cm.warp_splat(win.cam, ev, flow, cfg, ws).cpu().numpy()
     torch.cuda.synchronize()
     out["loss"] = float(loss.cpu().numpy()[0])
     out["loss_r"], out["nnz_r"] = ws.stats()
