@@ -215,7 +215,14 @@ typedef struct {
     float* dflow;           /* [H][W][2] dL/dflow, or NULL (then kept in the plan's memory) */
     float* dinv_depth;      /* [H][W] dL/d(inverse depth), or NULL (depth input only) */
     float* dego6;           /* [6] dL/d(ego-motion), or NULL (depth input only) */
+    void* scratch;          /* NULL, or 256-byte-aligned device memory of cm_window_scratch_query bytes
+                               holding this window's images of warped events, flow, reduction buffers
+                               and counters (instead of the plan's memory), e.g. kept resident per
+                               client stream by a server */
 } cm_window;
+
+/* Bytes of a window's own scratch (cm_window.scratch) for this camera and configuration. */
+int cm_window_scratch_query(const cm_camera* cam, const cm_loss_cfg* cfg, size_t* bytes);
 
 typedef struct cm_batch cm_batch;
 
@@ -259,6 +266,79 @@ int cm_batch_autotune(cm_batch* plan, void* stream, cm_batch_schedule* chosen);
  * non-empty counts (int32 [R]) of the last run. */
 int cm_batch_stats(const cm_batch* plan, int32_t window, const float** loss_r, const int32_t** nnz_r);
 int cm_batch_destroy(cm_batch* plan);
+
+/* ---- serving: continuous batching of requests from many event streams ----
+ * The paper learns on board from a live event stream (Sec. 3.5, Sec. 4.2);
+ * a server evaluates loss + gradient requests from many such streams on one
+ * GPU.  It reserves its whole HBM budget at creation (the only device
+ * allocation, released by cm_server_destroy) and keeps, inside it, a resident
+ * state per client stream (images of warped events, reduction buffers, inverse
+ * depth and gradients, an event buffer that grows to the largest request) and
+ * one batch plan per lane.  A scheduler thread admits queued requests into
+ * batches while a lane is free and their stream's state fits the budget
+ * (evicting idle streams' state, least recently used first); batches on
+ * different lanes overlap on the device.  Requests of one stream run in
+ * submission order, one at a time.  Results are bit-for-bit those of the same
+ * request evaluated alone up to the order of FP32 additions of the atomic
+ * splat (within the parity tolerances). */
+typedef struct {
+    size_t hbm_budget;  /* device bytes the server reserves (>= 1 MiB) */
+    int32_t max_batch;  /* requests per batch */
+    int32_t lanes;      /* batches in flight at once, each on its own CUDA stream (1..16) */
+    int32_t max_queue;  /* queued requests before cm_batch_submit returns CM_EBUSY */
+    int32_t nbins;      /* B for every request */
+    int32_t ref_mode;   /* CM_REF_END or CM_REF_ALL_EDGES */
+    float eps;          /* <= 0: 1e-9 */
+    int32_t device;     /* CUDA device ordinal */
+} cm_server_cfg;
+
+/* One request: a depth + ego-motion window of stream `stream_id`.  All
+ * pointers are HOST memory (pinned memory avoids staging copies) that must stay
+ * valid until the request is done; outputs are written when it completes. */
+typedef struct {
+    int32_t stream_id;
+    cm_camera cam;
+    const int16_t* x;
+    const int16_t* y;
+    const float* t;
+    const int8_t* p;
+    int64_t n;
+    float t0, t1;
+    const float* inv_depth;  /* [H][W] */
+    const float* ego6;       /* [6] */
+    float dt_window;
+    float* loss_out;         /* scalar */
+    float* dinv_depth_out;   /* [H][W] or NULL */
+    float* dego6_out;        /* [6] or NULL */
+} cm_request;
+
+typedef struct {
+    int32_t status;      /* CM_OK, or the error that ended the request */
+    int32_t batch_size;  /* requests in the batch it ran in */
+    double t_submit, t_start, t_done;  /* seconds on a monotonic clock */
+} cm_result;
+
+typedef struct {
+    int64_t submitted, completed, batches, batched_requests, evictions, memory_waits, queued;
+    size_t pool_bytes, pool_used, pool_peak;
+} cm_server_stats;
+
+typedef struct cm_server cm_server;
+
+/* Errors: CM_EINVAL, CM_ENOMEM (budget not allocatable), CM_ECUDA. */
+int cm_server_create(const cm_server_cfg* cfg, cm_server** server);
+/* Non-blocking: queue a request, get its ticket.  CM_EBUSY when the queue is
+ * full; CM_ENOMEM when the request could never fit the budget; CM_EINVAL. */
+int cm_batch_submit(cm_server* server, const cm_request* req, uint64_t* ticket);
+/* Non-blocking: *done = 1 and *result filled once the request completed (the
+ * ticket is then consumed); CM_ENOTFOUND for an unknown ticket. */
+int cm_batch_poll(cm_server* server, uint64_t ticket, cm_result* result, int32_t* done);
+/* Wait at most timeout_s seconds for a request; CM_ETIMEOUT when it is not done
+ * by then (the ticket stays valid). */
+int cm_batch_wait(cm_server* server, uint64_t ticket, double timeout_s, cm_result* result);
+int cm_server_get_stats(cm_server* server, cm_server_stats* stats);
+/* Stops the scheduler, waits for the batches in flight, frees the budget. */
+int cm_server_destroy(cm_server* server);
 
 /* ---- loss and flow gradient without any allocation ----
  * The paper has no counterpart of this entry point; it exists for callers that

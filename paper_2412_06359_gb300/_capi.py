@@ -46,11 +46,37 @@ class cm_window(ctypes.Structure):
     _fields_ = [("cam", cm_camera), ("ev", cm_events), ("flow", ctypes.c_void_p), ("inv_depth", ctypes.c_void_p),
                 ("ego6", ctypes.c_void_p), ("dt_window", ctypes.c_float), ("dloss", ctypes.c_void_p),
                 ("loss_out", ctypes.c_void_p), ("dflow", ctypes.c_void_p), ("dinv_depth", ctypes.c_void_p),
-                ("dego6", ctypes.c_void_p)]
+                ("dego6", ctypes.c_void_p), ("scratch", ctypes.c_void_p)]
 
 
 class cm_batch_schedule(ctypes.Structure):
     _fields_ = [("chains", ctypes.c_int32), ("group", ctypes.c_int32)]
+
+
+class cm_server_cfg(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_size_t), ("max_batch", ctypes.c_int32), ("lanes", ctypes.c_int32),
+                ("max_queue", ctypes.c_int32), ("nbins", ctypes.c_int32), ("ref_mode", ctypes.c_int32),
+                ("eps", ctypes.c_float), ("device", ctypes.c_int32)]
+
+
+class cm_request(ctypes.Structure):
+    _fields_ = [("stream_id", ctypes.c_int32), ("cam", cm_camera), ("x", ctypes.c_void_p), ("y", ctypes.c_void_p),
+                ("t", ctypes.c_void_p), ("p", ctypes.c_void_p), ("n", ctypes.c_int64), ("t0", ctypes.c_float),
+                ("t1", ctypes.c_float), ("inv_depth", ctypes.c_void_p), ("ego6", ctypes.c_void_p),
+                ("dt_window", ctypes.c_float), ("loss_out", ctypes.c_void_p), ("dinv_depth_out", ctypes.c_void_p),
+                ("dego6_out", ctypes.c_void_p)]
+
+
+class cm_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("batch_size", ctypes.c_int32), ("t_submit", ctypes.c_double),
+                ("t_start", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
+class cm_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("batches", ctypes.c_int64),
+                ("batched_requests", ctypes.c_int64), ("evictions", ctypes.c_int64),
+                ("memory_waits", ctypes.c_int64), ("queued", ctypes.c_int64), ("pool_bytes", ctypes.c_size_t),
+                ("pool_used", ctypes.c_size_t), ("pool_peak", ctypes.c_size_t)]
 
 
 class cm_kernel_stat(ctypes.Structure):
@@ -76,6 +102,7 @@ SIGNATURES = {
                         ctypes.c_int),
     "cm_loss_backward": ([_P(cm_camera), _P(cm_events), _vp, _i32, _vp, _vp, _f32, _P(cm_loss_cfg), _vp, _vp,
                           _vp, _vp, _vp, _vp], ctypes.c_int),
+    "cm_window_scratch_query": ([_P(cm_camera), _P(cm_loss_cfg), _P(_sz)], ctypes.c_int),
     "cm_batch_query": ([_P(cm_window), _i32, _P(cm_loss_cfg), _P(_sz)], ctypes.c_int),
     "cm_batch_create": ([_vp, _sz, _P(cm_window), _i32, _P(cm_loss_cfg), _P(_vp)], ctypes.c_int),
     "cm_batch_set_windows": ([_vp, _P(cm_window), _i32], ctypes.c_int),
@@ -85,6 +112,12 @@ SIGNATURES = {
     "cm_batch_autotune": ([_vp, _vp, _P(cm_batch_schedule)], ctypes.c_int),
     "cm_batch_stats": ([_vp, _i32, _P(_vp), _P(_vp)], ctypes.c_int),
     "cm_batch_destroy": ([_vp], ctypes.c_int),
+    "cm_server_create": ([_P(cm_server_cfg), _P(_vp)], ctypes.c_int),
+    "cm_batch_submit": ([_vp, _P(cm_request), _P(ctypes.c_uint64)], ctypes.c_int),
+    "cm_batch_poll": ([_vp, ctypes.c_uint64, _P(cm_result), _P(_i32)], ctypes.c_int),
+    "cm_batch_wait": ([_vp, ctypes.c_uint64, ctypes.c_double, _P(cm_result)], ctypes.c_int),
+    "cm_server_get_stats": ([_vp, _P(cm_server_stats)], ctypes.c_int),
+    "cm_server_destroy": ([_vp], ctypes.c_int),
     "cm_loss_grad_static": ([_P(cm_camera), _P(cm_events), _vp, _i32, _P(cm_loss_cfg), _vp, _vp, _vp, _vp],
                             ctypes.c_int),
     "cm_profile_enable": ([ctypes.c_int], ctypes.c_int),
@@ -182,6 +215,13 @@ def _win_array(wins):
     return arr
 
 
+def cm_window_scratch_query(cam, cfg) -> int:
+    out = _sz(0)
+    _check(lib().cm_window_scratch_query(ctypes.byref(cam), ctypes.byref(cfg), ctypes.byref(out)),
+           "cm_window_scratch_query")
+    return out.value
+
+
 def cm_batch_query(wins, cfg) -> int:
     out = _sz(0)
     _check(lib().cm_batch_query(_win_array(wins), len(wins), ctypes.byref(cfg), ctypes.byref(out)), "cm_batch_query")
@@ -228,6 +268,42 @@ def cm_batch_stats(plan: int, window: int) -> tuple[int, int]:
 
 def cm_batch_destroy(plan: int) -> None:
     _check(lib().cm_batch_destroy(plan), "cm_batch_destroy")
+
+
+def cm_server_create(cfg: cm_server_cfg) -> int:
+    h = _vp(0)
+    _check(lib().cm_server_create(ctypes.byref(cfg), ctypes.byref(h)), "cm_server_create")
+    return h.value
+
+
+def cm_batch_submit(server: int, req: cm_request) -> int:
+    t = ctypes.c_uint64(0)
+    _check(lib().cm_batch_submit(server, ctypes.byref(req), ctypes.byref(t)), "cm_batch_submit")
+    return t.value
+
+
+def cm_batch_poll(server: int, ticket: int):
+    """None while the request runs, else its cm_result."""
+    r = cm_result()
+    done = _i32(0)
+    _check(lib().cm_batch_poll(server, ticket, ctypes.byref(r), ctypes.byref(done)), "cm_batch_poll")
+    return r if done.value else None
+
+
+def cm_batch_wait(server: int, ticket: int, timeout_s: float) -> cm_result:
+    r = cm_result()
+    _check(lib().cm_batch_wait(server, ticket, float(timeout_s), ctypes.byref(r)), "cm_batch_wait")
+    return r
+
+
+def cm_server_get_stats(server: int) -> cm_server_stats:
+    s = cm_server_stats()
+    _check(lib().cm_server_get_stats(server, ctypes.byref(s)), "cm_server_get_stats")
+    return s
+
+
+def cm_server_destroy(server: int) -> None:
+    _check(lib().cm_server_destroy(server), "cm_server_destroy")
 
 
 def cm_loss_grad_static(cam, ev, flow: int, n_flow_bins: int, cfg, dloss: int, loss_out: int, dflow_out: int,

@@ -204,6 +204,7 @@ bool window_ok(const cm_window& w)
     if (!w.dloss || !w.loss_out) return false;
     if (!w.flow && (!w.inv_depth || !w.ego6 || !std::isfinite(w.dt_window))) return false;
     if (w.flow && (w.dinv_depth || w.dego6)) return false;
+    if (reinterpret_cast<uintptr_t>(w.scratch) % 256) return false;
     return true;
 }
 
@@ -220,6 +221,7 @@ Need need_of(const cm_window* wins, int32_t nwin, const cm_loss_cfg& cfg)
     Need n{};
     const int R = refs_of(cfg);
     for (int i = 0; i < nwin; ++i) {
+        if (wins[i].scratch) continue;  // the window brings its own buffers
         const size_t HW = (size_t)wins[i].cam.width * wins[i].cam.height;
         n.iwe += (size_t)R * HW * sizeof(float4);
         if (!wins[i].flow) n.flow += HW * sizeof(float2);
@@ -229,6 +231,37 @@ Need need_of(const cm_window* wins, int32_t nwin, const cm_loss_cfg& cfg)
         n.dego += (size_t)tiles_for(HW, 512) * 6 * sizeof(float);
     }
     return n;
+}
+
+// a window's own scratch: the per-window buffers, one after another
+struct WinScratch {
+    size_t iwe, flow, dflow, part, norm, lr, nnz, dego, sync, total;
+};
+
+WinScratch win_scratch(size_t HW, int R)
+{
+    WinScratch s;
+    size_t o = 0;
+    s.iwe = o;
+    o = up256(o + (size_t)R * HW * sizeof(float4));
+    s.flow = o;
+    o = up256(o + HW * sizeof(float2));
+    s.dflow = o;
+    o = up256(o + HW * sizeof(float2));
+    s.part = o;
+    o = up256(o + (size_t)R * tiles_for(HW, 256) * sizeof(float2));
+    s.norm = o;
+    o = up256(o + (size_t)R * sizeof(float));
+    s.lr = o;
+    o = up256(o + (size_t)R * sizeof(float));
+    s.nnz = o;
+    o = up256(o + (size_t)R * sizeof(int32_t));
+    s.dego = o;
+    o = up256(o + (size_t)tiles_for(HW, 512) * 6 * sizeof(float));
+    s.sync = o;
+    o = up256(o + 2 * sizeof(int32_t));
+    s.total = o;
+    return s;
 }
 
 struct Layout {
@@ -301,6 +334,8 @@ struct cm_batch {
     int nwin = 0;
     std::vector<long long> chunks;     // per window, host copy
     std::vector<int> ltiles, ptiles;   // per window, host copy
+    std::vector<const float*> stat_lr; // per window: device L_r and N_nz of the last run
+    std::vector<const int32_t*> stat_nnz;
     int grid_events = 0, grid_tiles = 0;
     cm_batch_schedule sched{2, 1};
     bool stale = true;                 // the graph must be (re)captured before the next replay
@@ -344,6 +379,8 @@ int stage_windows(cm_batch* b, const cm_window* wins, int32_t nwin)
     b->chunks.assign(nwin, 0);
     b->ltiles.assign(nwin, 0);
     b->ptiles.assign(nwin, 0);
+    b->stat_lr.assign(nwin, nullptr);
+    b->stat_nnz.assign(nwin, nullptr);
     for (int i = 0; i < nwin; ++i) {
         const cm_window& w = wins[i];
         const size_t HW = (size_t)w.cam.width * w.cam.height;
@@ -367,35 +404,54 @@ int stage_windows(cm_batch* b, const cm_window* wins, int32_t nwin)
         d.fy = w.cam.fy;
         d.cx = w.cam.cx;
         d.cy = w.cam.cy;
-        d.iwe = reinterpret_cast<float4*>(base + b->L.iwe + o_iwe);
-        o_iwe += (size_t)R * HW * sizeof(float4);
-        if (w.flow) {
-            d.flow = reinterpret_cast<const float2*>(w.flow);
+        d.loss_tiles = tiles_for(HW, 256);
+        d.pix_tiles = tiles_for(HW, 512);
+        if (w.scratch) {
+            // every per-window buffer in the window's own scratch
+            char* sc = static_cast<char*>(w.scratch);
+            const WinScratch ws = win_scratch(HW, R);
+            d.iwe = reinterpret_cast<float4*>(sc + ws.iwe);
+            d.flow = w.flow ? reinterpret_cast<const float2*>(w.flow) : reinterpret_cast<const float2*>(sc + ws.flow);
+            d.dflow = w.dflow ? reinterpret_cast<float2*>(w.dflow) : reinterpret_cast<float2*>(sc + ws.dflow);
+            d.loss_part = reinterpret_cast<float2*>(sc + ws.part);
+            d.norm = reinterpret_cast<float*>(sc + ws.norm);
+            d.loss_r = reinterpret_cast<float*>(sc + ws.lr);
+            d.nnz_r = reinterpret_cast<int32_t*>(sc + ws.nnz);
+            d.dego_part = reinterpret_cast<float*>(sc + ws.dego);
+            d.sync = reinterpret_cast<int32_t*>(sc + ws.sync);
         } else {
-            d.flow = reinterpret_cast<const float2*>(base + b->L.flow + o_flow);
-            o_flow += HW * sizeof(float2);
+            d.iwe = reinterpret_cast<float4*>(base + b->L.iwe + o_iwe);
+            o_iwe += (size_t)R * HW * sizeof(float4);
+            if (w.flow) {
+                d.flow = reinterpret_cast<const float2*>(w.flow);
+            } else {
+                d.flow = reinterpret_cast<const float2*>(base + b->L.flow + o_flow);
+                o_flow += HW * sizeof(float2);
+            }
+            if (w.dflow) {
+                d.dflow = reinterpret_cast<float2*>(w.dflow);
+            } else {
+                d.dflow = reinterpret_cast<float2*>(base + b->L.dflow + o_dflow);
+                o_dflow += HW * sizeof(float2);
+            }
+            d.loss_part = reinterpret_cast<float2*>(base + b->L.part + o_part);
+            o_part += (size_t)R * d.loss_tiles * sizeof(float2);
+            d.norm = reinterpret_cast<float*>(base + b->L.norm) + o_stat;
+            d.loss_r = reinterpret_cast<float*>(base + b->L.lr) + o_stat;
+            d.nnz_r = reinterpret_cast<int32_t*>(base + b->L.nnz) + o_stat;
+            o_stat += R;
+            d.dego_part = reinterpret_cast<float*>(base + b->L.dego + o_dego);
+            o_dego += (size_t)d.pix_tiles * 6 * sizeof(float);
+            d.sync = reinterpret_cast<int32_t*>(base + b->L.sync) + 2 * i;
+        }
+        if (!w.flow) {
             d.rho = w.inv_depth;
             d.ego = w.ego6;
             d.drho = w.dinv_depth;
             d.dego = w.dego6;
         }
-        if (w.dflow) {
-            d.dflow = reinterpret_cast<float2*>(w.dflow);
-        } else {
-            d.dflow = reinterpret_cast<float2*>(base + b->L.dflow + o_dflow);
-            o_dflow += HW * sizeof(float2);
-        }
-        d.loss_tiles = tiles_for(HW, 256);
-        d.pix_tiles = tiles_for(HW, 512);
-        d.loss_part = reinterpret_cast<float2*>(base + b->L.part + o_part);
-        o_part += (size_t)R * d.loss_tiles * sizeof(float2);
-        d.norm = reinterpret_cast<float*>(base + b->L.norm) + o_stat;
-        d.loss_r = reinterpret_cast<float*>(base + b->L.lr) + o_stat;
-        d.nnz_r = reinterpret_cast<int32_t*>(base + b->L.nnz) + o_stat;
-        o_stat += R;
-        d.dego_part = reinterpret_cast<float*>(base + b->L.dego + o_dego);
-        o_dego += (size_t)d.pix_tiles * 6 * sizeof(float);
-        d.sync = reinterpret_cast<int32_t*>(base + b->L.sync) + 2 * i;
+        b->stat_lr[i] = d.loss_r;
+        b->stat_nnz[i] = d.nnz_r;
         d.loss = w.loss_out;
         d.dloss = w.dloss;
         cs[i] = chunks;
@@ -667,6 +723,15 @@ TuneKey key_of(const cm_batch* b)
 
 extern "C" {
 
+int cm_window_scratch_query(const cm_camera* cam, const cm_loss_cfg* cfg, size_t* bytes)
+{
+    if (!cam || !bytes || !cfg_ok(cfg) || cam->width < 2 || cam->height < 2 || cam->width > 32767 ||
+        cam->height > 32767)
+        return CM_EINVAL;
+    *bytes = win_scratch((size_t)cam->width * cam->height, refs_of(*cfg)).total;
+    return CM_OK;
+}
+
 int cm_batch_query(const cm_window* wins, int32_t nwin, const cm_loss_cfg* cfg, size_t* bytes)
 {
     if (!wins || nwin < 1 || !bytes || !cfg_ok(cfg)) return CM_EINVAL;
@@ -800,9 +865,8 @@ int cm_batch_autotune(cm_batch* b, void* stream, cm_batch_schedule* chosen)
 int cm_batch_stats(const cm_batch* b, int32_t window, const float** loss_r, const int32_t** nnz_r)
 {
     if (!b || window < 0 || window >= b->nwin) return CM_EINVAL;
-    const int R = refs_of(b->cfg);
-    if (loss_r) *loss_r = reinterpret_cast<const float*>(b->base + b->L.lr) + (size_t)window * R;
-    if (nnz_r) *nnz_r = reinterpret_cast<const int32_t*>(b->base + b->L.nnz) + (size_t)window * R;
+    if (loss_r) *loss_r = b->stat_lr[window];
+    if (nnz_r) *nnz_r = b->stat_nnz[window];
     return CM_OK;
 }
 

@@ -1,0 +1,150 @@
+"""Serving: continuous batching of requests from many event streams
+(cm_server_create, cm_batch_submit / poll / wait).  Each result is the same
+alone and in the mix within the parity tolerances, requests arriving while
+others run are batched together, the HBM budget is enforced with eviction of
+idle streams, and waits are bounded."""
+import numpy as np
+import pytest
+
+from paper_2412_06359_gb300 import _capi as C
+from paper_2412_06359_gb300 import synth
+from tests.gpu_util import GRAD_RTOL_L2, LOSS_RTOL, gpu_lib, rel_l2, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [(96, 72), (160, 120), (128, 96), (200, 150)]
+
+
+def _requests(count, streams, seed):
+    from paper_2412_06359_gb300.serve import HostRequest
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        s = i % streams
+        W, H = SIZES[s % len(SIZES)]
+        n = int(rng.integers(500, 20000))
+        win = synth.depth_window(np.random.default_rng(seed * 1000 + i), W, H, n, nbins=10)
+        out.append(HostRequest.from_window(s, win))
+    return out
+
+
+def _server(budget=2 << 30, **kw):
+    gpu_lib()
+    from paper_2412_06359_gb300.serve import Server
+    return Server(budget, **kw)
+
+
+def _snapshot(req):
+    return float(req.loss[0]), req.drho.copy(), req.dego.copy()
+
+
+def test_results_alone_equal_results_in_the_mix():
+    reqs = _requests(14, 5, seed=3)
+    srv = _server(max_batch=6, lanes=1)
+    alone = []
+    for r in reqs:
+        res = srv.wait(srv.submit(r), 60)
+        assert res.status == 0 and res.batch_size == 1
+        alone.append(_snapshot(r))
+    # all at once: requests arrive while the first ones run on the GPU
+    tickets = [srv.submit(r) for r in reqs]
+    results = [srv.wait(t, 60) for t in tickets]
+    assert all(res.status == 0 for res in results)
+    assert max(res.batch_size for res in results) > 1  # continuous batching took several at once
+    for (la, ra, ea), r in zip(alone, reqs):
+        lm, rm, em = _snapshot(r)
+        assert abs(lm - la) <= LOSS_RTOL * abs(la)
+        assert rel_l2(rm, ra) <= GRAD_RTOL_L2
+        assert rel_l2(em, ea) <= GRAD_RTOL_L2
+    # and against the oracle
+    for r in reqs[:3]:
+        o = run_oracle(r.window)
+        assert abs(float(r.loss[0]) - o["loss"]) <= LOSS_RTOL * o["loss"]
+        assert rel_l2(r.drho, o["dinv_depth"]) <= GRAD_RTOL_L2
+        assert rel_l2(r.dego, o["dego"]) <= GRAD_RTOL_L2
+    st = srv.stats()
+    assert st.completed == 2 * len(reqs) and st.queued == 0
+    srv.close()
+
+
+def test_budget_admission_and_eviction():
+    # a budget that holds the plans and about two streams' state: the server evicts
+    # idle streams and makes requests wait for memory, and every result is right
+    reqs = _requests(10, 5, seed=8)
+    one = C.cm_window_scratch_query(C.cm_camera(200, 150, 1.0, 1.0, 0.0, 0.0),
+                                    C.cm_loss_cfg(10, C.CM_REF_ALL_EDGES, C.CM_SPLAT_ATOMIC, 0, 1e-9))
+    budget = 2 * (one + 2 * 200 * 150 * 4 + 20000 * 12) + (1 << 20)
+    srv = _server(budget=budget, max_batch=4, lanes=2)
+    tickets = [srv.submit(r) for r in reqs]
+    results = [srv.wait(t, 120) for t in tickets]
+    assert all(res.status == 0 for res in results)
+    st = srv.stats()
+    assert st.evictions > 0
+    assert st.pool_peak <= st.pool_bytes
+    for r in reqs[:4]:
+        o = run_oracle(r.window)
+        assert abs(float(r.loss[0]) - o["loss"]) <= LOSS_RTOL * o["loss"]
+    srv.close()
+
+
+def test_request_larger_than_budget_is_refused():
+    srv = _server(budget=64 << 20, max_batch=2, lanes=1)
+    from paper_2412_06359_gb300.serve import HostRequest
+    win = synth.depth_window(np.random.default_rng(1), 1280, 720, 1000, nbins=10)
+    with pytest.raises(C.CMError) as e:
+        srv.submit(HostRequest.from_window(0, win))
+    assert e.value.status == C.CM_ENOMEM
+    srv.close()
+
+
+def test_bounded_wait_times_out_then_completes():
+    srv = _server(max_batch=1, lanes=1)
+    from paper_2412_06359_gb300.serve import HostRequest
+    big = [HostRequest.from_window(i, synth.depth_window(np.random.default_rng(i), 640, 480, 400000, nbins=10))
+           for i in range(3)]
+    tickets = [srv.submit(r) for r in big]
+    with pytest.raises(C.CMError) as e:
+        srv.wait(tickets[-1], 1e-6)
+    assert e.value.status == C.CM_ETIMEOUT
+    for t in tickets:
+        assert srv.wait(t, 120).status == 0
+    with pytest.raises(C.CMError) as e:
+        srv.wait(tickets[0], 1.0)  # consumed
+    assert e.value.status == C.CM_ENOTFOUND
+    srv.close()
+
+
+def test_full_queue_returns_busy():
+    srv = _server(max_batch=1, lanes=1, max_queue=4)
+    from paper_2412_06359_gb300.serve import HostRequest
+    win = synth.depth_window(np.random.default_rng(2), 640, 480, 300000, nbins=10)
+    reqs = [HostRequest.from_window(0, win) for _ in range(40)]
+    busy = 0
+    tickets = []
+    for r in reqs:
+        try:
+            tickets.append(srv.submit(r))
+        except C.CMError as e:
+            assert e.status == C.CM_EBUSY
+            busy += 1
+    assert busy > 0
+    for t in tickets:
+        assert srv.wait(t, 120).status == 0
+    srv.close()
+
+
+def test_poll_is_non_blocking():
+    srv = _server(max_batch=4, lanes=2)
+    reqs = _requests(4, 2, seed=12)
+    tickets = [srv.submit(r) for r in reqs]
+    pending = set(tickets)
+    import time
+    t0 = time.time()
+    while pending and time.time() - t0 < 60:
+        for t in list(pending):
+            r = srv.poll(t)
+            if r is not None:
+                assert r.status == 0 and r.t_done >= r.t_start >= r.t_submit
+                pending.discard(t)
+    assert not pending
+    srv.close()
