@@ -45,6 +45,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="bound of the CPU oracle sample")
+    ap.add_argument("--serve", action="store_true", help="run the serving workload instead (one line per rate)")
+    ap.add_argument("--serve-scales", default="0.25,0.5,1.0", help="arrival-rate multipliers of 100 Hz per stream")
+    ap.add_argument("--serve-seconds", type=float, default=1.0)
+    ap.add_argument("--serve-pool", type=int, default=2, help="pre-generated windows per stream")
     return ap.parse_args()
 
 
@@ -441,9 +445,107 @@ def run_e2e(batch, args, stream):
             "d2h_bytes_per_step": int(d2h), "ms_per_step": ms}
 
 
+def run_serve(args):
+    """Serving workload: 32 streams (resolutions cycling 346x260 / 640x480 /
+    1280x720), Poisson arrivals at 100 Hz per stream scaled by --serve-scales,
+    event counts log-uniform in [10k, 2M], 10 bins, loss + gradient per request,
+    a 40 GB HBM budget.  Every stream cycles through --serve-pool pre-generated
+    windows held in pinned host memory.  Prints one JSON line per scale, plus the
+    plain path (one request at a time, no batching) on the same arrivals."""
+    import torch
+
+    from paper_2412_06359_gb300 import _capi as C
+    from paper_2412_06359_gb300 import build, synth
+    from paper_2412_06359_gb300.serve import HostRequest, Server
+    build.build()
+    C.lib()
+    torch.cuda.init()
+
+    def pinned(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+
+    streams = 32
+    pools = []
+    for s in range(streams):
+        rng = synth.rng_for(5, s)
+        W, H = synth.SERVE_RESOLUTIONS[s % len(synth.SERVE_RESOLUTIONS)]
+        reqs = []
+        for _ in range(args.serve_pool):
+            win = synth.depth_window(rng, W, H, synth.log_uniform_count(rng, 1e4, 2e6), nbins=10)
+            r = HostRequest.from_window(s, win)
+            for f in ("x", "y", "t", "p", "rho", "ego", "loss", "drho", "dego"):
+                setattr(r, f, pinned(getattr(r, f)))
+            reqs.append(r)
+        pools.append(reqs)
+
+    def arrivals(scale, seconds, seed=77):
+        rng = np.random.default_rng(seed)
+        out = []
+        for s in range(streams):
+            t = rng.exponential(1.0 / (100.0 * scale))
+            k = 0
+            while t < seconds:
+                out.append((t, s, k % args.serve_pool))
+                k += 1
+                t += rng.exponential(1.0 / (100.0 * scale))
+        return sorted(out)
+
+    def replay(srv, arr):
+        # warm up: one request per stream (allocates its state, captures the graphs)
+        for s in range(streams):
+            srv.wait(srv.submit(pools[s][0]), 120)
+        t0 = time.perf_counter()
+        tickets = []
+        for ta, s, k in arr:
+            dt = t0 + ta - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            while True:
+                try:
+                    tickets.append((srv.submit(pools[s][k]), pools[s][k].x.shape[0]))
+                    break
+                except C.CMError as e:
+                    if e.status != C.CM_EBUSY:
+                        raise
+                    time.sleep(1e-4)
+        res = [(srv.wait(t, 600), n) for t, n in tickets]
+        lat = np.array([1e3 * (r.t_done - r.t_submit) for r, _ in res])
+        first = min(r.t_submit for r, _ in res)
+        last = max(r.t_done for r, _ in res)
+        ev = sum(n for _, n in res)
+        sizes = [r.batch_size for r, _ in res]
+        return {"requests": len(res), "events": int(ev), "throughput": ev / (last - first) / 1e6,
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "mean_batch": float(np.mean(sizes)), "offered_mev_s": ev / arr[-1][0] / 1e6 if arr else 0.0,
+                "stats": {k: int(getattr(srv.stats(), k)) for k in ("batches", "evictions", "memory_waits",
+                                                                     "pool_peak")}}
+
+    budget = 40 << 30
+    for scale in [float(x) for x in args.serve_scales.split(",")]:
+        arr = arrivals(scale, args.serve_seconds)
+        srv = Server(budget, max_batch=8, lanes=3)
+        batched = replay(srv, arr)
+        srv.close()
+        plain = None
+        if not args.no_plain:
+            srv = Server(budget, max_batch=1, lanes=1)
+            plain = replay(srv, arr)
+            srv.close()
+        line = {"metric": "serving: CM loss+grad Mev/s and p50/p99 request latency", "unit": "Mev/s",
+                "value": batched["throughput"], "p50_ms": batched["p50_ms"], "p99_ms": batched["p99_ms"],
+                "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "serve32_mixed_res_poisson100hz", "rate_scale": scale,
+                           "seconds": args.serve_seconds, "streams": streams, "pool_per_stream": args.serve_pool,
+                           "max_batch": 8, "lanes": 3, "hbm_budget_gb": 40},
+                "batched": batched, "plain": plain}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.serve:
+        run_serve(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
