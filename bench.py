@@ -57,6 +57,29 @@ def dist_env():
 
 
 # ---------------------------------------------------------------------------
+# several GPUs: replicas.  Windows are independent, so every rank evaluates its
+# own windows (weak scaling) and the only collective is the timing reduction.
+
+
+def first_window_of(rank: int, windows: int) -> int:
+    """Rank r evaluates windows r*windows .. (r+1)*windows - 1 of the seeded sequence."""
+    return rank * windows
+
+
+def reduce_over_ranks(total_ms: float, events: int, device):
+    """(max over ranks of the timed region, sum over ranks of the events)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return total_ms, events
+    t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    e = torch.tensor([float(events)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(e, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(round(e.item()))
+
+
+# ---------------------------------------------------------------------------
 # GPU clocks during the timed region
 
 
@@ -288,7 +311,7 @@ def run_ours(args):
     C.lib()
 
     # weak scaling: every rank evaluates its own 64 windows
-    wins = synth.batch_windows(args.windows, first=rank * args.windows)
+    wins = synth.batch_windows(args.windows, first=first_window_of(rank, args.windows))
     batch = Batch(wins, dev)
     hw = wins[0].cam.width * wins[0].cam.height
     R = wins[0].nbins + 1
@@ -317,15 +340,13 @@ def run_ours(args):
     launches = C.cm_launch_count() - launches0
     step_ms = [ev_steps[k].elapsed_time(ev_steps[k + 1]) for k in range(args.steps)]
     total_ms = ev_steps[0].elapsed_time(ev_steps[-1])
+    total_ms, job_events = reduce_over_ranks(total_ms, batch.events, dev)
     if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
         dist.barrier()
     clocks = clk.summary()
     prof = C.cm_profile_collect()
     ms_per_step = total_ms / args.steps
-    value = world * batch.events / (ms_per_step * 1e-3) / 1e6
+    value = job_events / (ms_per_step * 1e-3) / 1e6
 
     # ---- roofline of the dominant kernel ----
     peak, peak_kind = measured_peak()
