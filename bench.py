@@ -408,7 +408,8 @@ def run_ours(args):
             "config": {"workload": WORKLOAD, "windows": len(wins), "events_per_step": batch.events,
                        "sensor": "640x480", "bins": wins[0].nbins, "refs": R, "splat": "atomic",
                        "path": "batched plan replayed from a CUDA graph",
-                       "schedule": {"chains": schedule[0], "windows_per_kernel": schedule[1]},
+                       "schedule": {"chains": schedule[0], "windows_per_kernel": schedule[1],
+                                    "tile_grouping": bool(schedule[2])},
                        "l2": "per-step IWE working set %.2f GB > L2 (no flush needed)" % (len(wins) * R * hw * 16 / 1e9)},
             "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
             "plain": plain, "roofline": roof, "roofline_iwe": roof_iwe, "cpu_baseline": cpu, "e2e": e2e,

@@ -248,11 +248,16 @@ int cm_batch_run(cm_batch* plan, void* stream);
  * graph covers one group) and the groups run on `chains` concurrent chains of
  * the graph, each chain one group after another; group 0 (with chains 1) puts
  * every window in each kernel.  Few windows in flight keep their images of
- * warped events in L2; several chains overlap each other's tails.  Default:
- * chains 2, group 1. */
+ * warped events in L2; several chains overlap each other's tails.  With `bin`
+ * the events of each window are first grouped by 32x32-pixel tile (two extra
+ * kernels), so that a block's events share a compact region whose flow the
+ * splat reads from shared memory; windows that do not fit the plan's grouping
+ * memory (sized for the windows it was created with) stay ungrouped.
+ * Default: chains 2, group 1, bin 0. */
 typedef struct {
     int32_t chains;  /* 1..8 */
     int32_t group;   /* windows per kernel; 0 = all */
+    int32_t bin;     /* 1: group events by tile first */
 } cm_batch_schedule;
 int cm_batch_set_schedule(cm_batch* plan, const cm_batch_schedule* schedule);
 int cm_batch_get_schedule(const cm_batch* plan, cm_batch_schedule* schedule);

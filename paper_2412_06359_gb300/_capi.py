@@ -50,7 +50,7 @@ class cm_window(ctypes.Structure):
 
 
 class cm_batch_schedule(ctypes.Structure):
-    _fields_ = [("chains", ctypes.c_int32), ("group", ctypes.c_int32)]
+    _fields_ = [("chains", ctypes.c_int32), ("group", ctypes.c_int32), ("bin", ctypes.c_int32)]
 
 
 class cm_server_cfg(ctypes.Structure):
@@ -243,21 +243,21 @@ def cm_batch_run(plan: int, stream: int) -> None:
     _check(lib().cm_batch_run(plan, stream), "cm_batch_run")
 
 
-def cm_batch_set_schedule(plan: int, chains: int, group: int) -> None:
-    s = cm_batch_schedule(chains, group)
+def cm_batch_set_schedule(plan: int, chains: int, group: int, bin: int = 0) -> None:
+    s = cm_batch_schedule(chains, group, bin)
     _check(lib().cm_batch_set_schedule(plan, ctypes.byref(s)), "cm_batch_set_schedule")
 
 
-def cm_batch_get_schedule(plan: int) -> tuple[int, int]:
+def cm_batch_get_schedule(plan: int) -> tuple[int, int, int]:
     s = cm_batch_schedule()
     _check(lib().cm_batch_get_schedule(plan, ctypes.byref(s)), "cm_batch_get_schedule")
-    return s.chains, s.group
+    return s.chains, s.group, s.bin
 
 
-def cm_batch_autotune(plan: int, stream: int) -> tuple[int, int]:
+def cm_batch_autotune(plan: int, stream: int) -> tuple[int, int, int]:
     s = cm_batch_schedule()
     _check(lib().cm_batch_autotune(plan, stream, ctypes.byref(s)), "cm_batch_autotune")
-    return s.chains, s.group
+    return s.chains, s.group, s.bin
 
 
 def cm_batch_stats(plan: int, window: int) -> tuple[int, int]:

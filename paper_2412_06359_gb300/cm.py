@@ -282,13 +282,16 @@ class BatchPlan:
     def run(self):
         C.cm_batch_run(self.handle, stream_handle(self.buf.device))
 
-    def set_schedule(self, chains: int, group: int):
-        C.cm_batch_set_schedule(self.handle, chains, group)
+    def set_schedule(self, chains: int, group: int, bin: int = 0):
+        """chains: concurrent kernel chains; group: windows per kernel (0: one
+        kernel over every window); bin: 1 to group each window's events by
+        32x32 pixel tile before the splat."""
+        C.cm_batch_set_schedule(self.handle, chains, group, bin)
 
-    def schedule(self) -> tuple[int, int]:
+    def schedule(self) -> tuple[int, int, int]:
         return C.cm_batch_get_schedule(self.handle)
 
-    def autotune(self) -> tuple[int, int]:
+    def autotune(self) -> tuple[int, int, int]:
         """Pick the fastest schedule for these windows (runs the plan several times)."""
         return C.cm_batch_autotune(self.handle, stream_handle(self.buf.device))
 

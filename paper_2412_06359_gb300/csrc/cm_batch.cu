@@ -20,6 +20,7 @@
 // cm_batch_set_windows rewrites the staging copy and the next cm_batch_run
 // uploads it before the replay.  With group 0 the graph stays valid for any
 // windows that fit the plan; otherwise it is captured again for the new set.
+#include <climits>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -81,19 +82,256 @@ __global__ void __launch_bounds__(256) k_prep_batch(const BatchHdr* h, const Win
         const int w = find_i(pstart, w0, w1, tile);
         const Win d = tab[w];
         const int ti = tile - pstart[w];
-        if (ti == 0 && threadIdx.x < 2) d.sync[threadIdx.x] = 0;
+        if (ti == 0 && threadIdx.x < 3) d.sync[threadIdx.x] = 0;
         const size_t HW = plane_size(d);
+        const size_t stride = (size_t)d.pix_tiles * blockDim.x;
         float2* flow = const_cast<float2*>(d.flow);
-        for (size_t i = (size_t)ti * blockDim.x + threadIdx.x; i < HW; i += (size_t)d.pix_tiles * blockDim.x) {
+        float m = 0.0f;  // max |flow component| over this tile's pixels (the halo of the flow boxes)
+        for (size_t i = (size_t)ti * blockDim.x + threadIdx.x; i < HW; i += stride) {
             for (int r = 0; r < d.R; ++r) d.iwe[(size_t)r * HW + i] = z4;
             d.dflow[i] = make_float2(0.f, 0.f);
+            float2 f;
             if (d.rho) {
                 const int v = (int)(i / d.W), u = (int)(i - (size_t)v * d.W);
-                flow[i] = motion_field(u, v, __ldg(d.rho + i), d.ego, d.fx, d.fy, d.cx, d.cy, d.dt);
+                f = motion_field(u, v, __ldg(d.rho + i), d.ego, d.fx, d.fy, d.cx, d.cy, d.dt);
+                flow[i] = f;
+            } else {
+                f = __ldg(d.flow + i);
             }
+            m = fmaxf(m, fmaxf(fabsf(f.x), fabsf(f.y)));
+        }
+        if (d.tile_cnt) {
+            const int nt = d.ntx * d.nty;
+            for (int i = ti * blockDim.x + threadIdx.x; i <= nt; i += (int)stride) {
+                d.tile_cnt[i] = 0;
+                if (i < nt) d.tile_cur[i] = 0;
+            }
+        }
+        // the tile's maximum, written where the gradient pass later keeps its partials
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        __shared__ float sm[32];
+        if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float a = 0.0f;
+            for (int i = 0; i < (int)(blockDim.x >> 5); ++i) a = fmaxf(a, sm[i]);
+            d.dego_part[(size_t)ti * 6] = a;
+        }
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ int tile_of(const Win& d, int x, int y)
+{
+    const int tx = min(max(x, 0), d.W - 1) / kBinTile, ty = min(max(y, 0), d.H - 1) / kBinTile;
+    return ty * d.ntx + tx;
+}
+
+// block-wide exclusive scan (any blockDim multiple of 32 up to 1024); returns
+// the block total through *total
+__device__ __forceinline__ int block_scan_excl(int v, int* total)
+{
+    __shared__ int ws[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int t = lane < nw ? ws[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        ws[lane] = t;
+    }
+    __syncthreads();
+    const int before = (w > 0 ? ws[w - 1] : 0) + x - v;
+    *total = ws[nw - 1];
+    __syncthreads();
+    return before;
+}
+
+// Binning works on super-chunks of kSuperChunk events of one window: a block
+// counts its super-chunk's events per tile in shared memory and touches the
+// global counters once per tile, not once per event.
+constexpr int kSuperChunk = 4096;
+constexpr int kMaxBinTiles = 2048;  // windows with more tiles are not grouped
+
+__device__ __forceinline__ void count_tiles(const Win& d, long long e0, long long e1, int* hist)
+{
+    const int nt = d.ntx * d.nty;
+    for (int i = threadIdx.x; i < nt; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    for (long long k = e0 + threadIdx.x; k < e1; k += blockDim.x) atomicAdd(hist + tile_of(d, d.x[k], d.y[k]), 1);
+    __syncthreads();
+}
+
+// binning, pass 1: events per tile; the block finishing a window's last
+// super-chunk turns the counts into tile starts and the cursors, and sets the
+// halo of the window's flow boxes (the largest flow component, at most 8 px:
+// samples outside a box read global memory)
+__global__ void __launch_bounds__(kEventThreads) k_bin_count_batch(const BatchHdr* h, const Win* tab,
+                                                                    const long long* sstart, int w0, int w1)
+{
+    __shared__ int hist[kMaxBinTiles];
+    w1 = clamp_end(h, w1);
+    if (w0 >= w1) return;
+    const long long cb = sstart[w0], ce = sstart[w1];
+    for (long long c = cb + blockIdx.x; c < ce; c += gridDim.x) {
+        const int w = find_ll(sstart, w0, w1, c);
+        const Win d = tab[w];
+        if (!d.tile_cnt) continue;
+        const long long e0 = (c - sstart[w]) * kSuperChunk;
+        const long long e1 = e0 + kSuperChunk < d.n ? e0 + kSuperChunk : d.n;
+        count_tiles(d, e0, e1, hist);
+        const int nt0 = d.ntx * d.nty;
+        for (int i = threadIdx.x; i < nt0; i += blockDim.x)
+            if (hist[i]) atomicAdd(d.tile_cnt + i, hist[i]);
+        const int chunks = (int)((d.n + kSuperChunk - 1) / kSuperChunk);
+        if (last_tile_done(d.sync + 2, chunks)) {
+            const int nt = d.ntx * d.nty;
+            int carry = 0;
+            for (int base = 0; base < nt; base += blockDim.x) {
+                const int i = base + threadIdx.x;
+                const int v = i < nt ? d.tile_cnt[i] : 0;
+                int tot = 0;
+                const int ex = block_scan_excl(v, &tot);
+                if (i < nt) {
+                    d.tile_cnt[i] = carry + ex;
+                    d.tile_cur[i] = carry + ex;
+                }
+                carry += tot;
+            }
+            float m = 0.0f;
+            for (int i = threadIdx.x; i < d.pix_tiles; i += blockDim.x) m = fmaxf(m, d.dego_part[(size_t)i * 6]);
+            __shared__ float sm[32];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+            if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                float a = 0.0f;
+                for (int i = 0; i < (int)(blockDim.x >> 5); ++i) a = fmaxf(a, sm[i]);
+                d.tile_cnt[nt] = carry;
+                d.sync[3] = (int)fminf(ceilf(a) + 2.0f, 8.0f);
+            }
+            __syncthreads();
         }
     }
 }
+
+// binning, pass 2: a block reserves, per tile, one range of slots for its
+// super-chunk's events (one global atomic per tile) and places them there
+__global__ void __launch_bounds__(kEventThreads) k_bin_scatter_batch(const BatchHdr* h, const Win* tab,
+                                                                      const long long* sstart, int w0, int w1)
+{
+    __shared__ int hist[kMaxBinTiles];
+    w1 = clamp_end(h, w1);
+    if (w0 >= w1) return;
+    const long long cb = sstart[w0], ce = sstart[w1];
+    for (long long c = cb + blockIdx.x; c < ce; c += gridDim.x) {
+        const int w = find_ll(sstart, w0, w1, c);
+        const Win d = tab[w];
+        if (!d.tile_cnt) continue;
+        const long long e0 = (c - sstart[w]) * kSuperChunk;
+        const long long e1 = e0 + kSuperChunk < d.n ? e0 + kSuperChunk : d.n;
+        count_tiles(d, e0, e1, hist);
+        const int nt = d.ntx * d.nty;
+        for (int i = threadIdx.x; i < nt; i += blockDim.x)
+            if (hist[i]) hist[i] = atomicAdd(d.tile_cur + i, hist[i]);  // the block's first slot in tile i
+        __syncthreads();
+        for (long long k = e0 + threadIdx.x; k < e1; k += blockDim.x) {
+            const int16_t x = d.x[k], y = d.y[k];
+            const int pos = atomicAdd(hist + tile_of(d, x, y), 1);
+            d.rx[pos] = x;
+            d.ry[pos] = y;
+            d.rt[pos] = __ldg(d.t + k);
+            d.rp[pos] = d.p[k];
+        }
+        __syncthreads();
+    }
+}
+
+// The flow box of one chunk of grouped events: their bounding box grown by the
+// window's halo, clipped to the image, loaded into shared memory when it holds
+// at most `cap` pixels (with a zeroed gradient accumulator behind it when
+// `grad`).  Called by every thread of the block; ends with __syncthreads.
+__device__ __forceinline__ void load_box(const Win& d, long long k, float2* sm, int cap, bool grad, FlowBox& fb)
+{
+    __shared__ int bb[4];
+    __shared__ int red[4][32];
+    const bool valid = k < d.n;
+    int x = 0, y = 0;
+    if (valid) {
+        x = min(max((int)d.x[k], 0), d.W - 1);
+        y = min(max((int)d.y[k], 0), d.H - 1);
+    }
+    int v[4] = {valid ? x : INT_MAX, valid ? y : INT_MAX, valid ? x : -1, valid ? y : -1};
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v[0] = min(v[0], __shfl_xor_sync(0xffffffffu, v[0], o));
+        v[1] = min(v[1], __shfl_xor_sync(0xffffffffu, v[1], o));
+        v[2] = max(v[2], __shfl_xor_sync(0xffffffffu, v[2], o));
+        v[3] = max(v[3], __shfl_xor_sync(0xffffffffu, v[3], o));
+    }
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0)
+        for (int q = 0; q < 4; ++q) red[q][wi] = v[q];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int a = INT_MAX, b = INT_MAX, c = -1, e = -1;
+        for (int i = 0; i < nw; ++i) {
+            a = min(a, red[0][i]);
+            b = min(b, red[1][i]);
+            c = max(c, red[2][i]);
+            e = max(e, red[3][i]);
+        }
+        const int hl = d.sync[3];
+        bb[0] = max(a - hl, 0);
+        bb[1] = max(b - hl, 0);
+        bb[2] = c < 0 ? -1 : min(c + hl + 1, d.W - 1);
+        bb[3] = e < 0 ? -1 : min(e + hl + 1, d.H - 1);
+    }
+    __syncthreads();
+    const int x0 = bb[0], y0 = bb[1], bw = bb[2] - x0 + 1, bh = bb[3] - y0 + 1;
+    if (bw <= 0 || bh <= 0 || bw * bh > cap || d.nfb != 1) {
+        fb = FlowBox();
+        return;
+    }
+    const int n = bw * bh;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int yy = i / bw, xx = i - yy * bw;
+        sm[i] = __ldg(d.flow + (size_t)(y0 + yy) * d.W + x0 + xx);
+        if (grad) sm[cap + i] = make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    fb.s = sm;
+    fb.g = grad ? sm + cap : nullptr;
+    fb.x0 = x0;
+    fb.y0 = y0;
+    fb.bw = bw;
+    fb.bh = bh;
+}
+
+// events of a grouped window are read in tile order
+__device__ __forceinline__ void use_grouped(Win& d)
+{
+    if (d.tile_cnt) {
+        d.x = d.rx;
+        d.y = d.ry;
+        d.t = d.rt;
+        d.p = d.rp;
+    }
+}
+
+constexpr int kBoxCap = 4096;  // pixels of a flow box (32 KB of float2)
 
 template <int MAXB>
 __global__ void __launch_bounds__(kEventThreads) k_splat_batch(const BatchHdr* h, const Win* tab,
@@ -101,12 +339,17 @@ __global__ void __launch_bounds__(kEventThreads) k_splat_batch(const BatchHdr* h
 {
     w1 = clamp_end(h, w1);
     if (w0 >= w1) return;
+    extern __shared__ float2 box_mem[];
     const long long cb = cstart[w0], ce = cstart[w1];
     for (long long c = cb + blockIdx.x; c < ce; c += gridDim.x) {
         const int w = find_ll(cstart, w0, w1, c);
-        const Win d = tab[w];
+        Win d = tab[w];
+        use_grouped(d);
         const long long k = (c - cstart[w]) * kEventThreads + threadIdx.x;
-        if (k < d.n) splat_event<MAXB>(d, k);
+        FlowBox fb;
+        if (d.tile_cnt) load_box(d, k, box_mem, kBoxCap, false, fb);
+        if (k < d.n) splat_event<MAXB>(d, k, RedSink(), fb);
+        __syncthreads();  // the next chunk reloads the box
     }
 }
 
@@ -119,8 +362,12 @@ __global__ void __launch_bounds__(kEventThreads) k_adjoint_batch(const BatchHdr*
     const long long cb = cstart[w0], ce = cstart[w1];
     for (long long c = cb + blockIdx.x; c < ce; c += gridDim.x) {
         const int w = find_ll(cstart, w0, w1, c);
-        const Win d = tab[w];
+        Win d = tab[w];
+        use_grouped(d);
         const long long k = (c - cstart[w]) * kEventThreads + threadIdx.x;
+        // grouped events only: no shared-memory box here (measured on GB300: the
+        // per-chunk barriers of a box cost more than the global traffic it saves
+        // on this kernel's long per-event dependency chains)
         if (k < d.n) adjoint_event<MAXB>(d, k, __ldg(d.dloss));
     }
 }
@@ -170,9 +417,11 @@ using cmk::Win;
 
 namespace {
 
-constexpr int kPhases = 5;
-const char* const kPhaseName[kPhases] = {"k_prep_batch", "k_splat_batch", "k_loss_batch", "k_adjoint_batch",
+constexpr int kPhases = 7;
+const char* const kPhaseName[kPhases] = {"k_prep_batch",  "k_bin_count_batch", "k_bin_scatter_batch",
+                                         "k_splat_batch", "k_loss_batch",      "k_adjoint_batch",
                                          "k_grad_batch"};
+constexpr int kSyncInts = 4;  // per window: loss, gradient and binning counters, halo
 constexpr int kMaxChains = 8;
 
 size_t up256(size_t v) { return (v + 255) / 256 * 256; }
@@ -189,7 +438,7 @@ int refs_of(const cm_loss_cfg& c) { return c.ref_mode == CM_REF_END ? 1 : c.nbin
 
 // device bytes of the per-window slabs for a list of windows
 struct Need {
-    size_t iwe, flow, dflow, part, stat, dego;
+    size_t iwe, flow, dflow, part, stat, dego, bins;
 };
 
 bool window_ok(const cm_window& w)
@@ -216,6 +465,8 @@ bool cfg_ok(const cm_loss_cfg* cfg)
     return cfg->store_warps == 0 && std::isfinite(cfg->eps);
 }
 
+size_t bin_bytes(int W, int H, int64_t n);
+
 Need need_of(const cm_window* wins, int32_t nwin, const cm_loss_cfg& cfg)
 {
     Need n{};
@@ -229,8 +480,18 @@ Need need_of(const cm_window* wins, int32_t nwin, const cm_loss_cfg& cfg)
         n.part += (size_t)R * tiles_for(HW, 256) * sizeof(float2);
         n.stat += (size_t)R;
         n.dego += (size_t)tiles_for(HW, 512) * 6 * sizeof(float);
+        n.bins += bin_bytes(wins[i].cam.width, wins[i].cam.height, wins[i].ev.n);
     }
     return n;
+}
+
+// device bytes of the spatial binning of a window: tile starts and cursors,
+// and the events grouped by tile
+size_t bin_bytes(int W, int H, int64_t n)
+{
+    const size_t nt = (size_t)((W + cmk::kBinTile - 1) / cmk::kBinTile) * ((H + cmk::kBinTile - 1) / cmk::kBinTile);
+    return up256((2 * nt + 1) * sizeof(int32_t)) + 2 * up256(2 * (size_t)n) + up256(4 * (size_t)n) +
+           up256((size_t)n);
 }
 
 // a window's own scratch: the per-window buffers, one after another
@@ -259,14 +520,14 @@ WinScratch win_scratch(size_t HW, int R)
     s.dego = o;
     o = up256(o + (size_t)tiles_for(HW, 512) * 6 * sizeof(float));
     s.sync = o;
-    o = up256(o + 2 * sizeof(int32_t));
+    o = up256(o + kSyncInts * sizeof(int32_t));
     s.total = o;
     return s;
 }
 
 struct Layout {
-    size_t hdr, tab, cstart, lstart, pstart, table_end;  // the uploaded region [0, table_end)
-    size_t iwe, flow, dflow, part, norm, lr, nnz, dego, sync, total;
+    size_t hdr, tab, cstart, sstart, lstart, pstart, table_end;  // the uploaded region [0, table_end)
+    size_t iwe, flow, dflow, part, norm, lr, nnz, dego, sync, bins, total;
 };
 
 Layout layout_of(int cap, const Need& n)
@@ -278,6 +539,8 @@ Layout layout_of(int cap, const Need& n)
     L.tab = o;
     o += (size_t)cap * sizeof(Win);
     L.cstart = o = (o + 15) / 16 * 16;
+    o += (size_t)(cap + 1) * sizeof(long long);
+    L.sstart = o;
     o += (size_t)(cap + 1) * sizeof(long long);
     L.lstart = o;
     o += (size_t)(cap + 1) * sizeof(int);
@@ -301,7 +564,9 @@ Layout layout_of(int cap, const Need& n)
     L.dego = o;
     o = up256(o + n.dego);
     L.sync = o;
-    o = up256(o + (size_t)cap * 2 * sizeof(int32_t));
+    o = up256(o + (size_t)cap * kSyncInts * sizeof(int32_t));
+    L.bins = o;
+    o = up256(o + n.bins);
     L.total = o;
     return L;
 }
@@ -336,8 +601,9 @@ struct cm_batch {
     std::vector<int> ltiles, ptiles;   // per window, host copy
     std::vector<const float*> stat_lr; // per window: device L_r and N_nz of the last run
     std::vector<const int32_t*> stat_nnz;
+    std::vector<cm_window> last;       // the windows of the last staging (re-staged when grouping changes)
     int grid_events = 0, grid_tiles = 0;
-    cm_batch_schedule sched{2, 1};
+    cm_batch_schedule sched{2, 1, 0};
     bool stale = true;                 // the graph must be (re)captured before the next replay
     cudaStream_t streams[kMaxChains] = {};
     cudaEvent_t fork = nullptr;
@@ -368,11 +634,13 @@ int stage_windows(cm_batch* b, const cm_window* wins, int32_t nwin)
     BatchHdr* h = reinterpret_cast<BatchHdr*>(s + b->L.hdr);
     Win* tab = reinterpret_cast<Win*>(s + b->L.tab);
     long long* cs = reinterpret_cast<long long*>(s + b->L.cstart);
+    long long* ss = reinterpret_cast<long long*>(s + b->L.sstart);
+    long long supers = 0;
     int* ls = reinterpret_cast<int*>(s + b->L.lstart);
     int* ps = reinterpret_cast<int*>(s + b->L.pstart);
     const int R = refs_of(b->cfg);
     const float eps = b->cfg.eps > 0.0f ? b->cfg.eps : 1e-9f;
-    size_t o_iwe = 0, o_flow = 0, o_dflow = 0, o_part = 0, o_stat = 0, o_dego = 0;
+    size_t o_iwe = 0, o_flow = 0, o_dflow = 0, o_part = 0, o_stat = 0, o_dego = 0, o_bins = 0;
     long long chunks = 0;
     int lt_total = 0, pt_total = 0;
     char* base = b->base;
@@ -442,7 +710,27 @@ int stage_windows(cm_batch* b, const cm_window* wins, int32_t nwin)
             o_stat += R;
             d.dego_part = reinterpret_cast<float*>(base + b->L.dego + o_dego);
             o_dego += (size_t)d.pix_tiles * 6 * sizeof(float);
-            d.sync = reinterpret_cast<int32_t*>(base + b->L.sync) + 2 * i;
+            d.sync = reinterpret_cast<int32_t*>(base + b->L.sync) + kSyncInts * i;
+            // events grouped by 32x32 tile, while the plan's binning memory lasts
+            const size_t bb = bin_bytes(d.W, d.H, d.n);
+            const int ntiles = ((d.W + cmk::kBinTile - 1) / cmk::kBinTile) * ((d.H + cmk::kBinTile - 1) / cmk::kBinTile);
+            if (b->sched.bin && d.n > 0 && ntiles <= cmk::kMaxBinTiles && o_bins + bb <= b->capn.bins) {
+                char* q = base + b->L.bins + o_bins;
+                o_bins += bb;
+                d.ntx = (d.W + cmk::kBinTile - 1) / cmk::kBinTile;
+                d.nty = (d.H + cmk::kBinTile - 1) / cmk::kBinTile;
+                const size_t nt = (size_t)d.ntx * d.nty;
+                d.tile_cnt = reinterpret_cast<int32_t*>(q);
+                d.tile_cur = d.tile_cnt + nt + 1;
+                q += up256((2 * nt + 1) * sizeof(int32_t));
+                d.rx = reinterpret_cast<int16_t*>(q);
+                q += up256(2 * (size_t)d.n);
+                d.ry = reinterpret_cast<int16_t*>(q);
+                q += up256(2 * (size_t)d.n);
+                d.rt = reinterpret_cast<float*>(q);
+                q += up256(4 * (size_t)d.n);
+                d.rp = reinterpret_cast<int8_t*>(q);
+            }
         }
         if (!w.flow) {
             d.rho = w.inv_depth;
@@ -455,6 +743,8 @@ int stage_windows(cm_batch* b, const cm_window* wins, int32_t nwin)
         d.loss = w.loss_out;
         d.dloss = w.dloss;
         cs[i] = chunks;
+        ss[i] = supers;
+        supers += (w.ev.n + cmk::kSuperChunk - 1) / cmk::kSuperChunk;
         ls[i] = lt_total;
         ps[i] = pt_total;
         b->chunks[i] = (w.ev.n + cmk::kEventThreads - 1) / cmk::kEventThreads;
@@ -465,6 +755,7 @@ int stage_windows(cm_batch* b, const cm_window* wins, int32_t nwin)
         pt_total += b->ptiles[i];
     }
     cs[nwin] = chunks;
+    ss[nwin] = supers;
     ls[nwin] = lt_total;
     ps[nwin] = pt_total;
     h->nwin = nwin;
@@ -473,6 +764,7 @@ int stage_windows(cm_batch* b, const cm_window* wins, int32_t nwin)
     h->total_ptiles = pt_total;
     h->iwe_f4 = (long long)(o_iwe / sizeof(float4));
     b->nwin = nwin;
+    if (b->last.data() != wins) b->last.assign(wins, wins + nwin);
     b->dirty = true;
     if (b->sched.group > 0) b->stale = true;  // the graph's window groups depend on the windows
     return CM_OK;
@@ -517,14 +809,21 @@ std::vector<Group> make_groups(const cm_batch* b)
     return g;
 }
 
+// dynamic shared memory of the event kernels: one flow box (splat), a flow box
+// and its gradient accumulator (adjoint)
+constexpr size_t kSplatSmem = cmk::kBoxCap * sizeof(float2);
+constexpr size_t kAdjointSmem = 0;
+
 template <int MAXB>
 void enqueue_event_kernel(cm_batch* b, cudaStream_t s, int which, int grid, int w0, int w1)
 {
     const BatchHdr* h = reinterpret_cast<const BatchHdr*>(b->base + b->L.hdr);
     const Win* tab = reinterpret_cast<const Win*>(b->base + b->L.tab);
     const long long* cs = reinterpret_cast<const long long*>(b->base + b->L.cstart);
-    if (which == 0) cmk::k_splat_batch<MAXB><<<grid, cmk::kEventThreads, 0, s>>>(h, tab, cs, w0, w1);
-    else cmk::k_adjoint_batch<MAXB><<<grid, cmk::kEventThreads, 0, s>>>(h, tab, cs, w0, w1);
+    if (which == 0)
+        cmk::k_splat_batch<MAXB><<<grid, cmk::kEventThreads, kSplatSmem, s>>>(h, tab, cs, w0, w1);
+    else
+        cmk::k_adjoint_batch<MAXB><<<grid, cmk::kEventThreads, kAdjointSmem, s>>>(h, tab, cs, w0, w1);
 }
 
 void enqueue_event(cm_batch* b, cudaStream_t s, int which, int grid, int w0, int w1)
@@ -571,6 +870,7 @@ int capture(cm_batch* b)
     const Win* tab = reinterpret_cast<const Win*>(b->base + b->L.tab);
     const int* ls = reinterpret_cast<const int*>(b->base + b->L.lstart);
     const int* ps = reinterpret_cast<const int*>(b->base + b->L.pstart);
+    const long long* ss = reinterpret_cast<const long long*>(b->base + b->L.sstart);
     cudaStream_t s0 = b->streams[0];
     if (cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return CM_ECUDA;
     bool ok = true;
@@ -582,6 +882,7 @@ int capture(cm_batch* b)
     for (const Group& g : groups) {
         cudaStream_t s = b->streams[g.chain];
         for (int ph = 0; ph < kPhases && ok; ++ph) {
+            if (!b->sched.bin && (ph == 1 || ph == 2)) continue;  // no grouping kernels
             ProfNode p{ph, nullptr, nullptr, nullptr, nullptr};
             ok = cudaEventCreate(&p.ea) == cudaSuccess && cudaEventCreate(&p.eb) == cudaSuccess;
             if (!ok) break;
@@ -590,12 +891,18 @@ int capture(cm_batch* b)
             const int gt = wide ? b->grid_tiles : clampi(g.ptiles, 1, b->grid_tiles);
             const int gl = wide ? b->grid_tiles : clampi(g.ltiles, 1, b->grid_tiles);
             const int ge = wide ? b->grid_events : clampi(g.chunks, 1, b->grid_events);
+            // super-chunks of the group: at most chunks / 16 rounded up per window
+            const int gs = wide ? b->grid_events
+                                : clampi(g.chunks / (cmk::kSuperChunk / cmk::kEventThreads) + (g.w1 - g.w0), 1,
+                                         b->grid_events);
             switch (ph) {
             case 0: cmk::k_prep_batch<<<gt, 256, 0, s>>>(h, tab, ps, g.w0, g.w1); break;
-            case 1: enqueue_event(b, s, 0, ge, g.w0, g.w1); break;
-            case 2: cmk::k_loss_batch<<<gl, 256, 0, s>>>(h, tab, ls, g.w0, g.w1); break;
-            case 3: enqueue_event(b, s, 1, ge, g.w0, g.w1); break;
-            case 4: cmk::k_grad_batch<<<gt, 256, 0, s>>>(h, tab, ps, g.w0, g.w1); break;
+            case 1: cmk::k_bin_count_batch<<<gs, cmk::kEventThreads, 0, s>>>(h, tab, ss, g.w0, g.w1); break;
+            case 2: cmk::k_bin_scatter_batch<<<gs, cmk::kEventThreads, 0, s>>>(h, tab, ss, g.w0, g.w1); break;
+            case 3: enqueue_event(b, s, 0, ge, g.w0, g.w1); break;
+            case 4: cmk::k_loss_batch<<<gl, 256, 0, s>>>(h, tab, ls, g.w0, g.w1); break;
+            case 5: enqueue_event(b, s, 1, ge, g.w0, g.w1); break;
+            case 6: cmk::k_grad_batch<<<gt, 256, 0, s>>>(h, tab, ps, g.w0, g.w1); break;
             }
             cudaEventRecordWithFlags(p.eb, s, cudaEventRecordExternal);
         }
@@ -654,8 +961,11 @@ template <int MAXB>
 int occupancy_blocks()
 {
     int a = 0, c = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, cmk::k_splat_batch<MAXB>, cmk::kEventThreads, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, cmk::k_adjoint_batch<MAXB>, cmk::kEventThreads, 0);
+    cudaFuncSetAttribute(cmk::k_splat_batch<MAXB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSplatSmem);
+    cudaFuncSetAttribute(cmk::k_adjoint_batch<MAXB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kAdjointSmem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, cmk::k_splat_batch<MAXB>, cmk::kEventThreads, kSplatSmem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, cmk::k_adjoint_batch<MAXB>, cmk::kEventThreads, kAdjointSmem);
     const int m = a < c ? a : c;
     return m < 1 ? 1 : m;
 }
@@ -759,7 +1069,7 @@ int cm_batch_create(void* dev_mem, size_t bytes, const cm_window* wins, int32_t 
     b->cap = nwin;
     b->capn = n;
     b->L = L;
-    b->sched = nwin > 1 ? cm_batch_schedule{2, 1} : cm_batch_schedule{1, 0};
+    b->sched = nwin > 1 ? cm_batch_schedule{2, 1, 0} : cm_batch_schedule{1, 0, 0};
     int st = CM_OK;
     if (cudaMallocHost(reinterpret_cast<void**>(&b->staging), L.table_end) != cudaSuccess) st = CM_ENOMEM;
     if (!st && cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming) != cudaSuccess) st = CM_ECUDA;
@@ -776,7 +1086,8 @@ int cm_batch_create(void* dev_mem, size_t bytes, const cm_window* wins, int32_t 
         st = stage_windows(b, wins, nwin);
     }
     // the completion counters start at zero (the prep kernel also resets them)
-    if (!st && cudaMemset(b->base + L.sync, 0, (size_t)nwin * 2 * sizeof(int32_t)) != cudaSuccess) st = CM_ECUDA;
+    if (!st && cudaMemset(b->base + L.sync, 0, (size_t)nwin * kSyncInts * sizeof(int32_t)) != cudaSuccess)
+        st = CM_ECUDA;
     if (st) {
         destroy_batch(b);
         return st;
@@ -791,13 +1102,28 @@ int cm_batch_set_windows(cm_batch* b, const cm_window* wins, int32_t nwin)
     return stage_windows(b, wins, nwin);
 }
 
+namespace {
+// take schedule `s`; a change of grouping re-stages the current windows, since
+// the binning buffers are assigned per window when the table is filled
+int apply_schedule(cm_batch* b, const cm_batch_schedule& s)
+{
+    const bool rebin = s.bin != b->sched.bin;
+    b->sched = s;
+    b->stale = true;
+    if (rebin && b->nwin > 0) {
+        const std::vector<cm_window> w = b->last;
+        return stage_windows(b, w.data(), (int32_t)w.size());
+    }
+    return CM_OK;
+}
+}  // namespace
+
 int cm_batch_set_schedule(cm_batch* b, const cm_batch_schedule* s)
 {
     if (!b || !s || s->chains < 1 || s->chains > kMaxChains || s->group < 0) return CM_EINVAL;
     if (s->group == 0 && s->chains != 1) return CM_EINVAL;
-    b->sched = *s;
-    b->stale = true;
-    return CM_OK;
+    if (s->bin != 0 && s->bin != 1) return CM_EINVAL;
+    return apply_schedule(b, *s);
 }
 
 int cm_batch_get_schedule(const cm_batch* b, cm_batch_schedule* s)
@@ -821,22 +1147,23 @@ int cm_batch_autotune(cm_batch* b, void* stream, cm_batch_schedule* chosen)
     for (const auto& e : g_tuned) {
         const TuneKey& q = e.first;
         if (q.nwin == k.nwin && q.W == k.W && q.H == k.H && q.R == k.R && q.ebucket == k.ebucket) {
-            b->sched = e.second;
-            b->stale = true;
+            const int st = apply_schedule(b, e.second);
             if (chosen) *chosen = b->sched;
-            return CM_OK;
+            return st;
         }
     }
-    std::vector<cm_batch_schedule> cand = {{1, 0}, {1, 1}, {2, 1}, {3, 1}, {4, 1}, {2, 2}, {4, 2}};
-    if (b->nwin == 1) cand = {{1, 0}};
+    std::vector<cm_batch_schedule> cand;
+    for (int bin = 0; bin < 2; ++bin)
+        for (const auto& cg : {std::pair<int, int>{1, 0}, {1, 1}, {2, 1}, {3, 1}, {4, 1}, {2, 2}, {4, 2}})
+            cand.push_back(cm_batch_schedule{cg.first, cg.second, bin});
+    if (b->nwin == 1) cand = {{1, 0, 0}, {1, 0, 1}};
     cudaEvent_t a = nullptr, z = nullptr;
     if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&z) != cudaSuccess) return CM_ECUDA;
     float best = 1e30f;
     cm_batch_schedule pick = b->sched;
     int st = CM_OK;
     for (const cm_batch_schedule& c : cand) {
-        b->sched = c;
-        b->stale = true;
+        if ((st = apply_schedule(b, c))) break;
         if ((st = run_plan(b, s))) break;  // capture + warm-up
         cudaEventRecord(a, s);
         for (int r = 0; r < 3 && !st; ++r) st = run_plan(b, s);
@@ -855,8 +1182,7 @@ int cm_batch_autotune(cm_batch* b, void* stream, cm_batch_schedule* chosen)
     cudaEventDestroy(a);
     cudaEventDestroy(z);
     if (st) return st;
-    b->sched = pick;
-    b->stale = true;
+    if ((st = apply_schedule(b, pick))) return st;
     g_tuned.push_back({k, pick});
     if (chosen) *chosen = pick;
     return CM_OK;

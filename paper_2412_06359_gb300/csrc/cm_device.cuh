@@ -58,8 +58,19 @@ struct Win {
     float* drho;             // [H][W]
     float* dego;             // [6]
     float* dego_part;        // [pix_tiles][6]
-    int32_t* sync;           // [2] tile-completion counters of the loss and gradient reductions (batched path)
+    int32_t* sync;           // [4] batched path: completion counters of the loss and gradient reductions and
+                             // of the binning count, then the halo (px) of the shared-memory flow boxes
+    // spatial binning (batched path; tile_cnt == nullptr: events are used in their given order)
+    int32_t* tile_cnt;       // [ntiles + 1] events per 32x32 tile, turned into tile starts by the scan
+    int32_t* tile_cur;       // [ntiles] scatter cursors
+    int16_t* rx;             // [n] events grouped by tile
+    int16_t* ry;
+    float* rt;
+    int8_t* rp;
+    int32_t ntx, nty;        // tiles per row and per column
 };
+
+constexpr int kBinTile = 32;  // px, side of the tiles events are grouped by
 
 __device__ __forceinline__ size_t plane_size(const Win& d) { return (size_t)d.W * (size_t)d.H; }
 
@@ -183,16 +194,55 @@ __device__ __forceinline__ bool load_event(const Win& d, int64_t k, EventAt& e)
     return true;
 }
 
+// A shared-memory copy of the flow (one field for all bins) over the box
+// [x0, x0+bw) x [y0, y0+bh) of the image, and optionally a shared-memory
+// accumulator of dL/dflow over the same box.  A block loads the box that covers
+// its events' trajectories; samples whose four corners fall inside it read
+// shared memory, the others global memory, with the same values either way.
+struct FlowBox {
+    const float2* s = nullptr;
+    float2* g = nullptr;
+    int x0 = 0, y0 = 0, bw = 0, bh = 0;
+
+    __device__ __forceinline__ bool holds(int ix, int iy, int ix1, int iy1) const
+    {
+        return s && ix >= x0 && iy >= y0 && ix1 < x0 + bw && iy1 < y0 + bh;
+    }
+};
+
+// the four flow values around a cell of field j, from the box when it holds them
+__device__ __forceinline__ Quad quad_at(const Win& d, int j, const Bil& s, const FlowBox& fb)
+{
+    const int ix1 = min(s.ix + 1, d.W - 1), iy1 = min(s.iy + 1, d.H - 1);
+    if (fb.holds(s.ix, s.iy, ix1, iy1)) {
+        const int lx = s.ix - fb.x0, ly = s.iy - fb.y0, lx1 = ix1 - fb.x0, ly1 = iy1 - fb.y0;
+        Quad q;
+        q.u00 = fb.s[ly * fb.bw + lx];
+        q.u10 = fb.s[ly * fb.bw + lx1];
+        q.u01 = fb.s[ly1 * fb.bw + lx];
+        q.u11 = fb.s[ly1 * fb.bw + lx1];
+        return q;
+    }
+    return load_quad(field(d, j), d.W, d.H, s);
+}
+
+__device__ __forceinline__ float2 flow_at_pixel(const Win& d, int j, int x, int y, const FlowBox& fb)
+{
+    if (fb.holds(x, y, x, y)) return fb.s[(y - fb.y0) * fb.bw + (x - fb.x0)];
+    return __ldg(field(d, j) + (size_t)y * d.W + x);
+}
+
 // S2 + S3: the trajectory of one event through all computed edges (forward
 // chain b+1..B; with all edges as references also the backward chain b..0)
 // and the global mask.  Returns false when any computed point leaves the image.
 template <int MAXB>
-__device__ __forceinline__ bool trajectory(const Win& d, const EventAt& e, Traj<MAXB>& P)
+__device__ __forceinline__ bool trajectory(const Win& d, const EventAt& e, Traj<MAXB>& P,
+                                           const FlowBox& fb = FlowBox())
 {
     const int W = d.W, H = d.H, B = d.B, b = e.b;
     const float W1 = (float)(W - 1), H1 = (float)(H - 1);
     const float h = __fdiv_rn(1.0f, (float)B);
-    const float2 u0 = __ldg(field(d, b) + (size_t)e.yk * W + e.xk);
+    const float2 u0 = flow_at_pixel(d, b, e.xk, e.yk, fb);
     const float fxk = (float)e.xk, fyk = (float)e.yk;
     bool ok = true;
     const float dtf = __fsub_rn(edge_tau(b + 1, B), e.tau);
@@ -204,7 +254,7 @@ __device__ __forceinline__ bool trajectory(const Win& d, const EventAt& e, Traj<
                 P.y[j] = __fmaf_rn(dtf, u0.y, fyk);
             } else if (ok) {
                 const Bil s = bil(P.x[j - 1], P.y[j - 1]);
-                const float2 u = interp(s, load_quad(field(d, j - 1), W, H, s));
+                const float2 u = interp(s, quad_at(d, j - 1, s, fb));
                 P.x[j] = __fmaf_rn(h, u.x, P.x[j - 1]);
                 P.y[j] = __fmaf_rn(h, u.y, P.y[j - 1]);
             } else {
@@ -226,7 +276,7 @@ __device__ __forceinline__ bool trajectory(const Win& d, const EventAt& e, Traj<
                     P.y[j] = __fmaf_rn(-dtb, u0.y, fyk);
                 } else if (ok) {
                     const Bil s = bil(P.x[j + 1], P.y[j + 1]);
-                    const float2 u = interp(s, load_quad(field(d, j), W, H, s));
+                    const float2 u = interp(s, quad_at(d, j, s, fb));
                     P.x[j] = __fmaf_rn(-h, u.x, P.x[j + 1]);
                     P.y[j] = __fmaf_rn(-h, u.y, P.y[j + 1]);
                 } else {
@@ -323,13 +373,63 @@ struct EmitSink {
     }
 };
 
+// Adds the flow-gradient scatter of the adjoint into the block's shared-memory
+// box (FlowBox::g) when all corners it touches lie inside, else into global
+// memory; the block flushes the box with vector reductions afterwards.
+struct BoxRedSink {
+    const FlowBox* fb;
+
+    __device__ __forceinline__ void splat(const Win& d, int r, float px, float py, float tbar, int pol2,
+                                          int64_t k) const
+    {
+        RedSink().splat(d, r, px, py, tbar, pol2, k);
+    }
+    __device__ __forceinline__ void scatter(const Win& d, int field, int edge, const Bil& s, float px, float py,
+                                            float hx, float hy, int64_t k) const
+    {
+        const int ix1 = s.ax > 0.0f ? s.ix + 1 : s.ix, iy1 = s.ay > 0.0f ? s.iy + 1 : s.iy;
+        if (!fb->g || !fb->holds(s.ix, s.iy, ix1, iy1)) {
+            RedSink().scatter(d, field, edge, s, px, py, hx, hy, k);
+            return;
+        }
+        const int bw = fb->bw;
+        float2* g = fb->g + (s.iy - fb->y0) * bw + (s.ix - fb->x0);
+        atomicAdd(&g[0].x, s.w00 * hx);
+        atomicAdd(&g[0].y, s.w00 * hy);
+        if (s.ax > 0.0f) {
+            atomicAdd(&g[1].x, s.w10 * hx);
+            atomicAdd(&g[1].y, s.w10 * hy);
+        }
+        if (s.ay > 0.0f) {
+            atomicAdd(&g[bw].x, s.w01 * hx);
+            atomicAdd(&g[bw].y, s.w01 * hy);
+        }
+        if (s.ax > 0.0f && s.ay > 0.0f) {
+            atomicAdd(&g[bw + 1].x, s.w11 * hx);
+            atomicAdd(&g[bw + 1].y, s.w11 * hy);
+        }
+    }
+    __device__ __forceinline__ void point(const Win& d, int field, int edge, int xk, int yk, float vx, float vy,
+                                          int64_t k) const
+    {
+        if (!fb->g || !fb->holds(xk, yk, xk, yk)) {
+            RedSink().point(d, field, edge, xk, yk, vx, vy, k);
+            return;
+        }
+        float2* g = fb->g + (yk - fb->y0) * fb->bw + (xk - fb->x0);
+        atomicAdd(&g->x, vx);
+        atomicAdd(&g->y, vy);
+    }
+};
+
 template <int MAXB, class Sink = RedSink>
-__device__ __forceinline__ void splat_event(const Win& d, int64_t k, const Sink& sink = Sink())
+__device__ __forceinline__ void splat_event(const Win& d, int64_t k, const Sink& sink = Sink(),
+                                            const FlowBox& fb = FlowBox())
 {
     EventAt e;
     if (!load_event(d, k, e)) return;
     Traj<MAXB> P;
-    if (!trajectory<MAXB>(d, e, P)) return;
+    if (!trajectory<MAXB>(d, e, P, fb)) return;
     if (d.ref_mode == kRefAll) {
 #pragma unroll
         for (int j = 0; j <= MAXB; ++j)
@@ -374,11 +474,10 @@ __device__ __forceinline__ float2 ref_adjoint(const Win& d, int r, int j, float 
 // gradient of field `field` and return lambda + hs J(x)^T lambda.
 template <class Sink>
 __device__ __forceinline__ float2 push_back(const Win& d, const Sink& sink, int field, int edge, float px, float py,
-                                            float hs, float2 lam, int64_t k)
+                                            float hs, float2 lam, int64_t k, const FlowBox& fb)
 {
-    const int W = d.W, H = d.H;
     const Bil s = bil(px, py);
-    const Quad q = load_quad(field_ptr(d, field), W, H, s);
+    const Quad q = quad_at(d, field, s, fb);
     const float hx = hs * lam.x, hy = hs * lam.y;
     sink.scatter(d, field, edge, s, px, py, hx, hy, k);
     const float jxx = s.by * (q.u10.x - q.u00.x) + s.ay * (q.u11.x - q.u01.x);
@@ -395,12 +494,13 @@ __device__ __forceinline__ float2 push_back(const Win& d, const Sink& sink, int 
 // each reference point is gathered from the loss-transformed IWE, and the
 // adjoint is carried back along both chains of pushes, scattering dL/dflow.
 template <int MAXB, class Sink = RedSink>
-__device__ __forceinline__ void adjoint_event(const Win& d, int64_t k, float dl, const Sink& sink = Sink())
+__device__ __forceinline__ void adjoint_event(const Win& d, int64_t k, float dl, const Sink& sink = Sink(),
+                                              const FlowBox& fb = FlowBox())
 {
     EventAt e;
     if (!load_event(d, k, e)) return;
     Traj<MAXB> P;
-    if (!trajectory<MAXB>(d, e, P)) return;
+    if (!trajectory<MAXB>(d, e, P, fb)) return;
     const int B = d.B, b = e.b;
     const float h = __fdiv_rn(1.0f, (float)B);
     const bool all = d.ref_mode == kRefAll;
@@ -415,7 +515,7 @@ __device__ __forceinline__ void adjoint_event(const Win& d, int64_t k, float dl,
                 lam.y += a.y;
             }
             if (j > b + 1) {
-                lam = push_back(d, sink, j - 1, j, P.x[j - 1], P.y[j - 1], h, lam, k);
+                lam = push_back(d, sink, j - 1, j, P.x[j - 1], P.y[j - 1], h, lam, k, fb);
             } else {
                 const float dtf = __fsub_rn(edge_tau(b + 1, B), e.tau);
                 sink.point(d, b, j, e.xk, e.yk, dtf * lam.x, dtf * lam.y, k);
@@ -432,7 +532,7 @@ __device__ __forceinline__ void adjoint_event(const Win& d, int64_t k, float dl,
             lam.x += a.x;
             lam.y += a.y;
             if (j < b) {
-                lam = push_back(d, sink, j, j, P.x[j + 1], P.y[j + 1], -h, lam, k);
+                lam = push_back(d, sink, j, j, P.x[j + 1], P.y[j + 1], -h, lam, k, fb);
             } else {
                 const float dtb = __fsub_rn(e.tau, edge_tau(b, B));
                 sink.point(d, b, j, e.xk, e.yk, -dtb * lam.x, -dtb * lam.y, k);
@@ -525,15 +625,25 @@ __device__ __forceinline__ void loss_tile(const Win& d, int r, int tile, int nti
     const float eps = d.eps;
     float s = 0.0f;
     int cnt = 0;
-    for (size_t i = (size_t)tile * blockDim.x + threadIdx.x; i < HW; i += (size_t)ntiles * blockDim.x) {
-        const float4 q = plane[i];
+    const size_t stride = (size_t)ntiles * blockDim.x;
+    auto one = [&](float4 q, size_t i) {
         const float cp = q.x + eps, cm = q.z + eps;
         const float tp = q.y / cp, tm = q.w / cm;
         s = fmaf(tp, tp, s);
         s = fmaf(tm, tm, s);
         cnt += (q.x > 0.0f || q.z > 0.0f) ? 1 : 0;
         plane[i] = make_float4(2.0f * tp / cp, tp, 2.0f * tm / cm, tm);
+    };
+    size_t i = (size_t)tile * blockDim.x + threadIdx.x;
+    // four independent loads in flight per thread (the pass is latency-bound otherwise)
+    for (; i + 3 * stride < HW; i += 4 * stride) {
+        const float4 q0 = plane[i], q1 = plane[i + stride], q2 = plane[i + 2 * stride], q3 = plane[i + 3 * stride];
+        one(q0, i);
+        one(q1, i + stride);
+        one(q2, i + 2 * stride);
+        one(q3, i + 3 * stride);
     }
+    for (; i < HW; i += stride) one(plane[i], i);
     __shared__ float ss[32];
     __shared__ int sc[32];
     s = warp_sum(s);
@@ -597,11 +707,9 @@ __device__ __forceinline__ void depth_ego_tile(const Win& d, int tile, int ntile
     const float ifx = 1.0f / d.fx, ify = 1.0f / d.fy;
     const float sx = d.dt * d.fx, sy = d.dt * d.fy;
     float g[6] = {0, 0, 0, 0, 0, 0};
-    for (size_t i = (size_t)tile * blockDim.x + threadIdx.x; i < HW; i += (size_t)ntiles * blockDim.x) {
+    auto one = [&](size_t i, float r, float2 df) {
         const int v = (int)(i / W), u = (int)(i - (size_t)v * W);
         const float xn = ((float)u - d.cx) * ifx, yn = ((float)v - d.cy) * ify;
-        const float r = __ldg(d.rho + i);
-        const float2 df = d.dflow[i];
         const float Gx = sx * df.x, Gy = sy * df.y;
         if (d.drho) d.drho[i] = Gx * (xn * vz - vx) + Gy * (yn * vz - vy);
         g[0] -= r * Gx;
@@ -610,7 +718,20 @@ __device__ __forceinline__ void depth_ego_tile(const Win& d, int tile, int ntile
         g[3] += xn * yn * Gx + (1.0f + yn * yn) * Gy;
         g[4] -= (1.0f + xn * xn) * Gx + xn * yn * Gy;
         g[5] += yn * Gx - xn * Gy;
+    };
+    const size_t stride = (size_t)ntiles * blockDim.x;
+    size_t i = (size_t)tile * blockDim.x + threadIdx.x;
+    for (; i + 3 * stride < HW; i += 4 * stride) {  // four independent load pairs in flight
+        const float r0 = __ldg(d.rho + i), r1 = __ldg(d.rho + i + stride);
+        const float r2 = __ldg(d.rho + i + 2 * stride), r3 = __ldg(d.rho + i + 3 * stride);
+        const float2 f0 = d.dflow[i], f1 = d.dflow[i + stride], f2 = d.dflow[i + 2 * stride],
+                     f3 = d.dflow[i + 3 * stride];
+        one(i, r0, f0);
+        one(i + stride, r1, f1);
+        one(i + 2 * stride, r2, f2);
+        one(i + 3 * stride, r3, f3);
     }
+    for (; i < HW; i += stride) one(i, __ldg(d.rho + i), d.dflow[i]);
     __shared__ float sg[32][6];
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
 #pragma unroll

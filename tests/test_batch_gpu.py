@@ -120,7 +120,7 @@ def test_batch_profiling_records_every_phase():
     cm = gpu_lib()
     wins = _mixed_windows(4, 11)
     plan = cm.BatchPlan(_dev_windows(cm, wins), cm.loss_cfg(10, cm.REF_ALL, cm.SPLAT_ATOMIC))
-    plan.set_schedule(2, 1)
+    plan.set_schedule(2, 1, 1)
     plan.run()
     C.cm_profile_reset()
     n0 = C.cm_launch_count()
@@ -130,9 +130,10 @@ def test_batch_profiling_records_every_phase():
     C.cm_profile_enable(False)
     plan.run()
     prof = C.cm_profile_collect()
-    per_run = 5 * len(wins)  # five kernels per window group, one window per group
+    per_run = 7 * len(wins)  # seven kernels per window group (with tile grouping), one window per group
     assert C.cm_launch_count() - n0 == 4 * per_run
-    assert set(prof) == {"k_prep_batch", "k_splat_batch", "k_loss_batch", "k_adjoint_batch", "k_grad_batch"}
+    assert set(prof) == {"k_prep_batch", "k_bin_count_batch", "k_bin_scatter_batch", "k_splat_batch", "k_loss_batch",
+                         "k_adjoint_batch", "k_grad_batch"}
     assert all(v[0] == 3 * len(wins) and v[1] > 0 for v in prof.values())
     # results still right after switching the timing events back
     g = _batch_result(plan, 1)
@@ -140,13 +141,14 @@ def test_batch_profiling_records_every_phase():
         assert_parity(g, run_oracle(wins[1]))
 
 
-@pytest.mark.parametrize("chains,group", [(1, 0), (1, 1), (2, 1), (3, 2), (4, 1)])
-def test_every_schedule_gives_the_same_results(chains, group):
+@pytest.mark.parametrize("chains,group,bin", [(1, 0, 0), (1, 1, 0), (2, 1, 0), (3, 2, 0), (4, 1, 0),
+                                              (1, 0, 1), (2, 1, 1), (3, 2, 1)])
+def test_every_schedule_gives_the_same_results(chains, group, bin):
     cm = gpu_lib()
     wins = _mixed_windows(7, 21)
     plan = cm.BatchPlan(_dev_windows(cm, wins), cm.loss_cfg(10, cm.REF_ALL, cm.SPLAT_ATOMIC))
-    plan.set_schedule(chains, group)
-    assert plan.schedule() == (chains, group)
+    plan.set_schedule(chains, group, bin)
+    assert plan.schedule() == (chains, group, bin)
     plan.run()
     plan.run()
     for i, w in enumerate(wins):
@@ -158,9 +160,9 @@ def test_autotune_picks_a_schedule_and_stays_correct():
     cm = gpu_lib()
     wins = synth.batch_windows(6)
     plan = cm.BatchPlan(_dev_windows(cm, wins), cm.loss_cfg(10, cm.REF_ALL, cm.SPLAT_ATOMIC))
-    chains, group = plan.autotune()
-    assert 1 <= chains <= 8 and group >= 0
-    assert plan.autotune() == (chains, group)  # cached for this shape
+    chains, group, bin = plan.autotune()
+    assert 1 <= chains <= 8 and group >= 0 and bin in (0, 1)
+    assert plan.autotune() == (chains, group, bin)  # cached for this shape
     plan.run()
     for i in (0, 3):
         assert_parity(_batch_result(plan, i), run_oracle(wins[i]))
