@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="bound of the CPU oracle sample")
+    ap.add_argument("--schedule", default="auto",
+                    help="batch schedule 'chains,windows_per_kernel,tile_grouping' (e.g. 4,2,0), or 'auto' to autotune")
     ap.add_argument("--serve", action="store_true", help="run the serving workload instead (one line per rate)")
     ap.add_argument("--serve-scales", default="0.25,0.5,1.0", help="arrival-rate multipliers of 100 Hz per stream")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
@@ -317,7 +319,11 @@ def run_ours(args):
     R = wins[0].nbins + 1
     stream = torch.cuda.current_stream()
 
-    schedule = batch.plan.autotune()  # picks chains / windows per kernel for this batch (cached per shape)
+    if args.schedule == "auto":
+        schedule = batch.plan.autotune()  # picks chains / windows per kernel for this batch (cached per shape)
+    else:
+        batch.plan.set_schedule(*[int(v) for v in args.schedule.split(",")])
+        schedule = batch.plan.schedule()
     for _ in range(args.warmup):
         batch.step()
     torch.cuda.synchronize()

@@ -69,8 +69,9 @@ __device__ __forceinline__ int clamp_end(const BatchHdr* h, int w1) { return w1 
 // Each kernel covers windows [w0, w1) of the table (clamped to the windows in
 // use).  Pixel passes walk per-window tiles, event passes chunks of 256 events.
 
-// zero the images of warped events and the flow-gradient target, compute the
-// flow of depth-input windows, reset the completion counters
+// zero the images of warped events and the quad accumulators of dL/dflow,
+// build the flow quads (the motion field for depth input), reset the
+// completion counters
 __global__ void __launch_bounds__(256) k_prep_batch(const BatchHdr* h, const Win* tab, const int* pstart, int w0,
                                                     int w1)
 {
@@ -85,20 +86,12 @@ __global__ void __launch_bounds__(256) k_prep_batch(const BatchHdr* h, const Win
         if (ti == 0 && threadIdx.x < 3) d.sync[threadIdx.x] = 0;
         const size_t HW = plane_size(d);
         const size_t stride = (size_t)d.pix_tiles * blockDim.x;
-        float2* flow = const_cast<float2*>(d.flow);
-        float m = 0.0f;  // max |flow component| over this tile's pixels (the halo of the flow boxes)
         for (size_t i = (size_t)ti * blockDim.x + threadIdx.x; i < HW; i += stride) {
             for (int r = 0; r < d.R; ++r) d.iwe[(size_t)r * HW + i] = z4;
-            d.dflow[i] = make_float2(0.f, 0.f);
-            float2 f;
-            if (d.rho) {
-                const int v = (int)(i / d.W), u = (int)(i - (size_t)v * d.W);
-                f = motion_field(u, v, __ldg(d.rho + i), d.ego, d.fx, d.fy, d.cx, d.cy, d.dt);
-                flow[i] = f;
-            } else {
-                f = __ldg(d.flow + i);
-            }
-            m = fmaxf(m, fmaxf(fabsf(f.x), fabsf(f.y)));
+            d.dq[i].a = z4;
+            d.dq[i].b = z4;
+            const int v = (int)(i / d.W), u = (int)(i - (size_t)v * d.W);
+            build_quad(d, u, v);
         }
         if (d.tile_cnt) {
             const int nt = d.ntx * d.nty;
@@ -107,18 +100,6 @@ __global__ void __launch_bounds__(256) k_prep_batch(const BatchHdr* h, const Win
                 if (i < nt) d.tile_cur[i] = 0;
             }
         }
-        // the tile's maximum, written where the gradient pass later keeps its partials
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-        __shared__ float sm[32];
-        if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            float a = 0.0f;
-            for (int i = 0; i < (int)(blockDim.x >> 5); ++i) a = fmaxf(a, sm[i]);
-            d.dego_part[(size_t)ti * 6] = a;
-        }
-        __syncthreads();
     }
 }
 
@@ -174,9 +155,7 @@ __device__ __forceinline__ void count_tiles(const Win& d, long long e0, long lon
 }
 
 // binning, pass 1: events per tile; the block finishing a window's last
-// super-chunk turns the counts into tile starts and the cursors, and sets the
-// halo of the window's flow boxes (the largest flow component, at most 8 px:
-// samples outside a box read global memory)
+// super-chunk turns the counts into tile starts and the cursors
 __global__ void __launch_bounds__(kEventThreads) k_bin_count_batch(const BatchHdr* h, const Win* tab,
                                                                     const long long* sstart, int w0, int w1)
 {
@@ -209,19 +188,7 @@ __global__ void __launch_bounds__(kEventThreads) k_bin_count_batch(const BatchHd
                 }
                 carry += tot;
             }
-            float m = 0.0f;
-            for (int i = threadIdx.x; i < d.pix_tiles; i += blockDim.x) m = fmaxf(m, d.dego_part[(size_t)i * 6]);
-            __shared__ float sm[32];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-            if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                float a = 0.0f;
-                for (int i = 0; i < (int)(blockDim.x >> 5); ++i) a = fmaxf(a, sm[i]);
-                d.tile_cnt[nt] = carry;
-                d.sync[3] = (int)fminf(ceilf(a) + 2.0f, 8.0f);
-            }
+            if (threadIdx.x == 0) d.tile_cnt[nt] = carry;
             __syncthreads();
         }
     }
@@ -259,67 +226,6 @@ __global__ void __launch_bounds__(kEventThreads) k_bin_scatter_batch(const Batch
     }
 }
 
-// The flow box of one chunk of grouped events: their bounding box grown by the
-// window's halo, clipped to the image, loaded into shared memory when it holds
-// at most `cap` pixels (with a zeroed gradient accumulator behind it when
-// `grad`).  Called by every thread of the block; ends with __syncthreads.
-__device__ __forceinline__ void load_box(const Win& d, long long k, float2* sm, int cap, bool grad, FlowBox& fb)
-{
-    __shared__ int bb[4];
-    __shared__ int red[4][32];
-    const bool valid = k < d.n;
-    int x = 0, y = 0;
-    if (valid) {
-        x = min(max((int)d.x[k], 0), d.W - 1);
-        y = min(max((int)d.y[k], 0), d.H - 1);
-    }
-    int v[4] = {valid ? x : INT_MAX, valid ? y : INT_MAX, valid ? x : -1, valid ? y : -1};
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        v[0] = min(v[0], __shfl_xor_sync(0xffffffffu, v[0], o));
-        v[1] = min(v[1], __shfl_xor_sync(0xffffffffu, v[1], o));
-        v[2] = max(v[2], __shfl_xor_sync(0xffffffffu, v[2], o));
-        v[3] = max(v[3], __shfl_xor_sync(0xffffffffu, v[3], o));
-    }
-    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if (lane == 0)
-        for (int q = 0; q < 4; ++q) red[q][wi] = v[q];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int a = INT_MAX, b = INT_MAX, c = -1, e = -1;
-        for (int i = 0; i < nw; ++i) {
-            a = min(a, red[0][i]);
-            b = min(b, red[1][i]);
-            c = max(c, red[2][i]);
-            e = max(e, red[3][i]);
-        }
-        const int hl = d.sync[3];
-        bb[0] = max(a - hl, 0);
-        bb[1] = max(b - hl, 0);
-        bb[2] = c < 0 ? -1 : min(c + hl + 1, d.W - 1);
-        bb[3] = e < 0 ? -1 : min(e + hl + 1, d.H - 1);
-    }
-    __syncthreads();
-    const int x0 = bb[0], y0 = bb[1], bw = bb[2] - x0 + 1, bh = bb[3] - y0 + 1;
-    if (bw <= 0 || bh <= 0 || bw * bh > cap || d.nfb != 1) {
-        fb = FlowBox();
-        return;
-    }
-    const int n = bw * bh;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const int yy = i / bw, xx = i - yy * bw;
-        sm[i] = __ldg(d.flow + (size_t)(y0 + yy) * d.W + x0 + xx);
-        if (grad) sm[cap + i] = make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-    fb.s = sm;
-    fb.g = grad ? sm + cap : nullptr;
-    fb.x0 = x0;
-    fb.y0 = y0;
-    fb.bw = bw;
-    fb.bh = bh;
-}
-
 // events of a grouped window are read in tile order
 __device__ __forceinline__ void use_grouped(Win& d)
 {
@@ -331,30 +237,24 @@ __device__ __forceinline__ void use_grouped(Win& d)
     }
 }
 
-constexpr int kBoxCap = 4096;  // pixels of a flow box (32 KB of float2)
-
 template <int MAXB>
 __global__ void __launch_bounds__(kEventThreads) k_splat_batch(const BatchHdr* h, const Win* tab,
                                                                 const long long* cstart, int w0, int w1)
 {
     w1 = clamp_end(h, w1);
     if (w0 >= w1) return;
-    extern __shared__ float2 box_mem[];
     const long long cb = cstart[w0], ce = cstart[w1];
     for (long long c = cb + blockIdx.x; c < ce; c += gridDim.x) {
         const int w = find_ll(cstart, w0, w1, c);
         Win d = tab[w];
         use_grouped(d);
         const long long k = (c - cstart[w]) * kEventThreads + threadIdx.x;
-        FlowBox fb;
-        if (d.tile_cnt) load_box(d, k, box_mem, kBoxCap, false, fb);
-        if (k < d.n) splat_event<MAXB>(d, k, RedSink(), fb);
-        __syncthreads();  // the next chunk reloads the box
+        if (k < d.n) splat_event<MAXB>(d, k);
     }
 }
 
 template <int MAXB>
-__global__ void __launch_bounds__(kEventThreads) k_adjoint_batch(const BatchHdr* h, const Win* tab,
+__global__ void __launch_bounds__(kEventThreads, MAXB <= 10 ? 3 : 2) k_adjoint_batch(const BatchHdr* h, const Win* tab,
                                                                   const long long* cstart, int w0, int w1)
 {
     w1 = clamp_end(h, w1);
@@ -365,9 +265,6 @@ __global__ void __launch_bounds__(kEventThreads) k_adjoint_batch(const BatchHdr*
         Win d = tab[w];
         use_grouped(d);
         const long long k = (c - cstart[w]) * kEventThreads + threadIdx.x;
-        // grouped events only: no shared-memory box here (measured on GB300: the
-        // per-chunk barriers of a box cost more than the global traffic it saves
-        // on this kernel's long per-event dependency chains)
         if (k < d.n) adjoint_event<MAXB>(d, k, __ldg(d.dloss));
     }
 }
@@ -389,8 +286,8 @@ __global__ void __launch_bounds__(256) k_loss_batch(const BatchHdr* h, const Win
     }
 }
 
-// depth / ego gradient per tile; the block completing a window's last tile
-// reduces the six ego sums
+// dL/dflow folded from the quad accumulators, and the depth / ego gradient per
+// tile; the block completing a window's last tile reduces the six ego sums
 __global__ void __launch_bounds__(256) k_grad_batch(const BatchHdr* h, const Win* tab, const int* pstart, int w0,
                                                     int w1)
 {
@@ -400,7 +297,10 @@ __global__ void __launch_bounds__(256) k_grad_batch(const BatchHdr* h, const Win
     for (int tile = tb + blockIdx.x; tile < te; tile += gridDim.x) {
         const int w = find_i(pstart, w0, w1, tile);
         const Win d = tab[w];
-        if (!d.rho) continue;
+        if (!d.rho) {
+            if (d.dq) fold_tile(d, tile - pstart[w], d.pix_tiles);  // flow input: dL/dflow only
+            continue;
+        }
         depth_ego_tile(d, tile - pstart[w], d.pix_tiles);
         if (last_tile_done(d.sync + 1, d.pix_tiles)) {
             __syncthreads();
@@ -421,7 +321,7 @@ constexpr int kPhases = 7;
 const char* const kPhaseName[kPhases] = {"k_prep_batch",  "k_bin_count_batch", "k_bin_scatter_batch",
                                          "k_splat_batch", "k_loss_batch",      "k_adjoint_batch",
                                          "k_grad_batch"};
-constexpr int kSyncInts = 4;  // per window: loss, gradient and binning counters, halo
+constexpr int kSyncInts = 4;  // per window: loss, gradient and binning counters (one spare)
 constexpr int kMaxChains = 8;
 
 size_t up256(size_t v) { return (v + 255) / 256 * 256; }
@@ -438,7 +338,7 @@ int refs_of(const cm_loss_cfg& c) { return c.ref_mode == CM_REF_END ? 1 : c.nbin
 
 // device bytes of the per-window slabs for a list of windows
 struct Need {
-    size_t iwe, flow, dflow, part, stat, dego, bins;
+    size_t iwe, flow, dflow, quad, part, stat, dego, bins;
 };
 
 bool window_ok(const cm_window& w)
@@ -475,8 +375,8 @@ Need need_of(const cm_window* wins, int32_t nwin, const cm_loss_cfg& cfg)
         if (wins[i].scratch) continue;  // the window brings its own buffers
         const size_t HW = (size_t)wins[i].cam.width * wins[i].cam.height;
         n.iwe += (size_t)R * HW * sizeof(float4);
-        if (!wins[i].flow) n.flow += HW * sizeof(float2);
         if (!wins[i].dflow) n.dflow += HW * sizeof(float2);
+        n.quad += 2 * HW * sizeof(cmk::FQ);
         n.part += (size_t)R * tiles_for(HW, 256) * sizeof(float2);
         n.stat += (size_t)R;
         n.dego += (size_t)tiles_for(HW, 512) * 6 * sizeof(float);
@@ -496,7 +396,7 @@ size_t bin_bytes(int W, int H, int64_t n)
 
 // a window's own scratch: the per-window buffers, one after another
 struct WinScratch {
-    size_t iwe, flow, dflow, part, norm, lr, nnz, dego, sync, total;
+    size_t iwe, flow, dflow, fq, dq, part, norm, lr, nnz, dego, sync, total;
 };
 
 WinScratch win_scratch(size_t HW, int R)
@@ -505,10 +405,12 @@ WinScratch win_scratch(size_t HW, int R)
     size_t o = 0;
     s.iwe = o;
     o = up256(o + (size_t)R * HW * sizeof(float4));
-    s.flow = o;
-    o = up256(o + HW * sizeof(float2));
     s.dflow = o;
     o = up256(o + HW * sizeof(float2));
+    s.fq = o;
+    o = up256(o + HW * sizeof(cmk::FQ));
+    s.dq = o;
+    o = up256(o + HW * sizeof(cmk::FQ));
     s.part = o;
     o = up256(o + (size_t)R * tiles_for(HW, 256) * sizeof(float2));
     s.norm = o;
@@ -527,7 +429,7 @@ WinScratch win_scratch(size_t HW, int R)
 
 struct Layout {
     size_t hdr, tab, cstart, sstart, lstart, pstart, table_end;  // the uploaded region [0, table_end)
-    size_t iwe, flow, dflow, part, norm, lr, nnz, dego, sync, bins, total;
+    size_t iwe, flow, dflow, quad, part, norm, lr, nnz, dego, sync, bins, total;
 };
 
 Layout layout_of(int cap, const Need& n)
@@ -549,10 +451,10 @@ Layout layout_of(int cap, const Need& n)
     L.table_end = o = up256(o);
     L.iwe = o;
     o = up256(o + n.iwe);
-    L.flow = o;
-    o = up256(o + n.flow);
     L.dflow = o;
     o = up256(o + n.dflow);
+    L.quad = o;
+    o = up256(o + n.quad);
     L.part = o;
     o = up256(o + n.part);
     L.norm = o;
@@ -624,8 +526,8 @@ int stage_windows(cm_batch* b, const cm_window* wins, int32_t nwin)
         if (!window_ok(wins[i])) return CM_EINVAL;
     const Need n = need_of(wins, nwin, b->cfg);
     const Need& c = b->capn;
-    if (n.iwe > c.iwe || n.flow > c.flow || n.dflow > c.dflow || n.part > c.part || n.stat > c.stat ||
-        n.dego > c.dego)
+    if (n.iwe > c.iwe || n.dflow > c.dflow || n.quad > c.quad || n.part > c.part ||
+        n.stat > c.stat || n.dego > c.dego)
         return CM_ENOMEM;
     // the previous upload must have left the staging buffer before it is rewritten
     if (cudaEventSynchronize(b->staged) != cudaSuccess) return CM_ECUDA;
@@ -640,7 +542,7 @@ int stage_windows(cm_batch* b, const cm_window* wins, int32_t nwin)
     int* ps = reinterpret_cast<int*>(s + b->L.pstart);
     const int R = refs_of(b->cfg);
     const float eps = b->cfg.eps > 0.0f ? b->cfg.eps : 1e-9f;
-    size_t o_iwe = 0, o_flow = 0, o_dflow = 0, o_part = 0, o_stat = 0, o_dego = 0, o_bins = 0;
+    size_t o_iwe = 0, o_dflow = 0, o_quad = 0, o_part = 0, o_stat = 0, o_dego = 0, o_bins = 0;
     long long chunks = 0;
     int lt_total = 0, pt_total = 0;
     char* base = b->base;
@@ -679,8 +581,10 @@ int stage_windows(cm_batch* b, const cm_window* wins, int32_t nwin)
             char* sc = static_cast<char*>(w.scratch);
             const WinScratch ws = win_scratch(HW, R);
             d.iwe = reinterpret_cast<float4*>(sc + ws.iwe);
-            d.flow = w.flow ? reinterpret_cast<const float2*>(w.flow) : reinterpret_cast<const float2*>(sc + ws.flow);
+            d.flow = reinterpret_cast<const float2*>(w.flow);  // nullptr for depth input (the quads hold its flow)
             d.dflow = w.dflow ? reinterpret_cast<float2*>(w.dflow) : reinterpret_cast<float2*>(sc + ws.dflow);
+            d.fq = reinterpret_cast<const cmk::FQ*>(sc + ws.fq);
+            d.dq = reinterpret_cast<cmk::FQ*>(sc + ws.dq);
             d.loss_part = reinterpret_cast<float2*>(sc + ws.part);
             d.norm = reinterpret_cast<float*>(sc + ws.norm);
             d.loss_r = reinterpret_cast<float*>(sc + ws.lr);
@@ -690,18 +594,17 @@ int stage_windows(cm_batch* b, const cm_window* wins, int32_t nwin)
         } else {
             d.iwe = reinterpret_cast<float4*>(base + b->L.iwe + o_iwe);
             o_iwe += (size_t)R * HW * sizeof(float4);
-            if (w.flow) {
-                d.flow = reinterpret_cast<const float2*>(w.flow);
-            } else {
-                d.flow = reinterpret_cast<const float2*>(base + b->L.flow + o_flow);
-                o_flow += HW * sizeof(float2);
-            }
+            d.flow = reinterpret_cast<const float2*>(w.flow);  // nullptr for depth input (the quads hold its flow)
             if (w.dflow) {
                 d.dflow = reinterpret_cast<float2*>(w.dflow);
             } else {
                 d.dflow = reinterpret_cast<float2*>(base + b->L.dflow + o_dflow);
                 o_dflow += HW * sizeof(float2);
             }
+            d.fq = reinterpret_cast<const cmk::FQ*>(base + b->L.quad + o_quad);
+            o_quad += HW * sizeof(cmk::FQ);
+            d.dq = reinterpret_cast<cmk::FQ*>(base + b->L.quad + o_quad);
+            o_quad += HW * sizeof(cmk::FQ);
             d.loss_part = reinterpret_cast<float2*>(base + b->L.part + o_part);
             o_part += (size_t)R * d.loss_tiles * sizeof(float2);
             d.norm = reinterpret_cast<float*>(base + b->L.norm) + o_stat;
@@ -809,11 +712,6 @@ std::vector<Group> make_groups(const cm_batch* b)
     return g;
 }
 
-// dynamic shared memory of the event kernels: one flow box (splat), a flow box
-// and its gradient accumulator (adjoint)
-constexpr size_t kSplatSmem = cmk::kBoxCap * sizeof(float2);
-constexpr size_t kAdjointSmem = 0;
-
 template <int MAXB>
 void enqueue_event_kernel(cm_batch* b, cudaStream_t s, int which, int grid, int w0, int w1)
 {
@@ -821,9 +719,9 @@ void enqueue_event_kernel(cm_batch* b, cudaStream_t s, int which, int grid, int 
     const Win* tab = reinterpret_cast<const Win*>(b->base + b->L.tab);
     const long long* cs = reinterpret_cast<const long long*>(b->base + b->L.cstart);
     if (which == 0)
-        cmk::k_splat_batch<MAXB><<<grid, cmk::kEventThreads, kSplatSmem, s>>>(h, tab, cs, w0, w1);
+        cmk::k_splat_batch<MAXB><<<grid, cmk::kEventThreads, 0, s>>>(h, tab, cs, w0, w1);
     else
-        cmk::k_adjoint_batch<MAXB><<<grid, cmk::kEventThreads, kAdjointSmem, s>>>(h, tab, cs, w0, w1);
+        cmk::k_adjoint_batch<MAXB><<<grid, cmk::kEventThreads, 0, s>>>(h, tab, cs, w0, w1);
 }
 
 void enqueue_event(cm_batch* b, cudaStream_t s, int which, int grid, int w0, int w1)
@@ -961,11 +859,8 @@ template <int MAXB>
 int occupancy_blocks()
 {
     int a = 0, c = 0;
-    cudaFuncSetAttribute(cmk::k_splat_batch<MAXB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSplatSmem);
-    cudaFuncSetAttribute(cmk::k_adjoint_batch<MAXB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)kAdjointSmem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, cmk::k_splat_batch<MAXB>, cmk::kEventThreads, kSplatSmem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, cmk::k_adjoint_batch<MAXB>, cmk::kEventThreads, kAdjointSmem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, cmk::k_splat_batch<MAXB>, cmk::kEventThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, cmk::k_adjoint_batch<MAXB>, cmk::kEventThreads, 0);
     const int m = a < c ? a : c;
     return m < 1 ? 1 : m;
 }

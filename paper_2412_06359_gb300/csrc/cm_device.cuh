@@ -30,6 +30,17 @@ constexpr int kRefEnd = 0;
 constexpr int kRefAll = 1;
 constexpr int kEventThreads = 256;
 
+// Flow quad: the four flow values a bilinear sample in cell (ix, iy) reads,
+// corner indices clamped to the image, a = (u00, u10), b = (u01, u11).  One
+// 32-byte load of a quad replaces four 8-byte gathers, and the L2 serves random
+// requests at the same rate whatever their width up to a 32-byte sector.  The
+// same record layout accumulates dL/dflow: a push adds its four corner terms to
+// its cell's record with two 16-byte vector reductions (instead of four 8-byte
+// ones), and a per-pixel fold sums every record corner that names a pixel.
+struct __align__(32) FQ {
+    float4 a, b;
+};
+
 // One window: events, flow, IWE and gradient buffers, statistics.
 struct Win {
     const int16_t* x;
@@ -45,6 +56,8 @@ struct Win {
     const float2* flow;      // [nfb][H][W]
     float4* iwe;             // [R][H][W]: (C+, S+, C-, S-); after the loss (A+, T+, A-, T-)
     float2* dflow;           // [nfb][H][W]
+    const FQ* fq;            // [nfb][H][W] flow quads, or nullptr (then samples gather from flow)
+    FQ* dq;                  // [nfb][H][W] quad accumulators of dL/dflow, or nullptr (then pushes reduce into dflow)
     float* norm;             // [R]: 1 / (R (N_nz(r) + eps))
     float* loss_r;           // [R]
     int32_t* nnz_r;          // [R]
@@ -59,7 +72,7 @@ struct Win {
     float* dego;             // [6]
     float* dego_part;        // [pix_tiles][6]
     int32_t* sync;           // [4] batched path: completion counters of the loss and gradient reductions and
-                             // of the binning count, then the halo (px) of the shared-memory flow boxes
+                             // of the binning count
     // spatial binning (batched path; tile_cnt == nullptr: events are used in their given order)
     int32_t* tile_cnt;       // [ntiles + 1] events per 32x32 tile, turned into tile starts by the scan
     int32_t* tile_cur;       // [ntiles] scatter cursors
@@ -194,41 +207,32 @@ __device__ __forceinline__ bool load_event(const Win& d, int64_t k, EventAt& e)
     return true;
 }
 
-// A shared-memory copy of the flow (one field for all bins) over the box
-// [x0, x0+bw) x [y0, y0+bh) of the image, and optionally a shared-memory
-// accumulator of dL/dflow over the same box.  A block loads the box that covers
-// its events' trajectories; samples whose four corners fall inside it read
-// shared memory, the others global memory, with the same values either way.
-struct FlowBox {
-    const float2* s = nullptr;
-    float2* g = nullptr;
-    int x0 = 0, y0 = 0, bw = 0, bh = 0;
-
-    __device__ __forceinline__ bool holds(int ix, int iy, int ix1, int iy1) const
-    {
-        return s && ix >= x0 && iy >= y0 && ix1 < x0 + bw && iy1 < y0 + bh;
-    }
-};
-
-// the four flow values around a cell of field j, from the box when it holds them
-__device__ __forceinline__ Quad quad_at(const Win& d, int j, const Bil& s, const FlowBox& fb)
+// one 32-byte load of a flow quad (read-only for the kernel's lifetime)
+__device__ __forceinline__ Quad load_fq(const FQ* p)
 {
-    const int ix1 = min(s.ix + 1, d.W - 1), iy1 = min(s.iy + 1, d.H - 1);
-    if (fb.holds(s.ix, s.iy, ix1, iy1)) {
-        const int lx = s.ix - fb.x0, ly = s.iy - fb.y0, lx1 = ix1 - fb.x0, ly1 = iy1 - fb.y0;
-        Quad q;
-        q.u00 = fb.s[ly * fb.bw + lx];
-        q.u10 = fb.s[ly * fb.bw + lx1];
-        q.u01 = fb.s[ly1 * fb.bw + lx];
-        q.u11 = fb.s[ly1 * fb.bw + lx1];
-        return q;
-    }
+    Quad q;
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(q.u00.x), "=f"(q.u00.y), "=f"(q.u10.x), "=f"(q.u10.y), "=f"(q.u01.x), "=f"(q.u01.y), "=f"(q.u11.x),
+          "=f"(q.u11.y)
+        : "l"(p));
+    return q;
+}
+
+__device__ __forceinline__ size_t cell_index(const Win& d, int j, int x, int y)
+{
+    return (d.nfb == 1 ? (size_t)0 : (size_t)j * plane_size(d)) + (size_t)y * d.W + x;
+}
+
+// the four flow values around a cell of field j: one quad load, else four gathers
+__device__ __forceinline__ Quad quad_at(const Win& d, int j, const Bil& s)
+{
+    if (d.fq) return load_fq(d.fq + cell_index(d, j, s.ix, s.iy));
     return load_quad(field(d, j), d.W, d.H, s);
 }
 
-__device__ __forceinline__ float2 flow_at_pixel(const Win& d, int j, int x, int y, const FlowBox& fb)
+__device__ __forceinline__ float2 flow_at_pixel(const Win& d, int j, int x, int y)
 {
-    if (fb.holds(x, y, x, y)) return fb.s[(y - fb.y0) * fb.bw + (x - fb.x0)];
+    if (d.fq) return __ldg(reinterpret_cast<const float2*>(d.fq + cell_index(d, j, x, y)));
     return __ldg(field(d, j) + (size_t)y * d.W + x);
 }
 
@@ -236,13 +240,12 @@ __device__ __forceinline__ float2 flow_at_pixel(const Win& d, int j, int x, int 
 // chain b+1..B; with all edges as references also the backward chain b..0)
 // and the global mask.  Returns false when any computed point leaves the image.
 template <int MAXB>
-__device__ __forceinline__ bool trajectory(const Win& d, const EventAt& e, Traj<MAXB>& P,
-                                           const FlowBox& fb = FlowBox())
+__device__ __forceinline__ bool trajectory(const Win& d, const EventAt& e, Traj<MAXB>& P)
 {
     const int W = d.W, H = d.H, B = d.B, b = e.b;
     const float W1 = (float)(W - 1), H1 = (float)(H - 1);
     const float h = __fdiv_rn(1.0f, (float)B);
-    const float2 u0 = flow_at_pixel(d, b, e.xk, e.yk, fb);
+    const float2 u0 = flow_at_pixel(d, b, e.xk, e.yk);
     const float fxk = (float)e.xk, fyk = (float)e.yk;
     bool ok = true;
     const float dtf = __fsub_rn(edge_tau(b + 1, B), e.tau);
@@ -254,7 +257,7 @@ __device__ __forceinline__ bool trajectory(const Win& d, const EventAt& e, Traj<
                 P.y[j] = __fmaf_rn(dtf, u0.y, fyk);
             } else if (ok) {
                 const Bil s = bil(P.x[j - 1], P.y[j - 1]);
-                const float2 u = interp(s, quad_at(d, j - 1, s, fb));
+                const float2 u = interp(s, quad_at(d, j - 1, s));
                 P.x[j] = __fmaf_rn(h, u.x, P.x[j - 1]);
                 P.y[j] = __fmaf_rn(h, u.y, P.y[j - 1]);
             } else {
@@ -276,7 +279,7 @@ __device__ __forceinline__ bool trajectory(const Win& d, const EventAt& e, Traj<
                     P.y[j] = __fmaf_rn(-dtb, u0.y, fyk);
                 } else if (ok) {
                     const Bil s = bil(P.x[j + 1], P.y[j + 1]);
-                    const float2 u = interp(s, quad_at(d, j, s, fb));
+                    const float2 u = interp(s, quad_at(d, j, s));
                     P.x[j] = __fmaf_rn(-h, u.x, P.x[j + 1]);
                     P.y[j] = __fmaf_rn(-h, u.y, P.y[j + 1]);
                 } else {
@@ -296,6 +299,12 @@ __device__ __forceinline__ bool trajectory(const Win& d, const EventAt& e, Traj<
 __device__ __forceinline__ void red_add_v2(float* addr, float a, float b)
 {
     asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(addr), "f"(a), "f"(b));
+}
+
+// 16-byte vector reduction (16-byte aligned address), same conventions
+__device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float c, float e)
+{
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a), "f"(b), "f"(c), "f"(e));
 }
 
 // S4: bilinear splat of one point (weight w to C_p, w * tbar to S_p) into one
@@ -330,6 +339,12 @@ struct RedSink {
                                             float hy, int64_t) const
     {
         const int W = d.W;
+        if (d.dq) {
+            float* q = reinterpret_cast<float*>(d.dq + cell_index(d, field, s.ix, s.iy));
+            red_add_v4(q, s.w00 * hx, s.w00 * hy, s.w10 * hx, s.w10 * hy);
+            if (s.ay > 0.0f) red_add_v4(q + 4, s.w01 * hx, s.w01 * hy, s.w11 * hx, s.w11 * hy);
+            return;
+        }
         float* g = reinterpret_cast<float*>(field_grad(d, field) + (size_t)s.iy * W + s.ix);
         red_add_v2(g, s.w00 * hx, s.w00 * hy);
         if (s.ax > 0.0f) red_add_v2(g + 2, s.w10 * hx, s.w10 * hy);
@@ -340,6 +355,10 @@ struct RedSink {
     __device__ __forceinline__ void point(const Win& d, int field, int, int xk, int yk, float vx, float vy,
                                           int64_t) const
     {
+        if (d.dq) {
+            red_add_v2(reinterpret_cast<float*>(d.dq + cell_index(d, field, xk, yk)), vx, vy);
+            return;
+        }
         red_add_v2(reinterpret_cast<float*>(field_grad(d, field) + (size_t)yk * d.W + xk), vx, vy);
     }
 };
@@ -373,63 +392,13 @@ struct EmitSink {
     }
 };
 
-// Adds the flow-gradient scatter of the adjoint into the block's shared-memory
-// box (FlowBox::g) when all corners it touches lie inside, else into global
-// memory; the block flushes the box with vector reductions afterwards.
-struct BoxRedSink {
-    const FlowBox* fb;
-
-    __device__ __forceinline__ void splat(const Win& d, int r, float px, float py, float tbar, int pol2,
-                                          int64_t k) const
-    {
-        RedSink().splat(d, r, px, py, tbar, pol2, k);
-    }
-    __device__ __forceinline__ void scatter(const Win& d, int field, int edge, const Bil& s, float px, float py,
-                                            float hx, float hy, int64_t k) const
-    {
-        const int ix1 = s.ax > 0.0f ? s.ix + 1 : s.ix, iy1 = s.ay > 0.0f ? s.iy + 1 : s.iy;
-        if (!fb->g || !fb->holds(s.ix, s.iy, ix1, iy1)) {
-            RedSink().scatter(d, field, edge, s, px, py, hx, hy, k);
-            return;
-        }
-        const int bw = fb->bw;
-        float2* g = fb->g + (s.iy - fb->y0) * bw + (s.ix - fb->x0);
-        atomicAdd(&g[0].x, s.w00 * hx);
-        atomicAdd(&g[0].y, s.w00 * hy);
-        if (s.ax > 0.0f) {
-            atomicAdd(&g[1].x, s.w10 * hx);
-            atomicAdd(&g[1].y, s.w10 * hy);
-        }
-        if (s.ay > 0.0f) {
-            atomicAdd(&g[bw].x, s.w01 * hx);
-            atomicAdd(&g[bw].y, s.w01 * hy);
-        }
-        if (s.ax > 0.0f && s.ay > 0.0f) {
-            atomicAdd(&g[bw + 1].x, s.w11 * hx);
-            atomicAdd(&g[bw + 1].y, s.w11 * hy);
-        }
-    }
-    __device__ __forceinline__ void point(const Win& d, int field, int edge, int xk, int yk, float vx, float vy,
-                                          int64_t k) const
-    {
-        if (!fb->g || !fb->holds(xk, yk, xk, yk)) {
-            RedSink().point(d, field, edge, xk, yk, vx, vy, k);
-            return;
-        }
-        float2* g = fb->g + (yk - fb->y0) * fb->bw + (xk - fb->x0);
-        atomicAdd(&g->x, vx);
-        atomicAdd(&g->y, vy);
-    }
-};
-
 template <int MAXB, class Sink = RedSink>
-__device__ __forceinline__ void splat_event(const Win& d, int64_t k, const Sink& sink = Sink(),
-                                            const FlowBox& fb = FlowBox())
+__device__ __forceinline__ void splat_event(const Win& d, int64_t k, const Sink& sink = Sink())
 {
     EventAt e;
     if (!load_event(d, k, e)) return;
     Traj<MAXB> P;
-    if (!trajectory<MAXB>(d, e, P, fb)) return;
+    if (!trajectory<MAXB>(d, e, P)) return;
     if (d.ref_mode == kRefAll) {
 #pragma unroll
         for (int j = 0; j <= MAXB; ++j)
@@ -474,10 +443,10 @@ __device__ __forceinline__ float2 ref_adjoint(const Win& d, int r, int j, float 
 // gradient of field `field` and return lambda + hs J(x)^T lambda.
 template <class Sink>
 __device__ __forceinline__ float2 push_back(const Win& d, const Sink& sink, int field, int edge, float px, float py,
-                                            float hs, float2 lam, int64_t k, const FlowBox& fb)
+                                            float hs, float2 lam, int64_t k)
 {
     const Bil s = bil(px, py);
-    const Quad q = quad_at(d, field, s, fb);
+    const Quad q = quad_at(d, field, s);
     const float hx = hs * lam.x, hy = hs * lam.y;
     sink.scatter(d, field, edge, s, px, py, hx, hy, k);
     const float jxx = s.by * (q.u10.x - q.u00.x) + s.ay * (q.u11.x - q.u01.x);
@@ -494,13 +463,12 @@ __device__ __forceinline__ float2 push_back(const Win& d, const Sink& sink, int 
 // each reference point is gathered from the loss-transformed IWE, and the
 // adjoint is carried back along both chains of pushes, scattering dL/dflow.
 template <int MAXB, class Sink = RedSink>
-__device__ __forceinline__ void adjoint_event(const Win& d, int64_t k, float dl, const Sink& sink = Sink(),
-                                              const FlowBox& fb = FlowBox())
+__device__ __forceinline__ void adjoint_event(const Win& d, int64_t k, float dl, const Sink& sink = Sink())
 {
     EventAt e;
     if (!load_event(d, k, e)) return;
     Traj<MAXB> P;
-    if (!trajectory<MAXB>(d, e, P, fb)) return;
+    if (!trajectory<MAXB>(d, e, P)) return;
     const int B = d.B, b = e.b;
     const float h = __fdiv_rn(1.0f, (float)B);
     const bool all = d.ref_mode == kRefAll;
@@ -515,7 +483,7 @@ __device__ __forceinline__ void adjoint_event(const Win& d, int64_t k, float dl,
                 lam.y += a.y;
             }
             if (j > b + 1) {
-                lam = push_back(d, sink, j - 1, j, P.x[j - 1], P.y[j - 1], h, lam, k, fb);
+                lam = push_back(d, sink, j - 1, j, P.x[j - 1], P.y[j - 1], h, lam, k);
             } else {
                 const float dtf = __fsub_rn(edge_tau(b + 1, B), e.tau);
                 sink.point(d, b, j, e.xk, e.yk, dtf * lam.x, dtf * lam.y, k);
@@ -532,7 +500,7 @@ __device__ __forceinline__ void adjoint_event(const Win& d, int64_t k, float dl,
             lam.x += a.x;
             lam.y += a.y;
             if (j < b) {
-                lam = push_back(d, sink, j, j, P.x[j + 1], P.y[j + 1], -h, lam, k, fb);
+                lam = push_back(d, sink, j, j, P.x[j + 1], P.y[j + 1], -h, lam, k);
             } else {
                 const float dtb = __fsub_rn(e.tau, edge_tau(b, B));
                 sink.point(d, b, j, e.xk, e.yk, -dtb * lam.x, -dtb * lam.y, k);
@@ -614,6 +582,85 @@ __device__ __forceinline__ void flow_tile(const Win& d, int tile, int ntiles)
     }
 }
 
+// S1 for the flow quads: writes record (u, v) from the flow at the cell's four
+// corners (clamped to the image): the motion field evaluated there for depth
+// input, the given field for flow input.  Returns the flow at (u, v).  Every
+// corner value is the same FP32 function of its own pixel as in flow_tile, so
+// a quad holds exactly the values four gathers would read.
+__device__ __forceinline__ float2 build_quad(const Win& d, int u, int v)
+{
+    const int u1 = min(u + 1, d.W - 1), v1 = min(v + 1, d.H - 1);
+    const size_t r0 = (size_t)v * d.W, r1 = (size_t)v1 * d.W;
+    float2 f00, f10, f01, f11;
+    if (d.rho) {
+        f00 = motion_field(u, v, __ldg(d.rho + r0 + u), d.ego, d.fx, d.fy, d.cx, d.cy, d.dt);
+        f10 = motion_field(u1, v, __ldg(d.rho + r0 + u1), d.ego, d.fx, d.fy, d.cx, d.cy, d.dt);
+        f01 = motion_field(u, v1, __ldg(d.rho + r1 + u), d.ego, d.fx, d.fy, d.cx, d.cy, d.dt);
+        f11 = motion_field(u1, v1, __ldg(d.rho + r1 + u1), d.ego, d.fx, d.fy, d.cx, d.cy, d.dt);
+    } else {
+        f00 = __ldg(d.flow + r0 + u);
+        f10 = __ldg(d.flow + r0 + u1);
+        f01 = __ldg(d.flow + r1 + u);
+        f11 = __ldg(d.flow + r1 + u1);
+    }
+    FQ* q = const_cast<FQ*>(d.fq) + r0 + u;
+    q->a = make_float4(f00.x, f00.y, f10.x, f10.y);
+    q->b = make_float4(f01.x, f01.y, f11.x, f11.y);
+    return f00;
+}
+
+// dL/dflow at pixel (x, y) from the quad accumulators (one field): the sum of
+// every record corner whose clamped index is this pixel.  Corner 00 of its own
+// cell; corner 10 of cell x-1 (and of its own cell on the right border);
+// corner 01 of cell y-1 (and of its own cell on the bottom border); corner 11
+// of the cells combining both.
+__device__ __forceinline__ float2 fold_dq(const Win& d, int x, int y)
+{
+    const int W = d.W, H = d.H;
+    const float4* Q = reinterpret_cast<const float4*>(d.dq);
+    auto at = [&](int qx, int qy, int half) { return Q[2 * ((size_t)qy * W + qx) + half]; };
+    const float4 own = at(x, y, 0);
+    float gx = own.x, gy = own.y;
+    if (x >= 1) {
+        const float4 t = at(x - 1, y, 0);
+        gx += t.z;
+        gy += t.w;
+    }
+    if (x == W - 1) {
+        gx += own.z;
+        gy += own.w;
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        if (k == 0 ? y < 1 : y != H - 1) continue;
+        const int qy = k == 0 ? y - 1 : y;
+        const float4 t = at(x, qy, 1);
+        gx += t.x;
+        gy += t.y;
+        if (x >= 1) {
+            const float4 l = at(x - 1, qy, 1);
+            gx += l.z;
+            gy += l.w;
+        }
+        if (x == W - 1) {
+            gx += t.z;
+            gy += t.w;
+        }
+    }
+    return make_float2(gx, gy);
+}
+
+// dL/dflow of one tile's pixels from the quad accumulators (flow-input windows)
+__device__ __forceinline__ void fold_tile(const Win& d, int tile, int ntiles)
+{
+    const int W = d.W;
+    const size_t HW = plane_size(d);
+    for (size_t i = (size_t)tile * blockDim.x + threadIdx.x; i < HW; i += (size_t)ntiles * blockDim.x) {
+        const int v = (int)(i / W), u = (int)(i - (size_t)v * W);
+        d.dflow[i] = fold_dq(d, u, v);
+    }
+}
+
 // S5 pass 1 over one tile of plane r: T = S/(C+eps) for both polarities, the
 // sum of T^2 and the non-empty count go to out[0]; the plane is rewritten in
 // place as (A+, T+, A-, T-) with A = 2T/(C+eps), all that the adjoint needs.
@@ -626,13 +673,15 @@ __device__ __forceinline__ void loss_tile(const Win& d, int r, int tile, int nti
     float s = 0.0f;
     int cnt = 0;
     const size_t stride = (size_t)ntiles * blockDim.x;
+    // one correctly rounded reciprocal per polarity instead of four
+    // full-precision divisions, which made this pass instruction-bound
     auto one = [&](float4 q, size_t i) {
-        const float cp = q.x + eps, cm = q.z + eps;
-        const float tp = q.y / cp, tm = q.w / cm;
+        const float rp = __frcp_rn(q.x + eps), rm = __frcp_rn(q.z + eps);
+        const float tp = q.y * rp, tm = q.w * rm;
         s = fmaf(tp, tp, s);
         s = fmaf(tm, tm, s);
         cnt += (q.x > 0.0f || q.z > 0.0f) ? 1 : 0;
-        plane[i] = make_float4(2.0f * tp / cp, tp, 2.0f * tm / cm, tm);
+        plane[i] = make_float4(2.0f * tp * rp, tp, 2.0f * tm * rm, tm);
     };
     size_t i = (size_t)tile * blockDim.x + threadIdx.x;
     // four independent loads in flight per thread (the pass is latency-bound otherwise)
@@ -707,6 +756,15 @@ __device__ __forceinline__ void depth_ego_tile(const Win& d, int tile, int ntile
     const float ifx = 1.0f / d.fx, ify = 1.0f / d.fy;
     const float sx = d.dt * d.fx, sy = d.dt * d.fy;
     float g[6] = {0, 0, 0, 0, 0, 0};
+    // dL/dflow at pixel i: folded from the quad accumulators (and stored) when
+    // the pushes went there, else read
+    auto dfl = [&](size_t i) -> float2 {
+        if (!d.dq) return d.dflow[i];
+        const int v = (int)(i / W), u = (int)(i - (size_t)v * W);
+        const float2 f = fold_dq(d, u, v);
+        d.dflow[i] = f;
+        return f;
+    };
     auto one = [&](size_t i, float r, float2 df) {
         const int v = (int)(i / W), u = (int)(i - (size_t)v * W);
         const float xn = ((float)u - d.cx) * ifx, yn = ((float)v - d.cy) * ify;
@@ -724,14 +782,13 @@ __device__ __forceinline__ void depth_ego_tile(const Win& d, int tile, int ntile
     for (; i + 3 * stride < HW; i += 4 * stride) {  // four independent load pairs in flight
         const float r0 = __ldg(d.rho + i), r1 = __ldg(d.rho + i + stride);
         const float r2 = __ldg(d.rho + i + 2 * stride), r3 = __ldg(d.rho + i + 3 * stride);
-        const float2 f0 = d.dflow[i], f1 = d.dflow[i + stride], f2 = d.dflow[i + 2 * stride],
-                     f3 = d.dflow[i + 3 * stride];
+        const float2 f0 = dfl(i), f1 = dfl(i + stride), f2 = dfl(i + 2 * stride), f3 = dfl(i + 3 * stride);
         one(i, r0, f0);
         one(i + stride, r1, f1);
         one(i + 2 * stride, r2, f2);
         one(i + 3 * stride, r3, f3);
     }
-    for (; i < HW; i += stride) one(i, __ldg(d.rho + i), d.dflow[i]);
+    for (; i < HW; i += stride) one(i, __ldg(d.rho + i), dfl(i));
     __shared__ float sg[32][6];
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
 #pragma unroll
