@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="bound of the CPU oracle sample")
     ap.add_argument("--schedule", default="auto",
                     help="batch schedule 'chains,windows_per_kernel,tile_grouping' (e.g. 4,2,0), or 'auto' to autotune")
+    ap.add_argument("--store-warps", type=int, default=0, choices=[0, 1],
+                    help="1: the forward stores the trajectory points for the backward (no recompute)")
     ap.add_argument("--serve", action="store_true", help="run the serving workload instead (one line per rate)")
     ap.add_argument("--serve-scales", default="0.25,0.5,1.0", help="arrival-rate multipliers of 100 Hz per stream")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
@@ -263,7 +265,7 @@ class Batch:
     of them (the timed path) and one workspace per window for the plain
     per-window comparison through the single-window entry points."""
 
-    def __init__(self, wins, device):
+    def __init__(self, wins, device, store_warps=False):
         import torch
 
         from paper_2412_06359_gb300 import cm
@@ -273,7 +275,7 @@ class Batch:
         self.items = []
         dev_wins = []
         for w in wins:
-            cfg = cm.loss_cfg(w.nbins, w.ref_mode, cm.SPLAT_ATOMIC)
+            cfg = cm.loss_cfg(w.nbins, w.ref_mode, cm.SPLAT_ATOMIC, store_warps=store_warps)
             ws = cm.Workspace(w.cam, cfg, w.events.n, 1, device)
             ev = cm.DeviceEvents.from_host(w.events, device)
             rho = torch.from_numpy(w.inv_depth).to(device)
@@ -283,7 +285,8 @@ class Batch:
             self.items.append((w, ws, ev, rho, ego, out, loss))
             dev_wins.append({"cam": w.cam, "ev": ev, "inv_depth": rho, "ego": ego, "dt": w.dt})
         self.dloss = torch.ones(1, device=device)
-        self.plan = cm.BatchPlan(dev_wins, cm.loss_cfg(wins[0].nbins, wins[0].ref_mode, cm.SPLAT_ATOMIC), device)
+        self.plan = cm.BatchPlan(dev_wins, cm.loss_cfg(wins[0].nbins, wins[0].ref_mode, cm.SPLAT_ATOMIC,
+                                                       store_warps=store_warps), device)
         self.events = sum(w.events.n for w in wins)
 
     def step(self):
@@ -314,7 +317,7 @@ def run_ours(args):
 
     # weak scaling: every rank evaluates its own 64 windows
     wins = synth.batch_windows(args.windows, first=first_window_of(rank, args.windows))
-    batch = Batch(wins, dev)
+    batch = Batch(wins, dev, store_warps=bool(args.store_warps))
     hw = wins[0].cam.width * wins[0].cam.height
     R = wins[0].nbins + 1
     stream = torch.cuda.current_stream()
@@ -413,6 +416,7 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "windows": len(wins), "events_per_step": batch.events,
                        "sensor": "640x480", "bins": wins[0].nbins, "refs": R, "splat": "atomic",
+                       "backward": "stored warps" if args.store_warps else "recompute",
                        "path": "batched plan replayed from a CUDA graph",
                        "schedule": {"chains": schedule[0], "windows_per_kernel": schedule[1],
                                     "tile_grouping": bool(schedule[2])},

@@ -99,7 +99,12 @@ typedef struct {
     int32_t nbins;        /* B, 1..CM_MAX_BINS */
     int32_t ref_mode;     /* CM_REF_END or CM_REF_ALL_EDGES */
     int32_t splat;        /* CM_SPLAT_* */
-    int32_t store_warps;  /* 0: the backward recomputes trajectories (default); 1: reserved */
+    int32_t store_warps;  /* 0: the backward recomputes the trajectories (default); 1: the forward
+                             stores every computed trajectory point ((B+1) x 8 bytes per event, in
+                             the workspace or the batch plan) and the backward reads them back, the
+                             choice of the paper's own backward (Sec. 3.3).  Same results either way
+                             (the points are the same FP32 values).  Windows that bring their own
+                             scratch (cm_window.scratch) always recompute. */
     float eps;            /* regulariser of both ratios; 1e-9 when <= 0 */
 } cm_loss_cfg;
 

@@ -34,8 +34,11 @@ def camera(cam) -> C.cm_camera:
     return C.cm_camera(int(cam.width), int(cam.height), float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy))
 
 
-def loss_cfg(nbins: int, ref_mode: int, splat: int = SPLAT_AUTO, eps: float = 1e-9) -> C.cm_loss_cfg:
-    return C.cm_loss_cfg(int(nbins), int(ref_mode), int(splat), 0, float(eps))
+def loss_cfg(nbins: int, ref_mode: int, splat: int = SPLAT_AUTO, eps: float = 1e-9,
+             store_warps: bool = False) -> C.cm_loss_cfg:
+    """store_warps: the forward keeps every trajectory point for the backward
+    ((B+1) x 8 bytes per event) instead of the backward recomputing them."""
+    return C.cm_loss_cfg(int(nbins), int(ref_mode), int(splat), int(bool(store_warps)), float(eps))
 
 
 def n_refs(cfg: C.cm_loss_cfg) -> int:

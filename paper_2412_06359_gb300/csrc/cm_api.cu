@@ -29,12 +29,14 @@ struct cm_workspace {
     float* loss_r;
     int32_t* nnz_r;
     float* dego_part;
+    float2* warp;            // [B+1][max_events] stored trajectory points (store_warps), else nullptr
     bool has_sort;           // buffers of the deterministic sort path are laid out
     cmk::SortBufs sb;
     // state of the last forward on this workspace
     int fwd_mode;            // 0 none, 1 flow input, 2 depth input
     const void* fwd_events;  // event x pointer of the last forward
     int64_t fwd_n;
+    bool fwd_warp;           // the last forward stored its trajectory points in `warp`
 };
 
 namespace {
@@ -54,7 +56,7 @@ int tiles_for(size_t hw, int cap)
 }
 
 struct Layout {
-    size_t iwe, flow, dflow, loss_part, norm, loss_r, nnz_r, dego_part, total;
+    size_t iwe, flow, dflow, loss_part, norm, loss_r, nnz_r, dego_part, warp, total;
     size_t ka, kb, va, vb, pay, hist, part, start;  // sort path (CM_SPLAT_SORT only)
     int R, loss_tiles, pix_tiles;
     bool sort;
@@ -77,7 +79,7 @@ int check_cfg(const cm_loss_cfg* cfg)
     if (cfg->nbins < 1 || cfg->nbins > CM_MAX_BINS) return CM_EINVAL;
     if (cfg->ref_mode != CM_REF_END && cfg->ref_mode != CM_REF_ALL_EDGES) return CM_EINVAL;
     if (cfg->splat != CM_SPLAT_AUTO && cfg->splat != CM_SPLAT_ATOMIC && cfg->splat != CM_SPLAT_SORT) return CM_EINVAL;
-    if (cfg->store_warps != 0) return CM_EINVAL;
+    if (cfg->store_warps != 0 && cfg->store_warps != 1) return CM_EINVAL;
     if (!std::isfinite(cfg->eps)) return CM_EINVAL;
     return CM_OK;
 }
@@ -118,6 +120,8 @@ Layout layout(const cm_camera& cam, const cm_loss_cfg& cfg, int32_t nfb, int64_t
     off = align_up(off + (size_t)L.R * sizeof(int32_t));
     L.dego_part = off;
     off = align_up(off + (size_t)L.pix_tiles * 6 * sizeof(float));
+    L.warp = off;
+    if (cfg.store_warps) off = align_up(off + (size_t)(cfg.nbins + 1) * max_events * sizeof(float2));
     L.sort = cfg.splat == CM_SPLAT_SORT;
     if (L.sort) {
         const cmk::SortSizes z = cmk::sort_sizes(max_events, L.R, cfg.nbins, nfb, HW);
@@ -189,8 +193,11 @@ void attach_ws(Win& d, cm_workspace* ws)
 bool same_shape(const cm_workspace* ws, const cm_camera& cam, const cm_loss_cfg& cfg, int32_t nfb)
 {
     return ws->cam.width == cam.width && ws->cam.height == cam.height && ws->cfg.nbins == cfg.nbins &&
-           ws->cfg.ref_mode == cfg.ref_mode && nfb <= ws->nfb;
+           ws->cfg.ref_mode == cfg.ref_mode && nfb <= ws->nfb && (!cfg.store_warps || ws->warp);
 }
+
+// stored warps: [B+1][n] points of this call's events in the workspace
+float2* warp_of(const cm_workspace* ws, const cm_loss_cfg& cfg) { return cfg.store_warps ? ws->warp : nullptr; }
 
 }  // namespace
 
@@ -267,6 +274,7 @@ int cm_workspace_create(void* dev_mem, size_t bytes, const cm_camera* cam, const
     ws->loss_r = reinterpret_cast<float*>(b + L.loss_r);
     ws->nnz_r = reinterpret_cast<int32_t*>(b + L.nnz_r);
     ws->dego_part = reinterpret_cast<float*>(b + L.dego_part);
+    ws->warp = cfg->store_warps ? reinterpret_cast<float2*>(b + L.warp) : nullptr;
     ws->has_sort = L.sort;
     if (L.sort) {
         ws->sb.ka = reinterpret_cast<uint32_t*>(b + L.ka);
@@ -350,6 +358,7 @@ int cm_loss_forward(const cm_camera* cam, const cm_events* ev, const float* flow
     Win d = make_win(*cam, ev, *cfg, n_flow_bins);
     attach_ws(d, ws);
     d.loss = loss_out;
+    d.warp = warp_of(ws, *cfg);
     if (depth) {
         d.rho = inv_depth;
         d.ego = ego6;
@@ -371,6 +380,7 @@ int cm_loss_forward(const cm_camera* cam, const cm_events* ev, const float* flow
     ws->fwd_mode = depth ? 2 : 1;
     ws->fwd_events = ev->x;
     ws->fwd_n = ev->n;
+    ws->fwd_warp = d.warp != nullptr;
     return CM_OK;
 }
 
@@ -392,6 +402,7 @@ int cm_loss_backward(const cm_camera* cam, const cm_events* ev, const float* flo
     Win d = make_win(*cam, ev, *cfg, n_flow_bins);
     attach_ws(d, ws);
     d.dloss = dloss;
+    d.warp = ws->fwd_warp ? ws->warp : nullptr;  // read back whenever the forward stored them
     d.flow = depth ? ws->flow : reinterpret_cast<const float2*>(flow);
     d.dflow = dflow ? reinterpret_cast<float2*>(dflow) : ws->dflow;
     if (!depth && !dflow) return CM_OK;

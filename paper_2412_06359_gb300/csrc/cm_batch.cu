@@ -6,14 +6,21 @@
 // tile to its window (binary search), so windows of very different sizes share
 // a launch with no padding.  Every kernel covers a range of windows.
 //
+// Layout.  A window's images of warped events are polarity planes of (C, S)
+// pairs ([R][2][H][W] float2), so the two corners of a splat row that start on
+// a 16-byte boundary take one 16-byte reduction (and one gather in the
+// adjoint).  The flow is kept as 32-byte quads (the four values a bilinear
+// sample reads) and dL/dflow is accumulated per cell in the same layout, then
+// folded per pixel by the gradient pass.
+//
 // Schedule.  A window's images of warped events (R x H x W x 16 bytes, 54 MB at
-// 640x480 with 11 references) are written by the splat, read and rewritten by
-// the loss pass and gathered by the adjoint; when the windows in flight exceed
-// the 129 MB L2 those passes go to DRAM.  The schedule therefore groups
-// windows (group = windows per kernel) and runs the groups on a few concurrent
-// chains of the graph, each chain taking its groups one after another: a few
-// windows are in flight, their images stay in L2, and the chains overlap each
-// other's tails and launch gaps.  group 0 puts every window in each kernel on
+// 640x480 with 11 references) are zeroed by the prep pass, reduced into by the
+// splat, read and rewritten by the loss pass and gathered by the adjoint; when
+// the windows in flight exceed the 129 MB L2 those passes go to DRAM.  The
+// schedule therefore groups windows (group = windows per kernel) and runs the
+// groups on a few concurrent chains of the graph, each chain taking its groups
+// one after another: a few windows are in flight, their images stay in L2, and
+// the chains overlap each other's tails and launch gaps.  group 0 puts every window in each kernel on
 // one chain.  cm_batch_autotune times the candidates on the plan's own windows.
 //
 // The window table, the prefix tables and the totals live in device memory;
@@ -265,7 +272,7 @@ __global__ void __launch_bounds__(kEventThreads, MAXB <= 10 ? 3 : 2) k_adjoint_b
         Win d = tab[w];
         use_grouped(d);
         const long long k = (c - cstart[w]) * kEventThreads + threadIdx.x;
-        if (k < d.n) adjoint_event<MAXB>(d, k, __ldg(d.dloss));
+        if (k < d.n) adjoint_event<MAXB, RedSink, true>(d, k, __ldg(d.dloss));  // polarity-plane images
     }
 }
 
@@ -338,7 +345,7 @@ int refs_of(const cm_loss_cfg& c) { return c.ref_mode == CM_REF_END ? 1 : c.nbin
 
 // device bytes of the per-window slabs for a list of windows
 struct Need {
-    size_t iwe, flow, dflow, quad, part, stat, dego, bins;
+    size_t iwe, flow, dflow, quad, part, stat, dego, bins, warp;
 };
 
 bool window_ok(const cm_window& w)
@@ -362,7 +369,7 @@ bool cfg_ok(const cm_loss_cfg* cfg)
     if (!cfg || cfg->nbins < 1 || cfg->nbins > CM_MAX_BINS) return false;
     if (cfg->ref_mode != CM_REF_END && cfg->ref_mode != CM_REF_ALL_EDGES) return false;
     if (cfg->splat != CM_SPLAT_AUTO && cfg->splat != CM_SPLAT_ATOMIC) return false;
-    return cfg->store_warps == 0 && std::isfinite(cfg->eps);
+    return (cfg->store_warps == 0 || cfg->store_warps == 1) && std::isfinite(cfg->eps);
 }
 
 size_t bin_bytes(int W, int H, int64_t n);
@@ -381,6 +388,7 @@ Need need_of(const cm_window* wins, int32_t nwin, const cm_loss_cfg& cfg)
         n.stat += (size_t)R;
         n.dego += (size_t)tiles_for(HW, 512) * 6 * sizeof(float);
         n.bins += bin_bytes(wins[i].cam.width, wins[i].cam.height, wins[i].ev.n);
+        if (cfg.store_warps) n.warp += up256((size_t)(cfg.nbins + 1) * wins[i].ev.n * sizeof(float2));
     }
     return n;
 }
@@ -429,7 +437,7 @@ WinScratch win_scratch(size_t HW, int R)
 
 struct Layout {
     size_t hdr, tab, cstart, sstart, lstart, pstart, table_end;  // the uploaded region [0, table_end)
-    size_t iwe, flow, dflow, quad, part, norm, lr, nnz, dego, sync, bins, total;
+    size_t iwe, flow, dflow, quad, part, norm, lr, nnz, dego, sync, bins, warp, total;
 };
 
 Layout layout_of(int cap, const Need& n)
@@ -469,6 +477,8 @@ Layout layout_of(int cap, const Need& n)
     o = up256(o + (size_t)cap * kSyncInts * sizeof(int32_t));
     L.bins = o;
     o = up256(o + n.bins);
+    L.warp = o;
+    o = up256(o + n.warp);
     L.total = o;
     return L;
 }
@@ -527,7 +537,7 @@ int stage_windows(cm_batch* b, const cm_window* wins, int32_t nwin)
     const Need n = need_of(wins, nwin, b->cfg);
     const Need& c = b->capn;
     if (n.iwe > c.iwe || n.dflow > c.dflow || n.quad > c.quad || n.part > c.part ||
-        n.stat > c.stat || n.dego > c.dego)
+        n.stat > c.stat || n.dego > c.dego || n.warp > c.warp)
         return CM_ENOMEM;
     // the previous upload must have left the staging buffer before it is rewritten
     if (cudaEventSynchronize(b->staged) != cudaSuccess) return CM_ECUDA;
@@ -542,7 +552,7 @@ int stage_windows(cm_batch* b, const cm_window* wins, int32_t nwin)
     int* ps = reinterpret_cast<int*>(s + b->L.pstart);
     const int R = refs_of(b->cfg);
     const float eps = b->cfg.eps > 0.0f ? b->cfg.eps : 1e-9f;
-    size_t o_iwe = 0, o_dflow = 0, o_quad = 0, o_part = 0, o_stat = 0, o_dego = 0, o_bins = 0;
+    size_t o_warp = 0, o_iwe = 0, o_dflow = 0, o_quad = 0, o_part = 0, o_stat = 0, o_dego = 0, o_bins = 0;
     long long chunks = 0;
     int lt_total = 0, pt_total = 0;
     char* base = b->base;
@@ -569,6 +579,7 @@ int stage_windows(cm_batch* b, const cm_window* wins, int32_t nwin)
         d.t0 = w.ev.t0;
         d.span = w.ev.t1 - w.ev.t0;
         d.eps = eps;
+        d.iwe_split = 1;  // polarity planes: row pairs of corners take one 16-byte reduction / gather
         d.dt = w.dt_window;
         d.fx = w.cam.fx;
         d.fy = w.cam.fy;
@@ -600,6 +611,10 @@ int stage_windows(cm_batch* b, const cm_window* wins, int32_t nwin)
             } else {
                 d.dflow = reinterpret_cast<float2*>(base + b->L.dflow + o_dflow);
                 o_dflow += HW * sizeof(float2);
+            }
+            if (b->cfg.store_warps && d.n > 0) {
+                d.warp = reinterpret_cast<float2*>(base + b->L.warp + o_warp);
+                o_warp += up256((size_t)(d.B + 1) * d.n * sizeof(float2));
             }
             d.fq = reinterpret_cast<const cmk::FQ*>(base + b->L.quad + o_quad);
             o_quad += HW * sizeof(cmk::FQ);

@@ -54,10 +54,15 @@ struct Win {
     float dt;                // window length (depth input)
     float fx, fy, cx, cy;    // intrinsics (depth input)
     const float2* flow;      // [nfb][H][W]
-    float4* iwe;             // [R][H][W]: (C+, S+, C-, S-); after the loss (A+, T+, A-, T-)
+    float4* iwe;             // iwe_split == 0: [R][H][W] (C+, S+, C-, S-);
+                             // iwe_split == 1: [R][2][H][W] float2 (C, S), one plane per polarity;
+                             // after the loss each (C, S) is (A, T) (see loss_tile)
+    int32_t iwe_split;
     float2* dflow;           // [nfb][H][W]
     const FQ* fq;            // [nfb][H][W] flow quads, or nullptr (then samples gather from flow)
     FQ* dq;                  // [nfb][H][W] quad accumulators of dL/dflow, or nullptr (then pushes reduce into dflow)
+    float2* warp;            // [B+1][n] trajectory points stored by the splat for the adjoint, or nullptr
+                             // (then the adjoint recomputes them)
     float* norm;             // [R]: 1 / (R (N_nz(r) + eps))
     float* loss_r;           // [R]
     int32_t* nnz_r;          // [R]
@@ -320,6 +325,32 @@ __device__ __forceinline__ void splat_point(float4* plane, int W, float px, floa
     if (s.ax > 0.0f && s.ay > 0.0f) red_add_v2(q + 4 * (size_t)W + 4, s.w11, __fmul_rn(s.w11, tbar));
 }
 
+// One row of a splat into polarity planes of (C, S) pairs: the left corner at
+// float2 index gi of the image, the right one behind it when `two`.  A pair
+// that starts on a 16-byte boundary takes one 16-byte reduction, else two
+// 8-byte ones (the L2 serves both widths at the same request rate).
+__device__ __forceinline__ void splat_row(float2* img, size_t gi, bool two, float wl, float wr, float tbar)
+{
+    float* q = reinterpret_cast<float*>(img + gi);
+    if (two && !(gi & 1)) {
+        red_add_v4(q, wl, __fmul_rn(wl, tbar), wr, __fmul_rn(wr, tbar));
+        return;
+    }
+    red_add_v2(q, wl, __fmul_rn(wl, tbar));
+    if (two) red_add_v2(q + 2, wr, __fmul_rn(wr, tbar));
+}
+
+// S4 into the polarity-plane layout: plane 2r + polarity
+__device__ __forceinline__ void splat_point_split(const Win& d, int r, float px, float py, float tbar, int pol2)
+{
+    const Bil s = bil(px, py);
+    const size_t gi = (size_t)(2 * r + (pol2 >> 1)) * plane_size(d) + (size_t)s.iy * d.W + s.ix;
+    float2* img = reinterpret_cast<float2*>(d.iwe);
+    const bool two = s.ax > 0.0f;
+    splat_row(img, gi, two, s.w00, s.w10, tbar);
+    if (s.ay > 0.0f) splat_row(img, gi + d.W, two, s.w01, s.w11, tbar);
+}
+
 // Where the splat (S4) and the flow-gradient scatter (S6) go.
 //
 // RedSink adds into the IWE / dL/dflow with 8-byte vector reductions (the order
@@ -332,7 +363,8 @@ struct RedSink {
     __device__ __forceinline__ void splat(const Win& d, int r, float px, float py, float tbar, int pol2,
                                           int64_t) const
     {
-        splat_point(d.iwe + (size_t)r * plane_size(d), d.W, px, py, tbar, pol2);
+        if (d.iwe_split) splat_point_split(d, r, px, py, tbar, pol2);
+        else splat_point(d.iwe + (size_t)r * plane_size(d), d.W, px, py, tbar, pol2);
     }
     // a push sampled at (px, py) in cell s: hs * w_c * lambda to the four corners
     __device__ __forceinline__ void scatter(const Win& d, int field, int, const Bil& s, float, float, float hx,
@@ -392,13 +424,56 @@ struct EmitSink {
     }
 };
 
+// Edge j of an event in bin b is a computed trajectory point: the forward
+// chain b+1..B, and with all edges as references also the backward chain 0..b.
+__device__ __forceinline__ bool computed_edge(const Win& d, int j, int b)
+{
+    return j <= d.B && (j > b || d.ref_mode == kRefAll);
+}
+
+// Stored warps: the splat writes every computed point of event k to
+// d.warp[j][k] (coalesced across a warp); the adjoint reads them back instead
+// of recomputing the trajectory, and takes the mask from them (a point outside
+// the image stays outside in every later point of its chain, so the test over
+// all stored points repeats the decision of the trajectory exactly).
+template <int MAXB>
+__device__ __forceinline__ void store_traj(const Win& d, const EventAt& e, const Traj<MAXB>& P, int64_t k)
+{
+#pragma unroll
+    for (int j = 0; j <= MAXB; ++j)
+        if (computed_edge(d, j, e.b)) d.warp[(size_t)j * d.n + k] = make_float2(P.x[j], P.y[j]);
+}
+
+template <int MAXB>
+__device__ __forceinline__ bool load_traj(const Win& d, const EventAt& e, Traj<MAXB>& P, int64_t k)
+{
+    const float W1 = (float)(d.W - 1), H1 = (float)(d.H - 1);
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j <= MAXB; ++j) {
+        if (computed_edge(d, j, e.b)) {
+            const float2 q = __ldg(d.warp + (size_t)j * d.n + k);
+            P.x[j] = q.x;
+            P.y[j] = q.y;
+            ok = ok && inside(q.x, q.y, W1, H1);
+            if (j == d.B) {
+                P.ex = q.x;
+                P.ey = q.y;
+            }
+        }
+    }
+    return ok;
+}
+
 template <int MAXB, class Sink = RedSink>
 __device__ __forceinline__ void splat_event(const Win& d, int64_t k, const Sink& sink = Sink())
 {
     EventAt e;
     if (!load_event(d, k, e)) return;
     Traj<MAXB> P;
-    if (!trajectory<MAXB>(d, e, P)) return;
+    const bool ok = trajectory<MAXB>(d, e, P);
+    if (d.warp) store_traj<MAXB>(d, e, P, k);
+    if (!ok) return;
     if (d.ref_mode == kRefAll) {
 #pragma unroll
         for (int j = 0; j <= MAXB; ++j)
@@ -408,15 +483,33 @@ __device__ __forceinline__ void splat_event(const Win& d, int64_t k, const Sink&
     }
 }
 
-// dL/dw for one corner from the loss-transformed image (A, T) = (2T/(C+eps), T):
-// phi = kappa * A * (tbar - T)
-__device__ __forceinline__ float phi_at(const float4* G, size_t i, int pol2, float kap, float tbar)
+// dL/dw_c of one corner from the loss-transformed pair (A, T), where
+// T = S/(C+eps) and A = 2T/(C+eps): phi = kappa * A * (tbar - T)
+__device__ __forceinline__ float phi_of(float A, float T, float kap, float tbar) { return kap * A * (tbar - T); }
+
+// phi of the two corners of one row in polarity-plane layout (left at float2
+// index gi, right behind it when `two`).  One 16-byte gather of the aligned
+// pair holding the left corner, plus an 8-byte one for the right corner when
+// the row starts at an odd index.  No branch: every lane issues its gathers
+// together, so the row costs one L2 latency (a divergent choice between the two
+// forms would serialise them).  The aligned pair never leaves the image: the
+// last float2 of the buffer has an odd index.
+__device__ __forceinline__ void phi_row(const float2* img, size_t gi, bool two, float kap, float tbar, float& pl,
+                                        float& pr)
 {
-    const float2 g = __ldg(reinterpret_cast<const float2*>(G + i) + (pol2 >> 1));
-    return kap * g.x * (tbar - g.y);
+    const bool odd = (gi & 1) != 0;
+    const float4 g = __ldg(reinterpret_cast<const float4*>(img + (gi & ~(size_t)1)));
+    float2 h = make_float2(0.0f, 0.0f);
+    if (two && odd) h = __ldg(img + gi + 1);
+    pl = odd ? phi_of(g.z, g.w, kap, tbar) : phi_of(g.x, g.y, kap, tbar);
+    pr = !two ? 0.0f : odd ? phi_of(h.x, h.y, kap, tbar) : phi_of(g.z, g.w, kap, tbar);
 }
 
-// position adjoint a = sum_c grad(w_c) phi_c at reference r, edge j
+// position adjoint a = sum_c grad(w_c) phi_c at reference r, edge j; corners
+// outside the image have phi = 0.  SPLIT: the image is in the polarity-plane
+// layout (Win::iwe_split == 1), a compile-time choice so that the event kernels
+// carry the code of one layout only.
+template <bool SPLIT>
 __device__ __forceinline__ float2 ref_adjoint(const Win& d, int r, int j, float px, float py, float tau, int pol2,
                                               float dl)
 {
@@ -425,13 +518,26 @@ __device__ __forceinline__ float2 ref_adjoint(const Win& d, int r, int j, float 
     const float kap = dl * __ldg(d.norm + r);
     const float tb = tbar_of(j, d.B, tau);
     const Bil s = bil(px, py);
-    const float4* G = d.iwe + (size_t)r * HW;
     const size_t i00 = (size_t)s.iy * W + s.ix;
     const bool inx = s.ix + 1 <= W - 1, iny = s.iy + 1 <= H - 1;
-    const float p00 = phi_at(G, i00, pol2, kap, tb);
-    const float p10 = inx ? phi_at(G, i00 + 1, pol2, kap, tb) : 0.0f;
-    const float p01 = iny ? phi_at(G, i00 + W, pol2, kap, tb) : 0.0f;
-    const float p11 = (inx && iny) ? phi_at(G, i00 + W + 1, pol2, kap, tb) : 0.0f;
+    float p00, p10 = 0.0f, p01 = 0.0f, p11 = 0.0f;
+    if (SPLIT) {
+        const float2* img = reinterpret_cast<const float2*>(d.iwe);
+        const size_t gi = (size_t)(2 * r + (pol2 >> 1)) * HW + i00;
+        phi_row(img, gi, inx, kap, tb, p00, p10);
+        phi_row(img, iny ? gi + W : gi, inx, kap, tb, p01, p11);  // unconditional: both rows in flight together
+        if (!iny) p01 = p11 = 0.0f;
+    } else {
+        const float2* G = reinterpret_cast<const float2*>(d.iwe + (size_t)r * HW) + (pol2 >> 1);
+        auto at = [&](size_t i) {
+            const float2 g = __ldg(G + 2 * i);
+            return phi_of(g.x, g.y, kap, tb);
+        };
+        p00 = at(i00);
+        if (inx) p10 = at(i00 + 1);
+        if (iny) p01 = at(i00 + W);
+        if (inx && iny) p11 = at(i00 + W + 1);
+    }
     float2 a;
     a.x = s.by * (p10 - p00) + s.ay * (p11 - p01);
     a.y = s.bx * (p01 - p00) + s.ax * (p11 - p10);
@@ -459,16 +565,17 @@ __device__ __forceinline__ float2 push_back(const Win& d, const Sink& sink, int 
     return out;
 }
 
-// S6: per-event adjoint.  The trajectory is recomputed; the position adjoint of
-// each reference point is gathered from the loss-transformed IWE, and the
-// adjoint is carried back along both chains of pushes, scattering dL/dflow.
-template <int MAXB, class Sink = RedSink>
+// S6: per-event adjoint.  The trajectory is recomputed (or read back when the
+// splat stored it); the position adjoint of each reference point is gathered
+// from the loss-transformed IWE, and the adjoint is carried back along both
+// chains of pushes, scattering dL/dflow.
+template <int MAXB, class Sink = RedSink, bool SPLIT = false>
 __device__ __forceinline__ void adjoint_event(const Win& d, int64_t k, float dl, const Sink& sink = Sink())
 {
     EventAt e;
     if (!load_event(d, k, e)) return;
     Traj<MAXB> P;
-    if (!trajectory<MAXB>(d, e, P)) return;
+    if (!(d.warp ? load_traj<MAXB>(d, e, P, k) : trajectory<MAXB>(d, e, P))) return;
     const int B = d.B, b = e.b;
     const float h = __fdiv_rn(1.0f, (float)B);
     const bool all = d.ref_mode == kRefAll;
@@ -478,7 +585,7 @@ __device__ __forceinline__ void adjoint_event(const Win& d, int64_t k, float dl,
     for (int j = MAXB; j >= 1; --j) {
         if (j <= B && j > b) {
             if (all || j == B) {
-                const float2 a = ref_adjoint(d, all ? j : 0, j, P.x[j], P.y[j], e.tau, e.pol2, dl);
+                const float2 a = ref_adjoint<SPLIT>(d, all ? j : 0, j, P.x[j], P.y[j], e.tau, e.pol2, dl);
                 lam.x += a.x;
                 lam.y += a.y;
             }
@@ -496,7 +603,7 @@ __device__ __forceinline__ void adjoint_event(const Win& d, int64_t k, float dl,
 #pragma unroll
     for (int j = 0; j <= MAXB - 1; ++j) {
         if (j <= b) {
-            const float2 a = ref_adjoint(d, j, j, P.x[j], P.y[j], e.tau, e.pol2, dl);
+            const float2 a = ref_adjoint<SPLIT>(d, j, j, P.x[j], P.y[j], e.tau, e.pol2, dl);
             lam.x += a.x;
             lam.y += a.y;
             if (j < b) {
@@ -661,38 +768,54 @@ __device__ __forceinline__ void fold_tile(const Win& d, int tile, int ntiles)
     }
 }
 
-// S5 pass 1 over one tile of plane r: T = S/(C+eps) for both polarities, the
-// sum of T^2 and the non-empty count go to out[0]; the plane is rewritten in
-// place as (A+, T+, A-, T-) with A = 2T/(C+eps), all that the adjoint needs.
-// Ends with __syncthreads (the caller may loop).
+// S5 pass 1 over one tile of reference r: T = S/(C+eps) for both polarities;
+// the sum of T^2 and the non-empty count go to out[0].  Each (C, S) pair is
+// rewritten in place as (A, T), A = 2T/(C+eps): all the adjoint needs at a
+// corner, in one gather and without a division.  Ends with __syncthreads (the
+// caller may loop).
 __device__ __forceinline__ void loss_tile(const Win& d, int r, int tile, int ntiles, float2* out)
 {
     const size_t HW = plane_size(d);
-    float4* plane = d.iwe + (size_t)r * HW;
     const float eps = d.eps;
     float s = 0.0f;
     int cnt = 0;
     const size_t stride = (size_t)ntiles * blockDim.x;
-    // one correctly rounded reciprocal per polarity instead of four
-    // full-precision divisions, which made this pass instruction-bound
+    // (C+, S+, C-, S-) of pixel i in either layout, and its rewrite
+    float4* plane = d.iwe + (size_t)r * HW;
+    float2* pos = reinterpret_cast<float2*>(d.iwe) + (size_t)2 * r * HW;
+    float2* neg = pos + HW;
+    const bool split = d.iwe_split != 0;
+    auto ld = [&](size_t i) {
+        if (!split) return plane[i];
+        const float2 a = pos[i], b = neg[i];
+        return make_float4(a.x, a.y, b.x, b.y);
+    };
+    // one correctly rounded reciprocal per polarity instead of full-precision
+    // divisions, which made this pass instruction-bound
     auto one = [&](float4 q, size_t i) {
         const float rp = __frcp_rn(q.x + eps), rm = __frcp_rn(q.z + eps);
         const float tp = q.y * rp, tm = q.w * rm;
         s = fmaf(tp, tp, s);
         s = fmaf(tm, tm, s);
         cnt += (q.x > 0.0f || q.z > 0.0f) ? 1 : 0;
-        plane[i] = make_float4(2.0f * tp * rp, tp, 2.0f * tm * rm, tm);
+        const float ap = 2.0f * tp * rp, am = 2.0f * tm * rm;
+        if (split) {
+            pos[i] = make_float2(ap, tp);
+            neg[i] = make_float2(am, tm);
+        } else {
+            plane[i] = make_float4(ap, tp, am, tm);
+        }
     };
     size_t i = (size_t)tile * blockDim.x + threadIdx.x;
     // four independent loads in flight per thread (the pass is latency-bound otherwise)
     for (; i + 3 * stride < HW; i += 4 * stride) {
-        const float4 q0 = plane[i], q1 = plane[i + stride], q2 = plane[i + 2 * stride], q3 = plane[i + 3 * stride];
+        const float4 q0 = ld(i), q1 = ld(i + stride), q2 = ld(i + 2 * stride), q3 = ld(i + 3 * stride);
         one(q0, i);
         one(q1, i + stride);
         one(q2, i + 2 * stride);
         one(q3, i + 3 * stride);
     }
-    for (; i < HW; i += stride) one(plane[i], i);
+    for (; i < HW; i += stride) one(ld(i), i);
     __shared__ float ss[32];
     __shared__ int sc[32];
     s = warp_sum(s);

@@ -22,14 +22,14 @@ def gpu_lib():
     return cm
 
 
-def run_gpu(win: synth.Window, *, splat=None, grad=True, dloss=1.0, eps=1e-9, want_iwe=False):
+def run_gpu(win: synth.Window, *, splat=None, grad=True, dloss=1.0, eps=1e-9, want_iwe=False, store_warps=False):
     """Loss (and gradients) of one window through cm_loss_forward / backward."""
     import torch
     cm = gpu_lib()
     if splat is None:
         splat = cm.SPLAT_ATOMIC
     dev = "cuda"
-    cfg = cm.loss_cfg(win.nbins, win.ref_mode, splat, eps)
+    cfg = cm.loss_cfg(win.nbins, win.ref_mode, splat, eps, store_warps)
     nfb = 1 if win.flow is None else win.flow.shape[0]
     ws = cm.Workspace(win.cam, cfg, max(win.events.n, 1), nfb, dev)
     ev = cm.DeviceEvents.from_host(win.events, dev)

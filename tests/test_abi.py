@@ -61,7 +61,7 @@ def test_workspace_query_sizes(lib):
 
 
 @pytest.mark.parametrize("bad", [
-    dict(nbins=0), dict(nbins=33), dict(ref_mode=2), dict(splat=7), dict(store_warps=1),
+    dict(nbins=0), dict(nbins=33), dict(ref_mode=2), dict(splat=7), dict(store_warps=2),
 ])
 def test_invalid_cfg_rejected(lib, bad):
     kw = dict(nbins=10, ref_mode=1, splat=1, store_warps=0, eps=1e-9)

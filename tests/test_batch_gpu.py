@@ -166,3 +166,16 @@ def test_autotune_picks_a_schedule_and_stays_correct():
     plan.run()
     for i in (0, 3):
         assert_parity(_batch_result(plan, i), run_oracle(wins[i]))
+
+
+@pytest.mark.parametrize("chains,group", [(1, 0), (2, 1)])
+def test_batch_with_stored_warps(chains, group):
+    cm = gpu_lib()
+    wins = _mixed_windows(6, 31)
+    plan = cm.BatchPlan(_dev_windows(cm, wins), cm.loss_cfg(10, cm.REF_ALL, cm.SPLAT_ATOMIC, store_warps=True))
+    plan.set_schedule(chains, group)
+    for _ in range(2):
+        plan.run()
+    for i, w in enumerate(wins):
+        if w.events.n:
+            assert_parity(_batch_result(plan, i), run_oracle(w))
