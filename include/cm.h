@@ -221,9 +221,9 @@ typedef struct {
     float* dinv_depth;      /* [H][W] dL/d(inverse depth), or NULL (depth input only) */
     float* dego6;           /* [6] dL/d(ego-motion), or NULL (depth input only) */
     void* scratch;          /* NULL, or 256-byte-aligned device memory of cm_window_scratch_query bytes
-                               holding this window's images of warped events, flow, reduction buffers
-                               and counters (instead of the plan's memory), e.g. kept resident per
-                               client stream by a server */
+                               holding this window's images of warped events, flow quads, gradient
+                               accumulators, reduction buffers and counters (instead of the plan's
+                               memory), e.g. kept resident per client stream by a server */
 } cm_window;
 
 /* Bytes of a window's own scratch (cm_window.scratch) for this camera and configuration. */
@@ -255,9 +255,10 @@ int cm_batch_run(cm_batch* plan, void* stream);
  * every window in each kernel.  Few windows in flight keep their images of
  * warped events in L2; several chains overlap each other's tails.  With `bin`
  * the events of each window are first grouped by 32x32-pixel tile (two extra
- * kernels), so that a block's events share a compact region whose flow the
- * splat reads from shared memory; windows that do not fit the plan's grouping
- * memory (sized for the windows it was created with) stay ungrouped.
+ * kernels), so that the events of a block touch a compact region of the flow
+ * and of the images; windows that do not fit the plan's grouping memory (sized
+ * for the windows it was created with) stay ungrouped.  Every schedule gives
+ * the same results up to the order of the floating-point reductions.
  * Default: chains 2, group 1, bin 0. */
 typedef struct {
     int32_t chains;  /* 1..8 */

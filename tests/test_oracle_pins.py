@@ -448,3 +448,35 @@ def test_depth_ego_gradient_matches_frozen_fd():
         v = rng.standard_normal(rho.shape)
         fd = (L(rho + 1e-6 * v, ego) - L(rho - 1e-6 * v, ego)) / 2e-6
         assert fd == pytest.approx(float((base["dinv_depth"] * v).sum()), rel=1e-5)
+
+
+# --------------------------------------------------------------------------
+# hand-derived worked cases (tests/golden/hand_cases.json, each with its
+# derivation and the passage it follows)
+
+
+def _golden_cases():
+    import json
+    import os
+    p = os.path.join(os.path.dirname(__file__), "golden", "hand_cases.json")
+    return json.load(open(p))["cases"]
+
+
+@pytest.mark.parametrize("case", _golden_cases(), ids=lambda c: c["name"])
+@pytest.mark.parametrize("positions", ["f64", "f32"])
+def test_golden_hand_cases(case, positions):
+    W, H = case["W"], case["H"]
+    xs, ys, ts, ps = zip(*case["events"])
+    e = ev(xs, ys, ts, ps)
+    mode = END if case["ref_mode"] == "end" else ALL
+    r = O.cm(e, uniform_flow(W, H, *case["flow"]), width=W, height=H, nbins=case["nbins"], ref_mode=mode,
+             positions=positions, want_iwe=True)
+    assert list(r["nnz_r"]) == case["nnz"]
+    assert r["loss"] == pytest.approx(case["loss"], rel=case["loss_rtol"], abs=1e-12)
+    iwe = r["iwe"]
+    expect = np.zeros_like(iwe)
+    for rr, x, y, pol, C, S in case["iwe"]:
+        k = 0 if pol > 0 else 2
+        expect[rr, y, x, k] += C
+        expect[rr, y, x, k + 1] += S
+    np.testing.assert_allclose(iwe, expect, rtol=0, atol=1e-12)
