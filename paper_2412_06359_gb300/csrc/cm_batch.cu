@@ -45,7 +45,6 @@ struct BatchHdr {
     long long total_chunks;  // event chunks of kEventThreads events
     int32_t total_ltiles;    // loss tiles (R x loss_tiles per window)
     int32_t total_ptiles;    // pixel tiles (pix_tiles per window)
-    long long iwe_f4;        // float4 elements of the IWE slab in use
 };
 
 // largest w in [lo, hi) with s[w] <= c (s non-decreasing; empty windows skipped)
@@ -93,11 +92,14 @@ __global__ void __launch_bounds__(256) k_prep_batch(const BatchHdr* h, const Win
         if (ti == 0 && threadIdx.x < 3) d.sync[threadIdx.x] = 0;
         const size_t HW = plane_size(d);
         const size_t stride = (size_t)d.pix_tiles * blockDim.x;
+        // the window's images as one flat run of 32-byte chunks (the slab is 32-byte aligned)
+        const size_t nf4 = (size_t)d.R * HW, n32 = nf4 / 2;
+        for (size_t c = (size_t)ti * blockDim.x + threadIdx.x; c < n32; c += stride) st_v8(d.iwe + 2 * c, z4, z4);
+        if ((nf4 & 1) && ti == 0 && threadIdx.x == 0) d.iwe[nf4 - 1] = z4;
         for (size_t i = (size_t)ti * blockDim.x + threadIdx.x; i < HW; i += stride) {
-            for (int r = 0; r < d.R; ++r) d.iwe[(size_t)r * HW + i] = z4;
-            d.dq[i].a = z4;
-            d.dq[i].b = z4;
-            const int v = (int)(i / d.W), u = (int)(i - (size_t)v * d.W);
+            st_v8(d.dq + i, z4, z4);
+            int u, v;
+            pixel_uv(i, d.W, u, v);
             build_quad(d, u, v);
         }
         if (d.tile_cnt) {
@@ -295,7 +297,7 @@ __global__ void __launch_bounds__(256) k_loss_batch(const BatchHdr* h, const Win
 
 // dL/dflow folded from the quad accumulators, and the depth / ego gradient per
 // tile; the block completing a window's last tile reduces the six ego sums
-__global__ void __launch_bounds__(256) k_grad_batch(const BatchHdr* h, const Win* tab, const int* pstart, int w0,
+__global__ void __launch_bounds__(256, 4) k_grad_batch(const BatchHdr* h, const Win* tab, const int* pstart, int w0,
                                                     int w1)
 {
     w1 = clamp_end(h, w1);
@@ -333,13 +335,21 @@ constexpr int kMaxChains = 8;
 
 size_t up256(size_t v) { return (v + 255) / 256 * 256; }
 
-int tiles_for(size_t hw, int cap)
+int tiles_for(size_t hw, size_t px_per_tile, int cap)
 {
-    size_t t = (hw + 2047) / 2048;
+    size_t t = (hw + px_per_tile - 1) / px_per_tile;
     if (t < 1) t = 1;
     if (t > (size_t)cap) t = cap;
     return (int)t;
 }
+
+// Tiles of a window's pixel passes (a tile is one block's share, 256 threads):
+// per reference for the loss pass (8 pixels per thread), per image for the prep
+// and gradient passes (2 pixels per thread).  Measured on GB300 at 640x480:
+// halving the loss tiles' pixels made the pass slower (per-tile reductions),
+// halving the prep tiles' pixels made prep faster.
+int loss_tiles_for(size_t hw) { return tiles_for(hw, 2048, 2048); }
+int pix_tiles_for(size_t hw) { return tiles_for(hw, 512, 4096); }
 
 int refs_of(const cm_loss_cfg& c) { return c.ref_mode == CM_REF_END ? 1 : c.nbins + 1; }
 
@@ -381,12 +391,12 @@ Need need_of(const cm_window* wins, int32_t nwin, const cm_loss_cfg& cfg)
     for (int i = 0; i < nwin; ++i) {
         if (wins[i].scratch) continue;  // the window brings its own buffers
         const size_t HW = (size_t)wins[i].cam.width * wins[i].cam.height;
-        n.iwe += (size_t)R * HW * sizeof(float4);
+        n.iwe += up256((size_t)R * HW * sizeof(float4));
         if (!wins[i].dflow) n.dflow += HW * sizeof(float2);
         n.quad += 2 * HW * sizeof(cmk::FQ);
-        n.part += (size_t)R * tiles_for(HW, 256) * sizeof(float2);
+        n.part += (size_t)R * loss_tiles_for(HW) * sizeof(float2);
         n.stat += (size_t)R;
-        n.dego += (size_t)tiles_for(HW, 512) * 6 * sizeof(float);
+        n.dego += (size_t)pix_tiles_for(HW) * 6 * sizeof(float);
         n.bins += bin_bytes(wins[i].cam.width, wins[i].cam.height, wins[i].ev.n);
         if (cfg.store_warps) n.warp += up256((size_t)(cfg.nbins + 1) * wins[i].ev.n * sizeof(float2));
     }
@@ -420,7 +430,7 @@ WinScratch win_scratch(size_t HW, int R)
     s.dq = o;
     o = up256(o + HW * sizeof(cmk::FQ));
     s.part = o;
-    o = up256(o + (size_t)R * tiles_for(HW, 256) * sizeof(float2));
+    o = up256(o + (size_t)R * loss_tiles_for(HW) * sizeof(float2));
     s.norm = o;
     o = up256(o + (size_t)R * sizeof(float));
     s.lr = o;
@@ -428,7 +438,7 @@ WinScratch win_scratch(size_t HW, int R)
     s.nnz = o;
     o = up256(o + (size_t)R * sizeof(int32_t));
     s.dego = o;
-    o = up256(o + (size_t)tiles_for(HW, 512) * 6 * sizeof(float));
+    o = up256(o + (size_t)pix_tiles_for(HW) * 6 * sizeof(float));
     s.sync = o;
     o = up256(o + kSyncInts * sizeof(int32_t));
     s.total = o;
@@ -585,8 +595,8 @@ int stage_windows(cm_batch* b, const cm_window* wins, int32_t nwin)
         d.fy = w.cam.fy;
         d.cx = w.cam.cx;
         d.cy = w.cam.cy;
-        d.loss_tiles = tiles_for(HW, 256);
-        d.pix_tiles = tiles_for(HW, 512);
+        d.loss_tiles = loss_tiles_for(HW);
+        d.pix_tiles = pix_tiles_for(HW);
         if (w.scratch) {
             // every per-window buffer in the window's own scratch
             char* sc = static_cast<char*>(w.scratch);
@@ -604,7 +614,7 @@ int stage_windows(cm_batch* b, const cm_window* wins, int32_t nwin)
             d.sync = reinterpret_cast<int32_t*>(sc + ws.sync);
         } else {
             d.iwe = reinterpret_cast<float4*>(base + b->L.iwe + o_iwe);
-            o_iwe += (size_t)R * HW * sizeof(float4);
+            o_iwe += up256((size_t)R * HW * sizeof(float4));
             d.flow = reinterpret_cast<const float2*>(w.flow);  // nullptr for depth input (the quads hold its flow)
             if (w.dflow) {
                 d.dflow = reinterpret_cast<float2*>(w.dflow);
@@ -680,7 +690,6 @@ int stage_windows(cm_batch* b, const cm_window* wins, int32_t nwin)
     h->total_chunks = chunks;
     h->total_ltiles = lt_total;
     h->total_ptiles = pt_total;
-    h->iwe_f4 = (long long)(o_iwe / sizeof(float4));
     b->nwin = nwin;
     if (b->last.data() != wins) b->last.assign(wins, wins + nwin);
     b->dirty = true;

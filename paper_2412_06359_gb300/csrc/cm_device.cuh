@@ -92,6 +92,17 @@ constexpr int kBinTile = 32;  // px, side of the tiles events are grouped by
 
 __device__ __forceinline__ size_t plane_size(const Win& d) { return (size_t)d.W * (size_t)d.H; }
 
+// column u and row v of pixel i of a W-wide image, in 32-bit arithmetic (an
+// image holds fewer than 2^31 pixels: W, H <= 32767); a 64-bit integer
+// division is a long software sequence on the GPU
+__device__ __forceinline__ void pixel_uv(size_t i, int W, int& u, int& v)
+{
+    const uint32_t ii = (uint32_t)i, w = (uint32_t)W;
+    const uint32_t q = ii / w;
+    v = (int)q;
+    u = (int)(ii - q * w);
+}
+
 __device__ __forceinline__ const float2* field(const Win& d, int j)
 {
     return d.flow + (d.nfb == 1 ? (size_t)0 : (size_t)j * plane_size(d));
@@ -304,6 +315,15 @@ __device__ __forceinline__ bool trajectory(const Win& d, const EventAt& e, Traj<
 __device__ __forceinline__ void red_add_v2(float* addr, float a, float b)
 {
     asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(addr), "f"(a), "f"(b));
+}
+
+// 32-byte stores (32-byte aligned address): one instruction where two 16-byte
+// stores would queue in the load/store unit
+__device__ __forceinline__ void st_v8(void* p, float4 a, float4 b)
+{
+    asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(a.x), "f"(a.y), "f"(a.z),
+                 "f"(a.w), "f"(b.x), "f"(b.y), "f"(b.z), "f"(b.w)
+                 : "memory");
 }
 
 // 16-byte vector reduction (16-byte aligned address), same conventions
@@ -684,7 +704,8 @@ __device__ __forceinline__ void flow_tile(const Win& d, int tile, int ntiles)
     const size_t HW = plane_size(d);
     float2* flow = const_cast<float2*>(d.flow);
     for (size_t i = (size_t)tile * blockDim.x + threadIdx.x; i < HW; i += (size_t)ntiles * blockDim.x) {
-        const int v = (int)(i / W), u = (int)(i - (size_t)v * W);
+        int u, v;
+        pixel_uv(i, W, u, v);
         flow[i] = motion_field(u, v, __ldg(d.rho + i), d.ego, d.fx, d.fy, d.cx, d.cy, d.dt);
     }
 }
@@ -710,9 +731,7 @@ __device__ __forceinline__ float2 build_quad(const Win& d, int u, int v)
         f01 = __ldg(d.flow + r1 + u);
         f11 = __ldg(d.flow + r1 + u1);
     }
-    FQ* q = const_cast<FQ*>(d.fq) + r0 + u;
-    q->a = make_float4(f00.x, f00.y, f10.x, f10.y);
-    q->b = make_float4(f01.x, f01.y, f11.x, f11.y);
+    st_v8(const_cast<FQ*>(d.fq) + r0 + u, make_float4(f00.x, f00.y, f10.x, f10.y), make_float4(f01.x, f01.y, f11.x, f11.y));
     return f00;
 }
 
@@ -763,7 +782,8 @@ __device__ __forceinline__ void fold_tile(const Win& d, int tile, int ntiles)
     const int W = d.W;
     const size_t HW = plane_size(d);
     for (size_t i = (size_t)tile * blockDim.x + threadIdx.x; i < HW; i += (size_t)ntiles * blockDim.x) {
-        const int v = (int)(i / W), u = (int)(i - (size_t)v * W);
+        int u, v;
+        pixel_uv(i, W, u, v);
         d.dflow[i] = fold_dq(d, u, v);
     }
 }
@@ -845,11 +865,19 @@ __device__ __forceinline__ void loss_final_window(const Win& d)
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
     __shared__ double lr[64];
     for (int r = w; r < d.R; r += nw) {
+        const float2* part = d.loss_part + (size_t)r * d.loss_tiles;
         double s = 0.0, c = 0.0;
-        for (int i = l; i < d.loss_tiles; i += 32) {
-            const float2 q = d.loss_part[(size_t)r * d.loss_tiles + i];
-            s += (double)q.x;
-            c += (double)q.y;
+        // lane l adds tiles l, l+32, ... in that order, with eight loads in flight
+        // (this single block is the pass's serial tail)
+        for (int i0 = l; i0 < d.loss_tiles; i0 += 32 * 8) {
+            float2 q[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) q[u] = i0 + 32 * u < d.loss_tiles ? part[i0 + 32 * u] : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                s += (double)q[u].x;
+                c += (double)q[u].y;
+            }
         }
         s = warp_sum(s);
         c = warp_sum(c);
@@ -883,13 +911,15 @@ __device__ __forceinline__ void depth_ego_tile(const Win& d, int tile, int ntile
     // the pushes went there, else read
     auto dfl = [&](size_t i) -> float2 {
         if (!d.dq) return d.dflow[i];
-        const int v = (int)(i / W), u = (int)(i - (size_t)v * W);
+        int u, v;
+        pixel_uv(i, W, u, v);
         const float2 f = fold_dq(d, u, v);
         d.dflow[i] = f;
         return f;
     };
     auto one = [&](size_t i, float r, float2 df) {
-        const int v = (int)(i / W), u = (int)(i - (size_t)v * W);
+        int u, v;
+        pixel_uv(i, W, u, v);
         const float xn = ((float)u - d.cx) * ifx, yn = ((float)v - d.cy) * ify;
         const float Gx = sx * df.x, Gy = sy * df.y;
         if (d.drho) d.drho[i] = Gx * (xn * vz - vx) + Gy * (yn * vz - vy);
@@ -902,16 +932,13 @@ __device__ __forceinline__ void depth_ego_tile(const Win& d, int tile, int ntile
     };
     const size_t stride = (size_t)ntiles * blockDim.x;
     size_t i = (size_t)tile * blockDim.x + threadIdx.x;
-    for (; i + 3 * stride < HW; i += 4 * stride) {  // four independent load pairs in flight
+    for (; i + stride < HW; i += 2 * stride) {  // two pixels' loads in flight
         const float r0 = __ldg(d.rho + i), r1 = __ldg(d.rho + i + stride);
-        const float r2 = __ldg(d.rho + i + 2 * stride), r3 = __ldg(d.rho + i + 3 * stride);
-        const float2 f0 = dfl(i), f1 = dfl(i + stride), f2 = dfl(i + 2 * stride), f3 = dfl(i + 3 * stride);
+        const float2 f0 = dfl(i), f1 = dfl(i + stride);
         one(i, r0, f0);
         one(i + stride, r1, f1);
-        one(i + 2 * stride, r2, f2);
-        one(i + 3 * stride, r3, f3);
     }
-    for (; i < HW; i += stride) one(i, __ldg(d.rho + i), dfl(i));
+    if (i < HW) one(i, __ldg(d.rho + i), dfl(i));
     __shared__ float sg[32][6];
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
 #pragma unroll
@@ -934,7 +961,14 @@ __device__ __forceinline__ void depth_ego_final_window(const Win& d)
     const int c = threadIdx.x >> 5, l = threadIdx.x & 31;
     if (c >= 6) return;
     double s = 0.0;
-    for (int i = l; i < d.pix_tiles; i += 32) s += (double)d.dego_part[(size_t)i * 6 + c];
+    // lane l adds tiles l, l+32, ... in that order, with eight loads in flight
+    for (int i0 = l; i0 < d.pix_tiles; i0 += 32 * 8) {
+        float q[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) q[u] = i0 + 32 * u < d.pix_tiles ? d.dego_part[(size_t)(i0 + 32 * u) * 6 + c] : 0.f;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s += (double)q[u];
+    }
     s = warp_sum(s);
     if (l == 0 && d.dego) d.dego[c] = (float)s;
 }

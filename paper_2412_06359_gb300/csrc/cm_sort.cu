@@ -209,7 +209,8 @@ __global__ void __launch_bounds__(kRsThreads) k_cell_gather(const uint32_t* star
     for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
         const int q = (int)(t / HW);
         const size_t p = t - (size_t)q * HW;
-        const int y = (int)(p / W), x = (int)(p - (size_t)y * W);
+        int x, y;
+        pixel_uv(p, W, x, y);
         const uint32_t* st = start + (size_t)q * HW;
         float a = 0.0f, b = 0.0f;
         // cell (x, y) as corner 00, (x-1, y) as 10, (x, y-1) as 01, (x-1, y-1) as 11
