@@ -15,7 +15,7 @@
 //
 // Schedule.  A window's images of warped events (R x H x W x 16 bytes, 54 MB at
 // 640x480 with 11 references) are zeroed by the prep pass, reduced into by the
-// splat, read and rewritten by the loss pass and gathered by the adjoint; when
+// splat, read by the loss pass and gathered by the adjoint; when
 // the windows in flight exceed the 129 MB L2 those passes go to DRAM.  The
 // schedule therefore groups windows (group = windows per kernel) and runs the
 // groups on a few concurrent chains of the graph, each chain taking its groups

@@ -55,8 +55,7 @@ struct Win {
     float fx, fy, cx, cy;    // intrinsics (depth input)
     const float2* flow;      // [nfb][H][W]
     float4* iwe;             // iwe_split == 0: [R][H][W] (C+, S+, C-, S-);
-                             // iwe_split == 1: [R][2][H][W] float2 (C, S), one plane per polarity;
-                             // after the loss each (C, S) is (A, T) (see loss_tile)
+                             // iwe_split == 1: [R][2][H][W] float2 (C, S), one plane per polarity
     int32_t iwe_split;
     float2* dflow;           // [nfb][H][W]
     const FQ* fq;            // [nfb][H][W] flow quads, or nullptr (then samples gather from flow)
@@ -326,6 +325,17 @@ __device__ __forceinline__ void st_v8(void* p, float4 a, float4 b)
                  : "memory");
 }
 
+// Reciprocal by the hardware approximation (rcp.approx.ftz.f32, at most 1 ulp
+// from the correctly rounded value; C + eps is a normal number).  The loss pass
+// and the adjoint both take T = S * recip(C + eps) and A = 2 T recip(C + eps),
+// so the adjoint recomputes exactly the loss pass's values.
+__device__ __forceinline__ float recip(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // 16-byte vector reduction (16-byte aligned address), same conventions
 __device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float c, float e)
 {
@@ -503,9 +513,14 @@ __device__ __forceinline__ void splat_event(const Win& d, int64_t k, const Sink&
     }
 }
 
-// dL/dw_c of one corner from the loss-transformed pair (A, T), where
-// T = S/(C+eps) and A = 2T/(C+eps): phi = kappa * A * (tbar - T)
-__device__ __forceinline__ float phi_of(float A, float T, float kap, float tbar) { return kap * A * (tbar - T); }
+// dL/dw_c of one corner from its count and timestamp sum, with the loss
+// pass's T = S/(C+eps) and A = 2T/(C+eps): phi = kappa * A * (tbar - T)
+__device__ __forceinline__ float phi_of(float C, float S, float eps, float kap, float tbar)
+{
+    const float rc = recip(C + eps);
+    const float T = S * rc;
+    return kap * (2.0f * T * rc) * (tbar - T);
+}
 
 // phi of the two corners of one row in polarity-plane layout (left at float2
 // index gi, right behind it when `two`).  One 16-byte gather of the aligned
@@ -514,15 +529,17 @@ __device__ __forceinline__ float phi_of(float A, float T, float kap, float tbar)
 // together, so the row costs one L2 latency (a divergent choice between the two
 // forms would serialise them).  The aligned pair never leaves the image: the
 // last float2 of the buffer has an odd index.
-__device__ __forceinline__ void phi_row(const float2* img, size_t gi, bool two, float kap, float tbar, float& pl,
-                                        float& pr)
+__device__ __forceinline__ void phi_row(const float2* img, size_t gi, bool two, float eps, float kap, float tbar,
+                                        float& pl, float& pr)
 {
     const bool odd = (gi & 1) != 0;
     const float4 g = __ldg(reinterpret_cast<const float4*>(img + (gi & ~(size_t)1)));
     float2 h = make_float2(0.0f, 0.0f);
     if (two && odd) h = __ldg(img + gi + 1);
-    pl = odd ? phi_of(g.z, g.w, kap, tbar) : phi_of(g.x, g.y, kap, tbar);
-    pr = !two ? 0.0f : odd ? phi_of(h.x, h.y, kap, tbar) : phi_of(g.z, g.w, kap, tbar);
+    const float2 l = odd ? make_float2(g.z, g.w) : make_float2(g.x, g.y);
+    const float2 r = odd ? h : make_float2(g.z, g.w);
+    pl = phi_of(l.x, l.y, eps, kap, tbar);
+    pr = two ? phi_of(r.x, r.y, eps, kap, tbar) : 0.0f;
 }
 
 // position adjoint a = sum_c grad(w_c) phi_c at reference r, edge j; corners
@@ -537,6 +554,7 @@ __device__ __forceinline__ float2 ref_adjoint(const Win& d, int r, int j, float 
     const int W = d.W, H = d.H;
     const float kap = dl * __ldg(d.norm + r);
     const float tb = tbar_of(j, d.B, tau);
+    const float eps = d.eps;
     const Bil s = bil(px, py);
     const size_t i00 = (size_t)s.iy * W + s.ix;
     const bool inx = s.ix + 1 <= W - 1, iny = s.iy + 1 <= H - 1;
@@ -544,14 +562,14 @@ __device__ __forceinline__ float2 ref_adjoint(const Win& d, int r, int j, float 
     if (SPLIT) {
         const float2* img = reinterpret_cast<const float2*>(d.iwe);
         const size_t gi = (size_t)(2 * r + (pol2 >> 1)) * HW + i00;
-        phi_row(img, gi, inx, kap, tb, p00, p10);
-        phi_row(img, iny ? gi + W : gi, inx, kap, tb, p01, p11);  // unconditional: both rows in flight together
+        phi_row(img, gi, inx, eps, kap, tb, p00, p10);
+        phi_row(img, iny ? gi + W : gi, inx, eps, kap, tb, p01, p11);  // unconditional: both rows in flight together
         if (!iny) p01 = p11 = 0.0f;
     } else {
         const float2* G = reinterpret_cast<const float2*>(d.iwe + (size_t)r * HW) + (pol2 >> 1);
         auto at = [&](size_t i) {
             const float2 g = __ldg(G + 2 * i);
-            return phi_of(g.x, g.y, kap, tb);
+            return phi_of(g.x, g.y, eps, kap, tb);
         };
         p00 = at(i00);
         if (inx) p10 = at(i00 + 1);
@@ -789,10 +807,9 @@ __device__ __forceinline__ void fold_tile(const Win& d, int tile, int ntiles)
 }
 
 // S5 pass 1 over one tile of reference r: T = S/(C+eps) for both polarities;
-// the sum of T^2 and the non-empty count go to out[0].  Each (C, S) pair is
-// rewritten in place as (A, T), A = 2T/(C+eps): all the adjoint needs at a
-// corner, in one gather and without a division.  Ends with __syncthreads (the
-// caller may loop).
+// the sum of T^2 and the non-empty count go to out[0].  Read-only: the adjoint
+// recomputes T and A = 2T/(C+eps) from (C, S) at the corners it gathers, with
+// the same operations (phi_of).  Ends with __syncthreads (the caller may loop).
 __device__ __forceinline__ void loss_tile(const Win& d, int r, int tile, int ntiles, float2* out)
 {
     const size_t HW = plane_size(d);
@@ -800,42 +817,32 @@ __device__ __forceinline__ void loss_tile(const Win& d, int r, int tile, int nti
     float s = 0.0f;
     int cnt = 0;
     const size_t stride = (size_t)ntiles * blockDim.x;
-    // (C+, S+, C-, S-) of pixel i in either layout, and its rewrite
-    float4* plane = d.iwe + (size_t)r * HW;
-    float2* pos = reinterpret_cast<float2*>(d.iwe) + (size_t)2 * r * HW;
-    float2* neg = pos + HW;
+    // (C+, S+, C-, S-) of pixel i in either layout
+    const float4* plane = d.iwe + (size_t)r * HW;
+    const float2* pos = reinterpret_cast<const float2*>(d.iwe) + (size_t)2 * r * HW;
+    const float2* neg = pos + HW;
     const bool split = d.iwe_split != 0;
     auto ld = [&](size_t i) {
         if (!split) return plane[i];
         const float2 a = pos[i], b = neg[i];
         return make_float4(a.x, a.y, b.x, b.y);
     };
-    // one correctly rounded reciprocal per polarity instead of full-precision
-    // divisions, which made this pass instruction-bound
-    auto one = [&](float4 q, size_t i) {
-        const float rp = __frcp_rn(q.x + eps), rm = __frcp_rn(q.z + eps);
-        const float tp = q.y * rp, tm = q.w * rm;
+    auto one = [&](float4 q) {
+        const float tp = q.y * recip(q.x + eps), tm = q.w * recip(q.z + eps);
         s = fmaf(tp, tp, s);
         s = fmaf(tm, tm, s);
         cnt += (q.x > 0.0f || q.z > 0.0f) ? 1 : 0;
-        const float ap = 2.0f * tp * rp, am = 2.0f * tm * rm;
-        if (split) {
-            pos[i] = make_float2(ap, tp);
-            neg[i] = make_float2(am, tm);
-        } else {
-            plane[i] = make_float4(ap, tp, am, tm);
-        }
     };
     size_t i = (size_t)tile * blockDim.x + threadIdx.x;
     // four independent loads in flight per thread (the pass is latency-bound otherwise)
     for (; i + 3 * stride < HW; i += 4 * stride) {
         const float4 q0 = ld(i), q1 = ld(i + stride), q2 = ld(i + 2 * stride), q3 = ld(i + 3 * stride);
-        one(q0, i);
-        one(q1, i + stride);
-        one(q2, i + 2 * stride);
-        one(q3, i + 3 * stride);
+        one(q0);
+        one(q1);
+        one(q2);
+        one(q3);
     }
-    for (; i < HW; i += stride) one(ld(i), i);
+    for (; i < HW; i += stride) one(ld(i));
     __shared__ float ss[32];
     __shared__ int sc[32];
     s = warp_sum(s);
