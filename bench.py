@@ -184,18 +184,31 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None
-    when the kernels changed since the counters were taken."""
-    p = os.path.join(ROOT, "profiles", "traffic.json")
+def recorded_counters(kernel: str):
+    """Per-event ncu counters of an event kernel from the committed summary
+    (profiles/event_kernels_ncu_counters.md: DRAM bytes and L2 requests per
+    input event), or None when the kernel sources changed since they were taken."""
+    p = os.path.join(ROOT, "profiles", "event_kernels_ncu_counters.md")
     try:
-        d = json.load(open(p))
+        text = open(p).read()
+        block = text.split("```json", 1)[1].split("```", 1)[0]
+        d = json.loads(block)
     except Exception:
         return None
     if d.get("source_hash") != kernel_source_hash():
         return None
-    k = d.get("kernels", {}).get(kernel)
-    return None if k is None else float(k["dram_bytes_per_launch_at_bench"])
+    return d.get("kernels", {}).get(kernel)
+
+
+def l2_rates(device):
+    """Random-request rates of this GPU's L2 (reductions/s, loads/s), measured
+    by the library's probe over a 64 MiB buffer (about one window's images)."""
+    import torch
+    from paper_2412_06359_gb300 import _capi as C
+    buf = torch.empty(64 << 20, dtype=torch.uint8, device=device)
+    red, ld = C.cm_measure_l2_rates(buf.data_ptr(), buf.numel(), torch.cuda.current_stream(device).cuda_stream)
+    del buf
+    return red, ld
 
 
 # ---------------------------------------------------------------------------
@@ -322,6 +335,7 @@ def run_ours(args):
     R = wins[0].nbins + 1
     stream = torch.cuda.current_stream()
 
+    l2 = l2_rates(dev)
     if args.schedule == "auto":
         schedule = batch.plan.autotune()  # picks chains / windows per kernel for this batch (cached per shape)
     else:
@@ -362,6 +376,7 @@ def run_ours(args):
     dom = max(prof.items(), key=lambda kv: kv[1][1])[0] if prof else None
     roof = None
     roof_iwe = None
+    roof_l2 = None
     if dom:
         nl, ms = prof[dom]
         per_launch_ms = ms / nl
@@ -373,14 +388,33 @@ def run_ours(args):
         for model in ("strict", "iwe"):
             b = kernel_bytes(dom, batch.events, hw * len(wins), R, model) / launches_per_step
             ach = b / (per_launch_ms * 1e-3) / 1e9
+            cnt = recorded_counters(dom)
+            events_per_launch = batch.events / launches_per_step
+            traffic = None if cnt is None or model != "strict" else cnt["dram_bytes_per_event"] * events_per_launch
             obj = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                   "traffic": recorded_traffic(dom) if model == "strict" else None, "kernel": dom,
+                   "traffic": traffic, "kernel": dom,
                    "launch_ms": per_launch_ms, "bytes_per_launch": b, "launches_per_step": launches_per_step,
                    "overlap": overlap, "peak_kind": f"{peak_kind} hbm_gbs"}
             if model == "strict":
                 roof = obj
             else:
                 roof_iwe = obj
+        # request-bound model: the kernel's L2 requests per launch (ncu counts per
+        # event x events per launch) against the measured random-request rates
+        cnt = recorded_counters(dom)
+        if cnt is not None and l2 is not None:
+            epl = batch.events / launches_per_step
+            rd, rq = cnt["l2_read_requests_per_event"] * epl, cnt["l2_red_requests_per_event"] * epl
+            t_min = rd / l2[1] + rq / l2[0]
+            ach = (rd + rq) / (per_launch_ms * 1e-3) / 1e9
+            pk = (rd + rq) / t_min / 1e9
+            roof_l2 = {"bound": "l2_requests", "achieved": ach, "peak": pk, "unit": "G requests/s",
+                       "frac": ach / pk, "kernel": dom, "requests_per_launch": rd + rq,
+                       "read_requests_per_event": cnt["l2_read_requests_per_event"],
+                       "red_requests_per_event": cnt["l2_red_requests_per_event"],
+                       "measured_red_per_s": l2[0], "measured_load_per_s": l2[1], "overlap": overlap,
+                       "frac_times_overlap": ach / pk * overlap,
+                       "peak_kind": "measured by cm_measure_l2_rates on this GPU before the timed region"}
 
     # ---- plain per-window comparison (a stream sync after every window) ----
     plain = None
@@ -396,6 +430,11 @@ def run_ours(args):
         el = time.perf_counter() - t0
         plain = {"value": batch.events / el / 1e6, "unit": "Mev/s", "p50_ms": float(np.percentile(lat, 50)),
                  "p99_ms": float(np.percentile(lat, 99)), "windows": len(wins)}
+
+    # ---- the two splat strategies through the single-window calls ----
+    splat_cmp = None
+    if not args.no_plain:
+        splat_cmp = compare_splats(batch, min(4, len(wins)))
 
     # ---- end to end through the public API with host buffers ----
     e2e = None
@@ -422,13 +461,46 @@ def run_ours(args):
                                     "tile_grouping": bool(schedule[2])},
                        "l2": "per-step IWE working set %.2f GB > L2 (no flush needed)" % (len(wins) * R * hw * 16 / 1e9)},
             "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
-            "plain": plain, "roofline": roof, "roofline_iwe": roof_iwe, "cpu_baseline": cpu, "e2e": e2e,
+            "plain": plain, "splat_compare": splat_cmp, "roofline": roof, "roofline_iwe": roof_iwe,
+            "roofline_l2": roof_l2, "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clocks, "gpu_launches": int(launches),
             "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])},
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def compare_splats(batch, nwin: int):
+    """Loss + gradient of the first `nwin` windows through the single-window
+    calls with the atomic and with the deterministic sort splat (a stream sync
+    after each window), in Mev/s."""
+    import torch
+    cm = batch.cm
+    out = {"windows": nwin, "path": "cm_loss_forward + cm_loss_backward per window"}
+    for name, splat in (("atomic", cm.SPLAT_ATOMIC), ("sort", cm.SPLAT_SORT)):
+        items = []
+        for (w, _, ev, rho, ego, res, loss) in batch.items[:nwin]:
+            cfg = cm.loss_cfg(w.nbins, w.ref_mode, splat)
+            items.append((w, cm.Workspace(w.cam, cfg, w.events.n, 1, batch.dev), ev, rho, ego, res, loss))
+
+        def one(it):
+            w, ws, ev, rho, ego, res, loss = it
+            cm.loss_forward(ws, ev, inv_depth=rho, ego=ego, dt=w.dt, out=loss)
+            cm.loss_backward(ws, ev, batch.dloss, inv_depth=rho, ego=ego, dt=w.dt, want_dflow=False, out=res)
+            torch.cuda.current_stream().synchronize()
+
+        for it in items:
+            one(it)
+        t0 = time.perf_counter()
+        for _ in range(3):
+            for it in items:
+                one(it)
+        el = (time.perf_counter() - t0) / 3
+        out[name] = sum(it[0].events.n for it in items) / el / 1e6
+        del items
+    out["unit"] = "Mev/s"
+    return out
 
 
 def run_e2e(batch, args, stream):

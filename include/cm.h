@@ -406,6 +406,16 @@ int cm_profile_reset(void);
  * count each kernel node). */
 int64_t cm_launch_count(void);
 
+/* Measured ceiling of the request-bound kernels (the splat and the adjoint
+ * scatter and gather at data-dependent addresses, so the L2's rate of random
+ * requests bounds them, not bytes; no counterpart in the paper).  Times random
+ * 8-byte vector reductions and random 8-byte loads over `buf` (device memory,
+ * 256-byte aligned, at least 16 MiB, about the size of one window's images to
+ * stay in L2; overwritten) with CUDA events on `stream`, and returns the best
+ * of three timed launches of each, in requests per second.  Synchronises
+ * `stream`.  Errors: CM_EINVAL, CM_ECUDA. */
+int cm_measure_l2_rates(void* buf, size_t bytes, void* stream, double* red_per_s, double* load_per_s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -124,6 +124,7 @@ SIGNATURES = {
     "cm_profile_collect": ([_P(cm_kernel_stat), _i32, _P(_i32)], ctypes.c_int),
     "cm_profile_reset": ([], ctypes.c_int),
     "cm_launch_count": ([], ctypes.c_int64),
+    "cm_measure_l2_rates": ([_vp, _sz, _vp, _P(ctypes.c_double), _P(ctypes.c_double)], ctypes.c_int),
 }
 
 
@@ -333,3 +334,11 @@ def cm_profile_reset() -> None:
 
 def cm_launch_count() -> int:
     return int(lib().cm_launch_count())
+
+
+def cm_measure_l2_rates(buf: int, nbytes: int, stream: int) -> tuple[float, float]:
+    """(random reductions / s, random loads / s) measured over device memory `buf`."""
+    red, ld = ctypes.c_double(), ctypes.c_double()
+    _check(lib().cm_measure_l2_rates(buf, nbytes, stream, ctypes.byref(red), ctypes.byref(ld)),
+           "cm_measure_l2_rates")
+    return red.value, ld.value
