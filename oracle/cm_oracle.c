@@ -211,6 +211,210 @@ void orc_flow_eq2(int32_t W, int32_t H, double fx, double fy, double cx, double 
     }
 }
 
+/*
+ * Eq. 2 with one pose per bin (the discrete-flow variant): bin i of nb moves
+ * the camera with velocity v_i and angular velocity w_i (ego[6i .. 6i+5]) for
+ * dt_bin seconds, and its flow is `scale` times the pixel displacement of
+ * orc_flow_eq2 (scale = nb expresses it in px per window when the nb bins
+ * split the window evenly, the unit of the iterative warp).  FP64, the plain
+ * definition.  flow is [nb][H][W][2].
+ */
+void orc_flow_eq2_bins(int32_t W, int32_t H, double fx, double fy, double cx, double cy, const double* rho,
+                       const double* ego, int32_t nb, double dt_bin, double scale, double* flow)
+{
+    const int64_t HW = (int64_t)W * H;
+    for (int32_t i = 0; i < nb; ++i) {
+        double* f = flow + 2 * HW * i;
+        orc_flow_eq2(W, H, fx, fy, cx, cy, rho, ego + 6 * i, dt_bin, f);
+        for (int64_t q = 0; q < 2 * HW; ++q) f[q] *= scale;
+    }
+}
+
+/*
+ * The same in FP32 with the operation sequence of the GPU kernels, which
+ * decides the positions of the FP32 trajectory when these flows drive it
+ * (every operation one correctly rounded IEEE single operation, fmaf fused):
+ *   per bin:  k = -(w * dt), t = -(v * dt) (componentwise);
+ *             kxx = kx*kx, kyy = ky*ky, kzz = kz*kz, kxy = kx*ky, kxz = kx*kz, kyz = ky*kz
+ *             s = (kxx + kyy) + kzz
+ *             a = sin(th)/th and b = (1 - cos th)/th^2 as their Taylor series in s
+ *                 (terms up to s^9, Horner from the highest term: c = fma(c, s, c_n))
+ *             R00 = fma(b, -(kyy + kzz), 1)   R01 = fma(b, kxy, -(a*kz))   R02 = fma(b, kxz, a*ky)
+ *             R10 = fma(b, kxy, a*kz)         R11 = fma(b, -(kxx + kzz), 1) R12 = fma(b, kyz, -(a*kx))
+ *             R20 = fma(b, kxz, -(a*ky))      R21 = fma(b, kyz, a*kx)      R22 = fma(b, -(kxx + kyy), 1)
+ *   per pixel: xn = (u - cx) * (1/fx), yn = (v - cy) * (1/fy), Z = 1/rho
+ *             X = (Z*xn, Z*yn, Z);  P_a = fma(R_a2, X2, fma(R_a1, X1, fma(R_a0, X0, t_a)))
+ *             iz = 1/P2;  d = (fx * (fma(-xn, P2, P0) * iz), fy * (fma(-yn, P2, P1) * iz))
+ *             flow = (scale * d.x, scale * d.y)
+ * The displacement is taken as fx (P0/P2 - xn), the same quantity as
+ * fx P0/P2 + cx - u, without cancelling against the pixel coordinate.
+ */
+static const double ORC_SIN_SERIES[10] = {1.0, -1.0 / 6.0, 1.0 / 120.0, -1.0 / 5040.0, 1.0 / 362880.0,
+                                          -1.0 / 39916800.0, 1.0 / 6227020800.0, -1.0 / 1307674368000.0,
+                                          1.0 / 355687428096000.0, -1.0 / 121645100408832000.0};
+static const double ORC_COS_SERIES[10] = {1.0 / 2.0, -1.0 / 24.0, 1.0 / 720.0, -1.0 / 40320.0, 1.0 / 3628800.0,
+                                          -1.0 / 479001600.0, 1.0 / 87178291200.0, -1.0 / 20922789888000.0,
+                                          1.0 / 6402373705728000.0, -1.0 / 2432902008176640000.0};
+
+static void rot_f32(const float* e, float dt, float Rm[9], float tv[3])
+{
+    const float kx = -(e[3] * dt), ky = -(e[4] * dt), kz = -(e[5] * dt);
+    tv[0] = -(e[0] * dt);
+    tv[1] = -(e[1] * dt);
+    tv[2] = -(e[2] * dt);
+    const float kxx = kx * kx, kyy = ky * ky, kzz = kz * kz;
+    const float kxy = kx * ky, kxz = kx * kz, kyz = ky * kz;
+    const float s = (kxx + kyy) + kzz;
+    float a = (float)ORC_SIN_SERIES[9], b = (float)ORC_COS_SERIES[9];
+    for (int n = 8; n >= 0; --n) {
+        a = fmaf(a, s, (float)ORC_SIN_SERIES[n]);
+        b = fmaf(b, s, (float)ORC_COS_SERIES[n]);
+    }
+    Rm[0] = fmaf(b, -(kyy + kzz), 1.0f);
+    Rm[1] = fmaf(b, kxy, -(a * kz));
+    Rm[2] = fmaf(b, kxz, a * ky);
+    Rm[3] = fmaf(b, kxy, a * kz);
+    Rm[4] = fmaf(b, -(kxx + kzz), 1.0f);
+    Rm[5] = fmaf(b, kyz, -(a * kx));
+    Rm[6] = fmaf(b, kxz, -(a * ky));
+    Rm[7] = fmaf(b, kyz, a * kx);
+    Rm[8] = fmaf(b, -(kxx + kyy), 1.0f);
+}
+
+void orc_flow_eq2_bins_f32(int32_t W, int32_t H, float fx, float fy, float cx, float cy, const float* rho,
+                           const float* ego, int32_t nb, float dt_bin, float scale, float* flow)
+{
+    const int64_t HW = (int64_t)W * H;
+    const float ifx = 1.0f / fx, ify = 1.0f / fy;
+    for (int32_t i = 0; i < nb; ++i) {
+        float Rm[9], tv[3];
+        rot_f32(ego + 6 * i, dt_bin, Rm, tv);
+        for (int32_t v = 0; v < H; ++v) {
+            for (int32_t u = 0; u < W; ++u) {
+                const int64_t q = (int64_t)v * W + u;
+                const float xn = ((float)u - cx) * ifx;
+                const float yn = ((float)v - cy) * ify;
+                const float Z = 1.0f / rho[q];
+                const float X0 = Z * xn, X1 = Z * yn, X2 = Z;
+                const float P0 = fmaf(Rm[2], X2, fmaf(Rm[1], X1, fmaf(Rm[0], X0, tv[0])));
+                const float P1 = fmaf(Rm[5], X2, fmaf(Rm[4], X1, fmaf(Rm[3], X0, tv[1])));
+                const float P2 = fmaf(Rm[8], X2, fmaf(Rm[7], X1, fmaf(Rm[6], X0, tv[2])));
+                const float iz = 1.0f / P2;
+                const float dx = fx * (fmaf(-xn, P2, P0) * iz);
+                const float dy = fy * (fmaf(-yn, P2, P1) * iz);
+                flow[2 * (HW * i + q) + 0] = scale * dx;
+                flow[2 * (HW * i + q) + 1] = scale * dy;
+            }
+        }
+    }
+}
+
+/*
+ * Derivative of the Rodrigues rotation R(k) = I + a K + b K^2, K = [k]x,
+ * a = sin(th)/th, b = (1 - cos th)/th^2, th = |k|, with respect to k_c:
+ *   dR/dk_c = a E_c + b (E_c K + K E_c) + (a'/th K + b'/th K^2) k_c,
+ * E_c = [e_c]x, a' = da/dth, b' = db/dth (derived from the formula by the
+ * product and chain rules).  Near th = 0 the ratios a'/th -> -1/3 and
+ * b'/th -> -1/12 are taken from their series.
+ */
+static void rodrigues_grad(const double k[3], double dR[3][3][3])
+{
+    const double th2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+    const double th = sqrt(th2);
+    double a, b, ap, bp; /* ap = a'/th, bp = b'/th */
+    if (th < 1e-4) {
+        a = 1.0 - th2 / 6.0;
+        b = 0.5 - th2 / 24.0;
+        ap = -1.0 / 3.0 + th2 / 30.0;
+        bp = -1.0 / 12.0 + th2 / 180.0;
+    } else {
+        const double sn = sin(th), cs = cos(th);
+        a = sn / th;
+        b = (1.0 - cs) / th2;
+        ap = (th * cs - sn) / (th2 * th);
+        bp = (th * sn - 2.0 * (1.0 - cs)) / (th2 * th2);
+    }
+    const double K[3][3] = {{0, -k[2], k[1]}, {k[2], 0, -k[0]}, {-k[1], k[0], 0}};
+    double K2[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            K2[i][j] = 0;
+            for (int l = 0; l < 3; ++l) K2[i][j] += K[i][l] * K[l][j];
+        }
+    for (int c = 0; c < 3; ++c) {
+        double E[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        /* [e_c]x */
+        if (c == 0) { E[1][2] = -1; E[2][1] = 1; }
+        if (c == 1) { E[0][2] = 1; E[2][0] = -1; }
+        if (c == 2) { E[0][1] = -1; E[1][0] = 1; }
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                double EK = 0, KE = 0;
+                for (int l = 0; l < 3; ++l) {
+                    EK += E[i][l] * K[l][j];
+                    KE += K[i][l] * E[l][j];
+                }
+                dR[c][i][j] = a * E[i][j] + b * (EK + KE) + (ap * K[i][j] + bp * K2[i][j]) * k[c];
+            }
+    }
+}
+
+/*
+ * Adjoint of orc_flow_eq2_bins: given dL/dflow [nb][H][W][2], dL/d(rho) [H][W]
+ * (summed over the bins) and dL/d(ego) [nb][6], FP64, by the chain rule
+ * through the projection, the rigid transform and Rodrigues' formula:
+ *   with P = R X + t, X = (xn, yn, 1)/rho and G = scale * dL/dflow,
+ *   dL/dP = (G_x fx / P2, G_y fy / P2, -(G_x fx P0 + G_y fy P1) / P2^2)
+ *   dL/dt = sum dL/dP, dL/dR = sum dL/dP X^T, dL/dX = R^T dL/dP,
+ *   dL/drho = -(dL/dX . (xn, yn, 1)) / rho^2,
+ *   dL/dv = -dt dL/dt, dL/dw_c = -dt sum_ab dL/dR_ab dR_ab/dk_c (k = -w dt).
+ */
+void orc_flow_eq2_grad(int32_t W, int32_t H, double fx, double fy, double cx, double cy, const double* rho,
+                       const double* ego, int32_t nb, double dt_bin, double scale, const double* dflow,
+                       double* drho, double* dego)
+{
+    const int64_t HW = (int64_t)W * H;
+    for (int64_t q = 0; q < HW; ++q) drho[q] = 0.0;
+    for (int32_t i = 0; i < nb; ++i) {
+        const double* e = ego + 6 * i;
+        const double k[3] = {-e[3] * dt_bin, -e[4] * dt_bin, -e[5] * dt_bin};
+        const double t[3] = {-e[0] * dt_bin, -e[1] * dt_bin, -e[2] * dt_bin};
+        double Rm[3][3];
+        rodrigues(k, Rm);
+        double gt[3] = {0, 0, 0}, M[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        for (int32_t v = 0; v < H; ++v) {
+            for (int32_t u = 0; u < W; ++u) {
+                const int64_t q = (int64_t)v * W + u;
+                const double xn = ((double)u - cx) / fx, yn = ((double)v - cy) / fy;
+                const double Z = 1.0 / rho[q];
+                const double X[3] = {Z * xn, Z * yn, Z};
+                double P[3];
+                for (int r = 0; r < 3; ++r) P[r] = Rm[r][0] * X[0] + Rm[r][1] * X[1] + Rm[r][2] * X[2] + t[r];
+                const double Gx = scale * dflow[2 * (HW * i + q) + 0], Gy = scale * dflow[2 * (HW * i + q) + 1];
+                const double dP[3] = {Gx * fx / P[2], Gy * fy / P[2],
+                                      -(Gx * fx * P[0] + Gy * fy * P[1]) / (P[2] * P[2])};
+                for (int r = 0; r < 3; ++r) {
+                    gt[r] += dP[r];
+                    for (int c = 0; c < 3; ++c) M[r][c] += dP[r] * X[c];
+                }
+                double dX[3];
+                for (int c = 0; c < 3; ++c) dX[c] = Rm[0][c] * dP[0] + Rm[1][c] * dP[1] + Rm[2][c] * dP[2];
+                const double dZ = dX[0] * xn + dX[1] * yn + dX[2];
+                drho[q] += -Z * Z * dZ;
+            }
+        }
+        double dR[3][3][3];
+        rodrigues_grad(k, dR);
+        for (int c = 0; c < 3; ++c) {
+            double dk = 0.0;
+            for (int r = 0; r < 3; ++r)
+                for (int s2 = 0; s2 < 3; ++s2) dk += M[r][s2] * dR[c][r][s2];
+            dego[6 * i + c] = -dt_bin * gt[c];
+            dego[6 * i + 3 + c] = -dt_bin * dk;
+        }
+    }
+}
+
 /* ------------------------------------------------------------------------- */
 /* S2-S6: warp, mask, splat, loss, gradient                                  */
 /* ------------------------------------------------------------------------- */

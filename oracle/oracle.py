@@ -63,6 +63,9 @@ def lib():
             l.orc_flow_from_depth_f32.argtypes = [i, i, f, f, f, f, vp, vp, f, vp]
             l.orc_depth_ego_grad.argtypes = [i, i, d, d, d, d, vp, vp, d, vp, vp, vp]
             l.orc_flow_eq2.argtypes = [i, i, d, d, d, d, vp, vp, d, vp]
+            l.orc_flow_eq2_bins.argtypes = [i, i, d, d, d, d, vp, vp, i, d, d, vp]
+            l.orc_flow_eq2_bins_f32.argtypes = [i, i, f, f, f, f, vp, vp, i, f, f, vp]
+            l.orc_flow_eq2_grad.argtypes = [i, i, d, d, d, d, vp, vp, i, d, d, vp, vp, vp]
             l.orc_cm.argtypes = [ctypes.POINTER(_Args)]
             l.orc_cm.restype = ctypes.c_int
             _lib = l
@@ -110,6 +113,43 @@ def flow_eq2(cam, inv_depth, ego, dt):
     out = np.empty((cam.height, cam.width, 2), np.float64)
     lib().orc_flow_eq2(cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy, _p(rho), _p(e), float(dt), _p(out))
     return out
+
+
+def flow_eq2_bins(cam, inv_depth, ego, dt_bin, scale):
+    """Eq. 2 with one pose per bin: ego [nb, 6] = (v, w) of each bin over
+    dt_bin seconds; flow [nb, H, W, 2] = scale x the pixel displacement, FP64."""
+    rho = _c(inv_depth, np.float64)
+    e = _c(ego, np.float64).reshape(-1, 6)
+    nb = e.shape[0]
+    out = np.empty((nb, cam.height, cam.width, 2), np.float64)
+    lib().orc_flow_eq2_bins(cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy, _p(rho), _p(e), nb,
+                            float(dt_bin), float(scale), _p(out))
+    return out
+
+
+def flow_eq2_bins_f32(cam, inv_depth, ego, dt_bin, scale):
+    """The same in FP32 with the kernels' operation sequence (the values that
+    decide the FP32 trajectory when these flows drive it)."""
+    rho = _c(inv_depth, np.float32)
+    e = _c(ego, np.float32).reshape(-1, 6)
+    nb = e.shape[0]
+    out = np.empty((nb, cam.height, cam.width, 2), np.float32)
+    lib().orc_flow_eq2_bins_f32(cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy, _p(rho), _p(e), nb,
+                                float(dt_bin), float(scale), _p(out))
+    return out
+
+
+def flow_eq2_grad(cam, inv_depth, ego, dt_bin, scale, dflow):
+    """Adjoint of flow_eq2_bins: dL/dflow [nb, H, W, 2] -> (dL/d inv_depth [H, W], dL/d ego [nb, 6])."""
+    rho = _c(inv_depth, np.float64)
+    e = _c(ego, np.float64).reshape(-1, 6)
+    nb = e.shape[0]
+    g = _c(dflow, np.float64).reshape(nb, cam.height, cam.width, 2)
+    drho = np.empty((cam.height, cam.width), np.float64)
+    dego = np.empty((nb, 6), np.float64)
+    lib().orc_flow_eq2_grad(cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy, _p(rho), _p(e), nb,
+                            float(dt_bin), float(scale), _p(g), _p(drho), _p(dego))
+    return drho, dego
 
 
 def depth_ego_grad(cam, inv_depth, ego, dt, dflow):
