@@ -195,6 +195,33 @@ int cm_loss_backward(const cm_camera* cam, const cm_events* ev, const float* flo
  */
 int cm_workspace_stats(const cm_workspace* ws, const float** loss_r, const int32_t** nnz_r);
 
+/* ---- discrete flow: Eq. 2 with one pose per bin ----
+ * The flow of bin i (of nb) by the reprojection of Eq. 2 (Sec. 3.2): pixel
+ * (u, v) with inverse depth rho is back-projected to X = (xn, yn, 1) / rho
+ * (xn = (u - cx)/fx, yn = (v - cy)/fy), moved as P = R X + t for a camera that
+ * moves with velocity v_i and angular velocity w_i (ego6[6i .. 6i+5] =
+ * (vx, vy, vz, wx, wy, wz), m/s and rad/s, camera frame) for dt_bin seconds
+ * (R = Rodrigues(-w_i dt_bin), t = -v_i dt_bin), and re-projected; the flow is
+ * `scale` times the displacement (fx (P0/P2 - xn), fy (P1/P2 - yn)), px.
+ * With nb = B bins splitting a window evenly, dt_bin = window / B and
+ * scale = B give px per window, the unit cm_loss_forward takes with
+ * n_flow_bins = B.  All pointers are device memory; stream-ordered.
+ *   flow_out [nb][H][W][2].  Errors: CM_EINVAL (bad camera, nb outside
+ *   1..CM_MAX_BINS, non-finite dt_bin / scale, NULL pointers), CM_ECUDA. */
+int cm_flow_eq2(const cm_camera* cam, const float* inv_depth, const float* ego6, int32_t nb, float dt_bin,
+                float scale, float* flow_out, void* stream);
+/* Device bytes of the scratch cm_flow_eq2_backward needs (per-tile partial sums). */
+int cm_flow_eq2_scratch_query(const cm_camera* cam, int32_t nb, size_t* bytes);
+/* Adjoint of cm_flow_eq2: from dflow [nb][H][W][2] = dL/dflow, writes
+ * dinv_depth [H][W] = dL/d(inverse depth) summed over the bins and
+ * dego6 [nb][6] = dL/d(v_i, w_i), through the projection, the rigid transform
+ * and the derivative of Rodrigues' formula (fixed-order reductions:
+ * deterministic).  scratch: device memory, 16-byte aligned, at least
+ * cm_flow_eq2_scratch_query bytes (CM_ENOMEM otherwise). */
+int cm_flow_eq2_backward(const cm_camera* cam, const float* inv_depth, const float* ego6, int32_t nb, float dt_bin,
+                         float scale, const float* dflow, float* dinv_depth, float* dego6, void* scratch,
+                         size_t scratch_bytes, void* stream);
+
 /* ---- batched evaluation ----
  * Loss and gradient of many windows at once (the batched training step of the
  * paper, supp. "Training": batches of 4-8 event windows on one GPU), with

@@ -124,6 +124,10 @@ SIGNATURES = {
     "cm_profile_collect": ([_P(cm_kernel_stat), _i32, _P(_i32)], ctypes.c_int),
     "cm_profile_reset": ([], ctypes.c_int),
     "cm_launch_count": ([], ctypes.c_int64),
+    "cm_flow_eq2": ([_P(cm_camera), _vp, _vp, _i32, _f32, _f32, _vp, _vp], ctypes.c_int),
+    "cm_flow_eq2_scratch_query": ([_P(cm_camera), _i32, _P(_sz)], ctypes.c_int),
+    "cm_flow_eq2_backward": ([_P(cm_camera), _vp, _vp, _i32, _f32, _f32, _vp, _vp, _vp, _vp, _sz, _vp],
+                             ctypes.c_int),
     "cm_measure_l2_rates": ([_vp, _sz, _vp, _P(ctypes.c_double), _P(ctypes.c_double)], ctypes.c_int),
 }
 
@@ -342,3 +346,20 @@ def cm_measure_l2_rates(buf: int, nbytes: int, stream: int) -> tuple[float, floa
     _check(lib().cm_measure_l2_rates(buf, nbytes, stream, ctypes.byref(red), ctypes.byref(ld)),
            "cm_measure_l2_rates")
     return red.value, ld.value
+
+
+def cm_flow_eq2(cam, inv_depth: int, ego6: int, nb: int, dt_bin: float, scale: float, flow_out: int,
+                stream: int) -> None:
+    _check(lib().cm_flow_eq2(ctypes.byref(cam), inv_depth, ego6, nb, dt_bin, scale, flow_out, stream), "cm_flow_eq2")
+
+
+def cm_flow_eq2_scratch_query(cam, nb: int) -> int:
+    n = _sz()
+    _check(lib().cm_flow_eq2_scratch_query(ctypes.byref(cam), nb, ctypes.byref(n)), "cm_flow_eq2_scratch_query")
+    return n.value
+
+
+def cm_flow_eq2_backward(cam, inv_depth: int, ego6: int, nb: int, dt_bin: float, scale: float, dflow: int,
+                         dinv_depth: int, dego6: int, scratch: int, scratch_bytes: int, stream: int) -> None:
+    _check(lib().cm_flow_eq2_backward(ctypes.byref(cam), inv_depth, ego6, nb, dt_bin, scale, dflow, dinv_depth,
+                                      dego6, scratch, scratch_bytes, stream), "cm_flow_eq2_backward")

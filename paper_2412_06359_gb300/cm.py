@@ -123,6 +123,35 @@ def flow_from_depth(cam, inv_depth: torch.Tensor, ego: torch.Tensor, dt: float) 
     return out
 
 
+def flow_eq2(cam, inv_depth: torch.Tensor, ego: torch.Tensor, dt_bin: float, scale: float) -> torch.Tensor:
+    """Per-bin flows [nb, H, W, 2] by the reprojection of Eq. 2: ego [nb, 6]
+    holds each bin's (v, w) over dt_bin seconds; the displacement is scaled by
+    `scale` (nb for px per window when the bins split the window evenly)."""
+    c = camera(cam)
+    ego = _require_cuda(ego, "ego", torch.float32)
+    nb = ego.numel() // 6
+    out = torch.empty((nb, c.height, c.width, 2), dtype=torch.float32, device=inv_depth.device)
+    C.cm_flow_eq2(c, _require_cuda(inv_depth, "inv_depth", torch.float32), ego, nb, float(dt_bin), float(scale),
+                  out.data_ptr(), stream_handle(inv_depth.device))
+    return out
+
+
+def flow_eq2_backward(cam, inv_depth: torch.Tensor, ego: torch.Tensor, dt_bin: float, scale: float,
+                      dflow: torch.Tensor) -> tuple[torch.Tensor, torch.Tensor]:
+    """Adjoint of flow_eq2: (dL/d inv_depth [H, W], dL/d ego [nb, 6])."""
+    c = camera(cam)
+    ego = _require_cuda(ego, "ego", torch.float32)
+    nb = ego.numel() // 6
+    dev = inv_depth.device
+    scratch = torch.empty(C.cm_flow_eq2_scratch_query(c, nb), dtype=torch.uint8, device=dev)
+    drho = torch.empty_like(inv_depth)
+    dego = torch.empty((nb, 6), dtype=torch.float32, device=dev)
+    C.cm_flow_eq2_backward(c, _require_cuda(inv_depth, "inv_depth", torch.float32), ego, nb, float(dt_bin),
+                           float(scale), _require_cuda(dflow, "dflow", torch.float32), drho.data_ptr(),
+                           dego.data_ptr(), scratch.data_ptr(), scratch.numel(), stream_handle(dev))
+    return drho, dego
+
+
 def warp_splat(cam, ev: DeviceEvents, flow: torch.Tensor, cfg: C.cm_loss_cfg,
                ws: "Workspace | None" = None) -> torch.Tensor:
     """IWEs [R, H, W, 4] = (C+, S+, C-, S-) of one window (the sort path needs
@@ -215,6 +244,33 @@ class CMLossFlow(torch.autograd.Function):
         dloss = grad.reshape(1).to(torch.float32).contiguous()
         g = loss_backward(ctx.ws, ctx.ev, dloss, flow=flow)
         return g["dflow"], None, None
+
+
+class CMLossEq2(torch.autograd.Function):
+    """L_CM of one window whose per-bin flows come from inverse depth and one
+    pose per bin through Eq. 2 (ego [nb, 6], nb = 1 or the window's bins);
+    backward: the CM adjoint to dL/dflow of every bin, then the Eq. 2 adjoint to
+    dL/d inverse depth and dL/d ego."""
+
+    @staticmethod
+    def forward(ctx, inv_depth, ego, ev: DeviceEvents, ws: Workspace, dt_bin: float, scale: float):
+        inv_depth = inv_depth.contiguous()
+        ego = ego.contiguous()
+        flow = flow_eq2(ws.cam, inv_depth, ego, dt_bin, scale)
+        if flow.shape[0] == 1:
+            flow = flow[0]
+        loss = loss_forward(ws, ev, flow=flow)
+        ctx.save_for_backward(inv_depth, ego, flow)
+        ctx.ev, ctx.ws, ctx.dt, ctx.scale = ev, ws, dt_bin, scale
+        return loss[0]
+
+    @staticmethod
+    def backward(ctx, grad):
+        inv_depth, ego, flow = ctx.saved_tensors
+        dloss = grad.reshape(1).to(torch.float32).contiguous()
+        g = loss_backward(ctx.ws, ctx.ev, dloss, flow=flow)
+        drho, dego = flow_eq2_backward(ctx.ws.cam, inv_depth, ego, ctx.dt, ctx.scale, g["dflow"])
+        return drho, dego.reshape(ego.shape), None, None, None, None
 
 
 def cm_loss(ev: DeviceEvents, ws: Workspace, *, flow=None, inv_depth=None, ego=None, dt: float = 0.01):
