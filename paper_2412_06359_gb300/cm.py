@@ -128,11 +128,10 @@ def flow_eq2(cam, inv_depth: torch.Tensor, ego: torch.Tensor, dt_bin: float, sca
     holds each bin's (v, w) over dt_bin seconds; the displacement is scaled by
     `scale` (nb for px per window when the bins split the window evenly)."""
     c = camera(cam)
-    ego = _require_cuda(ego, "ego", torch.float32)
     nb = ego.numel() // 6
     out = torch.empty((nb, c.height, c.width, 2), dtype=torch.float32, device=inv_depth.device)
-    C.cm_flow_eq2(c, _require_cuda(inv_depth, "inv_depth", torch.float32), ego, nb, float(dt_bin), float(scale),
-                  out.data_ptr(), stream_handle(inv_depth.device))
+    C.cm_flow_eq2(c, _require_cuda(inv_depth, "inv_depth", torch.float32), _require_cuda(ego, "ego", torch.float32),
+                  nb, float(dt_bin), float(scale), out.data_ptr(), stream_handle(inv_depth.device))
     return out
 
 
@@ -140,13 +139,13 @@ def flow_eq2_backward(cam, inv_depth: torch.Tensor, ego: torch.Tensor, dt_bin: f
                       dflow: torch.Tensor) -> tuple[torch.Tensor, torch.Tensor]:
     """Adjoint of flow_eq2: (dL/d inv_depth [H, W], dL/d ego [nb, 6])."""
     c = camera(cam)
-    ego = _require_cuda(ego, "ego", torch.float32)
     nb = ego.numel() // 6
     dev = inv_depth.device
     scratch = torch.empty(C.cm_flow_eq2_scratch_query(c, nb), dtype=torch.uint8, device=dev)
     drho = torch.empty_like(inv_depth)
     dego = torch.empty((nb, 6), dtype=torch.float32, device=dev)
-    C.cm_flow_eq2_backward(c, _require_cuda(inv_depth, "inv_depth", torch.float32), ego, nb, float(dt_bin),
+    C.cm_flow_eq2_backward(c, _require_cuda(inv_depth, "inv_depth", torch.float32),
+                           _require_cuda(ego, "ego", torch.float32), nb, float(dt_bin),
                            float(scale), _require_cuda(dflow, "dflow", torch.float32), drho.data_ptr(),
                            dego.data_ptr(), scratch.data_ptr(), scratch.numel(), stream_handle(dev))
     return drho, dego

@@ -49,6 +49,7 @@ __device__ constexpr float kCosSeries[10] = {
 struct Pose {
     float R[9];
     float t[3];
+    float Ad[3];  // diagonal of R - I, computed directly (no cancellation against 1)
 };
 
 __device__ __forceinline__ Pose pose_of(const float* __restrict__ e, float dt)
@@ -67,6 +68,9 @@ __device__ __forceinline__ Pose pose_of(const float* __restrict__ e, float dt)
         a = __fmaf_rn(a, s, kSinSeries[n]);
         b = __fmaf_rn(b, s, kCosSeries[n]);
     }
+    p.Ad[0] = __fmul_rn(b, -__fadd_rn(kyy, kzz));
+    p.Ad[1] = __fmul_rn(b, -__fadd_rn(kxx, kzz));
+    p.Ad[2] = __fmul_rn(b, -__fadd_rn(kxx, kyy));
     p.R[0] = __fmaf_rn(b, -__fadd_rn(kyy, kzz), 1.0f);
     p.R[1] = __fmaf_rn(b, kxy, -__fmul_rn(a, kz));
     p.R[2] = __fmaf_rn(b, kxz, __fmul_rn(a, ky));
@@ -170,11 +174,20 @@ __global__ void __launch_bounds__(kEq2Threads) k_flow_eq2_grad(Eq2Args a, const 
 #pragma unroll
                     for (int s = 0; s < 3; ++s) c[3 + 3 * r + s] = dP[r] * X[s];
                 }
-                // dL/dX = R^T dL/dP; dL/dZ = dL/dX . (xn, yn, 1); dL/drho = -Z^2 dL/dZ
-                float dX[3];
-#pragma unroll
-                for (int s = 0; s < 3; ++s) dX[s] = p.R[s] * dP[0] + p.R[3 + s] * dP[1] + p.R[6 + s] * dP[2];
-                dr -= q.Z * q.Z * (dX[0] * q.xn + dX[1] * q.yn + dX[2]);
+                // dL/d(rho) = -Z^2 dL/dZ.  With m = (xn, yn, 1), P = Z R m + t and
+                // e0 = P0 - xn P2 = Z s0 + u0 (s0 = sum_c (A_0c - xn A_2c) m_c,
+                // A = R - I, u0 = t0 - xn t2):  d(fx e0/P2)/dZ = fx (s0 t2 - u0 q2) / P2^2,
+                // q2 = (R m)_2, and likewise for y.  Written this way the two
+                // nearly equal terms of the direct chain (xn P2 against P0) never
+                // meet, so the derivative keeps FP32 relative precision (it is 0
+                // for a pure rotation, as it should be).
+                const float A00 = p.Ad[0], A11 = p.Ad[1], A22 = p.Ad[2];
+                const float q2 = p.R[6] * q.xn + p.R[7] * q.yn + p.R[8];
+                const float s0 = (A00 - q.xn * p.R[6]) * q.xn + (p.R[1] - q.xn * p.R[7]) * q.yn + (p.R[2] - q.xn * A22);
+                const float s1 = (p.R[3] - q.yn * p.R[6]) * q.xn + (A11 - q.yn * p.R[7]) * q.yn + (p.R[5] - q.yn * A22);
+                const float u0 = p.t[0] - q.xn * p.t[2], u1 = p.t[1] - q.yn * p.t[2];
+                const float dZ = (Gx * (s0 * p.t[2] - u0 * q2) + Gy * (s1 * p.t[2] - u1 * q2)) * iz * iz;
+                dr -= q.Z * q.Z * dZ;
             }
 #pragma unroll
             for (int k = 0; k < kEq2Partials; ++k) {
