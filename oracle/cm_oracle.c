@@ -415,6 +415,23 @@ void orc_flow_eq2_grad(int32_t W, int32_t H, double fx, double fy, double cx, do
     }
 }
 
+/*
+ * The network's input frame (Sec. 4.1, supp. Table 4: a (2, H, W) input): the
+ * events of a window accumulated per pixel and polarity, channel 0 positive,
+ * channel 1 negative; events outside the sensor are skipped.  frame is
+ * [2][H][W], overwritten.
+ */
+void orc_event_frame(int32_t W, int32_t H, int64_t n, const int16_t* x, const int16_t* y, const int8_t* p,
+                     double* frame)
+{
+    const int64_t HW = (int64_t)W * H;
+    for (int64_t q = 0; q < 2 * HW; ++q) frame[q] = 0.0;
+    for (int64_t k = 0; k < n; ++k) {
+        if (x[k] < 0 || x[k] >= W || y[k] < 0 || y[k] >= H) continue;
+        frame[(p[k] > 0 ? 0 : HW) + (int64_t)y[k] * W + x[k]] += 1.0;
+    }
+}
+
 /* ------------------------------------------------------------------------- */
 /* S2-S6: warp, mask, splat, loss, gradient                                  */
 /* ------------------------------------------------------------------------- */

@@ -66,6 +66,7 @@ def lib():
             l.orc_flow_eq2_bins.argtypes = [i, i, d, d, d, d, vp, vp, i, d, d, vp]
             l.orc_flow_eq2_bins_f32.argtypes = [i, i, f, f, f, f, vp, vp, i, f, f, vp]
             l.orc_flow_eq2_grad.argtypes = [i, i, d, d, d, d, vp, vp, i, d, d, vp, vp, vp]
+            l.orc_event_frame.argtypes = [i, i, ctypes.c_int64, vp, vp, vp, vp]
             l.orc_cm.argtypes = [ctypes.POINTER(_Args)]
             l.orc_cm.restype = ctypes.c_int
             _lib = l
@@ -150,6 +151,26 @@ def flow_eq2_grad(cam, inv_depth, ego, dt_bin, scale, dflow):
     lib().orc_flow_eq2_grad(cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy, _p(rho), _p(e), nb,
                             float(dt_bin), float(scale), _p(g), _p(drho), _p(dego))
     return drho, dego
+
+
+def event_frame(events, width, height):
+    """Per-pixel event counts [2, H, W] (channel 0 positive, 1 negative), the
+    network's input frame."""
+    out = np.empty((2, height, width), np.float64)
+    x, y, p = _c(events.x, np.int16), _c(events.y, np.int16), _c(events.p, np.int8)
+    lib().orc_event_frame(width, height, events.n, _p(x), _p(y), _p(p), _p(out))
+    return out
+
+
+def rsat(events, flow, *, width, height, nbins, ref_mode, eps=1e-9, flow32=None):
+    """Ratio of squared average timestamps: the CM loss with `flow` over the CM
+    loss with zero flow (the unwarped events), same references; 0 when the
+    zero-flow loss is 0 (no event in the image)."""
+    fl = np.asarray(flow, np.float64)
+    a = cm(events, fl, width=width, height=height, nbins=nbins, ref_mode=ref_mode, eps=eps, flow32=flow32)["loss"]
+    b = cm(events, np.zeros((height, width, 2)), width=width, height=height, nbins=nbins, ref_mode=ref_mode,
+           eps=eps)["loss"]
+    return a / b if b > 0 else 0.0
 
 
 def depth_ego_grad(cam, inv_depth, ego, dt, dflow):

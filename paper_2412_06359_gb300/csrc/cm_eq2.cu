@@ -135,8 +135,12 @@ __global__ void __launch_bounds__(kEq2Threads) k_flow_eq2(Eq2Args a, float2* __r
     }
 }
 
-// Adjoint per tile of 256 pixels (one per thread): dL/d(rho) per pixel (summed
-// over the bins), and per bin the tile's twelve sums dL/dt, dL/dR.
+// Adjoint per tile of kEq2Tile pixels (kEq2PerThread per thread, strided by
+// the block size): dL/d(rho) per pixel (summed over the bins), and per bin the
+// tile's twelve sums dL/dt, dL/dR (one block reduction per bin and tile).
+constexpr int kEq2PerThread = 8;
+constexpr int kEq2Tile = kEq2Threads * kEq2PerThread;
+
 __global__ void __launch_bounds__(kEq2Threads) k_flow_eq2_grad(Eq2Args a, const float2* __restrict__ dflow,
                                                                float* __restrict__ drho, float* __restrict__ part,
                                                                int ntiles)
@@ -148,31 +152,38 @@ __global__ void __launch_bounds__(kEq2Threads) k_flow_eq2_grad(Eq2Args a, const 
     const uint32_t HW = (uint32_t)a.W * (uint32_t)a.H;
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const uint32_t i = (uint32_t)tile * blockDim.x + threadIdx.x;
-        const bool in = i < HW;
-        PixelPoint q{0.0f, 0.0f, 0.0f};
-        if (in) {
-            const uint32_t v = i / (uint32_t)a.W, u = i - v * (uint32_t)a.W;
-            q = pixel_point(a, (int)u, (int)v, __ldg(a.rho + i));
+        PixelPoint q[kEq2PerThread];
+        float dr[kEq2PerThread];
+#pragma unroll
+        for (int k = 0; k < kEq2PerThread; ++k) {
+            const uint32_t i = (uint32_t)tile * kEq2Tile + k * kEq2Threads + threadIdx.x;
+            dr[k] = 0.0f;
+            q[k] = PixelPoint{0.0f, 0.0f, 0.0f};
+            if (i < HW) {
+                const uint32_t v = i / (uint32_t)a.W, u = i - v * (uint32_t)a.W;
+                q[k] = pixel_point(a, (int)u, (int)v, __ldg(a.rho + i));
+            }
         }
-        float dr = 0.0f;
         for (int b = 0; b < a.nb; ++b) {
+            const Pose& p = poses[b];
             float c[kEq2Partials];
 #pragma unroll
-            for (int k = 0; k < kEq2Partials; ++k) c[k] = 0.0f;
-            if (in) {
-                const Pose& p = poses[b];
+            for (int m = 0; m < kEq2Partials; ++m) c[m] = 0.0f;
+#pragma unroll
+            for (int k = 0; k < kEq2PerThread; ++k) {
+                const uint32_t i = (uint32_t)tile * kEq2Tile + k * kEq2Threads + threadIdx.x;
+                if (i >= HW) continue;
                 float X[3], P[3];
-                transform(p, q, X, P);
+                transform(p, q[k], X, P);
                 const float2 g = __ldg(dflow + (size_t)b * HW + i);
                 const float iz = 1.0f / P[2];
                 const float Gx = a.scale * g.x * a.fx, Gy = a.scale * g.y * a.fy;
                 const float dP[3] = {Gx * iz, Gy * iz, -(Gx * P[0] + Gy * P[1]) * iz * iz};
 #pragma unroll
                 for (int r = 0; r < 3; ++r) {
-                    c[r] = dP[r];
+                    c[r] += dP[r];
 #pragma unroll
-                    for (int s = 0; s < 3; ++s) c[3 + 3 * r + s] = dP[r] * X[s];
+                    for (int s = 0; s < 3; ++s) c[3 + 3 * r + s] += dP[r] * X[s];
                 }
                 // dL/d(rho) = -Z^2 dL/dZ.  With m = (xn, yn, 1), P = Z R m + t and
                 // e0 = P0 - xn P2 = Z s0 + u0 (s0 = sum_c (A_0c - xn A_2c) m_c,
@@ -181,28 +192,34 @@ __global__ void __launch_bounds__(kEq2Threads) k_flow_eq2_grad(Eq2Args a, const 
                 // nearly equal terms of the direct chain (xn P2 against P0) never
                 // meet, so the derivative keeps FP32 relative precision (it is 0
                 // for a pure rotation, as it should be).
-                const float A00 = p.Ad[0], A11 = p.Ad[1], A22 = p.Ad[2];
-                const float q2 = p.R[6] * q.xn + p.R[7] * q.yn + p.R[8];
-                const float s0 = (A00 - q.xn * p.R[6]) * q.xn + (p.R[1] - q.xn * p.R[7]) * q.yn + (p.R[2] - q.xn * A22);
-                const float s1 = (p.R[3] - q.yn * p.R[6]) * q.xn + (A11 - q.yn * p.R[7]) * q.yn + (p.R[5] - q.yn * A22);
-                const float u0 = p.t[0] - q.xn * p.t[2], u1 = p.t[1] - q.yn * p.t[2];
+                const PixelPoint& pq = q[k];
+                const float q2 = p.R[6] * pq.xn + p.R[7] * pq.yn + p.R[8];
+                const float s0 = (p.Ad[0] - pq.xn * p.R[6]) * pq.xn + (p.R[1] - pq.xn * p.R[7]) * pq.yn +
+                                 (p.R[2] - pq.xn * p.Ad[2]);
+                const float s1 = (p.R[3] - pq.yn * p.R[6]) * pq.xn + (p.Ad[1] - pq.yn * p.R[7]) * pq.yn +
+                                 (p.R[5] - pq.yn * p.Ad[2]);
+                const float u0 = p.t[0] - pq.xn * p.t[2], u1 = p.t[1] - pq.yn * p.t[2];
                 const float dZ = (Gx * (s0 * p.t[2] - u0 * q2) + Gy * (s1 * p.t[2] - u1 * q2)) * iz * iz;
-                dr -= q.Z * q.Z * dZ;
+                dr[k] -= pq.Z * pq.Z * dZ;
             }
 #pragma unroll
-            for (int k = 0; k < kEq2Partials; ++k) {
-                const float s = warp_sum(c[k]);
-                if (l == 0) red[w][k] = s;
+            for (int m = 0; m < kEq2Partials; ++m) {
+                const float s = warp_sum(c[m]);
+                if (l == 0) red[w][m] = s;
             }
             __syncthreads();
             if (threadIdx.x < kEq2Partials) {
                 float s = 0.0f;
-                for (int k = 0; k < kEq2Threads / 32; ++k) s += red[k][threadIdx.x];
+                for (int m = 0; m < kEq2Threads / 32; ++m) s += red[m][threadIdx.x];
                 part[((size_t)tile * a.nb + b) * kEq2Partials + threadIdx.x] = s;
             }
             __syncthreads();
         }
-        if (in) drho[i] = dr;
+#pragma unroll
+        for (int k = 0; k < kEq2PerThread; ++k) {
+            const uint32_t i = (uint32_t)tile * kEq2Tile + k * kEq2Threads + threadIdx.x;
+            if (i < HW) drho[i] = dr[k];
+        }
     }
 }
 
@@ -299,7 +316,7 @@ bool eq2_args(const cm_camera* cam, const float* rho, const float* ego, int32_t 
     return true;
 }
 
-int eq2_tiles(const cm_camera* cam) { return (int)(((size_t)cam->width * cam->height + kEq2Threads - 1) / kEq2Threads); }
+int eq2_tiles(const cm_camera* cam) { return (int)(((size_t)cam->width * cam->height + kEq2Tile - 1) / kEq2Tile); }
 
 int grid_for(int tiles)
 {
@@ -319,7 +336,7 @@ int cm_flow_eq2(const cm_camera* cam, const float* inv_depth, const float* ego6,
     cmk::Eq2Args a;
     if (!flow_out || !cmk::eq2_args(cam, inv_depth, ego6, nb, dt_bin, scale, a)) return CM_EINVAL;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    const int grid = cmk::grid_for(cmk::eq2_tiles(cam));
+    const int grid = cmk::grid_for((int)(((size_t)cam->width * cam->height + cmk::kEq2Threads - 1) / cmk::kEq2Threads));
     cmk::KernelScope ks("k_flow_eq2", s);
     cmk::k_flow_eq2<<<grid, cmk::kEq2Threads, 0, s>>>(a, reinterpret_cast<float2*>(flow_out));
     return cudaGetLastError() == cudaSuccess ? CM_OK : CM_ECUDA;
