@@ -195,6 +195,23 @@ int cm_loss_backward(const cm_camera* cam, const cm_events* ev, const float* flo
  */
 int cm_workspace_stats(const cm_workspace* ws, const float** loss_r, const int32_t** nnz_r);
 
+/* ---- network input and evaluation metric ----
+ * The network's input frame (supp. Table 4, a (2, H, W) input): the events of
+ * a window counted per pixel and polarity, channel 0 positive, channel 1
+ * negative, as float; events outside the sensor are skipped.  frame_out is
+ * device memory [2][H][W], overwritten.  Counts are exact integers, so the
+ * result is the same on every run.  Errors: CM_EINVAL, CM_ECUDA. */
+int cm_event_frame(const cm_camera* cam, const cm_events* ev, float* frame_out, void* stream);
+/* RSAT, the ratio of squared average timestamps (the deblurring metric the
+ * paper reports beside depth error, Sec. 4.3, Fig. 4): the CM loss of the
+ * events warped by `flow` over the CM loss of the unwarped events (zero flow),
+ * same configuration and references; 0 when the zero-flow loss is 0.  Runs two
+ * forwards on `ws` (whose own flow buffer holds the zero flow), so a
+ * following cm_loss_backward on `ws` returns CM_ESTATE until the next
+ * cm_loss_forward.  rsat_out: device scalar.  Errors as cm_loss_forward. */
+int cm_rsat(const cm_camera* cam, const cm_events* ev, const float* flow, int32_t n_flow_bins,
+            const cm_loss_cfg* cfg, cm_workspace* ws, float* rsat_out, void* stream);
+
 /* ---- discrete flow: Eq. 2 with one pose per bin ----
  * The flow of bin i (of nb) by the reprojection of Eq. 2 (Sec. 3.2): pixel
  * (u, v) with inverse depth rho is back-projected to X = (xn, yn, 1) / rho

@@ -125,6 +125,8 @@ SIGNATURES = {
     "cm_profile_reset": ([], ctypes.c_int),
     "cm_launch_count": ([], ctypes.c_int64),
     "cm_flow_eq2": ([_P(cm_camera), _vp, _vp, _i32, _f32, _f32, _vp, _vp], ctypes.c_int),
+    "cm_event_frame": ([_P(cm_camera), _P(cm_events), _vp, _vp], ctypes.c_int),
+    "cm_rsat": ([_P(cm_camera), _P(cm_events), _vp, _i32, _P(cm_loss_cfg), _vp, _vp, _vp], ctypes.c_int),
     "cm_flow_eq2_scratch_query": ([_P(cm_camera), _i32, _P(_sz)], ctypes.c_int),
     "cm_flow_eq2_backward": ([_P(cm_camera), _vp, _vp, _i32, _f32, _f32, _vp, _vp, _vp, _vp, _sz, _vp],
                              ctypes.c_int),
@@ -363,3 +365,12 @@ def cm_flow_eq2_backward(cam, inv_depth: int, ego6: int, nb: int, dt_bin: float,
                          dinv_depth: int, dego6: int, scratch: int, scratch_bytes: int, stream: int) -> None:
     _check(lib().cm_flow_eq2_backward(ctypes.byref(cam), inv_depth, ego6, nb, dt_bin, scale, dflow, dinv_depth,
                                       dego6, scratch, scratch_bytes, stream), "cm_flow_eq2_backward")
+
+
+def cm_event_frame(cam, ev, frame_out: int, stream: int) -> None:
+    _check(lib().cm_event_frame(ctypes.byref(cam), ctypes.byref(ev), frame_out, stream), "cm_event_frame")
+
+
+def cm_rsat(cam, ev, flow: int, n_flow_bins: int, cfg, ws: int, rsat_out: int, stream: int) -> None:
+    _check(lib().cm_rsat(ctypes.byref(cam), ctypes.byref(ev), flow, n_flow_bins, ctypes.byref(cfg), ws, rsat_out,
+                         stream), "cm_rsat")

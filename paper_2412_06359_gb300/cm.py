@@ -151,6 +151,24 @@ def flow_eq2_backward(cam, inv_depth: torch.Tensor, ego: torch.Tensor, dt_bin: f
     return drho, dego
 
 
+def event_frame(cam, ev: DeviceEvents) -> torch.Tensor:
+    """The network's input frame [2, H, W]: events per pixel, positive then negative."""
+    c = camera(cam)
+    out = torch.empty((2, c.height, c.width), dtype=torch.float32, device=ev.x.device)
+    C.cm_event_frame(c, ev.c(), out.data_ptr(), stream_handle(ev.x.device))
+    return out
+
+
+def rsat(ws: "Workspace", ev: DeviceEvents, flow: torch.Tensor) -> torch.Tensor:
+    """RSAT of one window (device tensor [1]): CM loss with `flow` over the CM
+    loss of the unwarped events."""
+    out = torch.empty(1, dtype=torch.float32, device=flow.device)
+    nfb = 1 if flow.dim() == 3 else flow.shape[0]
+    C.cm_rsat(ws.cam, ev.c(), _require_cuda(flow, "flow", torch.float32), nfb, ws.cfg, ws.handle, out.data_ptr(),
+              stream_handle(flow.device))
+    return out
+
+
 def warp_splat(cam, ev: DeviceEvents, flow: torch.Tensor, cfg: C.cm_loss_cfg,
                ws: "Workspace | None" = None) -> torch.Tensor:
     """IWEs [R, H, W, 4] = (C+, S+, C-, S-) of one window (the sort path needs

@@ -30,6 +30,7 @@ struct cm_workspace {
     int32_t* nnz_r;
     float* dego_part;
     float2* warp;            // [B+1][max_events] stored trajectory points (store_warps), else nullptr
+    float* scal;             // [4] device scalars of cm_rsat
     bool has_sort;           // buffers of the deterministic sort path are laid out
     cmk::SortBufs sb;
     // state of the last forward on this workspace
@@ -56,7 +57,7 @@ int tiles_for(size_t hw, int cap)
 }
 
 struct Layout {
-    size_t iwe, flow, dflow, loss_part, norm, loss_r, nnz_r, dego_part, warp, total;
+    size_t iwe, flow, dflow, loss_part, norm, loss_r, nnz_r, dego_part, warp, scal, total;
     size_t ka, kb, va, vb, pay, hist, part, start;  // sort path (CM_SPLAT_SORT only)
     int R, loss_tiles, pix_tiles;
     bool sort;
@@ -122,6 +123,8 @@ Layout layout(const cm_camera& cam, const cm_loss_cfg& cfg, int32_t nfb, int64_t
     off = align_up(off + (size_t)L.pix_tiles * 6 * sizeof(float));
     L.warp = off;
     if (cfg.store_warps) off = align_up(off + (size_t)(cfg.nbins + 1) * max_events * sizeof(float2));
+    L.scal = off;
+    off = align_up(off + 4 * sizeof(float));
     L.sort = cfg.splat == CM_SPLAT_SORT;
     if (L.sort) {
         const cmk::SortSizes z = cmk::sort_sizes(max_events, L.R, cfg.nbins, nfb, HW);
@@ -147,6 +150,9 @@ Layout layout(const cm_camera& cam, const cm_loss_cfg& cfg, int32_t nfb, int64_t
 }
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? CM_OK : CM_ECUDA; }
+
+// RSAT from the two losses (0 when the zero-flow loss is 0: no event in the image)
+__global__ void k_ratio(const float* ab, float* out) { out[0] = ab[1] > 0.0f ? ab[0] / ab[1] : 0.0f; }
 
 cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
@@ -275,6 +281,7 @@ int cm_workspace_create(void* dev_mem, size_t bytes, const cm_camera* cam, const
     ws->nnz_r = reinterpret_cast<int32_t*>(b + L.nnz_r);
     ws->dego_part = reinterpret_cast<float*>(b + L.dego_part);
     ws->warp = cfg->store_warps ? reinterpret_cast<float2*>(b + L.warp) : nullptr;
+    ws->scal = reinterpret_cast<float*>(b + L.scal);
     ws->has_sort = L.sort;
     if (L.sort) {
         ws->sb.ka = reinterpret_cast<uint32_t*>(b + L.ka);
@@ -423,6 +430,25 @@ int cm_loss_backward(const cm_camera* cam, const cm_events* ev, const float* flo
         if ((st = cuda_status(cmk::launch_depth_ego(d, s)))) return st;
     }
     return CM_OK;
+}
+
+int cm_rsat(const cm_camera* cam, const cm_events* ev, const float* flow, int32_t n_flow_bins,
+            const cm_loss_cfg* cfg, cm_workspace* ws, float* rsat_out, void* stream)
+{
+    if (!ws || !rsat_out || !flow) return CM_EINVAL;
+    cudaStream_t s = as_stream(stream);
+    int st = cm_loss_forward(cam, ev, flow, n_flow_bins, nullptr, nullptr, 0.0f, cfg, ws, ws->scal + 0, stream);
+    if (st) return st;
+    // the unwarped events: zero flow in the workspace's own flow buffer
+    if ((st = cuda_status(cudaMemsetAsync(ws->flow, 0, (size_t)cam->width * cam->height * sizeof(float2), s))))
+        return st;
+    st = cm_loss_forward(cam, ev, reinterpret_cast<const float*>(ws->flow), 1, nullptr, nullptr, 0.0f, cfg, ws,
+                         ws->scal + 1, stream);
+    ws->fwd_mode = 0;  // neither forward is left for a backward
+    if (st) return st;
+    cmk::KernelScope ks("k_ratio", s);
+    k_ratio<<<1, 1, 0, s>>>(ws->scal, rsat_out);
+    return cuda_status(cudaGetLastError());
 }
 
 }  // extern "C"
