@@ -479,8 +479,9 @@ def run_ours(args):
 
 def measure_eq2(device, peak: float, reps: int = 10):
     """The discrete flow (Eq. 2, one pose per bin) and its adjoint on a
-    1280x720 sensor with 20 bins: CUDA-event time per launch and achieved
-    bandwidth against the measured HBM peak (the flows, 147 MB, exceed L2)."""
+    1280x720 sensor with 20 bins: device time per call (the library's CUDA
+    events around its kernels) and achieved bandwidth against the measured HBM
+    peak (the flows, 147 MB, exceed L2)."""
     import torch
     from paper_2412_06359_gb300 import cm, synth
     W, H, nb = 1280, 720, 20
@@ -490,18 +491,23 @@ def measure_eq2(device, peak: float, reps: int = 10):
     ego = torch.from_numpy(np.stack([synth.ego_motion(rng) for _ in range(nb)]).astype(np.float32)).to(device)
     dt, scale = 0.01 / nb, float(nb)
     g = torch.randn(nb, H, W, 2, device=device)
-    stream = torch.cuda.current_stream(device)
+
+    from paper_2412_06359_gb300 import _capi as C
 
     def timed(fn):
+        # device time of the library's own kernels (CUDA events around each
+        # launch on its stream), so host-side call overhead is not counted
         for _ in range(3):
             fn()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
+        torch.cuda.synchronize(device)
+        C.cm_profile_reset()
+        C.cm_profile_enable(True)
         for _ in range(reps):
             fn()
-        b.record(stream)
         torch.cuda.synchronize(device)
-        return a.elapsed_time(b) / reps
+        C.cm_profile_enable(False)
+        prof = C.cm_profile_collect()
+        return sum(v[1] for v in prof.values()) / reps
 
     f_ms = timed(lambda: cm.flow_eq2(cam, rho, ego, dt, scale))
     b_ms = timed(lambda: cm.flow_eq2_backward(cam, rho, ego, dt, scale, g))

@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(kEq2Threads) k_flow_eq2(Eq2Args a, float2* __r
 // Adjoint per tile of kEq2Tile pixels (kEq2PerThread per thread, strided by
 // the block size): dL/d(rho) per pixel (summed over the bins), and per bin the
 // tile's twelve sums dL/dt, dL/dR (one block reduction per bin and tile).
-constexpr int kEq2PerThread = 8;
+constexpr int kEq2PerThread = 4;
 constexpr int kEq2Tile = kEq2Threads * kEq2PerThread;
 
 __global__ void __launch_bounds__(kEq2Threads) k_flow_eq2_grad(Eq2Args a, const float2* __restrict__ dflow,
@@ -146,7 +146,8 @@ __global__ void __launch_bounds__(kEq2Threads) k_flow_eq2_grad(Eq2Args a, const 
                                                                int ntiles)
 {
     __shared__ Pose poses[CM_MAX_BINS];
-    __shared__ float red[kEq2Threads / 32][kEq2Partials];
+    // per warp, bin and component: the warp's sum (one barrier per tile, not per bin)
+    __shared__ float red[kEq2Threads / 32][CM_MAX_BINS][kEq2Partials];
     if (threadIdx.x < a.nb) poses[threadIdx.x] = pose_of(a.ego + 6 * threadIdx.x, a.dt);
     __syncthreads();
     const uint32_t HW = (uint32_t)a.W * (uint32_t)a.H;
@@ -176,7 +177,7 @@ __global__ void __launch_bounds__(kEq2Threads) k_flow_eq2_grad(Eq2Args a, const 
                 float X[3], P[3];
                 transform(p, q[k], X, P);
                 const float2 g = __ldg(dflow + (size_t)b * HW + i);
-                const float iz = 1.0f / P[2];
+                const float iz = recip(P[2]);  // hardware reciprocal: the adjoint is ALU-bound
                 const float Gx = a.scale * g.x * a.fx, Gy = a.scale * g.y * a.fy;
                 const float dP[3] = {Gx * iz, Gy * iz, -(Gx * P[0] + Gy * P[1]) * iz * iz};
 #pragma unroll
@@ -205,21 +206,23 @@ __global__ void __launch_bounds__(kEq2Threads) k_flow_eq2_grad(Eq2Args a, const 
 #pragma unroll
             for (int m = 0; m < kEq2Partials; ++m) {
                 const float s = warp_sum(c[m]);
-                if (l == 0) red[w][m] = s;
+                if (l == 0) red[w][b][m] = s;
             }
-            __syncthreads();
-            if (threadIdx.x < kEq2Partials) {
-                float s = 0.0f;
-                for (int m = 0; m < kEq2Threads / 32; ++m) s += red[m][threadIdx.x];
-                part[((size_t)tile * a.nb + b) * kEq2Partials + threadIdx.x] = s;
-            }
-            __syncthreads();
         }
 #pragma unroll
         for (int k = 0; k < kEq2PerThread; ++k) {
             const uint32_t i = (uint32_t)tile * kEq2Tile + k * kEq2Threads + threadIdx.x;
             if (i < HW) drho[i] = dr[k];
         }
+        __syncthreads();
+        // the tile's partial of every (bin, component): its warps' sums in a fixed order
+        for (int j = threadIdx.x; j < a.nb * kEq2Partials; j += blockDim.x) {
+            const int b = j / kEq2Partials, m = j - b * kEq2Partials;
+            float s = 0.0f;
+            for (int k = 0; k < kEq2Threads / 32; ++k) s += red[k][b][m];
+            part[((size_t)tile * a.nb + b) * kEq2Partials + m] = s;
+        }
+        __syncthreads();
     }
 }
 
