@@ -416,6 +416,122 @@ void orc_flow_eq2_grad(int32_t W, int32_t H, double fx, double fy, double cx, do
 }
 
 /*
+ * Geometry-consistency loss (Sec. 3.2, Eq. 3), read as in the consistency loss
+ * the paper cites: every pixel x of view 0 with depth D0 = 1/rho0 is moved by
+ * the camera motion between the two views (the rigid transform of Eq. 2:
+ * P = R X + t, R = Rodrigues(-w dt), t = -v dt); its forward-projected depth
+ * is a = P2, its projection x' lands in view 1, where the interpolated depth b
+ * is the bilinear sample of D1 = 1/rho1 at x' (corner indices clamped).  Valid
+ * pixels V: P2 > 0 and x' inside the closed image box.
+ *   L_geo = (1 / |V|) sum_{x in V} |a - b| / (a + b)
+ * The projection decides integers (valid or not, the sample's cell), so the
+ * decisions are taken on the FP32 projection of the kernels (orc_geo_proj_f32)
+ * and the loss in FP64 on those decisions; the gradient is that of the branch
+ * the decisions select (sign(0) = 0 at a = b).
+ */
+void orc_geo_proj_f32(int32_t W, int32_t H, float fx, float fy, float cx, float cy, const float* rho0,
+                      const float* ego, float dt, float* proj, uint8_t* ok)
+{
+    float Rm[9], tv[3];
+    rot_f32(ego, dt, Rm, tv);
+    const float ifx = 1.0f / fx, ify = 1.0f / fy;
+    const float W1 = (float)(W - 1), H1 = (float)(H - 1);
+    for (int32_t v = 0; v < H; ++v) {
+        for (int32_t u = 0; u < W; ++u) {
+            const int64_t q = (int64_t)v * W + u;
+            const float xn = ((float)u - cx) * ifx;
+            const float yn = ((float)v - cy) * ify;
+            const float Z = 1.0f / rho0[q];
+            const float X0 = Z * xn, X1 = Z * yn, X2 = Z;
+            const float P0 = fmaf(Rm[2], X2, fmaf(Rm[1], X1, fmaf(Rm[0], X0, tv[0])));
+            const float P1 = fmaf(Rm[5], X2, fmaf(Rm[4], X1, fmaf(Rm[3], X0, tv[1])));
+            const float P2 = fmaf(Rm[8], X2, fmaf(Rm[7], X1, fmaf(Rm[6], X0, tv[2])));
+            const float iz = 1.0f / P2;
+            const float xp = (float)u + fx * (fmaf(-xn, P2, P0) * iz);
+            const float yp = (float)v + fy * (fmaf(-yn, P2, P1) * iz);
+            proj[2 * q] = xp;
+            proj[2 * q + 1] = yp;
+            ok[q] = P2 > 0.0f && xp >= 0.0f && xp <= W1 && yp >= 0.0f && yp <= H1;
+        }
+    }
+}
+
+double orc_geo(int32_t W, int32_t H, double fx, double fy, double cx, double cy, const double* rho0,
+               const double* rho1, const double* ego, double dt, const float* proj, const uint8_t* ok, double dloss,
+               int64_t* count, double* drho0, double* drho1, double* dego)
+{
+    const int64_t HW = (int64_t)W * H;
+    const double k[3] = {-ego[3] * dt, -ego[4] * dt, -ego[5] * dt};
+    const double t[3] = {-ego[0] * dt, -ego[1] * dt, -ego[2] * dt};
+    double Rm[3][3];
+    rodrigues(k, Rm);
+    int64_t nv = 0;
+    for (int64_t q = 0; q < HW; ++q) nv += ok[q] != 0;
+    *count = nv;
+    if (drho0)
+        for (int64_t q = 0; q < HW; ++q) drho0[q] = drho1[q] = 0.0;
+    double gt[3] = {0, 0, 0}, M[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    double sum = 0.0;
+    const double g = nv > 0 ? dloss / (double)nv : 0.0;
+    for (int32_t v = 0; v < H; ++v) {
+        for (int32_t u = 0; u < W; ++u) {
+            const int64_t q = (int64_t)v * W + u;
+            if (!ok[q]) continue;
+            const double xn = ((double)u - cx) / fx, yn = ((double)v - cy) / fy;
+            const double Z = 1.0 / rho0[q];
+            const double X[3] = {Z * xn, Z * yn, Z};
+            double P[3];
+            for (int r = 0; r < 3; ++r) P[r] = Rm[r][0] * X[0] + Rm[r][1] * X[1] + Rm[r][2] * X[2] + t[r];
+            const double xp = fx * P[0] / P[2] + cx, yp = fy * P[1] / P[2] + cy;
+            /* the decided cell; the weights from the FP64 position */
+            const int ix = (int)floorf(proj[2 * q]), iy = (int)floorf(proj[2 * q + 1]);
+            const int ix1 = ix + 1 < W ? ix + 1 : W - 1, iy1 = iy + 1 < H ? iy + 1 : H - 1;
+            const double ax = xp - ix, ay = yp - iy;
+            const int64_t c00 = (int64_t)iy * W + ix, c10 = (int64_t)iy * W + ix1;
+            const int64_t c01 = (int64_t)iy1 * W + ix, c11 = (int64_t)iy1 * W + ix1;
+            const double D00 = 1.0 / rho1[c00], D10 = 1.0 / rho1[c10], D01 = 1.0 / rho1[c01], D11 = 1.0 / rho1[c11];
+            const double w00 = (1 - ax) * (1 - ay), w10 = ax * (1 - ay), w01 = (1 - ax) * ay, w11 = ax * ay;
+            const double a = P[2];
+            const double b = w00 * D00 + w10 * D10 + w01 * D01 + w11 * D11;
+            sum += fabs(a - b) / (a + b);
+            if (!drho0) continue;
+            const double sg = a > b ? 1.0 : (a < b ? -1.0 : 0.0);
+            const double dfa = g * sg * 2.0 * b / ((a + b) * (a + b));
+            const double dfb = -g * sg * 2.0 * a / ((a + b) * (a + b));
+            const double dbx = (1 - ay) * (D10 - D00) + ay * (D11 - D01);
+            const double dby = (1 - ax) * (D01 - D00) + ax * (D11 - D10);
+            /* x' = fx P0/P2 + cx, y' = fy P1/P2 + cy */
+            const double dP[3] = {dfb * dbx * fx / P[2], dfb * dby * fy / P[2],
+                                  dfa - dfb * (dbx * fx * P[0] + dby * fy * P[1]) / (P[2] * P[2])};
+            for (int r = 0; r < 3; ++r) {
+                gt[r] += dP[r];
+                for (int c = 0; c < 3; ++c) M[r][c] += dP[r] * X[c];
+            }
+            double dX[3];
+            for (int c = 0; c < 3; ++c) dX[c] = Rm[0][c] * dP[0] + Rm[1][c] * dP[1] + Rm[2][c] * dP[2];
+            drho0[q] += -Z * Z * (dX[0] * xn + dX[1] * yn + dX[2]);
+            /* b = sum_c w_c / rho1_c */
+            drho1[c00] -= dfb * w00 * D00 * D00;
+            drho1[c10] -= dfb * w10 * D10 * D10;
+            drho1[c01] -= dfb * w01 * D01 * D01;
+            drho1[c11] -= dfb * w11 * D11 * D11;
+        }
+    }
+    if (drho0) {
+        double dR[3][3][3];
+        rodrigues_grad(k, dR);
+        for (int c = 0; c < 3; ++c) {
+            double dk = 0.0;
+            for (int r = 0; r < 3; ++r)
+                for (int s2 = 0; s2 < 3; ++s2) dk += M[r][s2] * dR[c][r][s2];
+            dego[c] = -dt * gt[c];
+            dego[3 + c] = -dt * dk;
+        }
+    }
+    return nv > 0 ? sum / (double)nv : 0.0;
+}
+
+/*
  * The network's input frame (Sec. 4.1, supp. Table 4: a (2, H, W) input): the
  * events of a window accumulated per pixel and polarity, channel 0 positive,
  * channel 1 negative; events outside the sensor are skipped.  frame is

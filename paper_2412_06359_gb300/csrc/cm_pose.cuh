@@ -1,0 +1,170 @@
+// cm_pose.cuh -- the rigid motion of a camera between two views (Sec. 3.2,
+// Eq. 2) as the kernels compute it: the rotation by Rodrigues' formula, the
+// transform of a pixel's back-projected point, and the derivative of the
+// rotation with respect to its exponential coordinates.  Shared by the
+// discrete flow (cm_eq2.cu) and the geometry-consistency loss (cm_geo.cu).
+//
+// A camera moving with velocity v and angular velocity w for dt seconds maps
+// the point X of a pixel (X = (xn, yn, 1) / rho) to P = R X + t with
+// R = Rodrigues(k), k = -w dt, t = -v dt.
+//
+// FP32 arithmetic contract.  The projected positions decide integer outcomes
+// downstream (cells, supports, the mask, valid pixels), so every operation is
+// one explicit correctly rounded single-precision operation in a fixed order:
+//   per bin:   kxx = kx*kx, kyy = ky*ky, kzz = kz*kz, kxy = kx*ky, kxz = kx*kz, kyz = ky*kz
+//              s = (kxx + kyy) + kzz
+//              a = sin(th)/th, b = (1 - cos th)/th^2 as Taylor series in s through s^9,
+//                  Horner from the highest term: c = fma(c, s, c_n)
+//              R00 = fma(b, -(kyy + kzz), 1)  R01 = fma(b, kxy, -(a*kz))  R02 = fma(b, kxz, a*ky)
+//              R10 = fma(b, kxy, a*kz)        R11 = fma(b, -(kxx + kzz), 1) R12 = fma(b, kyz, -(a*kx))
+//              R20 = fma(b, kxz, -(a*ky))     R21 = fma(b, kyz, a*kx)     R22 = fma(b, -(kxx + kyy), 1)
+//   per pixel: xn = (u - cx) * (1/fx), yn = (v - cy) * (1/fy), Z = 1/rho, X = (Z*xn, Z*yn, Z)
+//              P_a = fma(R_a2, X2, fma(R_a1, X1, fma(R_a0, X0, t_a))), iz = 1/P2
+//              displacement d = (fx * (fma(-xn, P2, P0) * iz), fy * (fma(-yn, P2, P1) * iz)),
+//              i.e. fx (P0/P2 - xn) without cancelling against the pixel coordinate
+#pragma once
+
+#include <cmath>
+#include <cstdint>
+
+#include "cm_device.cuh"
+
+namespace cmk {
+
+// Taylor coefficients of sin(th)/th and (1 - cos th)/th^2 in s = th^2
+__device__ constexpr float kSinSeries[10] = {
+    (float)1.0, (float)(-1.0 / 6.0), (float)(1.0 / 120.0), (float)(-1.0 / 5040.0), (float)(1.0 / 362880.0),
+    (float)(-1.0 / 39916800.0), (float)(1.0 / 6227020800.0), (float)(-1.0 / 1307674368000.0),
+    (float)(1.0 / 355687428096000.0), (float)(-1.0 / 121645100408832000.0)};
+__device__ constexpr float kCosSeries[10] = {
+    (float)(1.0 / 2.0), (float)(-1.0 / 24.0), (float)(1.0 / 720.0), (float)(-1.0 / 40320.0),
+    (float)(1.0 / 3628800.0), (float)(-1.0 / 479001600.0), (float)(1.0 / 87178291200.0),
+    (float)(-1.0 / 20922789888000.0), (float)(1.0 / 6402373705728000.0), (float)(-1.0 / 2432902008176640000.0)};
+
+struct Pose {
+    float R[9];
+    float t[3];
+    float Ad[3];  // diagonal of R - I, computed directly (no cancellation against 1)
+};
+
+__device__ __forceinline__ Pose pose_of(const float* __restrict__ e, float dt)
+{
+    Pose p;
+    const float kx = -__fmul_rn(__ldg(e + 3), dt), ky = -__fmul_rn(__ldg(e + 4), dt), kz = -__fmul_rn(__ldg(e + 5), dt);
+    p.t[0] = -__fmul_rn(__ldg(e + 0), dt);
+    p.t[1] = -__fmul_rn(__ldg(e + 1), dt);
+    p.t[2] = -__fmul_rn(__ldg(e + 2), dt);
+    const float kxx = __fmul_rn(kx, kx), kyy = __fmul_rn(ky, ky), kzz = __fmul_rn(kz, kz);
+    const float kxy = __fmul_rn(kx, ky), kxz = __fmul_rn(kx, kz), kyz = __fmul_rn(ky, kz);
+    const float s = __fadd_rn(__fadd_rn(kxx, kyy), kzz);
+    float a = kSinSeries[9], b = kCosSeries[9];
+#pragma unroll
+    for (int n = 8; n >= 0; --n) {
+        a = __fmaf_rn(a, s, kSinSeries[n]);
+        b = __fmaf_rn(b, s, kCosSeries[n]);
+    }
+    p.Ad[0] = __fmul_rn(b, -__fadd_rn(kyy, kzz));
+    p.Ad[1] = __fmul_rn(b, -__fadd_rn(kxx, kzz));
+    p.Ad[2] = __fmul_rn(b, -__fadd_rn(kxx, kyy));
+    p.R[0] = __fmaf_rn(b, -__fadd_rn(kyy, kzz), 1.0f);
+    p.R[1] = __fmaf_rn(b, kxy, -__fmul_rn(a, kz));
+    p.R[2] = __fmaf_rn(b, kxz, __fmul_rn(a, ky));
+    p.R[3] = __fmaf_rn(b, kxy, __fmul_rn(a, kz));
+    p.R[4] = __fmaf_rn(b, -__fadd_rn(kxx, kzz), 1.0f);
+    p.R[5] = __fmaf_rn(b, kyz, -__fmul_rn(a, kx));
+    p.R[6] = __fmaf_rn(b, kxz, -__fmul_rn(a, ky));
+    p.R[7] = __fmaf_rn(b, kyz, __fmul_rn(a, kx));
+    p.R[8] = __fmaf_rn(b, -__fadd_rn(kxx, kyy), 1.0f);
+    return p;
+}
+
+// the camera-frame point of pixel (u, v) and its normalised coordinates
+struct PixelPoint {
+    float xn, yn, Z;
+};
+
+__device__ __forceinline__ PixelPoint pixel_point(int u, int v, float rho, float fx, float fy, float cx, float cy)
+{
+    PixelPoint q;
+    q.xn = __fmul_rn(__fsub_rn((float)u, cx), __fdiv_rn(1.0f, fx));
+    q.yn = __fmul_rn(__fsub_rn((float)v, cy), __fdiv_rn(1.0f, fy));
+    q.Z = __fdiv_rn(1.0f, rho);
+    return q;
+}
+
+__device__ __forceinline__ void transform(const Pose& p, const PixelPoint& q, float X[3], float P[3])
+{
+    X[0] = __fmul_rn(q.Z, q.xn);
+    X[1] = __fmul_rn(q.Z, q.yn);
+    X[2] = q.Z;
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+        P[r] = __fmaf_rn(p.R[3 * r + 2], X[2], __fmaf_rn(p.R[3 * r + 1], X[1], __fmaf_rn(p.R[3 * r], X[0], p.t[r])));
+}
+
+// Derivative of Rodrigues' formula R(k) = I + a K + b K^2 (K = [k]x,
+// a = sin(th)/th, b = (1 - cos th)/th^2) with respect to k_c, in FP64:
+//   dR/dk_c = a E_c + b (E_c K + K E_c) + (a'/th K + b'/th K^2) k_c,  E_c = [e_c]x,
+// the ratios a'/th, b'/th from their series near th = 0.
+__device__ inline void rodrigues_grad(const double k[3], double dR[3][9])
+{
+    const double th2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+    const double th = sqrt(th2);
+    double a, b, ap, bp;
+    if (th < 1e-4) {
+        a = 1.0 - th2 / 6.0;
+        b = 0.5 - th2 / 24.0;
+        ap = -1.0 / 3.0 + th2 / 30.0;
+        bp = -1.0 / 12.0 + th2 / 180.0;
+    } else {
+        const double sn = sin(th), cs = cos(th);
+        a = sn / th;
+        b = (1.0 - cs) / th2;
+        ap = (th * cs - sn) / (th2 * th);
+        bp = (th * sn - 2.0 * (1.0 - cs)) / (th2 * th2);
+    }
+    const double K[9] = {0, -k[2], k[1], k[2], 0, -k[0], -k[1], k[0], 0};
+    double K2[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) K2[3 * i + j] = K[3 * i] * K[j] + K[3 * i + 1] * K[3 + j] + K[3 * i + 2] * K[6 + j];
+    for (int c = 0; c < 3; ++c) {
+        double E[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        if (c == 0) {
+            E[5] = -1;
+            E[7] = 1;
+        } else if (c == 1) {
+            E[2] = 1;
+            E[6] = -1;
+        } else {
+            E[1] = -1;
+            E[3] = 1;
+        }
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                double EK = 0.0, KE = 0.0;
+                for (int l = 0; l < 3; ++l) {
+                    EK += E[3 * i + l] * K[3 * l + j];
+                    KE += K[3 * i + l] * E[3 * l + j];
+                }
+                dR[c][3 * i + j] = a * E[3 * i + j] + b * (EK + KE) + (ap * K[3 * i + j] + bp * K2[3 * i + j]) * k[c];
+            }
+    }
+}
+
+// dL/d(v, w) of one pose from the sums dL/dt (s[0..2]) and dL/dR = sum dL/dP X^T
+// (s[3..11], row-major), FP64: dL/dv = -dt dL/dt, dL/dw_c = -dt sum dL/dR_ab dR_ab/dk_c
+__device__ inline void pose_grad(const double s[12], const float* e, float dtf, float* out6)
+{
+    const double dt = (double)dtf;
+    const double k[3] = {-(double)e[3] * dt, -(double)e[4] * dt, -(double)e[5] * dt};
+    double dR[3][9];
+    rodrigues_grad(k, dR);
+    for (int j = 0; j < 3; ++j) {
+        double dk = 0.0;
+        for (int m = 0; m < 9; ++m) dk += s[3 + m] * dR[j][m];
+        out6[j] = (float)(-dt * s[j]);
+        out6[3 + j] = (float)(-dt * dk);
+    }
+}
+
+}  // namespace cmk
