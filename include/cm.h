@@ -239,6 +239,30 @@ int cm_flow_eq2_backward(const cm_camera* cam, const float* inv_depth, const flo
                          float scale, const float* dflow, float* dinv_depth, float* dego6, void* scratch,
                          size_t scratch_bytes, void* stream);
 
+/* ---- geometry-consistency loss (Eq. 3) ----
+ * Between the depth of view 0 (inv_depth0) moved by the camera motion from
+ * view 0 to view 1 (ego6 = (v, w) over dt seconds, the rigid transform of
+ * cm_flow_eq2: P = R X + t) and the depth of view 1 (inv_depth1): for every
+ * pixel x of view 0 the forward-projected depth a = P2 and the depth b of
+ * view 1 bilinearly interpolated at the projection x' (corner indices
+ * clamped); valid pixels V have P2 > 0 and x' inside the closed image box;
+ *   L_geo = (1/|V|) sum_V |a - b| / (a + b)   (0 when V is empty).
+ * The total loss of Eq. 4 is L_CM + lambda L_geo (lambda = 0.05 in the paper),
+ * composed by the caller.  The projection follows the FP32 sequence of
+ * cm_flow_eq2 (x' = u + displacement), so the valid set is a fixed function
+ * of the inputs; fixed-order reductions.  All pointers are device memory.
+ * scratch: 16-byte aligned, cm_geo_scratch_query bytes; the backward reads the
+ * valid count the forward left there, so it follows a forward on the same
+ * inputs and scratch.  dinv_depth1 is overwritten (its pixels receive the
+ * bilinear adjoint, in no fixed order).  Errors: CM_EINVAL, CM_ENOMEM
+ * (scratch too small), CM_ECUDA. */
+int cm_geo_scratch_query(const cm_camera* cam, size_t* bytes);
+int cm_geo_forward(const cm_camera* cam, const float* inv_depth0, const float* inv_depth1, const float* ego6,
+                   float dt, void* scratch, size_t scratch_bytes, float* loss_out, void* stream);
+int cm_geo_backward(const cm_camera* cam, const float* inv_depth0, const float* inv_depth1, const float* ego6,
+                    float dt, const float* dloss, float* dinv_depth0, float* dinv_depth1, float* dego6, void* scratch,
+                    size_t scratch_bytes, void* stream);
+
 /* ---- batched evaluation ----
  * Loss and gradient of many windows at once (the batched training step of the
  * paper, supp. "Training": batches of 4-8 event windows on one GPU), with

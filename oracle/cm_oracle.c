@@ -242,12 +242,10 @@ void orc_flow_eq2_bins(int32_t W, int32_t H, double fx, double fy, double cx, do
  *             R00 = fma(b, -(kyy + kzz), 1)   R01 = fma(b, kxy, -(a*kz))   R02 = fma(b, kxz, a*ky)
  *             R10 = fma(b, kxy, a*kz)         R11 = fma(b, -(kxx + kzz), 1) R12 = fma(b, kyz, -(a*kx))
  *             R20 = fma(b, kxz, -(a*ky))      R21 = fma(b, kyz, a*kx)      R22 = fma(b, -(kxx + kyy), 1)
- *   per pixel: xn = (u - cx) * (1/fx), yn = (v - cy) * (1/fy), Z = 1/rho
- *             X = (Z*xn, Z*yn, Z);  P_a = fma(R_a2, X2, fma(R_a1, X1, fma(R_a0, X0, t_a)))
- *             iz = 1/P2;  d = (fx * (fma(-xn, P2, P0) * iz), fy * (fma(-yn, P2, P1) * iz))
- *             flow = (scale * d.x, scale * d.y)
- * The displacement is taken as fx (P0/P2 - xn), the same quantity as
- * fx P0/P2 + cx - u, without cancelling against the pixel coordinate.
+ *             Ad_i = b * -(...) (the diagonal of R - I, the same sums as R_ii)
+ *   per pixel: xn = (u - cx) * (1/fx), yn = (v - cy) * (1/fy), Z = 1/rho,
+ *             the displacement d of disp_f32 below; flow = (scale * d.x, scale * d.y)
+ * The displacement is fx (P0/P2 - xn), the same quantity as fx P0/P2 + cx - u.
  */
 static const double ORC_SIN_SERIES[10] = {1.0, -1.0 / 6.0, 1.0 / 120.0, -1.0 / 5040.0, 1.0 / 362880.0,
                                           -1.0 / 39916800.0, 1.0 / 6227020800.0, -1.0 / 1307674368000.0,
@@ -256,7 +254,7 @@ static const double ORC_COS_SERIES[10] = {1.0 / 2.0, -1.0 / 24.0, 1.0 / 720.0, -
                                           -1.0 / 479001600.0, 1.0 / 87178291200.0, -1.0 / 20922789888000.0,
                                           1.0 / 6402373705728000.0, -1.0 / 2432902008176640000.0};
 
-static void rot_f32(const float* e, float dt, float Rm[9], float tv[3])
+static void rot_f32(const float* e, float dt, float Rm[9], float tv[3], float Ad[3])
 {
     const float kx = -(e[3] * dt), ky = -(e[4] * dt), kz = -(e[5] * dt);
     tv[0] = -(e[0] * dt);
@@ -270,6 +268,9 @@ static void rot_f32(const float* e, float dt, float Rm[9], float tv[3])
         a = fmaf(a, s, (float)ORC_SIN_SERIES[n]);
         b = fmaf(b, s, (float)ORC_COS_SERIES[n]);
     }
+    Ad[0] = b * -(kyy + kzz);
+    Ad[1] = b * -(kxx + kzz);
+    Ad[2] = b * -(kxx + kyy);
     Rm[0] = fmaf(b, -(kyy + kzz), 1.0f);
     Rm[1] = fmaf(b, kxy, -(a * kz));
     Rm[2] = fmaf(b, kxz, a * ky);
@@ -281,27 +282,48 @@ static void rot_f32(const float* e, float dt, float Rm[9], float tv[3])
     Rm[8] = fmaf(b, -(kxx + kyy), 1.0f);
 }
 
+/* The displacement of pixel (u, v) in FP32 (the sequence of the kernels):
+ * with m = (xn, yn, 1) and A = R - I (its diagonal built directly),
+ *   c_0j = fma(-xn, A_2j, A_0j), c_1j = fma(-yn, A_2j, A_1j)      (j = 0, 1, 2)
+ *   s0 = fma(c_00, xn, fma(c_01, yn, c_02)),  s1 = fma(c_10, xn, fma(c_11, yn, c_12))
+ *   e0 = fma(Z, s0, fma(-xn, t2, t0)),        e1 = fma(Z, s1, fma(-yn, t2, t1))
+ *   P2 = fma(Z, fma(R20, xn, fma(R21, yn, R22)), t2),  iz = 1 / P2
+ *   d = (fx * (e0 * iz), fy * (e1 * iz))
+ * e0 = P0 - xn P2 taken in this form is exactly 0 for a camera at rest and
+ * never cancels two large terms. */
+static void disp_f32(const float Rm[9], const float tv[3], const float Ad[3], float xn, float yn, float Z, float fx,
+                     float fy, float* dx, float* dy, float* P2out)
+{
+    const float A00 = Ad[0], A11 = Ad[1], A22 = Ad[2];
+    const float c00 = fmaf(-xn, Rm[6], A00), c01 = fmaf(-xn, Rm[7], Rm[1]), c02 = fmaf(-xn, A22, Rm[2]);
+    const float c10 = fmaf(-yn, Rm[6], Rm[3]), c11 = fmaf(-yn, Rm[7], A11), c12 = fmaf(-yn, A22, Rm[5]);
+    const float s0 = fmaf(c00, xn, fmaf(c01, yn, c02));
+    const float s1 = fmaf(c10, xn, fmaf(c11, yn, c12));
+    const float e0 = fmaf(Z, s0, fmaf(-xn, tv[2], tv[0]));
+    const float e1 = fmaf(Z, s1, fmaf(-yn, tv[2], tv[1]));
+    const float P2 = fmaf(Z, fmaf(Rm[6], xn, fmaf(Rm[7], yn, Rm[8])), tv[2]);
+    const float iz = 1.0f / P2;
+    *dx = fx * (e0 * iz);
+    *dy = fy * (e1 * iz);
+    *P2out = P2;
+}
+
 void orc_flow_eq2_bins_f32(int32_t W, int32_t H, float fx, float fy, float cx, float cy, const float* rho,
                            const float* ego, int32_t nb, float dt_bin, float scale, float* flow)
 {
     const int64_t HW = (int64_t)W * H;
     const float ifx = 1.0f / fx, ify = 1.0f / fy;
     for (int32_t i = 0; i < nb; ++i) {
-        float Rm[9], tv[3];
-        rot_f32(ego + 6 * i, dt_bin, Rm, tv);
+        float Rm[9], tv[3], Ad[3];
+        rot_f32(ego + 6 * i, dt_bin, Rm, tv, Ad);
         for (int32_t v = 0; v < H; ++v) {
             for (int32_t u = 0; u < W; ++u) {
                 const int64_t q = (int64_t)v * W + u;
                 const float xn = ((float)u - cx) * ifx;
                 const float yn = ((float)v - cy) * ify;
                 const float Z = 1.0f / rho[q];
-                const float X0 = Z * xn, X1 = Z * yn, X2 = Z;
-                const float P0 = fmaf(Rm[2], X2, fmaf(Rm[1], X1, fmaf(Rm[0], X0, tv[0])));
-                const float P1 = fmaf(Rm[5], X2, fmaf(Rm[4], X1, fmaf(Rm[3], X0, tv[1])));
-                const float P2 = fmaf(Rm[8], X2, fmaf(Rm[7], X1, fmaf(Rm[6], X0, tv[2])));
-                const float iz = 1.0f / P2;
-                const float dx = fx * (fmaf(-xn, P2, P0) * iz);
-                const float dy = fy * (fmaf(-yn, P2, P1) * iz);
+                float dx, dy, P2;
+                disp_f32(Rm, tv, Ad, xn, yn, Z, fx, fy, &dx, &dy, &P2);
                 flow[2 * (HW * i + q) + 0] = scale * dx;
                 flow[2 * (HW * i + q) + 1] = scale * dy;
             }
@@ -432,8 +454,8 @@ void orc_flow_eq2_grad(int32_t W, int32_t H, double fx, double fy, double cx, do
 void orc_geo_proj_f32(int32_t W, int32_t H, float fx, float fy, float cx, float cy, const float* rho0,
                       const float* ego, float dt, float* proj, uint8_t* ok)
 {
-    float Rm[9], tv[3];
-    rot_f32(ego, dt, Rm, tv);
+    float Rm[9], tv[3], Ad[3];
+    rot_f32(ego, dt, Rm, tv, Ad);
     const float ifx = 1.0f / fx, ify = 1.0f / fy;
     const float W1 = (float)(W - 1), H1 = (float)(H - 1);
     for (int32_t v = 0; v < H; ++v) {
@@ -442,13 +464,10 @@ void orc_geo_proj_f32(int32_t W, int32_t H, float fx, float fy, float cx, float 
             const float xn = ((float)u - cx) * ifx;
             const float yn = ((float)v - cy) * ify;
             const float Z = 1.0f / rho0[q];
-            const float X0 = Z * xn, X1 = Z * yn, X2 = Z;
-            const float P0 = fmaf(Rm[2], X2, fmaf(Rm[1], X1, fmaf(Rm[0], X0, tv[0])));
-            const float P1 = fmaf(Rm[5], X2, fmaf(Rm[4], X1, fmaf(Rm[3], X0, tv[1])));
-            const float P2 = fmaf(Rm[8], X2, fmaf(Rm[7], X1, fmaf(Rm[6], X0, tv[2])));
-            const float iz = 1.0f / P2;
-            const float xp = (float)u + fx * (fmaf(-xn, P2, P0) * iz);
-            const float yp = (float)v + fy * (fmaf(-yn, P2, P1) * iz);
+            float dx, dy, P2;
+            disp_f32(Rm, tv, Ad, xn, yn, Z, fx, fy, &dx, &dy, &P2);
+            const float xp = (float)u + dx;
+            const float yp = (float)v + dy;
             proj[2 * q] = xp;
             proj[2 * q + 1] = yp;
             ok[q] = P2 > 0.0f && xp >= 0.0f && xp <= W1 && yp >= 0.0f && yp <= H1;

@@ -126,6 +126,9 @@ SIGNATURES = {
     "cm_launch_count": ([], ctypes.c_int64),
     "cm_flow_eq2": ([_P(cm_camera), _vp, _vp, _i32, _f32, _f32, _vp, _vp], ctypes.c_int),
     "cm_event_frame": ([_P(cm_camera), _P(cm_events), _vp, _vp], ctypes.c_int),
+    "cm_geo_scratch_query": ([_P(cm_camera), _P(_sz)], ctypes.c_int),
+    "cm_geo_forward": ([_P(cm_camera), _vp, _vp, _vp, _f32, _vp, _sz, _vp, _vp], ctypes.c_int),
+    "cm_geo_backward": ([_P(cm_camera), _vp, _vp, _vp, _f32, _vp, _vp, _vp, _vp, _vp, _sz, _vp], ctypes.c_int),
     "cm_rsat": ([_P(cm_camera), _P(cm_events), _vp, _i32, _P(cm_loss_cfg), _vp, _vp, _vp], ctypes.c_int),
     "cm_flow_eq2_scratch_query": ([_P(cm_camera), _i32, _P(_sz)], ctypes.c_int),
     "cm_flow_eq2_backward": ([_P(cm_camera), _vp, _vp, _i32, _f32, _f32, _vp, _vp, _vp, _vp, _sz, _vp],
@@ -374,3 +377,21 @@ def cm_event_frame(cam, ev, frame_out: int, stream: int) -> None:
 def cm_rsat(cam, ev, flow: int, n_flow_bins: int, cfg, ws: int, rsat_out: int, stream: int) -> None:
     _check(lib().cm_rsat(ctypes.byref(cam), ctypes.byref(ev), flow, n_flow_bins, ctypes.byref(cfg), ws, rsat_out,
                          stream), "cm_rsat")
+
+
+def cm_geo_scratch_query(cam) -> int:
+    n = _sz()
+    _check(lib().cm_geo_scratch_query(ctypes.byref(cam), ctypes.byref(n)), "cm_geo_scratch_query")
+    return n.value
+
+
+def cm_geo_forward(cam, rho0: int, rho1: int, ego6: int, dt: float, scratch: int, scratch_bytes: int, loss_out: int,
+                   stream: int) -> None:
+    _check(lib().cm_geo_forward(ctypes.byref(cam), rho0, rho1, ego6, dt, scratch, scratch_bytes, loss_out, stream),
+           "cm_geo_forward")
+
+
+def cm_geo_backward(cam, rho0: int, rho1: int, ego6: int, dt: float, dloss: int, drho0: int, drho1: int, dego6: int,
+                    scratch: int, scratch_bytes: int, stream: int) -> None:
+    _check(lib().cm_geo_backward(ctypes.byref(cam), rho0, rho1, ego6, dt, dloss, drho0, drho1, dego6, scratch,
+                                 scratch_bytes, stream), "cm_geo_backward")

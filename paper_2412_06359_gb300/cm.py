@@ -290,6 +290,45 @@ class CMLossEq2(torch.autograd.Function):
         return drho, dego.reshape(ego.shape), None, None, None, None
 
 
+LAMBDA_GEO = 0.05  # weight of the geometry-consistency term in the total loss (Eq. 4; supp. "Training")
+
+
+class GeoLoss(torch.autograd.Function):
+    """Geometry-consistency loss (Eq. 3) between two views' inverse depths
+    under the camera motion ego [6] over dt; backward to both inverse depths
+    and the motion."""
+
+    @staticmethod
+    def forward(ctx, inv_depth0, inv_depth1, ego, cam, dt: float):
+        c = camera(cam)
+        r0, r1, e = inv_depth0.contiguous(), inv_depth1.contiguous(), ego.contiguous()
+        dev = r0.device
+        scratch = torch.empty(C.cm_geo_scratch_query(c), dtype=torch.uint8, device=dev)
+        loss = torch.empty(1, dtype=torch.float32, device=dev)
+        C.cm_geo_forward(c, _require_cuda(r0, "inv_depth0", torch.float32), _require_cuda(r1, "inv_depth1",
+                         torch.float32), _require_cuda(e, "ego", torch.float32), float(dt), scratch.data_ptr(),
+                         scratch.numel(), loss.data_ptr(), stream_handle(dev))
+        ctx.save_for_backward(r0, r1, e, scratch)
+        ctx.cam, ctx.dt = c, dt
+        return loss[0]
+
+    @staticmethod
+    def backward(ctx, grad):
+        r0, r1, e, scratch = ctx.saved_tensors
+        dloss = grad.reshape(1).to(torch.float32).contiguous()
+        d0, d1 = torch.empty_like(r0), torch.empty_like(r1)
+        de = torch.empty(6, dtype=torch.float32, device=r0.device)
+        C.cm_geo_backward(ctx.cam, r0.data_ptr(), r1.data_ptr(), e.data_ptr(), float(ctx.dt), dloss.data_ptr(),
+                          d0.data_ptr(), d1.data_ptr(), de.data_ptr(), scratch.data_ptr(), scratch.numel(),
+                          stream_handle(r0.device))
+        return d0, d1, de, None, None
+
+
+def geo_loss(cam, inv_depth0, inv_depth1, ego, dt: float):
+    """Differentiable geometry-consistency loss (Eq. 3)."""
+    return GeoLoss.apply(inv_depth0, inv_depth1, ego, cam, dt)
+
+
 def cm_loss(ev: DeviceEvents, ws: Workspace, *, flow=None, inv_depth=None, ego=None, dt: float = 0.01):
     """Differentiable CM loss: pass flow, or inv_depth and ego."""
     if flow is not None:

@@ -8,9 +8,8 @@
 // displacement fx (P0/P2 - xn), fy (P1/P2 - yn) (scale = number of bins gives
 // px per window, the unit of the iterative warp).
 //
-// The FP32 operation sequence of the rotation, the transform and the
-// displacement is stated in cm_pose.cuh; the flow itself is
-//   flow = (scale * (fx * (fma(-xn, P2, P0) * iz)), scale * (fy * (fma(-yn, P2, P1) * iz))),  iz = 1/P2.
+// The FP32 operation sequence of the rotation and of the displacement d is
+// stated in cm_pose.cuh; the flow is (scale * d.x, scale * d.y).
 // The adjoint is FP32 per pixel with fixed-order FP64 final sums; the
 // derivative of Rodrigues' formula is taken in FP64 once per bin.
 #include <cmath>
@@ -45,12 +44,9 @@ __global__ void __launch_bounds__(kEq2Threads) k_flow_eq2(Eq2Args a, float2* __r
         const uint32_t v = i / (uint32_t)a.W, u = i - v * (uint32_t)a.W;
         const PixelPoint q = pixel_point((int)u, (int)v, __ldg(a.rho + i), a.fx, a.fy, a.cx, a.cy);
         for (int b = 0; b < a.nb; ++b) {
-            float X[3], P[3];
-            transform(poses[b], q, X, P);
-            const float iz = __fdiv_rn(1.0f, P[2]);
-            const float dx = __fmul_rn(a.fx, __fmul_rn(__fmaf_rn(-q.xn, P[2], P[0]), iz));
-            const float dy = __fmul_rn(a.fy, __fmul_rn(__fmaf_rn(-q.yn, P[2], P[1]), iz));
-            flow[(size_t)b * HW + i] = make_float2(__fmul_rn(a.scale, dx), __fmul_rn(a.scale, dy));
+            float P2;
+            const float2 d = displacement(poses[b], q, a.fx, a.fy, P2);
+            flow[(size_t)b * HW + i] = make_float2(__fmul_rn(a.scale, d.x), __fmul_rn(a.scale, d.y));
         }
     }
 }

@@ -18,10 +18,16 @@
 //              R00 = fma(b, -(kyy + kzz), 1)  R01 = fma(b, kxy, -(a*kz))  R02 = fma(b, kxz, a*ky)
 //              R10 = fma(b, kxy, a*kz)        R11 = fma(b, -(kxx + kzz), 1) R12 = fma(b, kyz, -(a*kx))
 //              R20 = fma(b, kxz, -(a*ky))     R21 = fma(b, kyz, a*kx)     R22 = fma(b, -(kxx + kyy), 1)
-//   per pixel: xn = (u - cx) * (1/fx), yn = (v - cy) * (1/fy), Z = 1/rho, X = (Z*xn, Z*yn, Z)
-//              P_a = fma(R_a2, X2, fma(R_a1, X1, fma(R_a0, X0, t_a))), iz = 1/P2
-//              displacement d = (fx * (fma(-xn, P2, P0) * iz), fy * (fma(-yn, P2, P1) * iz)),
-//              i.e. fx (P0/P2 - xn) without cancelling against the pixel coordinate
+//              Ad_i = b * -(...), the diagonal of A = R - I (the same sums as R_ii)
+//   per pixel: xn = (u - cx) * (1/fx), yn = (v - cy) * (1/fy), Z = 1/rho, m = (xn, yn, 1)
+//              c_0j = fma(-xn, A_2j, A_0j), c_1j = fma(-yn, A_2j, A_1j)     (j = 0, 1, 2)
+//              s0 = fma(c_00, xn, fma(c_01, yn, c_02)),  s1 = fma(c_10, xn, fma(c_11, yn, c_12))
+//              e0 = fma(Z, s0, fma(-xn, t2, t0)),        e1 = fma(Z, s1, fma(-yn, t2, t1))
+//              P2 = fma(Z, fma(R20, xn, fma(R21, yn, R22)), t2),  iz = 1/P2
+//              displacement d = (fx * (e0 * iz), fy * (e1 * iz))
+// e0 is P0 - xn P2 (P = R X + t, X = Z m), so d = fx (P0/P2 - xn), the
+// displacement of the pixel, taken in a form that is exactly 0 for a camera
+// at rest and never cancels two large terms.
 #pragma once
 
 #include <cmath>
@@ -90,6 +96,24 @@ __device__ __forceinline__ PixelPoint pixel_point(int u, int v, float rho, float
     q.yn = __fmul_rn(__fsub_rn((float)v, cy), __fdiv_rn(1.0f, fy));
     q.Z = __fdiv_rn(1.0f, rho);
     return q;
+}
+
+// the displacement of the pixel and the depth P2 of its moved point (the
+// sequence of the contract above)
+__device__ __forceinline__ float2 displacement(const Pose& p, const PixelPoint& q, float fx, float fy, float& P2)
+{
+    const float xn = q.xn, yn = q.yn;
+    const float c00 = __fmaf_rn(-xn, p.R[6], p.Ad[0]), c01 = __fmaf_rn(-xn, p.R[7], p.R[1]);
+    const float c02 = __fmaf_rn(-xn, p.Ad[2], p.R[2]);
+    const float c10 = __fmaf_rn(-yn, p.R[6], p.R[3]), c11 = __fmaf_rn(-yn, p.R[7], p.Ad[1]);
+    const float c12 = __fmaf_rn(-yn, p.Ad[2], p.R[5]);
+    const float s0 = __fmaf_rn(c00, xn, __fmaf_rn(c01, yn, c02));
+    const float s1 = __fmaf_rn(c10, xn, __fmaf_rn(c11, yn, c12));
+    const float e0 = __fmaf_rn(q.Z, s0, __fmaf_rn(-xn, p.t[2], p.t[0]));
+    const float e1 = __fmaf_rn(q.Z, s1, __fmaf_rn(-yn, p.t[2], p.t[1]));
+    P2 = __fmaf_rn(q.Z, __fmaf_rn(p.R[6], xn, __fmaf_rn(p.R[7], yn, p.R[8])), p.t[2]);
+    const float iz = __fdiv_rn(1.0f, P2);
+    return make_float2(__fmul_rn(fx, __fmul_rn(e0, iz)), __fmul_rn(fy, __fmul_rn(e1, iz)));
 }
 
 __device__ __forceinline__ void transform(const Pose& p, const PixelPoint& q, float X[3], float P[3])
