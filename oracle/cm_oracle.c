@@ -446,13 +446,18 @@ void orc_flow_eq2_grad(int32_t W, int32_t H, double fx, double fy, double cx, do
  * is the bilinear sample of D1 = 1/rho1 at x' (corner indices clamped).  Valid
  * pixels V: P2 > 0 and x' inside the closed image box.
  *   L_geo = (1 / |V|) sum_{x in V} |a - b| / (a + b)
- * The projection decides integers (valid or not, the sample's cell), so the
- * decisions are taken on the FP32 projection of the kernels (orc_geo_proj_f32)
- * and the loss in FP64 on those decisions; the gradient is that of the branch
- * the decisions select (sign(0) = 0 at a = b).
+ * The projection decides integers (valid or not, the sample's cell, the sign
+ * of a - b), so the decisions are taken in the kernels' FP32 sequence
+ * (orc_geo_proj_f32) and the loss in FP64 on those decisions; the gradient is
+ * that of the branch the decisions select (sign 0 when a = b in FP32).
  */
+/* The decisions in FP32: the projection, the valid flag, and the sign of
+ * a - b (the branch of |a - b|), with
+ *   ax = x' - floor(x'), bx = 1 - ax (likewise y), w00 = bx*by, w10 = ax*by,
+ *   w01 = bx*ay, w11 = ax*ay, D_c = 1/rho1_c,
+ *   b = fma(w11, D11, fma(w01, D01, fma(w10, D10, w00*D00))),  a = P2. */
 void orc_geo_proj_f32(int32_t W, int32_t H, float fx, float fy, float cx, float cy, const float* rho0,
-                      const float* ego, float dt, float* proj, uint8_t* ok)
+                      const float* rho1, const float* ego, float dt, float* proj, uint8_t* ok, int8_t* sgn)
 {
     float Rm[9], tv[3], Ad[3];
     rot_f32(ego, dt, Rm, tv, Ad);
@@ -471,13 +476,24 @@ void orc_geo_proj_f32(int32_t W, int32_t H, float fx, float fy, float cx, float 
             proj[2 * q] = xp;
             proj[2 * q + 1] = yp;
             ok[q] = P2 > 0.0f && xp >= 0.0f && xp <= W1 && yp >= 0.0f && yp <= H1;
+            sgn[q] = 0;
+            if (!ok[q]) continue;
+            const float fx0 = floorf(xp), fy0 = floorf(yp);
+            const int ix = (int)fx0, iy = (int)fy0;
+            const int ix1 = ix + 1 < W ? ix + 1 : W - 1, iy1 = iy + 1 < H ? iy + 1 : H - 1;
+            const float ax = xp - fx0, ay = yp - fy0, bx = 1.0f - ax, by = 1.0f - ay;
+            const float w00 = bx * by, w10 = ax * by, w01 = bx * ay, w11 = ax * ay;
+            const float D00 = 1.0f / rho1[(int64_t)iy * W + ix], D10 = 1.0f / rho1[(int64_t)iy * W + ix1];
+            const float D01 = 1.0f / rho1[(int64_t)iy1 * W + ix], D11 = 1.0f / rho1[(int64_t)iy1 * W + ix1];
+            const float b = fmaf(w11, D11, fmaf(w01, D01, fmaf(w10, D10, w00 * D00)));
+            sgn[q] = P2 > b ? 1 : (P2 < b ? -1 : 0);
         }
     }
 }
 
 double orc_geo(int32_t W, int32_t H, double fx, double fy, double cx, double cy, const double* rho0,
-               const double* rho1, const double* ego, double dt, const float* proj, const uint8_t* ok, double dloss,
-               int64_t* count, double* drho0, double* drho1, double* dego)
+               const double* rho1, const double* ego, double dt, const float* proj, const uint8_t* ok,
+               const int8_t* sgn, double dloss, int64_t* count, double* drho0, double* drho1, double* dego)
 {
     const int64_t HW = (int64_t)W * H;
     const double k[3] = {-ego[3] * dt, -ego[4] * dt, -ego[5] * dt};
@@ -512,9 +528,9 @@ double orc_geo(int32_t W, int32_t H, double fx, double fy, double cx, double cy,
             const double w00 = (1 - ax) * (1 - ay), w10 = ax * (1 - ay), w01 = (1 - ax) * ay, w11 = ax * ay;
             const double a = P[2];
             const double b = w00 * D00 + w10 * D10 + w01 * D01 + w11 * D11;
-            sum += fabs(a - b) / (a + b);
+            const double sg = (double)sgn[q]; /* the branch of |a - b| decided in FP32 */
+            sum += (sg != 0.0 ? sg * (a - b) : fabs(a - b)) / (a + b);
             if (!drho0) continue;
-            const double sg = a > b ? 1.0 : (a < b ? -1.0 : 0.0);
             const double dfa = g * sg * 2.0 * b / ((a + b) * (a + b));
             const double dfb = -g * sg * 2.0 * a / ((a + b) * (a + b));
             const double dbx = (1 - ay) * (D10 - D00) + ay * (D11 - D01);

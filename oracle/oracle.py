@@ -67,8 +67,8 @@ def lib():
             l.orc_flow_eq2_bins_f32.argtypes = [i, i, f, f, f, f, vp, vp, i, f, f, vp]
             l.orc_flow_eq2_grad.argtypes = [i, i, d, d, d, d, vp, vp, i, d, d, vp, vp, vp]
             l.orc_event_frame.argtypes = [i, i, ctypes.c_int64, vp, vp, vp, vp]
-            l.orc_geo_proj_f32.argtypes = [i, i, f, f, f, f, vp, vp, f, vp, vp]
-            l.orc_geo.argtypes = [i, i, d, d, d, d, vp, vp, vp, d, vp, vp, d, vp, vp, vp, vp]
+            l.orc_geo_proj_f32.argtypes = [i, i, f, f, f, f, vp, vp, vp, f, vp, vp, vp]
+            l.orc_geo.argtypes = [i, i, d, d, d, d, vp, vp, vp, d, vp, vp, vp, d, vp, vp, vp, vp]
             l.orc_geo.restype = d
             l.orc_cm.argtypes = [ctypes.POINTER(_Args)]
             l.orc_cm.restype = ctypes.c_int
@@ -156,28 +156,29 @@ def flow_eq2_grad(cam, inv_depth, ego, dt_bin, scale, dflow):
     return drho, dego
 
 
-def geo_proj_f32(cam, inv_depth0, ego, dt):
-    """FP32 projection of every pixel of view 0 into view 1 with the kernels'
-    operation sequence: positions [H, W, 2] and valid flags [H, W] (the
-    decisions of the geometry-consistency loss)."""
-    rho = _c(inv_depth0, np.float32)
+def geo_proj_f32(cam, inv_depth0, inv_depth1, ego, dt):
+    """The decisions of the geometry-consistency loss in the kernels' FP32
+    sequence: the projection of every pixel of view 0 into view 1 [H, W, 2],
+    the valid flags [H, W] and the sign of a - b [H, W]."""
+    r0, r1 = _c(inv_depth0, np.float32), _c(inv_depth1, np.float32)
     e = _c(ego, np.float32)
     proj = np.empty((cam.height, cam.width, 2), np.float32)
     ok = np.empty((cam.height, cam.width), np.uint8)
-    lib().orc_geo_proj_f32(cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy, _p(rho), _p(e), float(dt),
-                           _p(proj), _p(ok))
-    return proj, ok
+    sgn = np.empty((cam.height, cam.width), np.int8)
+    lib().orc_geo_proj_f32(cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy, _p(r0), _p(r1), _p(e), float(dt),
+                           _p(proj), _p(ok), _p(sgn))
+    return proj, ok, sgn
 
 
 def geo(cam, inv_depth0, inv_depth1, ego, dt, *, decisions=None, grad=False, dloss=1.0):
     """Geometry-consistency loss (Eq. 3) between the depth of view 0 moved by
     the camera motion (v, w) over dt and the depth of view 1, FP64 on the
-    decisions of the FP32 projection (computed here unless given as
-    (proj, ok)).  Returns loss, count (valid pixels) and, with grad, dL/d
-    inv_depth0 [H, W], dL/d inv_depth1 [H, W], dL/d ego [6] for dloss."""
+    FP32 decisions (computed here unless given).  Returns loss, count (valid pixels) and, with grad, dL/d
+    inv_depth0 [H, W], dL/d inv_depth1 [H, W], dL/d ego [6] for dloss.
+    decisions: (proj, ok, sign) of geo_proj_f32."""
     if decisions is None:
-        decisions = geo_proj_f32(cam, inv_depth0, ego, dt)
-    proj, ok = decisions
+        decisions = geo_proj_f32(cam, inv_depth0, inv_depth1, ego, dt)
+    proj, ok, sgn = decisions
     r0, r1 = _c(inv_depth0, np.float64), _c(inv_depth1, np.float64)
     e = _c(ego, np.float64)
     cnt = ctypes.c_int64()
@@ -190,7 +191,8 @@ def geo(cam, inv_depth0, inv_depth1, ego, dt, *, decisions=None, grad=False, dlo
     else:
         g0 = g1 = ge = None
     out["loss"] = lib().orc_geo(cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy, _p(r0), _p(r1), _p(e),
-                                float(dt), _p(_c(proj, np.float32)), _p(_c(ok, np.uint8)), float(dloss),
+                                float(dt), _p(_c(proj, np.float32)), _p(_c(ok, np.uint8)), _p(_c(sgn, np.int8)),
+                                float(dloss),
                                 ctypes.byref(cnt), g0, g1, ge)
     out["count"] = cnt.value
     return out

@@ -8,9 +8,10 @@
 // 1/rho1 at x' (corner indices clamped).  Valid pixels: P2 > 0 and x' inside
 // the closed image box.  L_geo = (1/|V|) sum_V |a - b| / (a + b).
 // The projection and the valid flags follow the FP32 sequence of
-// cm_pose.cuh (x' = u + d.x, y' = v + d.y, correctly rounded), so the valid
-// set and the sample cells are fixed functions of the inputs; sums are
-// fixed-order (per-tile partials, FP64 final).
+// cm_pose.cuh (x' = u + d.x, y' = v + d.y, correctly rounded), and b and the
+// sign of a - b a fixed FP32 sequence too (geo_pixel), so the valid set, the
+// sample cells and the branch of |a - b| are fixed functions of the inputs;
+// sums are fixed-order (per-tile partials, FP64 final).
 #include <cmath>
 #include <cstdint>
 
@@ -57,7 +58,7 @@ GeoScratch geo_scratch(void* base, int tiles)
 struct GeoPixel {
     bool valid;
     int ix, iy, ix1, iy1;
-    float ax, ay, a, b;
+    float ax, ay, a, b, sg;
     float D00, D10, D01, D11;
 };
 
@@ -74,15 +75,20 @@ __device__ __forceinline__ GeoPixel geo_pixel(const GeoArgs& g, const Pose& p, c
     r.iy = (int)fy0;
     r.ix1 = min(r.ix + 1, g.W - 1);
     r.iy1 = min(r.iy + 1, g.H - 1);
-    r.ax = xp - fx0;
-    r.ay = yp - fy0;
-    r.D00 = 1.0f / __ldg(g.rho1 + (size_t)r.iy * g.W + r.ix);
-    r.D10 = 1.0f / __ldg(g.rho1 + (size_t)r.iy * g.W + r.ix1);
-    r.D01 = 1.0f / __ldg(g.rho1 + (size_t)r.iy1 * g.W + r.ix);
-    r.D11 = 1.0f / __ldg(g.rho1 + (size_t)r.iy1 * g.W + r.ix1);
-    const float bx = 1.0f - r.ax, by = 1.0f - r.ay;
-    r.b = bx * by * r.D00 + r.ax * by * r.D10 + bx * r.ay * r.D01 + r.ax * r.ay * r.D11;
+    // b and the sign of a - b in a fixed FP32 sequence (the sign is the
+    // branch of |a - b|, decided the same way by the CPU oracle)
+    r.ax = __fsub_rn(xp, fx0);
+    r.ay = __fsub_rn(yp, fy0);
+    r.D00 = __fdiv_rn(1.0f, __ldg(g.rho1 + (size_t)r.iy * g.W + r.ix));
+    r.D10 = __fdiv_rn(1.0f, __ldg(g.rho1 + (size_t)r.iy * g.W + r.ix1));
+    r.D01 = __fdiv_rn(1.0f, __ldg(g.rho1 + (size_t)r.iy1 * g.W + r.ix));
+    r.D11 = __fdiv_rn(1.0f, __ldg(g.rho1 + (size_t)r.iy1 * g.W + r.ix1));
+    const float bx = __fsub_rn(1.0f, r.ax), by = __fsub_rn(1.0f, r.ay);
+    const float w00 = __fmul_rn(bx, by), w10 = __fmul_rn(r.ax, by), w01 = __fmul_rn(bx, r.ay);
+    const float w11 = __fmul_rn(r.ax, r.ay);
+    r.b = __fmaf_rn(w11, r.D11, __fmaf_rn(w01, r.D01, __fmaf_rn(w10, r.D10, __fmul_rn(w00, r.D00))));
     r.a = P2;
+    r.sg = r.a > r.b ? 1.0f : (r.a < r.b ? -1.0f : 0.0f);
     return r;
 }
 
@@ -111,7 +117,7 @@ __global__ void __launch_bounds__(kGeoThreads) k_geo_forward(GeoArgs g, float* _
             pixel_uv32(i, g.W, u, v);
             const GeoPixel r = geo_pixel(g, pose, pixel_point(u, v, __ldg(g.rho0 + i), g.fx, g.fy, g.cx, g.cy), u, v);
             if (!r.valid) continue;
-            sum += fabsf(r.a - r.b) / (r.a + r.b);
+            sum += r.sg * (r.a - r.b) / (r.a + r.b);
             cnt += 1.0f;
         }
         sum = warp_sum(sum);
@@ -179,8 +185,7 @@ __global__ void __launch_bounds__(kGeoThreads) k_geo_backward(GeoArgs g, const f
                 continue;
             }
             const float a = r.a, b = r.b, s2 = (a + b) * (a + b);
-            const float sg = a > b ? 1.0f : (a < b ? -1.0f : 0.0f);
-            const float dfa = gl * sg * 2.0f * b / s2, dfb = -gl * sg * 2.0f * a / s2;
+            const float dfa = gl * r.sg * 2.0f * b / s2, dfb = -gl * r.sg * 2.0f * a / s2;
             const float dbx = (1.0f - r.ay) * (r.D10 - r.D00) + r.ay * (r.D11 - r.D01);
             const float dby = (1.0f - r.ax) * (r.D01 - r.D00) + r.ax * (r.D11 - r.D10);
             float X[3], P[3];

@@ -45,7 +45,7 @@ def test_pan_over_a_plane():
     rho = np.full((cam.height, cam.width), 1 / Z0)
     ego = np.array([0, 0, 0, 0, wy, 0])
     r = O.geo(cam, rho, rho, ego, dt)
-    proj, ok = O.geo_proj_f32(cam, rho, ego, dt)
+    proj, ok, _ = O.geo_proj_f32(cam, rho, rho, ego, dt)
     th = -wy * dt
     v, u = np.mgrid[0:cam.height, 0:cam.width]
     xn = (u - cam.cx) / cam.fx
@@ -66,7 +66,7 @@ def test_gradient_matches_central_differences_on_frozen_decisions():
     r1 = r0 * rng.uniform(0.8, 1.2, r0.shape)
     e = np.array([0.3, -0.2, 0.8, 0.4, -0.6, 0.2])
     dt = 0.05
-    dec = O.geo_proj_f32(cam, r0, e, dt)
+    dec = O.geo_proj_f32(cam, r0, r1, e, dt)
     assert 0 < dec[1].sum() < r0.size  # some pixels leave the image
     g = O.geo(cam, r0, r1, e, dt, decisions=dec, grad=True, dloss=1.7)
     for name, x in (("dinv_depth0", r0), ("dinv_depth1", r1)):
