@@ -437,10 +437,10 @@ def run_ours(args):
     if not args.no_plain:
         splat_cmp = compare_splats(batch, min(4, len(wins)))
 
-    # ---- the discrete flow of Eq. 2 and its adjoint (per-pixel streams) ----
-    eq2 = None
+    # ---- the kernels beside the CM path (discrete flow, geometry loss, event frame) ----
+    others = None
     if rank == 0 and not args.no_plain:
-        eq2 = measure_eq2(dev, peak)
+        others = measure_other_kernels(dev, peak)
 
     # ---- end to end through the public API with host buffers ----
     e2e = None
@@ -468,7 +468,7 @@ def run_ours(args):
                        "l2": "per-step IWE working set %.2f GB > L2 (no flush needed)" % (len(wins) * R * hw * 16 / 1e9)},
             "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
             "plain": plain, "splat_compare": splat_cmp, "roofline": roof, "roofline_iwe": roof_iwe,
-            "roofline_l2": roof_l2, "eq2": eq2, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline_l2": roof_l2, "other_kernels": others, "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clocks, "gpu_launches": int(launches),
             "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])},
         }
@@ -477,49 +477,80 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def measure_eq2(device, peak: float, reps: int = 10):
-    """The discrete flow (Eq. 2, one pose per bin) and its adjoint on a
-    1280x720 sensor with 20 bins: device time per call (the library's CUDA
-    events around its kernels) and achieved bandwidth against the measured HBM
-    peak (the flows, 147 MB, exceed L2)."""
+def measure_other_kernels(device, peak: float, reps: int = 10):
+    """The kernels beside the CM path on a 1280x720 sensor: the discrete flow
+    (Eq. 2, 20 bins) and its adjoint, the geometry-consistency loss (Eq. 3)
+    and its gradient, and the network's event frame of 2M events.  Device time
+    per call from the library's CUDA events around its own kernels; between
+    calls a 256 MB buffer is written so that no call finds its inputs in L2.
+    Achieved bandwidth is over the algorithmic bytes against the measured HBM
+    peak."""
     import torch
+    from paper_2412_06359_gb300 import _capi as C
     from paper_2412_06359_gb300 import cm, synth
     W, H, nb = 1280, 720, 20
+    hw = W * H
     cam = synth.camera_for(W, H)
     rng = synth.rng_for(4)
     rho = torch.from_numpy(synth.inv_depth_map(rng, W, H)).to(device)
+    rho1 = rho * 1.02
     ego = torch.from_numpy(np.stack([synth.ego_motion(rng) for _ in range(nb)]).astype(np.float32)).to(device)
     dt, scale = 0.01 / nb, float(nb)
     g = torch.randn(nb, H, W, 2, device=device)
-
-    from paper_2412_06359_gb300 import _capi as C
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
+    ev = cm.DeviceEvents.from_host(synth.uniform_events(rng, W, H, 2_000_000), device)
 
     def timed(fn):
-        # device time of the library's own kernels (CUDA events around each
-        # launch on its stream), so host-side call overhead is not counted
         for _ in range(3):
             fn()
         torch.cuda.synchronize(device)
         C.cm_profile_reset()
-        C.cm_profile_enable(True)
         for _ in range(reps):
+            flush.fill_(1)
+            C.cm_profile_enable(True)
             fn()
+            C.cm_profile_enable(False)
         torch.cuda.synchronize(device)
-        C.cm_profile_enable(False)
         prof = C.cm_profile_collect()
         return sum(v[1] for v in prof.values()) / reps
 
-    f_ms = timed(lambda: cm.flow_eq2(cam, rho, ego, dt, scale))
-    b_ms = timed(lambda: cm.flow_eq2_backward(cam, rho, ego, dt, scale, g))
-    hw = W * H
-    f_bytes = 4.0 * hw + nb * 8.0 * hw
-    b_bytes = 4.0 * hw + nb * 8.0 * hw + 4.0 * hw
-    fg, bg = f_bytes / (f_ms * 1e-3) / 1e9, b_bytes / (b_ms * 1e-3) / 1e9
-    return {"workload": "eq2_1280x720_b20", "bins": nb, "flow_ms": f_ms, "flow_gbs": fg, "flow_frac": fg / peak,
-            "backward_ms": b_ms, "backward_gbs": bg, "backward_frac": bg / peak,
-            "bytes": {"flow": f_bytes, "backward": b_bytes}, "unit": "GB/s", "peak": peak,
-            "note": "algorithmic bytes: inverse depth read, per-bin flows written (flow); inverse depth and "
-                    "per-bin dL/dflow read, dL/d inverse depth written (backward)"}
+    def entry(ms, nbytes, unit_count, unit):
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        return {"ms": ms, "bytes": nbytes, "gbs": gbs, "frac": gbs / peak, "per_s": unit_count / (ms * 1e-3),
+                "unit": unit}
+
+    e0 = ego[0].contiguous()
+    scratch = torch.empty(C.cm_geo_scratch_query(cm.camera(cam)), dtype=torch.uint8, device=device)
+    loss = torch.empty(1, device=device)
+    ones = torch.ones(1, device=device)
+    d0, d1, de = torch.empty_like(rho), torch.empty_like(rho), torch.empty(6, device=device)
+    c = cm.camera(cam)
+
+    def geo_f():
+        C.cm_geo_forward(c, rho.data_ptr(), rho1.data_ptr(), e0.data_ptr(), 0.01, scratch.data_ptr(), scratch.numel(),
+                         loss.data_ptr(), cm.stream_handle(device))
+
+    def geo_b():
+        C.cm_geo_backward(c, rho.data_ptr(), rho1.data_ptr(), e0.data_ptr(), 0.01, ones.data_ptr(), d0.data_ptr(),
+                          d1.data_ptr(), de.data_ptr(), scratch.data_ptr(), scratch.numel(), cm.stream_handle(device))
+
+    geo_f()
+    out = {
+        "sensor": "1280x720", "peak_gbs": peak,
+        "flow_eq2_b20": entry(timed(lambda: cm.flow_eq2(cam, rho, ego, dt, scale)), 4.0 * hw + nb * 8.0 * hw, hw,
+                              "pixels"),
+        "flow_eq2_backward_b20": entry(timed(lambda: cm.flow_eq2_backward(cam, rho, ego, dt, scale, g)),
+                                       8.0 * hw + nb * 8.0 * hw, hw, "pixels"),
+        "geo_forward": entry(timed(geo_f), 8.0 * hw, hw, "pixels"),
+        "geo_backward": entry(timed(geo_b), 16.0 * hw, hw, "pixels"),
+        "event_frame_2M": entry(timed(lambda: cm.event_frame(cam, ev)), 5.0 * ev.n + 8.0 * hw, ev.n, "events"),
+        "bytes_note": "algorithmic: inverse depth read and per-bin flows written (Eq. 2 flow); inverse depth and "
+                      "per-bin dL/dflow read, dL/d inverse depth written (its adjoint); both inverse depths read "
+                      "(geometry forward), and their gradients written (backward); 5 B per event read and the "
+                      "2-channel frame written (event frame)",
+    }
+    del flush
+    return out
 
 
 def compare_splats(batch, nwin: int):
