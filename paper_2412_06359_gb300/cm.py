@@ -358,10 +358,26 @@ class BatchPlan:
         self.handle = C.cm_batch_create(self.ptr, self.nbytes, self.structs, cfg)
 
     def _structs(self, windows):
+        # every output lives in one float32 arena (self.output_arena), in window
+        # order, so that a caller can fetch all of them with one copy
+        sizes = []
+        for w in windows:
+            cam = camera(w["cam"])
+            hw = cam.width * cam.height
+            if w.get("flow") is not None:
+                sizes.append([("dflow", (cam.height, cam.width, 2))])
+            else:
+                e = [("dinv_depth", (cam.height, cam.width)), ("dego", (6,))]
+                if self.want_dflow:
+                    e.append(("dflow", (cam.height, cam.width, 2)))
+                sizes.append(e)
+        total = sum(((int(np.prod(shape)) + 63) // 64) * 64 for e in sizes for _, shape in e)
+        self.output_arena = torch.empty(max(total, 1), dtype=torch.float32, device=self.device)
         out = []
         self.outputs = []
         self.keep = [windows]
-        for i, w in enumerate(windows):
+        off = 0
+        for i, (w, e) in enumerate(zip(windows, sizes)):
             cam = camera(w["cam"])
             s = C.cm_window()
             s.cam = cam
@@ -369,20 +385,20 @@ class BatchPlan:
             s.dloss = self.dloss.data_ptr() + 4 * i
             s.loss_out = self.loss.data_ptr() + 4 * i
             o = {}
+            for name, shape in e:
+                n = int(np.prod(shape))
+                o[name] = self.output_arena[off:off + n].view(shape)
+                off += (n + 63) // 64 * 64
             if w.get("flow") is not None:
                 s.flow = _require_cuda(w["flow"], "flow", torch.float32)
-                o["dflow"] = torch.empty_like(w["flow"])
                 s.dflow = o["dflow"].data_ptr()
             else:
                 s.inv_depth = _require_cuda(w["inv_depth"], "inv_depth", torch.float32)
                 s.ego6 = _require_cuda(w["ego"], "ego", torch.float32)
                 s.dt_window = float(w.get("dt", 0.01))
-                o["dinv_depth"] = torch.empty_like(w["inv_depth"])
-                o["dego"] = torch.empty(6, dtype=torch.float32, device=self.device)
                 s.dinv_depth = o["dinv_depth"].data_ptr()
                 s.dego6 = o["dego"].data_ptr()
                 if self.want_dflow:
-                    o["dflow"] = torch.empty((cam.height, cam.width, 2), dtype=torch.float32, device=self.device)
                     s.dflow = o["dflow"].data_ptr()
             self.outputs.append(o)
             out.append(s)
