@@ -627,9 +627,9 @@ __device__ __forceinline__ float2 push_back(const Win& d, const Sink& sink, int 
 }
 
 // S6: per-event adjoint.  The trajectory is recomputed (or read back when the
-// splat stored it); the position adjoint of each reference point is gathered
-// from the loss-transformed IWE, and the adjoint is carried back along both
-// chains of pushes, scattering dL/dflow.
+// splat stored it); the position adjoint of each reference point comes from
+// the (C, S) pairs gathered at its corners (phi_of), and the adjoint is
+// carried back along both chains of pushes, scattering dL/dflow.
 template <int MAXB, class Sink = RedSink, bool SPLIT = false, class TrajT = Traj<MAXB>>
 __device__ __forceinline__ void adjoint_event(const Win& d, int64_t k, float dl, const Sink& sink = Sink())
 {
