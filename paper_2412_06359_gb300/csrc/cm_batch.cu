@@ -258,12 +258,12 @@ __global__ void __launch_bounds__(kEventThreads) k_splat_batch(const BatchHdr* h
         Win d = tab[w];
         use_grouped(d);
         const long long k = (c - cstart[w]) * kEventThreads + threadIdx.x;
-        if (k < d.n) splat_event<MAXB, RedSink, TrajShared<MAXB>>(d, k);  // trajectory points in shared memory
+        if (k < d.n) splat_event<MAXB>(d, k);
     }
 }
 
 template <int MAXB>
-__global__ void __launch_bounds__(kEventThreads, MAXB <= 10 ? 4 : 2) k_adjoint_batch(const BatchHdr* h, const Win* tab,
+__global__ void __launch_bounds__(kEventThreads, MAXB <= 10 ? 3 : 2) k_adjoint_batch(const BatchHdr* h, const Win* tab,
                                                                   const long long* cstart, int w0, int w1)
 {
     w1 = clamp_end(h, w1);
@@ -274,8 +274,7 @@ __global__ void __launch_bounds__(kEventThreads, MAXB <= 10 ? 4 : 2) k_adjoint_b
         Win d = tab[w];
         use_grouped(d);
         const long long k = (c - cstart[w]) * kEventThreads + threadIdx.x;
-        // polarity-plane images; trajectory points in shared memory
-        if (k < d.n) adjoint_event<MAXB, RedSink, true, TrajShared<MAXB>>(d, k, __ldg(d.dloss));
+        if (k < d.n) adjoint_event<MAXB, RedSink, true>(d, k, __ldg(d.dloss));  // polarity-plane images
     }
 }
 
@@ -744,10 +743,9 @@ void enqueue_event_kernel(cm_batch* b, cudaStream_t s, int which, int grid, int 
     const Win* tab = reinterpret_cast<const Win*>(b->base + b->L.tab);
     const long long* cs = reinterpret_cast<const long long*>(b->base + b->L.cstart);
     if (which == 0)
-        cmk::k_splat_batch<MAXB><<<grid, cmk::kEventThreads, cmk::TrajShared<MAXB>::kBytes, s>>>(h, tab, cs, w0, w1);
+        cmk::k_splat_batch<MAXB><<<grid, cmk::kEventThreads, 0, s>>>(h, tab, cs, w0, w1);
     else
-        cmk::k_adjoint_batch<MAXB><<<grid, cmk::kEventThreads, cmk::TrajShared<MAXB>::kBytes, s>>>(h, tab, cs, w0,
-                                                                                                   w1);
+        cmk::k_adjoint_batch<MAXB><<<grid, cmk::kEventThreads, 0, s>>>(h, tab, cs, w0, w1);
 }
 
 void enqueue_event(cm_batch* b, cudaStream_t s, int which, int grid, int w0, int w1)
@@ -885,11 +883,8 @@ template <int MAXB>
 int occupancy_blocks()
 {
     int a = 0, c = 0;
-    const size_t smem = cmk::TrajShared<MAXB>::kBytes;
-    cudaFuncSetAttribute(cmk::k_splat_batch<MAXB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(cmk::k_adjoint_batch<MAXB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, cmk::k_splat_batch<MAXB>, cmk::kEventThreads, smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, cmk::k_adjoint_batch<MAXB>, cmk::kEventThreads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, cmk::k_splat_batch<MAXB>, cmk::kEventThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, cmk::k_adjoint_batch<MAXB>, cmk::kEventThreads, 0);
     const int m = a < c ? a : c;
     return m < 1 ? 1 : m;
 }

@@ -195,37 +195,14 @@ __device__ __forceinline__ float2 interp(const Bil& s, const Quad& q)
     return make_float2(ux, uy);
 }
 
-// Trajectory points at the computed edges, in registers (indices are
-// compile-time after unrolling).
+// Trajectory points at the computed edges (registers; indices are compile-time
+// after unrolling).
 template <int MAXB>
 struct Traj {
-    float x_[MAXB + 1];
-    float y_[MAXB + 1];
+    float x[MAXB + 1];
+    float y[MAXB + 1];
     float ex, ey;  // the point at the window end (edge B), kept in scalars so that
                    // selecting it never needs a run-time array index
-    __device__ __forceinline__ float& x(int j) { return x_[j]; }
-    __device__ __forceinline__ float& y(int j) { return y_[j]; }
-    __device__ __forceinline__ float x(int j) const { return x_[j]; }
-    __device__ __forceinline__ float y(int j) const { return y_[j]; }
-};
-
-// The same points in the block's dynamic shared memory (2 (MAXB+1) floats per
-// thread, stride blockDim.x, conflict-free): frees the registers the points
-// would hold, so that more warps fit on an SM.  The kernel launches with
-// TrajShared<MAXB>::kBytes of dynamic shared memory per kEventThreads-thread block.
-extern __shared__ float cm_traj_smem[];
-
-template <int MAXB>
-struct TrajShared {
-    static constexpr size_t kBytes = 2 * (MAXB + 1) * kEventThreads * sizeof(float);
-    float ex, ey;
-    __device__ __forceinline__ float& x(int j) { return cm_traj_smem[j * kEventThreads + threadIdx.x]; }
-    __device__ __forceinline__ float& y(int j) { return cm_traj_smem[(MAXB + 1 + j) * kEventThreads + threadIdx.x]; }
-    __device__ __forceinline__ float x(int j) const { return cm_traj_smem[j * kEventThreads + threadIdx.x]; }
-    __device__ __forceinline__ float y(int j) const
-    {
-        return cm_traj_smem[(MAXB + 1 + j) * kEventThreads + threadIdx.x];
-    }
 };
 
 // Per-event quantities shared by the forward and backward kernels.
@@ -277,8 +254,8 @@ __device__ __forceinline__ float2 flow_at_pixel(const Win& d, int j, int x, int 
 // S2 + S3: the trajectory of one event through all computed edges (forward
 // chain b+1..B; with all edges as references also the backward chain b..0)
 // and the global mask.  Returns false when any computed point leaves the image.
-template <int MAXB, class TrajT>
-__device__ __forceinline__ bool trajectory(const Win& d, const EventAt& e, TrajT& P)
+template <int MAXB>
+__device__ __forceinline__ bool trajectory(const Win& d, const EventAt& e, Traj<MAXB>& P)
 {
     const int W = d.W, H = d.H, B = d.B, b = e.b;
     const float W1 = (float)(W - 1), H1 = (float)(H - 1);
@@ -291,20 +268,20 @@ __device__ __forceinline__ bool trajectory(const Win& d, const EventAt& e, TrajT
     for (int j = 1; j <= MAXB; ++j) {
         if (j <= B && j > b) {
             if (j == b + 1) {
-                P.x(j) = __fmaf_rn(dtf, u0.x, fxk);
-                P.y(j) = __fmaf_rn(dtf, u0.y, fyk);
+                P.x[j] = __fmaf_rn(dtf, u0.x, fxk);
+                P.y[j] = __fmaf_rn(dtf, u0.y, fyk);
             } else if (ok) {
-                const Bil s = bil(P.x(j - 1), P.y(j - 1));
+                const Bil s = bil(P.x[j - 1], P.y[j - 1]);
                 const float2 u = interp(s, quad_at(d, j - 1, s));
-                P.x(j) = __fmaf_rn(h, u.x, P.x(j - 1));
-                P.y(j) = __fmaf_rn(h, u.y, P.y(j - 1));
+                P.x[j] = __fmaf_rn(h, u.x, P.x[j - 1]);
+                P.y[j] = __fmaf_rn(h, u.y, P.y[j - 1]);
             } else {
-                P.x(j) = P.x(j - 1);
-                P.y(j) = P.y(j - 1);
+                P.x[j] = P.x[j - 1];
+                P.y[j] = P.y[j - 1];
             }
-            ok = ok && inside(P.x(j), P.y(j), W1, H1);
-            P.ex = P.x(j);
-            P.ey = P.y(j);
+            ok = ok && inside(P.x[j], P.y[j], W1, H1);
+            P.ex = P.x[j];
+            P.ey = P.y[j];
         }
     }
     if (d.ref_mode == kRefAll) {
@@ -313,18 +290,18 @@ __device__ __forceinline__ bool trajectory(const Win& d, const EventAt& e, TrajT
         for (int j = MAXB - 1; j >= 0; --j) {
             if (j <= b) {
                 if (j == b) {
-                    P.x(j) = __fmaf_rn(-dtb, u0.x, fxk);
-                    P.y(j) = __fmaf_rn(-dtb, u0.y, fyk);
+                    P.x[j] = __fmaf_rn(-dtb, u0.x, fxk);
+                    P.y[j] = __fmaf_rn(-dtb, u0.y, fyk);
                 } else if (ok) {
-                    const Bil s = bil(P.x(j + 1), P.y(j + 1));
+                    const Bil s = bil(P.x[j + 1], P.y[j + 1]);
                     const float2 u = interp(s, quad_at(d, j, s));
-                    P.x(j) = __fmaf_rn(-h, u.x, P.x(j + 1));
-                    P.y(j) = __fmaf_rn(-h, u.y, P.y(j + 1));
+                    P.x[j] = __fmaf_rn(-h, u.x, P.x[j + 1]);
+                    P.y[j] = __fmaf_rn(-h, u.y, P.y[j + 1]);
                 } else {
-                    P.x(j) = P.x(j + 1);
-                    P.y(j) = P.y(j + 1);
+                    P.x[j] = P.x[j + 1];
+                    P.y[j] = P.y[j + 1];
                 }
-                ok = ok && inside(P.x(j), P.y(j), W1, H1);
+                ok = ok && inside(P.x[j], P.y[j], W1, H1);
             }
         }
     }
@@ -489,16 +466,16 @@ __device__ __forceinline__ bool computed_edge(const Win& d, int j, int b)
 // of recomputing the trajectory, and takes the mask from them (a point outside
 // the image stays outside in every later point of its chain, so the test over
 // all stored points repeats the decision of the trajectory exactly).
-template <int MAXB, class TrajT>
-__device__ __forceinline__ void store_traj(const Win& d, const EventAt& e, const TrajT& P, int64_t k)
+template <int MAXB>
+__device__ __forceinline__ void store_traj(const Win& d, const EventAt& e, const Traj<MAXB>& P, int64_t k)
 {
 #pragma unroll
     for (int j = 0; j <= MAXB; ++j)
-        if (computed_edge(d, j, e.b)) d.warp[(size_t)j * d.n + k] = make_float2(P.x(j), P.y(j));
+        if (computed_edge(d, j, e.b)) d.warp[(size_t)j * d.n + k] = make_float2(P.x[j], P.y[j]);
 }
 
-template <int MAXB, class TrajT>
-__device__ __forceinline__ bool load_traj(const Win& d, const EventAt& e, TrajT& P, int64_t k)
+template <int MAXB>
+__device__ __forceinline__ bool load_traj(const Win& d, const EventAt& e, Traj<MAXB>& P, int64_t k)
 {
     const float W1 = (float)(d.W - 1), H1 = (float)(d.H - 1);
     bool ok = true;
@@ -506,8 +483,8 @@ __device__ __forceinline__ bool load_traj(const Win& d, const EventAt& e, TrajT&
     for (int j = 0; j <= MAXB; ++j) {
         if (computed_edge(d, j, e.b)) {
             const float2 q = __ldg(d.warp + (size_t)j * d.n + k);
-            P.x(j) = q.x;
-            P.y(j) = q.y;
+            P.x[j] = q.x;
+            P.y[j] = q.y;
             ok = ok && inside(q.x, q.y, W1, H1);
             if (j == d.B) {
                 P.ex = q.x;
@@ -518,19 +495,19 @@ __device__ __forceinline__ bool load_traj(const Win& d, const EventAt& e, TrajT&
     return ok;
 }
 
-template <int MAXB, class Sink = RedSink, class TrajT = Traj<MAXB>>
+template <int MAXB, class Sink = RedSink>
 __device__ __forceinline__ void splat_event(const Win& d, int64_t k, const Sink& sink = Sink())
 {
     EventAt e;
     if (!load_event(d, k, e)) return;
-    TrajT P;
+    Traj<MAXB> P;
     const bool ok = trajectory<MAXB>(d, e, P);
     if (d.warp) store_traj<MAXB>(d, e, P, k);
     if (!ok) return;
     if (d.ref_mode == kRefAll) {
 #pragma unroll
         for (int j = 0; j <= MAXB; ++j)
-            if (j <= d.B) sink.splat(d, j, P.x(j), P.y(j), tbar_of(j, d.B, e.tau), e.pol2, k);
+            if (j <= d.B) sink.splat(d, j, P.x[j], P.y[j], tbar_of(j, d.B, e.tau), e.pol2, k);
     } else {
         sink.splat(d, 0, P.ex, P.ey, tbar_of(d.B, d.B, e.tau), e.pol2, k);
     }
@@ -630,12 +607,12 @@ __device__ __forceinline__ float2 push_back(const Win& d, const Sink& sink, int 
 // splat stored it); the position adjoint of each reference point comes from
 // the (C, S) pairs gathered at its corners (phi_of), and the adjoint is
 // carried back along both chains of pushes, scattering dL/dflow.
-template <int MAXB, class Sink = RedSink, bool SPLIT = false, class TrajT = Traj<MAXB>>
+template <int MAXB, class Sink = RedSink, bool SPLIT = false>
 __device__ __forceinline__ void adjoint_event(const Win& d, int64_t k, float dl, const Sink& sink = Sink())
 {
     EventAt e;
     if (!load_event(d, k, e)) return;
-    TrajT P;
+    Traj<MAXB> P;
     if (!(d.warp ? load_traj<MAXB>(d, e, P, k) : trajectory<MAXB>(d, e, P))) return;
     const int B = d.B, b = e.b;
     const float h = __fdiv_rn(1.0f, (float)B);
@@ -646,12 +623,12 @@ __device__ __forceinline__ void adjoint_event(const Win& d, int64_t k, float dl,
     for (int j = MAXB; j >= 1; --j) {
         if (j <= B && j > b) {
             if (all || j == B) {
-                const float2 a = ref_adjoint<SPLIT>(d, all ? j : 0, j, P.x(j), P.y(j), e.tau, e.pol2, dl);
+                const float2 a = ref_adjoint<SPLIT>(d, all ? j : 0, j, P.x[j], P.y[j], e.tau, e.pol2, dl);
                 lam.x += a.x;
                 lam.y += a.y;
             }
             if (j > b + 1) {
-                lam = push_back(d, sink, j - 1, j, P.x(j - 1), P.y(j - 1), h, lam, k);
+                lam = push_back(d, sink, j - 1, j, P.x[j - 1], P.y[j - 1], h, lam, k);
             } else {
                 const float dtf = __fsub_rn(edge_tau(b + 1, B), e.tau);
                 sink.point(d, b, j, e.xk, e.yk, dtf * lam.x, dtf * lam.y, k);
@@ -664,11 +641,11 @@ __device__ __forceinline__ void adjoint_event(const Win& d, int64_t k, float dl,
 #pragma unroll
     for (int j = 0; j <= MAXB - 1; ++j) {
         if (j <= b) {
-            const float2 a = ref_adjoint<SPLIT>(d, j, j, P.x(j), P.y(j), e.tau, e.pol2, dl);
+            const float2 a = ref_adjoint<SPLIT>(d, j, j, P.x[j], P.y[j], e.tau, e.pol2, dl);
             lam.x += a.x;
             lam.y += a.y;
             if (j < b) {
-                lam = push_back(d, sink, j, j, P.x(j + 1), P.y(j + 1), -h, lam, k);
+                lam = push_back(d, sink, j, j, P.x[j + 1], P.y[j + 1], -h, lam, k);
             } else {
                 const float dtb = __fsub_rn(e.tau, edge_tau(b, B));
                 sink.point(d, b, j, e.xk, e.yk, -dtb * lam.x, -dtb * lam.y, k);
