@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="bound of the CPU oracle sample")
     ap.add_argument("--schedule", default="auto",
                     help="batch schedule 'chains,windows_per_kernel,tile_grouping' (e.g. 4,2,0), or 'auto' to autotune")
+    ap.add_argument("--events", default="iid", choices=["iid", "motion"],
+                    help="iid: the headline workload; motion: motion-consistent events with their true flow "
+                         "(flow input, many events per pixel after the warp: the contention stress variant)")
     ap.add_argument("--store-warps", type=int, default=0, choices=[0, 1],
                     help="1: the forward stores the trajectory points for the backward (no recompute)")
     ap.add_argument("--serve", action="store_true", help="run the serving workload instead (one line per rate)")
@@ -152,17 +155,24 @@ class ClockSampler:
 
 def kernel_bytes(name: str, n: int, hw: int, R: int, model: str) -> float:
     """Algorithmic bytes of one launch of `name` that processes n events over
-    hw pixels (summed over the windows the launch covers) with R references."""
+    hw pixels (summed over the windows the launch covers) with R references.
+    strict: events read by the splat and the adjoint (9 B each), inverse depth
+    read by the prep pass and its gradient written by the gradient pass (4 B
+    per pixel each).  iwe adds the dense traffic of this design: the images
+    (16 B per pixel and reference) zeroed by the prep pass, reduced into by the
+    splat, read by the loss pass and gathered by the adjoint; the 32-byte flow
+    quads and gradient records written by the prep pass and read by the
+    gradient pass, which also writes dL/dflow (8 B per pixel)."""
     iwe = model == "iwe"
     base = name.replace("_batch", "")
     if base in ("k_splat", "k_adjoint"):
         return 9.0 * n + (16.0 * R * hw if iwe else 0.0)
-    if base in ("k_flow", "k_depth_ego"):
-        return 4.0 * hw + (8.0 * hw if iwe else 0.0)
-    if base == "k_loss_partial":
-        return 32.0 * R * hw if iwe else 0.0
-    if base == "k_zero":
+    if base == "k_prep":
+        return 4.0 * hw + ((16.0 * R + 64.0) * hw if iwe else 0.0)
+    if base == "k_loss":
         return 16.0 * R * hw if iwe else 0.0
+    if base == "k_grad":
+        return 4.0 * hw + (40.0 * hw if iwe else 0.0)
     return 0.0
 
 
@@ -277,7 +287,9 @@ def run_reference(args):
 class Batch:
     """The windows of one step resident on the device: a batched plan over all
     of them (the timed path) and one workspace per window for the plain
-    per-window comparison through the single-window entry points."""
+    per-window comparison through the single-window entry points.  Windows
+    take inverse depth and ego-motion, or a given flow (the motion-consistent
+    stress variant)."""
 
     def __init__(self, wins, device, store_warps=False):
         import torch
@@ -287,17 +299,23 @@ class Batch:
         self.wins = wins
         self.dev = device
         self.items = []
+        self.flow_input = wins[0].flow is not None
         dev_wins = []
         for w in wins:
             cfg = cm.loss_cfg(w.nbins, w.ref_mode, cm.SPLAT_ATOMIC, store_warps=store_warps)
             ws = cm.Workspace(w.cam, cfg, w.events.n, 1, device)
             ev = cm.DeviceEvents.from_host(w.events, device)
-            rho = torch.from_numpy(w.inv_depth).to(device)
-            ego = torch.from_numpy(w.ego).to(device)
-            out = {"dinv_depth": torch.empty_like(rho), "dego": torch.empty(6, device=device)}
             loss = torch.empty(1, device=device)
-            self.items.append((w, ws, ev, rho, ego, out, loss))
-            dev_wins.append({"cam": w.cam, "ev": ev, "inv_depth": rho, "ego": ego, "dt": w.dt})
+            if self.flow_input:
+                flow = torch.from_numpy(np.ascontiguousarray(w.flow[0])).to(device)
+                self.items.append((w, ws, ev, flow, None, {"dflow": torch.empty_like(flow)}, loss))
+                dev_wins.append({"cam": w.cam, "ev": ev, "flow": flow})
+            else:
+                rho = torch.from_numpy(w.inv_depth).to(device)
+                ego = torch.from_numpy(w.ego).to(device)
+                out = {"dinv_depth": torch.empty_like(rho), "dego": torch.empty(6, device=device)}
+                self.items.append((w, ws, ev, rho, ego, out, loss))
+                dev_wins.append({"cam": w.cam, "ev": ev, "inv_depth": rho, "ego": ego, "dt": w.dt})
         self.dloss = torch.ones(1, device=device)
         self.plan = cm.BatchPlan(dev_wins, cm.loss_cfg(wins[0].nbins, wins[0].ref_mode, cm.SPLAT_ATOMIC,
                                                        store_warps=store_warps), device)
@@ -306,11 +324,19 @@ class Batch:
     def step(self):
         self.plan.run()
 
+    def window_call(self, it):
+        """Loss and gradient of one window through the single-window calls."""
+        w, ws, ev, a, b, out, loss = it
+        if self.flow_input:
+            self.cm.loss_forward(ws, ev, flow=a, out=loss)
+            self.cm.loss_backward(ws, ev, self.dloss, flow=a, out=out)
+        else:
+            self.cm.loss_forward(ws, ev, inv_depth=a, ego=b, dt=w.dt, out=loss)
+            self.cm.loss_backward(ws, ev, self.dloss, inv_depth=a, ego=b, dt=w.dt, want_dflow=False, out=out)
+
     def plain_window(self, i):
         import torch
-        w, ws, ev, rho, ego, out, loss = self.items[i]
-        self.cm.loss_forward(ws, ev, inv_depth=rho, ego=ego, dt=w.dt, out=loss)
-        self.cm.loss_backward(ws, ev, self.dloss, inv_depth=rho, ego=ego, dt=w.dt, want_dflow=False, out=out)
+        self.window_call(self.items[i])
         torch.cuda.current_stream().synchronize()
 
 
@@ -330,7 +356,10 @@ def run_ours(args):
     C.lib()
 
     # weak scaling: every rank evaluates its own 64 windows
-    wins = synth.batch_windows(args.windows, first=first_window_of(rank, args.windows))
+    if args.events == "motion":
+        wins = synth.batch_windows_motion(args.windows, first=first_window_of(rank, args.windows))
+    else:
+        wins = synth.batch_windows(args.windows, first=first_window_of(rank, args.windows))
     batch = Batch(wins, dev, store_warps=bool(args.store_warps))
     hw = wins[0].cam.width * wins[0].cam.height
     R = wins[0].nbins + 1
@@ -444,7 +473,7 @@ def run_ours(args):
 
     # ---- end to end through the public API with host buffers ----
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not batch.flow_input:
         e2e = run_e2e(batch, args, stream, schedule)
 
     # ---- CPU oracle baseline (rank 0 at N = 1 only) ----
@@ -459,7 +488,10 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": "Mev/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "windows": len(wins), "events_per_step": batch.events,
+            "config": {"workload": WORKLOAD if args.events == "iid" else WORKLOAD + "_motion",
+                       "events": "iid (gradient-sampled pixels, uniform times)" if args.events == "iid"
+                       else "motion-consistent, flow input with the true flow (contention stress variant)",
+                       "windows": len(wins), "events_per_step": batch.events,
                        "sensor": "640x480", "bins": wins[0].nbins, "refs": R, "splat": "atomic",
                        "backward": "stored warps" if args.store_warps else "recompute",
                        "path": "batched plan replayed from a CUDA graph",
@@ -562,14 +594,12 @@ def compare_splats(batch, nwin: int):
     out = {"windows": nwin, "path": "cm_loss_forward + cm_loss_backward per window"}
     for name, splat in (("atomic", cm.SPLAT_ATOMIC), ("sort", cm.SPLAT_SORT)):
         items = []
-        for (w, _, ev, rho, ego, res, loss) in batch.items[:nwin]:
+        for (w, _, ev, a, b, res, loss) in batch.items[:nwin]:
             cfg = cm.loss_cfg(w.nbins, w.ref_mode, splat)
-            items.append((w, cm.Workspace(w.cam, cfg, w.events.n, 1, batch.dev), ev, rho, ego, res, loss))
+            items.append((w, cm.Workspace(w.cam, cfg, w.events.n, 1, batch.dev), ev, a, b, res, loss))
 
         def one(it):
-            w, ws, ev, rho, ego, res, loss = it
-            cm.loss_forward(ws, ev, inv_depth=rho, ego=ego, dt=w.dt, out=loss)
-            cm.loss_backward(ws, ev, batch.dloss, inv_depth=rho, ego=ego, dt=w.dt, want_dflow=False, out=res)
+            batch.window_call(it)
             torch.cuda.current_stream().synchronize()
 
         for it in items:

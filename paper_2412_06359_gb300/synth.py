@@ -235,6 +235,43 @@ def depth_window(rng: np.random.Generator, width: int, height: int, n: int, nbin
     return Window(cam, ev, nbins=nbins, ref_mode=ref_mode, inv_depth=rho, ego=ego)
 
 
+def motion_window(rng: np.random.Generator, width: int, height: int, n: int, nbins: int = 10,
+                  per_point: int = 50, max_mag: float = 8.0) -> Window:
+    """Motion-consistent events (the contention stress case): n / per_point
+    scene points at random sub-pixel positions, each with one polarity, fire
+    events at uniform times as they move along a given smooth flow (a
+    sinusoid field, px per window); each event is the point's position at its
+    time, rounded to a pixel.  With that flow as the window's flow every
+    point's events gather in a small spot at each reference: the sharp images
+    of a converged estimate, with many events per pixel."""
+    flow = sinusoid_flow(rng, width, height, max_mag)
+    npts = max(1, n // per_point)
+    px = rng.uniform(0, width - 1, npts)
+    py = rng.uniform(0, height - 1, npts)
+    pol = np.where(rng.random(npts) < 0.5, 1, -1).astype(np.int8)
+    k = rng.integers(0, npts, size=n)
+    t = _timestamps(rng, n, 0.0, WINDOW_S)
+    tau = (t.astype(np.float64) - 0.0) / WINDOW_S
+    ix, iy = np.rint(px[k]).astype(np.int64), np.rint(py[k]).astype(np.int64)
+    u = flow[iy, ix].astype(np.float64)
+    x = np.clip(np.rint(px[k] + tau * u[:, 0]), 0, width - 1).astype(np.int16)
+    y = np.clip(np.rint(py[k] + tau * u[:, 1]), 0, height - 1).astype(np.int16)
+    ev = Events(x, y, t, pol[k], 0.0, float(np.float32(WINDOW_S)))
+    return Window(camera_for(width, height), ev, nbins=nbins, ref_mode=REF_ALL, flow=flow[None])
+
+
+def batch_windows_motion(count: int = 64, width: int = 640, height: int = 480, lo: float = 5e3, hi: float = 5e5,
+                         first: int = 0) -> list[Window]:
+    """The uneven batch with motion-consistent events (flow input, the true
+    flow): the contention stress variant of batch_windows."""
+    out = []
+    for i in range(first, first + count):
+        rng = rng_for(6, i)
+        n = log_uniform_count(rng, lo, hi)
+        out.append(motion_window(rng, width, height, n))
+    return out
+
+
 def davis_window(n: int = 100_000) -> Window:
     """346x260 DAVIS sensor, 100,000 events, 10 bins, all 11 bin edges as references."""
     return depth_window(rng_for(2), 346, 260, n)
