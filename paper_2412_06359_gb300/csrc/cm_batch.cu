@@ -43,7 +43,7 @@ struct BatchHdr {
     int32_t nwin;
     int32_t pad;
     long long total_chunks;  // event chunks of kEventThreads events
-    int32_t total_ltiles;    // loss tiles (R x loss_tiles per window)
+    int32_t total_ltiles;    // loss / gradient tiles (loss_tiles per window)
     int32_t total_ptiles;    // pixel tiles (pix_tiles per window)
 };
 
@@ -288,38 +288,47 @@ __global__ void __launch_bounds__(256) k_loss_batch(const BatchHdr* h, const Win
     for (int tile = tb + blockIdx.x; tile < te; tile += gridDim.x) {
         const int w = find_i(lstart, w0, w1, tile);
         const Win d = tab[w];
-        const int local = tile - lstart[w];
-        const int r = local / d.loss_tiles, ti = local - r * d.loss_tiles;
-        loss_tile(d, r, ti, d.loss_tiles, d.loss_part + (size_t)r * d.loss_tiles + ti);
-        if (last_tile_done(d.sync + 0, d.R * d.loss_tiles)) loss_final_window(d);
+        const int ti = tile - lstart[w];
+        if (d.iwe_split) {
+            if (plane_size(d) & 1)
+                loss_tile_planes<false>(d, ti, d.loss_tiles);
+            else
+                loss_tile_planes<true>(d, ti, d.loss_tiles);
+        } else {
+            for (int r = 0; r < d.R; ++r) loss_tile(d, r, ti, d.loss_tiles, d.loss_part + (size_t)r * d.loss_tiles + ti);
+        }
+        if (last_tile_done(d.sync + 0, d.loss_tiles)) loss_final_window(d);
     }
 }
 
 // dL/dflow folded from the quad accumulators, and the depth / ego gradient per
-// tile; the block completing a window's last tile reduces the six ego sums
-__global__ void __launch_bounds__(256, 4) k_grad_batch(const BatchHdr* h, const Win* tab, const int* pstart, int w0,
+// tile (the loss pass's tiles); the block completing a window's last tile
+// reduces the six ego sums
+__global__ void __launch_bounds__(256, 3) k_grad_batch(const BatchHdr* h, const Win* tab, const int* lstart, int w0,
                                                     int w1)
 {
     w1 = clamp_end(h, w1);
     if (w0 >= w1) return;
-    const int tb = pstart[w0], te = pstart[w1];
+    const int tb = lstart[w0], te = lstart[w1];
     for (int tile = tb + blockIdx.x; tile < te; tile += gridDim.x) {
-        const int w = find_i(pstart, w0, w1, tile);
+        const int w = find_i(lstart, w0, w1, tile);
         const Win d = tab[w];
         if (!d.rho) {
-            if (d.dq) fold_tile(d, tile - pstart[w], d.pix_tiles);  // flow input: dL/dflow only
+            if (d.dq) fold_tile(d, tile - lstart[w], d.loss_tiles);  // flow input: dL/dflow only
             continue;
         }
-        depth_ego_tile(d, tile - pstart[w], d.pix_tiles);
-        if (last_tile_done(d.sync + 1, d.pix_tiles)) {
+        depth_ego_tile(d, tile - lstart[w], d.loss_tiles);
+        if (last_tile_done(d.sync + 1, d.loss_tiles)) {
             __syncthreads();
-            depth_ego_final_window(d);
+            depth_ego_final_window(d, d.loss_tiles);
         }
     }
 }
 
 
 }  // namespace cmk
+
+static_assert(cmk::kMaxRefs >= CM_MAX_BINS + 1, "per-reference shared arrays hold every reference");
 
 using cmk::BatchHdr;
 using cmk::Win;
@@ -344,10 +353,9 @@ int tiles_for(size_t hw, size_t px_per_tile, int cap)
 }
 
 // Tiles of a window's pixel passes (a tile is one block's share, 256 threads):
-// per reference for the loss pass (8 pixels per thread), per image for the prep
-// and gradient passes (2 pixels per thread).  Measured on GB300 at 640x480:
-// halving the loss tiles' pixels made the pass slower (per-tile reductions),
-// halving the prep tiles' pixels made prep faster.
+// 2048 pixels of every reference for the loss pass and the gradient pass (8
+// pixels per thread), 512 pixels for the prep pass (2 per thread: halving the
+// prep tiles' pixels made prep faster on GB300 at 640x480).
 int loss_tiles_for(size_t hw) { return tiles_for(hw, 2048, 2048); }
 int pix_tiles_for(size_t hw) { return tiles_for(hw, 512, 4096); }
 
@@ -392,11 +400,11 @@ Need need_of(const cm_window* wins, int32_t nwin, const cm_loss_cfg& cfg)
         if (wins[i].scratch) continue;  // the window brings its own buffers
         const size_t HW = (size_t)wins[i].cam.width * wins[i].cam.height;
         n.iwe += up256((size_t)R * HW * sizeof(float4));
-        if (!wins[i].dflow) n.dflow += HW * sizeof(float2);
+        if (!wins[i].dflow && wins[i].flow) n.dflow += HW * sizeof(float2);
         n.quad += 2 * HW * sizeof(cmk::FQ);
         n.part += (size_t)R * loss_tiles_for(HW) * sizeof(float2);
         n.stat += (size_t)R;
-        n.dego += (size_t)pix_tiles_for(HW) * 6 * sizeof(float);
+        n.dego += (size_t)loss_tiles_for(HW) * 6 * sizeof(float);
         n.bins += bin_bytes(wins[i].cam.width, wins[i].cam.height, wins[i].ev.n);
         if (cfg.store_warps) n.warp += up256((size_t)(cfg.nbins + 1) * wins[i].ev.n * sizeof(float2));
     }
@@ -438,7 +446,7 @@ WinScratch win_scratch(size_t HW, int R)
     s.nnz = o;
     o = up256(o + (size_t)R * sizeof(int32_t));
     s.dego = o;
-    o = up256(o + (size_t)pix_tiles_for(HW) * 6 * sizeof(float));
+    o = up256(o + (size_t)loss_tiles_for(HW) * 6 * sizeof(float));
     s.sync = o;
     o = up256(o + kSyncInts * sizeof(int32_t));
     s.total = o;
@@ -603,7 +611,9 @@ int stage_windows(cm_batch* b, const cm_window* wins, int32_t nwin)
             const WinScratch ws = win_scratch(HW, R);
             d.iwe = reinterpret_cast<float4*>(sc + ws.iwe);
             d.flow = reinterpret_cast<const float2*>(w.flow);  // nullptr for depth input (the quads hold its flow)
-            d.dflow = w.dflow ? reinterpret_cast<float2*>(w.dflow) : reinterpret_cast<float2*>(sc + ws.dflow);
+            // dL/dflow of a depth window is stored only where the caller asks for it
+            d.dflow = w.dflow ? reinterpret_cast<float2*>(w.dflow)
+                              : (w.flow ? reinterpret_cast<float2*>(sc + ws.dflow) : nullptr);
             d.fq = reinterpret_cast<const cmk::FQ*>(sc + ws.fq);
             d.dq = reinterpret_cast<cmk::FQ*>(sc + ws.dq);
             d.loss_part = reinterpret_cast<float2*>(sc + ws.part);
@@ -618,9 +628,11 @@ int stage_windows(cm_batch* b, const cm_window* wins, int32_t nwin)
             d.flow = reinterpret_cast<const float2*>(w.flow);  // nullptr for depth input (the quads hold its flow)
             if (w.dflow) {
                 d.dflow = reinterpret_cast<float2*>(w.dflow);
-            } else {
+            } else if (w.flow) {
                 d.dflow = reinterpret_cast<float2*>(base + b->L.dflow + o_dflow);
                 o_dflow += HW * sizeof(float2);
+            } else {
+                d.dflow = nullptr;  // dL/dflow of a depth window is stored only where the caller asks for it
             }
             if (b->cfg.store_warps && d.n > 0) {
                 d.warp = reinterpret_cast<float2*>(base + b->L.warp + o_warp);
@@ -637,7 +649,7 @@ int stage_windows(cm_batch* b, const cm_window* wins, int32_t nwin)
             d.nnz_r = reinterpret_cast<int32_t*>(base + b->L.nnz) + o_stat;
             o_stat += R;
             d.dego_part = reinterpret_cast<float*>(base + b->L.dego + o_dego);
-            o_dego += (size_t)d.pix_tiles * 6 * sizeof(float);
+            o_dego += (size_t)d.loss_tiles * 6 * sizeof(float);
             d.sync = reinterpret_cast<int32_t*>(base + b->L.sync) + kSyncInts * i;
             // events grouped by 32x32 tile, while the plan's binning memory lasts
             const size_t bb = bin_bytes(d.W, d.H, d.n);
@@ -676,7 +688,7 @@ int stage_windows(cm_batch* b, const cm_window* wins, int32_t nwin)
         ls[i] = lt_total;
         ps[i] = pt_total;
         b->chunks[i] = (w.ev.n + cmk::kEventThreads - 1) / cmk::kEventThreads;
-        b->ltiles[i] = R * d.loss_tiles;
+        b->ltiles[i] = d.loss_tiles;
         b->ptiles[i] = d.pix_tiles;
         chunks += b->chunks[i];
         lt_total += b->ltiles[i];
@@ -724,7 +736,7 @@ std::vector<Group> make_groups(const cm_batch* b)
             x.chunks += b->chunks[i];
             x.ltiles += b->ltiles[i];
             x.ptiles += b->ptiles[i];
-            work += (double)b->chunks[i] + 0.5 * b->ltiles[i];
+            work += (double)b->chunks[i] + 0.5 * refs_of(b->cfg) * b->ltiles[i];
         }
         int best = 0;
         for (int c = 1; c < chains; ++c)
@@ -824,7 +836,7 @@ int capture(cm_batch* b)
             case 3: enqueue_event(b, s, 0, ge, g.w0, g.w1); break;
             case 4: cmk::k_loss_batch<<<gl, 256, 0, s>>>(h, tab, ls, g.w0, g.w1); break;
             case 5: enqueue_event(b, s, 1, ge, g.w0, g.w1); break;
-            case 6: cmk::k_grad_batch<<<gt, 256, 0, s>>>(h, tab, ps, g.w0, g.w1); break;
+            case 6: cmk::k_grad_batch<<<gl, 256, 0, s>>>(h, tab, ls, g.w0, g.w1); break;
             }
             cudaEventRecordWithFlags(p.eb, s, cudaEventRecordExternal);
         }

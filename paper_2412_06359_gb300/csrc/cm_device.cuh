@@ -57,7 +57,7 @@ struct Win {
     float4* iwe;             // iwe_split == 0: [R][H][W] (C+, S+, C-, S-);
                              // iwe_split == 1: [R][2][H][W] float2 (C, S), one plane per polarity
     int32_t iwe_split;
-    float2* dflow;           // [nfb][H][W]
+    float2* dflow;           // [nfb][H][W]; nullptr: dL/dflow of a depth window is not stored
     const FQ* fq;            // [nfb][H][W] flow quads, or nullptr (then samples gather from flow)
     FQ* dq;                  // [nfb][H][W] quad accumulators of dL/dflow, or nullptr (then pushes reduce into dflow)
     float2* warp;            // [B+1][n] trajectory points stored by the splat for the adjoint, or nullptr
@@ -74,7 +74,7 @@ struct Win {
     const float* ego;        // [6]
     float* drho;             // [H][W]
     float* dego;             // [6]
-    float* dego_part;        // [pix_tiles][6]
+    float* dego_part;        // [gradient tiles][6] (pix_tiles; loss_tiles on the batched path)
     int32_t* sync;           // [4] batched path: completion counters of the loss and gradient reductions and
                              // of the binning count
     // spatial binning (batched path; tile_cnt == nullptr: events are used in their given order)
@@ -88,6 +88,7 @@ struct Win {
 };
 
 constexpr int kBinTile = 32;  // px, side of the tiles events are grouped by
+constexpr int kMaxRefs = 33;  // references of a window at most (B + 1), for per-reference shared arrays
 
 __device__ __forceinline__ size_t plane_size(const Win& d) { return (size_t)d.W * (size_t)d.H; }
 
@@ -865,6 +866,91 @@ __device__ __forceinline__ void loss_tile(const Win& d, int r, int tile, int nti
     __syncthreads();
 }
 
+// S5 pass 1 over one pixel tile of a window and every reference, for the
+// polarity-plane layout (iwe_split == 1): the sum of T^2 and the non-empty
+// count of reference r over the tile go to loss_part[r][tile].  Same per-pixel
+// operations as loss_tile.  Two references per round and four pixel pairs
+// per polarity (PAIRS: 16-byte loads, for planes 16-byte aligned: HW even):
+// sixteen loads in flight per thread.  Padding slots read (0, 0), which adds
+// exactly nothing.  Ends with __syncthreads (the caller may loop).
+template <bool PAIRS>
+__device__ __forceinline__ void loss_tile_planes(const Win& d, int tile, int ntiles)
+{
+    constexpr int K = 4, RK = 2;
+    const uint32_t HW = (uint32_t)plane_size(d);
+    const float eps = d.eps;
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    __shared__ float ss[kMaxRefs][32];
+    __shared__ int sc[kMaxRefs][32];
+    const uint32_t stride = (uint32_t)ntiles * blockDim.x, first = (uint32_t)tile * blockDim.x + threadIdx.x;
+    const float2* planes = reinterpret_cast<const float2*>(d.iwe);
+    const uint32_t n = PAIRS ? HW >> 1 : HW;  // loads per plane
+    for (int r0 = 0; r0 < d.R; r0 += RK) {
+        float s[RK];
+        int cnt[RK];
+#pragma unroll
+        for (int q = 0; q < RK; ++q) {
+            s[q] = 0.0f;
+            cnt[q] = 0;
+        }
+        auto one = [&](int q, float cp, float sp, float cm, float sm) {
+            const float tp = sp * recip(cp + eps), tm = sm * recip(cm + eps);
+            s[q] = fmaf(tp, tp, s[q]);
+            s[q] = fmaf(tm, tm, s[q]);
+            cnt[q] += (cp > 0.0f || cm > 0.0f) ? 1 : 0;
+        };
+        for (uint32_t j0 = first; j0 < n; j0 += K * stride) {
+            float4 a[RK][K], b[RK][K];
+#pragma unroll
+            for (int q = 0; q < RK; ++q) {
+                const float2* pos = planes + (size_t)2 * (r0 + q) * HW;
+                const float2* neg = pos + HW;
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    const uint32_t j = j0 + k * stride;
+                    const bool in = j < n && r0 + q < d.R;
+                    if (PAIRS) {
+                        a[q][k] = in ? reinterpret_cast<const float4*>(pos)[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+                        b[q][k] = in ? reinterpret_cast<const float4*>(neg)[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    } else {
+                        const float2 x = in ? pos[j] : make_float2(0.f, 0.f), y = in ? neg[j] : make_float2(0.f, 0.f);
+                        a[q][k] = make_float4(x.x, x.y, 0.f, 0.f);
+                        b[q][k] = make_float4(y.x, y.y, 0.f, 0.f);
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < RK; ++q)
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    one(q, a[q][k].x, a[q][k].y, b[q][k].x, b[q][k].y);
+                    if (PAIRS) one(q, a[q][k].z, a[q][k].w, b[q][k].z, b[q][k].w);
+                }
+        }
+#pragma unroll
+        for (int q = 0; q < RK; ++q) {
+            const float sq = warp_sum(s[q]);
+            const int cq = warp_sum(cnt[q]);
+            if (l == 0 && r0 + q < d.R) {
+                ss[r0 + q][w] = sq;
+                sc[r0 + q][w] = cq;
+            }
+        }
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < d.R) {
+        const int r = threadIdx.x;
+        float a = 0.0f;
+        int c = 0;
+        for (int i = 0; i < nw; ++i) {
+            a += ss[r][i];
+            c += sc[r][i];
+        }
+        d.loss_part[(size_t)r * ntiles + tile] = make_float2(a, (float)c);
+    }
+    __syncthreads();
+}
+
 // S5 pass 2 for one window (one block): fixed-order reduction of the tiles,
 // L_r, N_nz(r), 1/(R(N_nz + eps)) and the loss.
 __device__ __forceinline__ void loss_final_window(const Win& d)
@@ -921,7 +1007,7 @@ __device__ __forceinline__ void depth_ego_tile(const Win& d, int tile, int ntile
         int u, v;
         pixel_uv(i, W, u, v);
         const float2 f = fold_dq(d, u, v);
-        d.dflow[i] = f;
+        if (d.dflow) d.dflow[i] = f;
         return f;
     };
     auto one = [&](size_t i, float r, float2 df) {
@@ -937,15 +1023,24 @@ __device__ __forceinline__ void depth_ego_tile(const Win& d, int tile, int ntile
         g[4] -= (1.0f + xn * xn) * Gx + xn * yn * Gy;
         g[5] += yn * Gx - xn * Gy;
     };
+    // four pixels' loads in flight, added in the order i, i + stride, ...
+    constexpr int K = 4;
     const size_t stride = (size_t)ntiles * blockDim.x;
-    size_t i = (size_t)tile * blockDim.x + threadIdx.x;
-    for (; i + stride < HW; i += 2 * stride) {  // two pixels' loads in flight
-        const float r0 = __ldg(d.rho + i), r1 = __ldg(d.rho + i + stride);
-        const float2 f0 = dfl(i), f1 = dfl(i + stride);
-        one(i, r0, f0);
-        one(i + stride, r1, f1);
+    for (size_t i0 = (size_t)tile * blockDim.x + threadIdx.x; i0 < HW; i0 += K * stride) {
+        float r[K];
+        float2 f[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const size_t i = i0 + k * stride;
+            if (i < HW) {
+                r[k] = __ldg(d.rho + i);
+                f[k] = dfl(i);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            if (i0 + k * stride < HW) one(i0 + k * stride, r[k], f[k]);
     }
-    if (i < HW) one(i, __ldg(d.rho + i), dfl(i));
     __shared__ float sg[32][6];
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
 #pragma unroll
@@ -962,17 +1057,17 @@ __device__ __forceinline__ void depth_ego_tile(const Win& d, int tile, int ntile
     __syncthreads();
 }
 
-// S7 final for one window: warps 0..5 reduce the tiles of one component each.
-__device__ __forceinline__ void depth_ego_final_window(const Win& d)
+// S7 final for one window: warps 0..5 reduce the ntiles tiles of one component each.
+__device__ __forceinline__ void depth_ego_final_window(const Win& d, int ntiles)
 {
     const int c = threadIdx.x >> 5, l = threadIdx.x & 31;
     if (c >= 6) return;
     double s = 0.0;
     // lane l adds tiles l, l+32, ... in that order, with eight loads in flight
-    for (int i0 = l; i0 < d.pix_tiles; i0 += 32 * 8) {
+    for (int i0 = l; i0 < ntiles; i0 += 32 * 8) {
         float q[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) q[u] = i0 + 32 * u < d.pix_tiles ? d.dego_part[(size_t)(i0 + 32 * u) * 6 + c] : 0.f;
+        for (int u = 0; u < 8; ++u) q[u] = i0 + 32 * u < ntiles ? d.dego_part[(size_t)(i0 + 32 * u) * 6 + c] : 0.f;
 #pragma unroll
         for (int u = 0; u < 8; ++u) s += (double)q[u];
     }

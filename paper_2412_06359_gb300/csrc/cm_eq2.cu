@@ -25,6 +25,7 @@ namespace {
 
 constexpr int kEq2Threads = 256;
 constexpr int kEq2Partials = 12;  // dL/dt (3) and dL/dR = sum dL/dP X^T (9), per bin and tile
+static_assert(kEq2Partials == 12, "the adjoint reduces its partials with warp_sum12");
 
 struct Eq2Args {
     int32_t W, H, nb;
@@ -51,18 +52,21 @@ __global__ void __launch_bounds__(kEq2Threads) k_flow_eq2(Eq2Args a, float2* __r
     }
 }
 
-// Adjoint per tile of kEq2Tile pixels (kEq2PerThread per thread, strided by
-// the block size): dL/d(rho) per pixel (summed over the bins), and per bin the
-// tile's twelve sums dL/dt, dL/dR (one block reduction per bin and tile).
+// Pixels per thread of the adjoint: a thread keeps its pixels' points in
+// registers and reads each bin's pose from shared memory once for all of them.
 constexpr int kEq2PerThread = 4;
 constexpr int kEq2Tile = kEq2Threads * kEq2PerThread;
 
-__global__ void __launch_bounds__(kEq2Threads) k_flow_eq2_grad(Eq2Args a, const float2* __restrict__ dflow,
-                                                               float* __restrict__ drho, float* __restrict__ part,
-                                                               int ntiles)
+// Adjoint per tile of kEq2Tile pixels (kEq2PerThread per thread, strided by
+// the block size): dL/d(rho) per pixel (summed over the bins), and per bin the
+// tile's twelve sums dL/dt, dL/dR (one warp reduction per bin and warp, one
+// barrier per tile).
+__global__ void __launch_bounds__(kEq2Threads, 3) k_flow_eq2_grad(Eq2Args a, const float2* __restrict__ dflow,
+                                                                  float* __restrict__ drho, float* __restrict__ part,
+                                                                  int ntiles)
 {
     __shared__ Pose poses[CM_MAX_BINS];
-    // per warp, bin and component: the warp's sum (one barrier per tile, not per bin)
+    // per warp, bin and component: the warp's sum
     __shared__ float red[kEq2Threads / 32][CM_MAX_BINS][kEq2Partials];
     if (threadIdx.x < a.nb) poses[threadIdx.x] = pose_of(a.ego + 6 * threadIdx.x, a.dt);
     __syncthreads();
@@ -82,7 +86,13 @@ __global__ void __launch_bounds__(kEq2Threads) k_flow_eq2_grad(Eq2Args a, const 
             }
         }
         for (int b = 0; b < a.nb; ++b) {
-            const Pose& p = poses[b];
+            const Pose p = poses[b];
+            float2 g[kEq2PerThread];
+#pragma unroll
+            for (int k = 0; k < kEq2PerThread; ++k) {
+                const uint32_t i = (uint32_t)tile * kEq2Tile + k * kEq2Threads + threadIdx.x;
+                g[k] = i < HW ? __ldg(dflow + (size_t)b * HW + i) : make_float2(0.0f, 0.0f);
+            }
             float c[kEq2Partials];
 #pragma unroll
             for (int m = 0; m < kEq2Partials; ++m) c[m] = 0.0f;
@@ -92,9 +102,8 @@ __global__ void __launch_bounds__(kEq2Threads) k_flow_eq2_grad(Eq2Args a, const 
                 if (i >= HW) continue;
                 float X[3], P[3];
                 transform(p, q[k], X, P);
-                const float2 g = __ldg(dflow + (size_t)b * HW + i);
                 const float iz = recip(P[2]);  // hardware reciprocal: the adjoint is ALU-bound
-                const float Gx = a.scale * g.x * a.fx, Gy = a.scale * g.y * a.fy;
+                const float Gx = a.scale * g[k].x * a.fx, Gy = a.scale * g[k].y * a.fy;
                 const float dP[3] = {Gx * iz, Gy * iz, -(Gx * P[0] + Gy * P[1]) * iz * iz};
 #pragma unroll
                 for (int r = 0; r < 3; ++r) {
@@ -119,10 +128,10 @@ __global__ void __launch_bounds__(kEq2Threads) k_flow_eq2_grad(Eq2Args a, const 
                 const float dZ = (Gx * (s0 * p.t[2] - u0 * q2) + Gy * (s1 * p.t[2] - u1 * q2)) * iz * iz;
                 dr[k] -= pq.Z * pq.Z * dZ;
             }
+            warp_sum12(c);
+            if ((l & 7) == 0) {
 #pragma unroll
-            for (int m = 0; m < kEq2Partials; ++m) {
-                const float s = warp_sum(c[m]);
-                if (l == 0) red[w][b][m] = s;
+                for (int j = 0; j < 3; ++j) red[w][b][3 * (l >> 3) + j] = c[j];
             }
         }
 #pragma unroll
@@ -177,10 +186,12 @@ bool eq2_args(const cm_camera* cam, const float* rho, const float* ego, int32_t 
 
 int eq2_tiles(const cm_camera* cam) { return (int)(((size_t)cam->width * cam->height + kEq2Tile - 1) / kEq2Tile); }
 
-int grid_for(int tiles)
+// blocks of a launch over `units` units of work: at most `per_sm` resident
+// blocks on every SM, the units distributed over them in whole rounds
+int grid_for(int units, int per_sm)
 {
-    const int cap = sm_count_current() * 8;
-    return tiles < cap ? (tiles < 1 ? 1 : tiles) : cap;
+    const int cap = sm_count_current() * per_sm;
+    return units < cap ? (units < 1 ? 1 : units) : cap;
 }
 
 }  // namespace
@@ -195,9 +206,9 @@ int cm_flow_eq2(const cm_camera* cam, const float* inv_depth, const float* ego6,
     cmk::Eq2Args a;
     if (!flow_out || !cmk::eq2_args(cam, inv_depth, ego6, nb, dt_bin, scale, a)) return CM_EINVAL;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    const int grid = cmk::grid_for((int)(((size_t)cam->width * cam->height + cmk::kEq2Threads - 1) / cmk::kEq2Threads));
+    const int tiles = (int)(((size_t)cam->width * cam->height + cmk::kEq2Threads - 1) / cmk::kEq2Threads);
     cmk::KernelScope ks("k_flow_eq2", s);
-    cmk::k_flow_eq2<<<grid, cmk::kEq2Threads, 0, s>>>(a, reinterpret_cast<float2*>(flow_out));
+    cmk::k_flow_eq2<<<cmk::grid_for(tiles, 8), cmk::kEq2Threads, 0, s>>>(a, reinterpret_cast<float2*>(flow_out));
     return cudaGetLastError() == cudaSuccess ? CM_OK : CM_ECUDA;
 }
 
@@ -224,7 +235,7 @@ int cm_flow_eq2_backward(const cm_camera* cam, const float* inv_depth, const flo
     float* part = static_cast<float*>(scratch);
     {
         cmk::KernelScope ks("k_flow_eq2_grad", s);
-        cmk::k_flow_eq2_grad<<<cmk::grid_for(tiles), cmk::kEq2Threads, 0, s>>>(
+        cmk::k_flow_eq2_grad<<<cmk::grid_for(tiles, 3), cmk::kEq2Threads, 0, s>>>(
             a, reinterpret_cast<const float2*>(dflow), dinv_depth, part, tiles);
     }
     {

@@ -27,6 +27,7 @@ constexpr int kGeoThreads = 256;
 constexpr int kGeoPerThread = 4;
 constexpr int kGeoTile = kGeoThreads * kGeoPerThread;
 constexpr int kGeoPartials = 12;  // dL/dt (3) and dL/dR = sum dL/dP X^T (9)
+static_assert(kGeoPartials == 12, "the backward reduces its partials with warp_sum12");
 
 struct GeoArgs {
     int32_t W, H;
@@ -92,6 +93,20 @@ __device__ __forceinline__ GeoPixel geo_pixel(const GeoArgs& g, const Pose& p, c
     return r;
 }
 
+// adds a to row[x0] and b to row[x1] (x1 = x0 + 1, or x0 at the right border):
+// one 8-byte reduction when the pair is contiguous and 8-byte aligned (the row
+// base of a W-wide image, element 0 of the image 8-byte aligned)
+__device__ __forceinline__ void push_row(float* row, int x0, int x1, float a, float b)
+{
+    float* q = row + x0;
+    if (x1 == x0 + 1 && (reinterpret_cast<uintptr_t>(q) & 7) == 0) {
+        red_add_v2(q, a, b);
+    } else {
+        atomicAdd(q, a);
+        atomicAdd(row + x1, b);
+    }
+}
+
 __device__ __forceinline__ void pixel_uv32(uint32_t i, int W, int& u, int& v)
 {
     const uint32_t q = i / (uint32_t)W;
@@ -143,7 +158,14 @@ __global__ void __launch_bounds__(64) k_geo_forward_final(const float* __restric
     const int c = threadIdx.x >> 5, l = threadIdx.x & 31;
     __shared__ double tot[2];
     double s = 0.0;
-    for (int i = l; i < ntiles; i += 32) s += (double)part[(size_t)i * 2 + c];
+    // lane l adds tiles l, l + 32, ... in that order, eight loads in flight
+    for (int i0 = l; i0 < ntiles; i0 += 32 * 8) {
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = i0 + 32 * u < ntiles ? part[(size_t)(i0 + 32 * u) * 2 + c] : 0.0f;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s += (double)v[u];
+    }
     s = warp_sum(s);
     if (l == 0) tot[c] = s;
     __syncthreads();
@@ -211,15 +233,15 @@ __global__ void __launch_bounds__(kGeoThreads) k_geo_backward(GeoArgs g, const f
             drho0[i] = -q.Z * q.Z * dZ;
             // b = sum_c w_c / rho1_c
             const float bx = 1.0f - r.ax, by = 1.0f - r.ay;
-            atomicAdd(drho1 + (size_t)r.iy * g.W + r.ix, -dfb * bx * by * r.D00 * r.D00);
-            atomicAdd(drho1 + (size_t)r.iy * g.W + r.ix1, -dfb * r.ax * by * r.D10 * r.D10);
-            atomicAdd(drho1 + (size_t)r.iy1 * g.W + r.ix, -dfb * bx * r.ay * r.D01 * r.D01);
-            atomicAdd(drho1 + (size_t)r.iy1 * g.W + r.ix1, -dfb * r.ax * r.ay * r.D11 * r.D11);
+            push_row(drho1 + (size_t)r.iy * g.W, r.ix, r.ix1, -dfb * bx * by * r.D00 * r.D00,
+                     -dfb * r.ax * by * r.D10 * r.D10);
+            push_row(drho1 + (size_t)r.iy1 * g.W, r.ix, r.ix1, -dfb * bx * r.ay * r.D01 * r.D01,
+                     -dfb * r.ax * r.ay * r.D11 * r.D11);
         }
+        warp_sum12(c);
+        if ((l & 7) == 0) {
 #pragma unroll
-        for (int m = 0; m < kGeoPartials; ++m) {
-            const float s = warp_sum(c[m]);
-            if (l == 0) red[w][m] = s;
+            for (int j = 0; j < 3; ++j) red[w][3 * (l >> 3) + j] = c[j];
         }
         __syncthreads();
         if (threadIdx.x < kGeoPartials) {
@@ -237,7 +259,15 @@ __global__ void __launch_bounds__(kGeoPartials * 32) k_geo_backward_final(GeoArg
     __shared__ double sum[kGeoPartials];
     const int c = threadIdx.x >> 5, l = threadIdx.x & 31;
     double s = 0.0;
-    for (int i = l; i < ntiles; i += 32) s += (double)part[(size_t)i * kGeoPartials + c];
+    // lane l adds tiles l, l + 32, ... in that order, eight loads in flight
+    for (int i0 = l; i0 < ntiles; i0 += 32 * 8) {
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            v[u] = i0 + 32 * u < ntiles ? part[(size_t)(i0 + 32 * u) * kGeoPartials + c] : 0.0f;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s += (double)v[u];
+    }
     s = warp_sum(s);
     if (l == 0) sum[c] = s;
     __syncthreads();

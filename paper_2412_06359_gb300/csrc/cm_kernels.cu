@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(1024) k_loss_final(Win d) { loss_final_window(
 // S7: dL/d(rho) per pixel and the six dL/d(ego) sums (fixed-order reduction)
 __global__ void __launch_bounds__(256) k_depth_ego(Win d) { depth_ego_tile(d, blockIdx.x, gridDim.x); }
 
-__global__ void __launch_bounds__(192) k_depth_ego_final(Win d) { depth_ego_final_window(d); }
+__global__ void __launch_bounds__(192) k_depth_ego_final(Win d) { depth_ego_final_window(d, d.pix_tiles); }
 
 // ---------------------------------------------------------------------------
 // launchers

@@ -85,6 +85,31 @@ __device__ __forceinline__ Pose pose_of(const float* __restrict__ e, float dt)
 }
 
 // the camera-frame point of pixel (u, v) and its normalised coordinates
+// Sums of c[0..11] over the 32 lanes of a warp by recursive halving (each lane
+// passes on the half it does not keep: 6 + 3 exchanges, then three butterfly
+// steps on 3 values; 18 shuffles instead of 60).  Afterwards c[0..2] of lane l
+// hold the sums of elements 3 (l >> 3) .. 3 (l >> 3) + 2.
+__device__ __forceinline__ void warp_sum12(float (&c)[12])
+{
+    const int l = threadIdx.x & 31;
+    const bool h16 = (l & 16) != 0, h8 = (l & 8) != 0;
+    float h[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        const float keep = h16 ? c[6 + j] : c[j], give = h16 ? c[j] : c[6 + j];
+        h[j] = keep + __shfl_xor_sync(0xffffffffu, give, 16);
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const float keep = h8 ? h[3 + j] : h[j], give = h8 ? h[j] : h[3 + j];
+        c[j] = keep + __shfl_xor_sync(0xffffffffu, give, 8);
+    }
+#pragma unroll
+    for (int o = 4; o >= 1; o >>= 1)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) c[j] += __shfl_xor_sync(0xffffffffu, c[j], o);
+}
+
 struct PixelPoint {
     float xn, yn, Z;
 };

@@ -194,3 +194,31 @@ def test_batch_of_motion_consistent_windows_matches_oracle():
             g = _batch_result(plan, i)
             g["dflow"] = g["dflow"][None]
             assert_parity(g, run_oracle(w))
+
+
+def test_batch_odd_sized_images_and_requested_dflow():
+    # images with an odd pixel count (the loss pass then reads single pixels,
+    # not 16-byte pairs) among even ones, depth and flow windows mixed; depth
+    # windows also return dL/dflow when asked for it
+    cm = gpu_lib()
+    rng = np.random.default_rng(41)
+    wins = []
+    for i, (W, H) in enumerate([(97, 61), (96, 72), (81, 45), (131, 99)]):
+        n = 2500 + 700 * i
+        if i == 2:
+            ev = synth.uniform_events(rng, W, H, n)
+            flow = synth.sinusoid_flow(rng, W, H, 3.0)[None]
+            wins.append(synth.Window(synth.Camera(W, H, 60.0, 60.0, W / 2, H / 2), ev, 10, synth.REF_ALL,
+                                     flow=flow))
+        else:
+            wins.append(synth.depth_window(np.random.default_rng(4100 + i), W, H, n, nbins=10))
+    plan = cm.BatchPlan(_dev_windows(cm, wins), cm.loss_cfg(10, cm.REF_ALL, cm.SPLAT_ATOMIC), want_dflow=True)
+    for rep in range(2):
+        plan.run()
+        for i, w in enumerate(wins):
+            g = _batch_result(plan, i)
+            o = run_oracle(w)
+            if w.flow is not None:
+                g["dflow"] = g["dflow"][None]
+            assert "dflow" in g and "dflow" in o
+            assert_parity(g, o)  # dflow included
