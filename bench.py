@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--store-warps", type=int, default=0, choices=[0, 1],
                     help="1: the forward stores the trajectory points for the backward (no recompute)")
     ap.add_argument("--serve", action="store_true", help="run the serving workload instead (one line per rate)")
+    ap.add_argument("--other-kernels", action="store_true",
+                    help="time only the kernels beside the CM path (Eq. 2 flow, geometry loss, event frame)")
     ap.add_argument("--serve-scales", default="0.25,0.5,1.0", help="arrival-rate multipliers of 100 Hz per stream")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--serve-pool", type=int, default=2, help="pre-generated windows per stream")
@@ -799,10 +801,21 @@ def run_serve(args):
         print(json.dumps(line), flush=True)
 
 
+def run_other(args):
+    """One JSON line: the kernels beside the CM path on a 1280x720 sensor."""
+    import torch
+    dev = torch.device("cuda", 0)
+    peak, kind = measured_peak()
+    out = measure_other_kernels(dev, peak)
+    print(json.dumps({"other_kernels": out, "peak_kind": kind}), flush=True)
+
+
 def main():
     args = parse()
     if args.serve:
         run_serve(args)
+    elif args.other_kernels:
+        run_other(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

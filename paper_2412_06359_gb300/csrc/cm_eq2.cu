@@ -34,11 +34,12 @@ struct Eq2Args {
     const float* ego;   // [nb][6]
 };
 
-// flow of every bin at every pixel; the block's poses are built once in shared memory
+// flow of every bin at every pixel; the block's poses are built once in shared
+// memory, packed for the displacement (the pixel loop is instruction-bound)
 __global__ void __launch_bounds__(kEq2Threads) k_flow_eq2(Eq2Args a, float2* __restrict__ flow)
 {
-    __shared__ Pose poses[CM_MAX_BINS];
-    if (threadIdx.x < a.nb) poses[threadIdx.x] = pose_of(a.ego + 6 * threadIdx.x, a.dt);
+    __shared__ PoseD poses[CM_MAX_BINS];
+    if (threadIdx.x < a.nb) poses[threadIdx.x] = pack_displacement(pose_of(a.ego + 6 * threadIdx.x, a.dt));
     __syncthreads();
     const uint32_t HW = (uint32_t)a.W * (uint32_t)a.H;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < HW; i += gridDim.x * blockDim.x) {

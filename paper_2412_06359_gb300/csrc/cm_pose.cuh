@@ -124,21 +124,49 @@ __device__ __forceinline__ PixelPoint pixel_point(int u, int v, float rho, float
 }
 
 // the displacement of the pixel and the depth P2 of its moved point (the
-// sequence of the contract above)
-__device__ __forceinline__ float2 displacement(const Pose& p, const PixelPoint& q, float fx, float fy, float& P2)
+// sequence of the contract above), from the thirteen entries of the pose it uses
+__device__ __forceinline__ float2 displacement_of(float Ad0, float R1, float R2, float R3, float Ad1, float R5,
+                                                  float R6, float R7, float Ad2, float R8, float t0, float t1,
+                                                  float t2, const PixelPoint& q, float fx, float fy, float& P2)
 {
     const float xn = q.xn, yn = q.yn;
-    const float c00 = __fmaf_rn(-xn, p.R[6], p.Ad[0]), c01 = __fmaf_rn(-xn, p.R[7], p.R[1]);
-    const float c02 = __fmaf_rn(-xn, p.Ad[2], p.R[2]);
-    const float c10 = __fmaf_rn(-yn, p.R[6], p.R[3]), c11 = __fmaf_rn(-yn, p.R[7], p.Ad[1]);
-    const float c12 = __fmaf_rn(-yn, p.Ad[2], p.R[5]);
+    const float c00 = __fmaf_rn(-xn, R6, Ad0), c01 = __fmaf_rn(-xn, R7, R1);
+    const float c02 = __fmaf_rn(-xn, Ad2, R2);
+    const float c10 = __fmaf_rn(-yn, R6, R3), c11 = __fmaf_rn(-yn, R7, Ad1);
+    const float c12 = __fmaf_rn(-yn, Ad2, R5);
     const float s0 = __fmaf_rn(c00, xn, __fmaf_rn(c01, yn, c02));
     const float s1 = __fmaf_rn(c10, xn, __fmaf_rn(c11, yn, c12));
-    const float e0 = __fmaf_rn(q.Z, s0, __fmaf_rn(-xn, p.t[2], p.t[0]));
-    const float e1 = __fmaf_rn(q.Z, s1, __fmaf_rn(-yn, p.t[2], p.t[1]));
-    P2 = __fmaf_rn(q.Z, __fmaf_rn(p.R[6], xn, __fmaf_rn(p.R[7], yn, p.R[8])), p.t[2]);
+    const float e0 = __fmaf_rn(q.Z, s0, __fmaf_rn(-xn, t2, t0));
+    const float e1 = __fmaf_rn(q.Z, s1, __fmaf_rn(-yn, t2, t1));
+    P2 = __fmaf_rn(q.Z, __fmaf_rn(R6, xn, __fmaf_rn(R7, yn, R8)), t2);
     const float iz = __fdiv_rn(1.0f, P2);
     return make_float2(__fmul_rn(fx, __fmul_rn(e0, iz)), __fmul_rn(fy, __fmul_rn(e1, iz)));
+}
+
+__device__ __forceinline__ float2 displacement(const Pose& p, const PixelPoint& q, float fx, float fy, float& P2)
+{
+    return displacement_of(p.Ad[0], p.R[1], p.R[2], p.R[3], p.Ad[1], p.R[5], p.R[6], p.R[7], p.Ad[2], p.R[8], p.t[0],
+                           p.t[1], p.t[2], q, fx, fy, P2);
+}
+
+// The entries of a pose the displacement uses, packed for three 16-byte and
+// one 4-byte shared-memory loads: (Ad0, R01, R02, R10), (Ad1, R12, R20, R21),
+// (Ad2, R22, t0, t1), t2.
+struct PoseD {
+    float4 a, b, c;
+    float t2;
+};
+
+__device__ __forceinline__ PoseD pack_displacement(const Pose& p)
+{
+    return PoseD{make_float4(p.Ad[0], p.R[1], p.R[2], p.R[3]), make_float4(p.Ad[1], p.R[5], p.R[6], p.R[7]),
+                 make_float4(p.Ad[2], p.R[8], p.t[0], p.t[1]), p.t[2]};
+}
+
+__device__ __forceinline__ float2 displacement(const PoseD& p, const PixelPoint& q, float fx, float fy, float& P2)
+{
+    return displacement_of(p.a.x, p.a.y, p.a.z, p.a.w, p.b.x, p.b.y, p.b.z, p.b.w, p.c.x, p.c.y, p.c.z, p.c.w, p.t2,
+                           q, fx, fy, P2);
 }
 
 __device__ __forceinline__ void transform(const Pose& p, const PixelPoint& q, float X[3], float P[3])
