@@ -80,10 +80,10 @@ __device__ __forceinline__ GeoPixel geo_pixel(const GeoArgs& g, const Pose& p, c
     // branch of |a - b|, decided the same way by the CPU oracle)
     r.ax = __fsub_rn(xp, fx0);
     r.ay = __fsub_rn(yp, fy0);
-    r.D00 = __fdiv_rn(1.0f, __ldg(g.rho1 + (size_t)r.iy * g.W + r.ix));
-    r.D10 = __fdiv_rn(1.0f, __ldg(g.rho1 + (size_t)r.iy * g.W + r.ix1));
-    r.D01 = __fdiv_rn(1.0f, __ldg(g.rho1 + (size_t)r.iy1 * g.W + r.ix));
-    r.D11 = __fdiv_rn(1.0f, __ldg(g.rho1 + (size_t)r.iy1 * g.W + r.ix1));
+    r.D00 = __frcp_rn(__ldg(g.rho1 + (size_t)r.iy * g.W + r.ix));
+    r.D10 = __frcp_rn(__ldg(g.rho1 + (size_t)r.iy * g.W + r.ix1));
+    r.D01 = __frcp_rn(__ldg(g.rho1 + (size_t)r.iy1 * g.W + r.ix));
+    r.D11 = __frcp_rn(__ldg(g.rho1 + (size_t)r.iy1 * g.W + r.ix1));
     const float bx = __fsub_rn(1.0f, r.ax), by = __fsub_rn(1.0f, r.ay);
     const float w00 = __fmul_rn(bx, by), w10 = __fmul_rn(r.ax, by), w01 = __fmul_rn(bx, r.ay);
     const float w11 = __fmul_rn(r.ax, r.ay);

@@ -222,3 +222,17 @@ def test_batch_odd_sized_images_and_requested_dflow():
                 g["dflow"] = g["dflow"][None]
             assert "dflow" in g and "dflow" in o
             assert_parity(g, o)  # dflow included
+
+
+@pytest.mark.parametrize("B,ref_mode", [(32, synth.REF_ALL), (20, synth.REF_ALL), (32, synth.REF_END),
+                                        (1, synth.REF_END), (1, synth.REF_ALL)])
+def test_batch_bin_counts_up_to_the_maximum(B, ref_mode):
+    # every event-kernel instantiation (1, 10, 20 and 32 bins) and the loss
+    # pass's reference rounds (R = 1, 2, 21, 33) in the batched plan
+    cm = gpu_lib()
+    wins = [synth.depth_window(np.random.default_rng(5200 + i), W, H, n, nbins=B, ref_mode=ref_mode)
+            for i, (W, H, n) in enumerate([(120, 90, 3000), (97, 61, 1500), (160, 100, 4000)])]
+    plan = cm.BatchPlan(_dev_windows(cm, wins), cm.loss_cfg(B, ref_mode, cm.SPLAT_ATOMIC))
+    plan.run()
+    for i, w in enumerate(wins):
+        assert_parity(_batch_result(plan, i), run_oracle(w))
