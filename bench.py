@@ -46,7 +46,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="bound of the CPU oracle sample")
     ap.add_argument("--schedule", default="auto",
-                    help="batch schedule 'chains,windows_per_kernel,tile_grouping' (e.g. 4,2,0), or 'auto' to autotune")
+                    help="batch schedule 'chains,windows_per_kernel,grouping' (grouping 0: given order, 1: 32x32 "
+                         "tiles, 2: 32-row bands; e.g. 6,2,2), or 'auto' to autotune")
     ap.add_argument("--events", default="iid", choices=["iid", "motion"],
                     help="iid: the headline workload; motion: motion-consistent events with their true flow "
                          "(flow input, many events per pixel after the warp: the contention stress variant)")
@@ -176,6 +177,10 @@ def kernel_bytes(name: str, n: int, hw: int, R: int, model: str) -> float:
     if base == "k_grad":
         return 4.0 * hw + (40.0 * hw if iwe else 0.0)
     return 0.0
+
+
+# the batch schedule's event grouping modes (cm_batch_schedule.bin)
+GROUPING = ("given order", "32x32 tiles", "32-row bands")
 
 
 def measured_peak():
@@ -498,7 +503,7 @@ def run_ours(args):
                        "backward": "stored warps" if args.store_warps else "recompute",
                        "path": "batched plan replayed from a CUDA graph",
                        "schedule": {"chains": schedule[0], "windows_per_kernel": schedule[1],
-                                    "tile_grouping": bool(schedule[2])},
+                                    "grouping": GROUPING[schedule[2]]},
                        "l2": "per-step IWE working set %.2f GB > L2 (no flush needed)" % (len(wins) * R * hw * 16 / 1e9)},
             "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
             "plain": plain, "splat_compare": splat_cmp, "roofline": roof, "roofline_iwe": roof_iwe,

@@ -322,16 +322,20 @@ int cm_batch_run(cm_batch* plan, void* stream);
  * the graph, each chain one group after another; group 0 (with chains 1) puts
  * every window in each kernel.  Few windows in flight keep their images of
  * warped events in L2; several chains overlap each other's tails.  With `bin`
- * the events of each window are first grouped by 32x32-pixel tile (two extra
- * kernels), so that the events of a block touch a compact region of the flow
- * and of the images; windows that do not fit the plan's grouping memory (sized
- * for the windows it was created with) stay ungrouped.  Every schedule gives
+ * the events of each window are first regrouped by two extra kernels into a
+ * copy in the plan's memory: bin 1 by 32x32-pixel tile (unordered within a
+ * tile), bin 2 by band of 32 image rows with a counting sort that keeps the
+ * order of 4096-event super-chunks within a band (with time-ordered input the
+ * events of a warp then share their bin).  Either way the events in flight touch a
+ * compact region of the flow and of the images.  Windows that do not fit the
+ * plan's grouping memory (sized for the windows it was created with), and
+ * sensors taller than 4096 rows in bin 2, stay ungrouped.  Every schedule gives
  * the same results up to the order of the floating-point reductions.
  * Default: chains 2, group 1, bin 0. */
 typedef struct {
     int32_t chains;  /* 1..8 */
     int32_t group;   /* windows per kernel; 0 = all */
-    int32_t bin;     /* 1: group events by tile first */
+    int32_t bin;     /* 0: events in their given order; 1: grouped by tile; 2: by row band, stable */
 } cm_batch_schedule;
 int cm_batch_set_schedule(cm_batch* plan, const cm_batch_schedule* schedule);
 int cm_batch_get_schedule(const cm_batch* plan, cm_batch_schedule* schedule);

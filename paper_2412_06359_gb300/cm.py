@@ -416,7 +416,8 @@ class BatchPlan:
     def set_schedule(self, chains: int, group: int, bin: int = 0):
         """chains: concurrent kernel chains; group: windows per kernel (0: one
         kernel over every window); bin: 1 to group each window's events by
-        32x32 pixel tile before the splat."""
+        32x32 pixel tile before the splat, 2 by band of 32 rows keeping the
+        order of 4096-event super-chunks within a band."""
         C.cm_batch_set_schedule(self.handle, chains, group, bin)
 
     def schedule(self) -> tuple[int, int, int]:

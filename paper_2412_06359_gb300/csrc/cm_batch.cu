@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(256) k_prep_batch(const BatchHdr* h, const Win
             pixel_uv(i, d.W, u, v);
             build_quad(d, u, v);
         }
-        if (d.tile_cnt) {
+        if (d.tile_cnt && !d.band_rows) {
             const int nt = d.ntx * d.nty;
             for (int i = ti * blockDim.x + threadIdx.x; i <= nt; i += (int)stride) {
                 d.tile_cnt[i] = 0;
@@ -153,6 +153,8 @@ __device__ __forceinline__ int block_scan_excl(int v, int* total)
 // global counters once per tile, not once per event.
 constexpr int kSuperChunk = 4096;
 constexpr int kMaxBinTiles = 2048;  // windows with more tiles are not grouped
+constexpr int kBandRows = 32;       // rows per band of the stable band grouping
+constexpr int kMaxBands = 128;      // windows with more bands (H > 4096) are not grouped
 
 __device__ __forceinline__ void count_tiles(const Win& d, long long e0, long long e1, int* hist)
 {
@@ -163,8 +165,103 @@ __device__ __forceinline__ void count_tiles(const Win& d, long long e0, long lon
     __syncthreads();
 }
 
-// binning, pass 1: events per tile; the block finishing a window's last
-// super-chunk turns the counts into tile starts and the cursors
+__device__ __forceinline__ int band_of(const Win& d, int y) { return min(max(y, 0), d.H - 1) / d.band_rows; }
+
+__device__ __forceinline__ int super_chunks(const Win& d) { return (int)((d.n + kSuperChunk - 1) / kSuperChunk); }
+
+constexpr int kRounds = kSuperChunk / kEventThreads;  // 256-event rounds of a super-chunk
+static_assert(kRounds * kEventThreads == kSuperChunk, "a super-chunk is whole rounds of a block");
+
+// band grouping, pass 1 for super-chunk sc = [e0, e1): its events per band,
+// column sc of the band-major [band][super-chunk] table (warp-aggregated
+// shared-memory counts; the rows of all rounds are loaded first, so the block
+// waits on memory once).  The block completing a window's last super-chunk
+// scans the whole table in band-major order: entry (b, sc) becomes the first
+// slot of super-chunk sc's events of band b, so the bands keep the order of
+// the super-chunks.
+__device__ __forceinline__ void band_count(const Win& d, int sc, long long e0, long long e1, int* hist)
+{
+    const int nb = d.nty, nsc = super_chunks(d), lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) hist[i] = 0;
+    int16_t yr[kRounds];
+#pragma unroll
+    for (int r = 0; r < kRounds; ++r) {
+        const long long k = e0 + r * kEventThreads + threadIdx.x;
+        yr[r] = k < e1 ? d.y[k] : (int16_t)0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kRounds; ++r) {
+        const long long k = e0 + r * kEventThreads + threadIdx.x;
+        const int b = k < e1 ? band_of(d, yr[r]) : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, b);
+        if (b >= 0 && lane == __ffs(peers) - 1) atomicAdd(hist + b, __popc(peers));
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) d.tile_cnt[(size_t)i * nsc + sc] = hist[i];
+    if (last_tile_done(d.sync + 2, nsc)) {
+        const int total = nb * nsc;
+        int carry = 0;
+        for (int base = 0; base < total; base += blockDim.x) {
+            const int i = base + threadIdx.x;
+            const int v = i < total ? __ldcg(d.tile_cnt + i) : 0;  // other blocks' columns, from L2
+            int tot = 0;
+            const int ex = block_scan_excl(v, &tot);
+            if (i < total) d.tile_cnt[i] = carry + ex;
+            carry += tot;
+        }
+        __syncthreads();
+    }
+}
+
+// band grouping, pass 2 for super-chunk sc: its events (all rounds loaded
+// first) go to the slots of their band that the count pass reserved for this
+// super-chunk, so the bands keep the order of the super-chunks; within one
+// super-chunk's share of a band (4096 consecutive events, a small part of the
+// window's time span) a warp takes a run of slots per band through one
+// shared-memory atomic (lanes in order), the warps and rounds in any order
+__device__ __forceinline__ void band_scatter(const Win& d, int sc, long long e0, long long e1)
+{
+    __shared__ int cur[kMaxBands];
+    const int nb = d.nty, nsc = super_chunks(d), lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) cur[i] = d.tile_cnt[(size_t)i * nsc + sc];
+    int16_t xr[kRounds], yr[kRounds];
+    float tr[kRounds];
+    int8_t pr[kRounds];
+#pragma unroll
+    for (int r = 0; r < kRounds; ++r) {
+        const long long k = e0 + r * kEventThreads + threadIdx.x;
+        const bool ok = k < e1;
+        xr[r] = ok ? d.x[k] : (int16_t)0;
+        yr[r] = ok ? d.y[k] : (int16_t)0;
+        tr[r] = ok ? __ldg(d.t + k) : 0.0f;
+        pr[r] = ok ? d.p[k] : (int8_t)0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kRounds; ++r) {
+        const long long k = e0 + r * kEventThreads + threadIdx.x;
+        const bool ok = k < e1;
+        const int b = ok ? band_of(d, yr[r]) : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, b);
+        const int leader = __ffs(peers) - 1;
+        int first = 0;
+        if (ok && lane == leader) first = atomicAdd(cur + b, __popc(peers));
+        first = __shfl_sync(0xffffffffu, first, leader);
+        if (ok) {
+            const int pos = first + __popc(peers & ((1u << lane) - 1u));
+            d.rx[pos] = xr[r];
+            d.ry[pos] = yr[r];
+            d.rt[pos] = tr[r];
+            d.rp[pos] = pr[r];
+        }
+    }
+    __syncthreads();
+}
+
+// binning, pass 1: events per tile (or per band and super-chunk); the block
+// finishing a window's last super-chunk turns the counts into tile starts and
+// the cursors (or into stable band offsets)
 __global__ void __launch_bounds__(kEventThreads) k_bin_count_batch(const BatchHdr* h, const Win* tab,
                                                                     const long long* sstart, int w0, int w1)
 {
@@ -178,6 +275,10 @@ __global__ void __launch_bounds__(kEventThreads) k_bin_count_batch(const BatchHd
         if (!d.tile_cnt) continue;
         const long long e0 = (c - sstart[w]) * kSuperChunk;
         const long long e1 = e0 + kSuperChunk < d.n ? e0 + kSuperChunk : d.n;
+        if (d.band_rows) {
+            band_count(d, (int)(c - sstart[w]), e0, e1, hist);
+            continue;
+        }
         count_tiles(d, e0, e1, hist);
         const int nt0 = d.ntx * d.nty;
         for (int i = threadIdx.x; i < nt0; i += blockDim.x)
@@ -204,7 +305,8 @@ __global__ void __launch_bounds__(kEventThreads) k_bin_count_batch(const BatchHd
 }
 
 // binning, pass 2: a block reserves, per tile, one range of slots for its
-// super-chunk's events (one global atomic per tile) and places them there
+// super-chunk's events (one global atomic per tile) and places them there (or
+// places them at their stable band slots)
 __global__ void __launch_bounds__(kEventThreads) k_bin_scatter_batch(const BatchHdr* h, const Win* tab,
                                                                       const long long* sstart, int w0, int w1)
 {
@@ -218,6 +320,10 @@ __global__ void __launch_bounds__(kEventThreads) k_bin_scatter_batch(const Batch
         if (!d.tile_cnt) continue;
         const long long e0 = (c - sstart[w]) * kSuperChunk;
         const long long e1 = e0 + kSuperChunk < d.n ? e0 + kSuperChunk : d.n;
+        if (d.band_rows) {
+            band_scatter(d, (int)(c - sstart[w]), e0, e1);
+            continue;
+        }
         count_tiles(d, e0, e1, hist);
         const int nt = d.ntx * d.nty;
         for (int i = threadIdx.x; i < nt; i += blockDim.x)
@@ -411,13 +517,16 @@ Need need_of(const cm_window* wins, int32_t nwin, const cm_loss_cfg& cfg)
     return n;
 }
 
-// device bytes of the spatial binning of a window: tile starts and cursors,
-// and the events grouped by tile
+// device bytes of the spatial grouping of a window: the count table (tile
+// starts and cursors, or the band x super-chunk offsets, whichever is larger)
+// and the grouped events
 size_t bin_bytes(int W, int H, int64_t n)
 {
     const size_t nt = (size_t)((W + cmk::kBinTile - 1) / cmk::kBinTile) * ((H + cmk::kBinTile - 1) / cmk::kBinTile);
-    return up256((2 * nt + 1) * sizeof(int32_t)) + 2 * up256(2 * (size_t)n) + up256(4 * (size_t)n) +
-           up256((size_t)n);
+    const size_t nband = (size_t)((H + cmk::kBandRows - 1) / cmk::kBandRows) *
+                         (size_t)((n + cmk::kSuperChunk - 1) / cmk::kSuperChunk);
+    const size_t table = 2 * nt + 1 > nband ? 2 * nt + 1 : nband;
+    return up256(table * sizeof(int32_t)) + 2 * up256(2 * (size_t)n) + up256(4 * (size_t)n) + up256((size_t)n);
 }
 
 // a window's own scratch: the per-window buffers, one after another
@@ -651,18 +760,25 @@ int stage_windows(cm_batch* b, const cm_window* wins, int32_t nwin)
             d.dego_part = reinterpret_cast<float*>(base + b->L.dego + o_dego);
             o_dego += (size_t)d.loss_tiles * 6 * sizeof(float);
             d.sync = reinterpret_cast<int32_t*>(base + b->L.sync) + kSyncInts * i;
-            // events grouped by 32x32 tile, while the plan's binning memory lasts
+            // events grouped by 32x32 tile (bin 1) or by 32-row band in their given
+            // order (bin 2), while the plan's grouping memory lasts
             const size_t bb = bin_bytes(d.W, d.H, d.n);
-            const int ntiles = ((d.W + cmk::kBinTile - 1) / cmk::kBinTile) * ((d.H + cmk::kBinTile - 1) / cmk::kBinTile);
-            if (b->sched.bin && d.n > 0 && ntiles <= cmk::kMaxBinTiles && o_bins + bb <= b->capn.bins) {
+            const bool bands = b->sched.bin == 2;
+            const int tx = bands ? 1 : (d.W + cmk::kBinTile - 1) / cmk::kBinTile;
+            const int ty = bands ? (d.H + cmk::kBandRows - 1) / cmk::kBandRows : (d.H + cmk::kBinTile - 1) / cmk::kBinTile;
+            const bool fits = bands ? ty <= cmk::kMaxBands : tx * ty <= cmk::kMaxBinTiles;
+            if (b->sched.bin && d.n > 0 && fits && o_bins + bb <= b->capn.bins) {
                 char* q = base + b->L.bins + o_bins;
                 o_bins += bb;
-                d.ntx = (d.W + cmk::kBinTile - 1) / cmk::kBinTile;
-                d.nty = (d.H + cmk::kBinTile - 1) / cmk::kBinTile;
+                d.ntx = tx;
+                d.nty = ty;
+                d.band_rows = bands ? cmk::kBandRows : 0;
                 const size_t nt = (size_t)d.ntx * d.nty;
                 d.tile_cnt = reinterpret_cast<int32_t*>(q);
-                d.tile_cur = d.tile_cnt + nt + 1;
-                q += up256((2 * nt + 1) * sizeof(int32_t));
+                d.tile_cur = bands ? nullptr : d.tile_cnt + nt + 1;
+                const size_t nband = (size_t)ty * ((d.n + cmk::kSuperChunk - 1) / cmk::kSuperChunk);
+                const size_t table = 2 * nt + 1 > nband ? 2 * nt + 1 : nband;
+                q += up256(table * sizeof(int32_t));
                 d.rx = reinterpret_cast<int16_t*>(q);
                 q += up256(2 * (size_t)d.n);
                 d.ry = reinterpret_cast<int16_t*>(q);
@@ -1053,7 +1169,7 @@ int cm_batch_set_schedule(cm_batch* b, const cm_batch_schedule* s)
 {
     if (!b || !s || s->chains < 1 || s->chains > kMaxChains || s->group < 0) return CM_EINVAL;
     if (s->group == 0 && s->chains != 1) return CM_EINVAL;
-    if (s->bin != 0 && s->bin != 1) return CM_EINVAL;
+    if (s->bin < 0 || s->bin > 2) return CM_EINVAL;
     return apply_schedule(b, *s);
 }
 
@@ -1084,10 +1200,11 @@ int cm_batch_autotune(cm_batch* b, void* stream, cm_batch_schedule* chosen)
         }
     }
     std::vector<cm_batch_schedule> cand;
-    for (int bin = 0; bin < 2; ++bin)
-        for (const auto& cg : {std::pair<int, int>{1, 0}, {1, 1}, {2, 1}, {3, 1}, {4, 1}, {2, 2}, {4, 2}})
+    for (int bin = 0; bin < 3; ++bin)
+        for (const auto& cg : {std::pair<int, int>{1, 0}, {1, 1}, {2, 1}, {3, 1}, {4, 1}, {2, 2}, {4, 2}, {6, 1},
+                               {6, 2}, {8, 1}, {8, 2}})
             cand.push_back(cm_batch_schedule{cg.first, cg.second, bin});
-    if (b->nwin == 1) cand = {{1, 0, 0}, {1, 0, 1}};
+    if (b->nwin == 1) cand = {{1, 0, 0}, {1, 0, 1}, {1, 0, 2}};
     cudaEvent_t a = nullptr, z = nullptr;
     if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&z) != cudaSuccess) return CM_ECUDA;
     float best = 1e30f;

@@ -77,14 +77,17 @@ struct Win {
     float* dego_part;        // [gradient tiles][6] (pix_tiles; loss_tiles on the batched path)
     int32_t* sync;           // [4] batched path: completion counters of the loss and gradient reductions and
                              // of the binning count
-    // spatial binning (batched path; tile_cnt == nullptr: events are used in their given order)
-    int32_t* tile_cnt;       // [ntiles + 1] events per 32x32 tile, turned into tile starts by the scan
-    int32_t* tile_cur;       // [ntiles] scatter cursors
+    // spatial grouping (batched path; tile_cnt == nullptr: events are used in their given order)
+    int32_t* tile_cnt;       // tiles: [ntiles + 1] events per 32x32 tile, turned into tile starts by the scan;
+                             // bands: [nty][super-chunks] events per band and super-chunk, turned into
+                             // stable write offsets by the scan
+    int32_t* tile_cur;       // [ntiles] scatter cursors (tiles only)
     int16_t* rx;             // [n] events grouped by tile
     int16_t* ry;
     float* rt;
     int8_t* rp;
-    int32_t ntx, nty;        // tiles per row and per column
+    int32_t ntx, nty;        // tiles per row and per column (bands: 1 and the number of bands)
+    int32_t band_rows;       // 0: 32x32 tiles; else rows per band (stable grouping by band)
 };
 
 constexpr int kBinTile = 32;  // px, side of the tiles events are grouped by

@@ -92,6 +92,24 @@ def test_batch_equals_plain_path_on_the_640x480_windows():
         assert rel_l2(g["dego"], p["dego"]) <= GRAD_RTOL_L2
 
 
+def test_band_grouping_on_the_640x480_windows_equals_the_plain_path():
+    # bin 2: each window's events regrouped by 32-row band with a counting
+    # sort over many 4096-event super-chunks (up to ~120 per window)
+    cm = gpu_lib()
+    wins = synth.batch_windows(4)
+    plan = cm.BatchPlan(_dev_windows(cm, wins), cm.loss_cfg(10, cm.REF_ALL, cm.SPLAT_ATOMIC))
+    plan.set_schedule(2, 1, 2)
+    for _ in range(2):
+        plan.run()
+    for i, w in enumerate(wins):
+        g = _batch_result(plan, i)
+        p = run_gpu(w)
+        assert np.array_equal(g["nnz_r"], p["nnz_r"])
+        assert abs(g["loss"] - p["loss"]) <= LOSS_RTOL * abs(p["loss"])
+        assert rel_l2(g["dinv_depth"], p["dinv_depth"]) <= GRAD_RTOL_L2
+        assert rel_l2(g["dego"], p["dego"]) <= GRAD_RTOL_L2
+
+
 def test_batch_set_windows_reuses_the_graph():
     import torch
     cm = gpu_lib()
@@ -142,7 +160,7 @@ def test_batch_profiling_records_every_phase():
 
 
 @pytest.mark.parametrize("chains,group,bin", [(1, 0, 0), (1, 1, 0), (2, 1, 0), (3, 2, 0), (4, 1, 0),
-                                              (1, 0, 1), (2, 1, 1), (3, 2, 1)])
+                                              (1, 0, 1), (2, 1, 1), (3, 2, 1), (1, 0, 2), (2, 1, 2), (4, 2, 2)])
 def test_every_schedule_gives_the_same_results(chains, group, bin):
     cm = gpu_lib()
     wins = _mixed_windows(7, 21)
@@ -161,7 +179,7 @@ def test_autotune_picks_a_schedule_and_stays_correct():
     wins = synth.batch_windows(6)
     plan = cm.BatchPlan(_dev_windows(cm, wins), cm.loss_cfg(10, cm.REF_ALL, cm.SPLAT_ATOMIC))
     chains, group, bin = plan.autotune()
-    assert 1 <= chains <= 8 and group >= 0 and bin in (0, 1)
+    assert 1 <= chains <= 8 and group >= 0 and bin in (0, 1, 2)
     assert plan.autotune() == (chains, group, bin)  # cached for this shape
     plan.run()
     for i in (0, 3):
@@ -187,7 +205,7 @@ def test_batch_of_motion_consistent_windows_matches_oracle():
     cm = gpu_lib()
     wins = [synth.motion_window(np.random.default_rng(70 + i), 160, 120, 20000 + 15000 * i) for i in range(3)]
     plan = cm.BatchPlan(_dev_windows(cm, wins), cm.loss_cfg(10, cm.REF_ALL, cm.SPLAT_ATOMIC))
-    for sched in ((2, 1, 0), (1, 0, 1)):
+    for sched in ((2, 1, 0), (1, 0, 1), (2, 1, 2)):
         plan.set_schedule(*sched)
         plan.run()
         for i, w in enumerate(wins):
