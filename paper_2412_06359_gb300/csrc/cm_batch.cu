@@ -75,43 +75,6 @@ __device__ __forceinline__ int clamp_end(const BatchHdr* h, int w1) { return w1 
 // Each kernel covers windows [w0, w1) of the table (clamped to the windows in
 // use).  Pixel passes walk per-window tiles, event passes chunks of 256 events.
 
-// zero the images of warped events and the quad accumulators of dL/dflow,
-// build the flow quads (the motion field for depth input), reset the
-// completion counters
-__global__ void __launch_bounds__(256) k_prep_batch(const BatchHdr* h, const Win* tab, const int* pstart, int w0,
-                                                    int w1)
-{
-    w1 = clamp_end(h, w1);
-    if (w0 >= w1) return;
-    const int tb = pstart[w0], te = pstart[w1];
-    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int tile = tb + blockIdx.x; tile < te; tile += gridDim.x) {
-        const int w = find_i(pstart, w0, w1, tile);
-        const Win d = tab[w];
-        const int ti = tile - pstart[w];
-        if (ti == 0 && threadIdx.x < 3) d.sync[threadIdx.x] = 0;
-        const size_t HW = plane_size(d);
-        const size_t stride = (size_t)d.pix_tiles * blockDim.x;
-        // the window's images as one flat run of 32-byte chunks (the slab is 32-byte aligned)
-        const size_t nf4 = (size_t)d.R * HW, n32 = nf4 / 2;
-        for (size_t c = (size_t)ti * blockDim.x + threadIdx.x; c < n32; c += stride) st_v8(d.iwe + 2 * c, z4, z4);
-        if ((nf4 & 1) && ti == 0 && threadIdx.x == 0) d.iwe[nf4 - 1] = z4;
-        for (size_t i = (size_t)ti * blockDim.x + threadIdx.x; i < HW; i += stride) {
-            st_v8(d.dq + i, z4, z4);
-            int u, v;
-            pixel_uv(i, d.W, u, v);
-            build_quad(d, u, v);
-        }
-        if (d.tile_cnt && !d.band_rows) {
-            const int nt = d.ntx * d.nty;
-            for (int i = ti * blockDim.x + threadIdx.x; i <= nt; i += (int)stride) {
-                d.tile_cnt[i] = 0;
-                if (i < nt) d.tile_cur[i] = 0;
-            }
-        }
-    }
-}
-
 __device__ __forceinline__ int tile_of(const Win& d, int x, int y)
 {
     const int tx = min(max(x, 0), d.W - 1) / kBinTile, ty = min(max(y, 0), d.H - 1) / kBinTile;
@@ -257,6 +220,58 @@ __device__ __forceinline__ void band_scatter(const Win& d, int sc, long long e0,
         }
     }
     __syncthreads();
+}
+
+// zero the images of warped events and the quad accumulators of dL/dflow,
+// build the flow quads (the motion field for depth input), reset the
+// completion counters.  With `bands`, the blocks first run pass 1 of the band
+// grouping (the count per band and super-chunk); it needs no zeroed state (the
+// table's columns are written whole and its completion counter returns to zero
+// when the last block has scanned the table), so it is not reset here.
+__global__ void __launch_bounds__(kEventThreads) k_prep_batch(const BatchHdr* h, const Win* tab, const int* pstart,
+                                                              const long long* sstart, int bands, int w0, int w1)
+{
+    __shared__ int hist[kMaxBands];
+    w1 = clamp_end(h, w1);
+    if (w0 >= w1) return;
+    if (bands) {
+        const long long cb = sstart[w0], ce = sstart[w1];
+        for (long long c = cb + blockIdx.x; c < ce; c += gridDim.x) {
+            const int w = find_ll(sstart, w0, w1, c);
+            const Win d = tab[w];
+            if (!d.tile_cnt || !d.band_rows) continue;
+            const long long e0 = (c - sstart[w]) * kSuperChunk;
+            const long long e1 = e0 + kSuperChunk < d.n ? e0 + kSuperChunk : d.n;
+            band_count(d, (int)(c - sstart[w]), e0, e1, hist);
+        }
+    }
+    const int tb = pstart[w0], te = pstart[w1];
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int tile = tb + blockIdx.x; tile < te; tile += gridDim.x) {
+        const int w = find_i(pstart, w0, w1, tile);
+        const Win d = tab[w];
+        const int ti = tile - pstart[w];
+        if (ti == 0 && threadIdx.x < (d.band_rows ? 2 : 3)) d.sync[threadIdx.x] = 0;
+        const size_t HW = plane_size(d);
+        const size_t stride = (size_t)d.pix_tiles * blockDim.x;
+        // the window's images as one flat run of 32-byte chunks (the slab is 32-byte aligned)
+        const size_t nf4 = (size_t)d.R * HW, n32 = nf4 / 2;
+        for (size_t c = (size_t)ti * blockDim.x + threadIdx.x; c < n32; c += stride) st_v8(d.iwe + 2 * c, z4, z4);
+        if ((nf4 & 1) && ti == 0 && threadIdx.x == 0) d.iwe[nf4 - 1] = z4;
+        for (size_t i = (size_t)ti * blockDim.x + threadIdx.x; i < HW; i += stride) {
+            st_v8(d.dq + i, z4, z4);
+            int u, v;
+            pixel_uv(i, d.W, u, v);
+            build_quad(d, u, v);
+        }
+        if (d.tile_cnt && !d.band_rows) {
+            const int nt = d.ntx * d.nty;
+            for (int i = ti * blockDim.x + threadIdx.x; i <= nt; i += (int)stride) {
+                d.tile_cnt[i] = 0;
+                if (i < nt) d.tile_cur[i] = 0;
+            }
+        }
+    }
 }
 
 // binning, pass 1: events per tile (or per band and super-chunk); the block
@@ -933,6 +948,7 @@ int capture(cm_batch* b)
         cudaStream_t s = b->streams[g.chain];
         for (int ph = 0; ph < kPhases && ok; ++ph) {
             if (!b->sched.bin && (ph == 1 || ph == 2)) continue;  // no grouping kernels
+            if (b->sched.bin == 2 && ph == 1) continue;             // the band count runs inside the prep pass
             ProfNode p{ph, nullptr, nullptr, nullptr, nullptr};
             ok = cudaEventCreate(&p.ea) == cudaSuccess && cudaEventCreate(&p.eb) == cudaSuccess;
             if (!ok) break;
@@ -946,7 +962,7 @@ int capture(cm_batch* b)
                                 : clampi(g.chunks / (cmk::kSuperChunk / cmk::kEventThreads) + (g.w1 - g.w0), 1,
                                          b->grid_events);
             switch (ph) {
-            case 0: cmk::k_prep_batch<<<gt, 256, 0, s>>>(h, tab, ps, g.w0, g.w1); break;
+            case 0: cmk::k_prep_batch<<<gt, cmk::kEventThreads, 0, s>>>(h, tab, ps, ss, b->sched.bin == 2, g.w0, g.w1); break;
             case 1: cmk::k_bin_count_batch<<<gs, cmk::kEventThreads, 0, s>>>(h, tab, ss, g.w0, g.w1); break;
             case 2: cmk::k_bin_scatter_batch<<<gs, cmk::kEventThreads, 0, s>>>(h, tab, ss, g.w0, g.w1); break;
             case 3: enqueue_event(b, s, 0, ge, g.w0, g.w1); break;

@@ -254,3 +254,29 @@ def test_batch_bin_counts_up_to_the_maximum(B, ref_mode):
     plan.run()
     for i, w in enumerate(wins):
         assert_parity(_batch_result(plan, i), run_oracle(w))
+
+
+def test_band_grouping_with_events_outside_the_sensor_and_a_1280x720_window():
+    # bin 2 with events whose (x, y) lies outside the sensor (their band is
+    # that of the nearest row; they are masked as in the oracle) and with a
+    # 1280x720 window (23 bands, 74 super-chunks) against the plain path
+    cm = gpu_lib()
+    small = synth.depth_window(np.random.default_rng(92), 160, 100, 5000, nbins=10)
+    e = small.events
+    x, y = e.x.copy(), e.y.copy()
+    x[::97] = -2
+    y[1::89] = 103
+    x[2::101] = 161
+    y[3::103] = -5
+    small.events = synth.Events(x, y, e.t, e.p, e.t0, e.t1)
+    hd = synth.depth_window(np.random.default_rng(93), 1280, 720, 300000, nbins=10)
+    plan = cm.BatchPlan(_dev_windows(cm, [small, hd]), cm.loss_cfg(10, cm.REF_ALL, cm.SPLAT_ATOMIC))
+    plan.set_schedule(2, 1, 2)
+    for _ in range(2):
+        plan.run()
+    assert_parity(_batch_result(plan, 0), run_oracle(small))
+    g, p = _batch_result(plan, 1), run_gpu(hd)
+    assert np.array_equal(g["nnz_r"], p["nnz_r"])
+    assert abs(g["loss"] - p["loss"]) <= LOSS_RTOL * abs(p["loss"])
+    assert rel_l2(g["dinv_depth"], p["dinv_depth"]) <= GRAD_RTOL_L2
+    assert rel_l2(g["dego"], p["dego"]) <= GRAD_RTOL_L2
