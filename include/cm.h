@@ -322,8 +322,9 @@ int cm_batch_run(cm_batch* plan, void* stream);
  * the graph, each chain one group after another; group 0 (with chains 1) puts
  * every window in each kernel.  Few windows in flight keep their images of
  * warped events in L2; several chains overlap each other's tails.  With `bin`
- * the events of each window are first regrouped by two extra kernels into a
- * copy in the plan's memory: bin 1 by 32x32-pixel tile (unordered within a
+ * the events of each window are first regrouped into a copy in the plan's
+ * memory (bin 1: two extra kernels; bin 2: a count inside the prep pass and one
+ * extra kernel): bin 1 by 32x32-pixel tile (unordered within a
  * tile), bin 2 by band of 32 image rows with a counting sort that keeps the
  * order of 4096-event super-chunks within a band (with time-ordered input the
  * events of a warp then share their bin).  Either way the events in flight touch a
