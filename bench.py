@@ -701,7 +701,7 @@ def run_e2e(batch, args, stream, schedule):
 
     run_steps(4)
     a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    K = max(4, args.steps // 3)
+    K = max(4, args.steps)
     run_steps(K, a, z)
     ms = a.elapsed_time(z) / K
     return {"value": batch.events / (ms * 1e-3) / 1e6, "unit": "Mev/s", "h2d_bytes_per_step": int(h2d),
