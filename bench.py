@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--serve-scales", default="0.25,0.5,1.0", help="arrival-rate multipliers of 100 Hz per stream")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--serve-pool", type=int, default=2, help="pre-generated windows per stream")
+    ap.add_argument("--serve-lanes", type=int, default=6, help="concurrent lanes of the server")
+    ap.add_argument("--serve-batch", type=int, default=8, help="requests per batch of a lane")
     return ap.parse_args()
 
 
@@ -788,7 +790,7 @@ def run_serve(args):
     budget = 40 << 30
     for scale in [float(x) for x in args.serve_scales.split(",")]:
         arr = arrivals(scale, args.serve_seconds)
-        srv = Server(budget, max_batch=8, lanes=3)
+        srv = Server(budget, max_batch=args.serve_batch, lanes=args.serve_lanes)
         batched = replay(srv, arr)
         srv.close()
         plain = None
@@ -801,7 +803,7 @@ def run_serve(args):
                 "higher_is_better": True, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": "serve32_mixed_res_poisson100hz", "rate_scale": scale,
                            "seconds": args.serve_seconds, "streams": streams, "pool_per_stream": args.serve_pool,
-                           "max_batch": 8, "lanes": 3, "hbm_budget_gb": 40},
+                           "max_batch": args.serve_batch, "lanes": args.serve_lanes, "hbm_budget_gb": 40},
                 "batched": batched, "plain": plain}
         print(json.dumps(line), flush=True)
 
