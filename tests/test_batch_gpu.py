@@ -280,3 +280,25 @@ def test_band_grouping_with_events_outside_the_sensor_and_a_1280x720_window():
     assert abs(g["loss"] - p["loss"]) <= LOSS_RTOL * abs(p["loss"])
     assert rel_l2(g["dinv_depth"], p["dinv_depth"]) <= GRAD_RTOL_L2
     assert rel_l2(g["dego"], p["dego"]) <= GRAD_RTOL_L2
+
+
+def test_band_grouping_across_set_windows_and_schedule_changes():
+    # bin 2 across new windows (event counts that change, some beyond the plan's
+    # grouping memory, which then run in their given order) and across
+    # switches between the grouping modes; every run against the oracle
+    cm = gpu_lib()
+    first = _mixed_windows(6, 57)
+    plan = cm.BatchPlan(_dev_windows(cm, first), cm.loss_cfg(10, cm.REF_ALL, cm.SPLAT_ATOMIC))
+    plan.set_schedule(2, 1, 2)
+    plan.run()
+    second = []
+    for i, w in enumerate(reversed(first)):
+        # some grow past the grouping memory; at least 500 events (a lone event's gradient is eps-bound)
+        n = w.events.n * 2 + 300 if i % 2 else max(w.events.n // 3, 500)
+        second.append(synth.depth_window(np.random.default_rng(5800 + i), w.cam.width, w.cam.height, n, nbins=10))
+    plan.set_windows(_dev_windows(cm, second))
+    for sched in ((2, 1, 2), (1, 0, 1), (3, 2, 2), (1, 0, 0), (2, 1, 2)):
+        plan.set_schedule(*sched)
+        plan.run()
+        for i, w in enumerate(second):
+            assert_parity(_batch_result(plan, i), run_oracle(w))
