@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--store-warps", type=int, default=0, choices=[0, 1],
                     help="1: the forward stores the trajectory points for the backward (no recompute)")
     ap.add_argument("--serve", action="store_true", help="run the serving workload instead (one line per rate)")
+    ap.add_argument("--latency", action="store_true",
+                    help="single-window latency of the parity workloads (128x128 flow, 346x260 and 1280x720 depth)")
+    ap.add_argument("--reps", type=int, default=200, help="repetitions per workload of --latency")
     ap.add_argument("--other-kernels", action="store_true",
                     help="time only the kernels beside the CM path (Eq. 2 flow, geometry loss, event frame)")
     ap.add_argument("--serve-scales", default="0.25,0.5,1.0", help="arrival-rate multipliers of 100 Hz per stream")
@@ -870,6 +873,52 @@ def run_serve(args):
         print(json.dumps(line), flush=True)
 
 
+def run_latency(args):
+    """One JSON line: loss + gradient latency of one window of each parity
+    workload, through the single-window calls (a stream sync after each call,
+    as a per-window caller would) and through a one-window batched plan
+    (autotuned, replayed from its CUDA graph, synced after each run); p50/p99
+    over --reps calls after 10 warm-up calls, host clock."""
+    import torch
+    from paper_2412_06359_gb300 import _capi as C
+    from paper_2412_06359_gb300 import build, synth
+    build.build()
+    C.lib()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+
+    def lat(fn):
+        for _ in range(10):
+            fn()
+        t = []
+        for _ in range(args.reps):
+            s = time.perf_counter()
+            fn()
+            t.append(1e3 * (time.perf_counter() - s))
+        return float(np.percentile(t, 50)), float(np.percentile(t, 99))
+
+    out = {}
+    for name, win in (("flow_128x128_b1_end", synth.flow_window()), ("depth_346x260_b10_all", synth.davis_window()),
+                      ("depth_1280x720_b20_all", synth.hd_window())):
+        b = Batch([win], dev)
+        b.plan.autotune()
+
+        def plan_run():
+            b.plan.run()
+            torch.cuda.current_stream(dev).synchronize()
+
+        n = win.events.n
+        p50, p99 = lat(lambda: b.plain_window(0))
+        q50, q99 = lat(plan_run)
+        out[name] = {"events": n, "plain": {"p50_ms": p50, "p99_ms": p99, "mev_s_at_p50": n / p50 / 1e3},
+                     "plan": {"p50_ms": q50, "p99_ms": q99, "mev_s_at_p50": n / q50 / 1e3,
+                              "schedule": list(b.plan.schedule())}}
+        del b
+        torch.cuda.empty_cache()
+    print(json.dumps({"metric": "single-window loss+grad latency", "unit": "ms", "reps": args.reps,
+                      "higher_is_better": False, "data": "synthetic", "latency": out}), flush=True)
+
+
 def run_other(args):
     """One JSON line: the kernels beside the CM path on a 1280x720 sensor."""
     import torch
@@ -885,6 +934,8 @@ def main():
         run_serve(args)
     elif args.other_kernels:
         run_other(args)
+    elif args.latency:
+        run_latency(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
