@@ -302,3 +302,20 @@ def test_band_grouping_across_set_windows_and_schedule_changes():
         plan.run()
         for i, w in enumerate(second):
             assert_parity(_batch_result(plan, i), run_oracle(w))
+
+
+@pytest.mark.parametrize("chains,group,bin", [(0, 1, 0), (9, 1, 0), (2, -1, 0), (2, 0, 0), (1, 1, 3), (1, 1, -1)])
+def test_invalid_schedules_are_refused_and_leave_the_plan_as_it_was(chains, group, bin):
+    from paper_2412_06359_gb300 import _capi as C
+    cm = gpu_lib()
+    wins = _mixed_windows(3, 61)
+    plan = cm.BatchPlan(_dev_windows(cm, wins), cm.loss_cfg(10, cm.REF_ALL, cm.SPLAT_ATOMIC))
+    plan.set_schedule(1, 1, 2)
+    with pytest.raises(C.CMError) as e:
+        plan.set_schedule(chains, group, bin)
+    assert e.value.status == C.CM_EINVAL
+    assert plan.schedule() == (1, 1, 2)
+    plan.run()
+    for i, w in enumerate(wins):
+        if w.events.n:
+            assert_parity(_batch_result(plan, i), run_oracle(w))
