@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--other-kernels", action="store_true",
                     help="time only the kernels beside the CM path (Eq. 2 flow, geometry loss, event frame)")
     ap.add_argument("--serve-scales", default="0.25,0.5,1.0", help="arrival-rate multipliers of 100 Hz per stream")
-    ap.add_argument("--serve-seconds", type=float, default=1.0)
+    ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--serve-pool", type=int, default=2, help="pre-generated windows per stream")
     ap.add_argument("--serve-lanes", type=int, default=6, help="concurrent lanes of the server")
     ap.add_argument("--serve-batch", type=int, default=8, help="requests per batch of a lane")
