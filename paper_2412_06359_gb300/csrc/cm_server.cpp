@@ -17,6 +17,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <unordered_set>
 #include <map>
 #include <mutex>
 #include <new>
@@ -338,24 +339,24 @@ struct cm_server {
             if (L.busy || queue.empty()) continue;
             std::vector<uint64_t> batch;
             std::vector<Item> items;
-            std::vector<int32_t> seen;  // streams with an earlier request still queued keep their order
-            std::deque<uint64_t> rest;
-            while (!queue.empty()) {
+            std::unordered_set<int32_t> seen;  // streams with an earlier request still queued keep their order
+            std::vector<uint64_t> rest;         // requests passed over, in queue order
+            // scan from the front until the batch is full: a pass costs what it admits
+            // and passes over, not the length of the queue
+            while (!queue.empty() && (int)batch.size() < cfg.max_batch) {
                 const uint64_t tk = queue.front();
                 queue.pop_front();
                 Request& R = reqs[tk];
                 StreamState& s = streams[R.r.stream_id];
                 s.id = R.r.stream_id;
-                bool blocked = s.busy || (int)batch.size() >= cfg.max_batch;
-                for (int32_t id : seen)
-                    if (id == s.id) blocked = true;
+                bool blocked = s.busy || seen.count(s.id) != 0;
                 bool init = false;
                 if (!blocked && !ensure_state(s, R.r, &init)) {
                     blocked = true;
                     st.memory_waits += 1;
                 }
                 if (blocked) {
-                    seen.push_back(s.id);
+                    seen.insert(s.id);
                     rest.push_back(tk);
                     continue;
                 }
@@ -364,7 +365,8 @@ struct cm_server {
                 items.push_back(Item{R.r, at(s.fixed_off), at(s.ev_off), s.ev_cap, s.o_scratch, s.o_rho, s.o_drho,
                                      s.o_small, init});
             }
-            queue.swap(rest);
+            // the requests passed over go back to the front, in their order
+            for (auto it = rest.rbegin(); it != rest.rend(); ++it) queue.push_front(*it);
             if (batch.empty()) break;
             const double t = now_s();
             for (uint64_t tk : batch) {
