@@ -27,3 +27,13 @@ def test_strict_byte_model():
 
 def test_grouping_names_cover_every_schedule_mode():
     assert len(bench.GROUPING) == 3 and bench.GROUPING[2] == "32-row bands"
+
+
+def test_oracle_on_every_core_covers_the_windows_once():
+    # two windows of the batch workload on two spawned processes
+    from paper_2412_06359_gb300 import synth
+    sizes = [w.events.n for w in synth.batch_windows(2)]
+    r = bench.oracle_all_cores(sizes, False, limit_s=120.0)
+    assert r is not None
+    ev, sec, nproc = r
+    assert ev == sum(sizes) and sec > 0 and nproc == 2
