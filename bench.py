@@ -184,6 +184,25 @@ def kernel_bytes(name: str, n: int, hw: int, R: int, model: str) -> float:
     return 0.0
 
 
+def kernel_bytes_step(n: int, hw: int, R: int) -> float:
+    """Strict algorithmic bytes of a whole step: 18 B per event (read by the
+    splat and by the adjoint) and 8 B per pixel (inverse depth read, its
+    gradient written)."""
+    return 18.0 * n + 8.0 * hw
+
+
+def workload_config(wins, events_kind: str, events_per_step: int) -> dict:
+    """The workload as both arms name it (the `config` of the JSON line)."""
+    R = wins[0].nbins + 1 if wins[0].ref_mode == 1 else 1
+    hw = wins[0].cam.width * wins[0].cam.height
+    return {"workload": WORKLOAD if events_kind == "iid" else WORKLOAD + "_motion",
+            "events": "iid (gradient-sampled pixels, uniform times)" if events_kind == "iid"
+            else "motion-consistent, flow input with the true flow (contention stress variant)",
+            "windows": len(wins), "events_per_step": int(events_per_step),
+            "sensor": f"{wins[0].cam.width}x{wins[0].cam.height}", "bins": wins[0].nbins, "refs": R,
+            "l2": "per-step IWE working set %.2f GB > L2 (no flush needed)" % (len(wins) * R * hw * 16 / 1e9)}
+
+
 # the batch schedule's event grouping modes (cm_batch_schedule.bin)
 GROUPING = ("given order", "32x32 tiles", "32-row bands")
 
@@ -248,7 +267,7 @@ def oracle_sample(windows, seconds: float):
     used = 0
     for w in windows:
         t0 = time.perf_counter()
-        O.cm_window(w, grad=True, positions="f32")
+        O.cm_window(w, grad=True)
         t_total += time.perf_counter() - t0
         ev += w.events.n
         used += 1
@@ -268,7 +287,7 @@ def _oracle_share(j: int, idx: list, motion: bool, ready_q, go, out_q):
     go.wait()
     ev = 0
     for w in wins:
-        O.cm_window(w, grad=True, positions="f32")
+        O.cm_window(w, grad=True)
         ev += w.events.n
     out_q.put(ev)
 
@@ -322,14 +341,14 @@ def run_reference(args):
     O.build()
     # each step: the oracle on one window of the batch (rotating), a bounded sample
     for i in range(args.warmup):
-        O.cm_window(wins[i % len(wins)], grad=True, positions="f32")
+        O.cm_window(wins[i % len(wins)], grad=True)
     ev = 0
     t0 = time.perf_counter()
     times = []
     for i in range(args.steps):
         w = wins[i % len(wins)]
         s = time.perf_counter()
-        O.cm_window(w, grad=True, positions="f32")
+        O.cm_window(w, grad=True)
         times.append(time.perf_counter() - s)
         ev += w.events.n
     el = time.perf_counter() - t0
@@ -338,7 +357,8 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": v, "unit": "Mev/s", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "windows": args.windows, "sample": "one window of the batch per step"},
+        "config": workload_config(wins, "iid", sum(w.events.n for w in wins)),
+        "sample": "one window of the batch per step (rotating through the batch)",
         "cpu_baseline": {"value": v, "unit": "Mev/s", "cores": 1, "kind": "oracle",
                          "sample": f"{args.steps} windows of the 64-window batch, one per step, loss + gradient"},
         "e2e": {"value": v, "unit": "Mev/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -476,12 +496,15 @@ def run_ours(args):
     roof_l2 = None
     if dom:
         nl, ms = prof[dom]
-        per_launch_ms = ms / nl
         launches_per_step = nl / args.steps
-        # kernel time summed over the chains per step / step time: above 1 when
-        # kernels of concurrent chains overlap (each launch's duration then includes
-        # the time it shares the GPU)
-        overlap = sum(v[1] for v in prof.values()) / args.steps / ms_per_step
+        # the kernel's time: its share of the summed kernel time (CUDA events
+        # around every launch), applied to the step's device time.  Launches of
+        # concurrent chains overlap, so a launch's own event interval includes
+        # the time it shares the GPU; the share does not.
+        summed = sum(v[1] for v in prof.values())
+        overlap = summed / args.steps / ms_per_step
+        share = ms / summed
+        per_launch_ms = share * ms_per_step / launches_per_step
         for model in ("strict", "iwe"):
             b = kernel_bytes(dom, batch.events, hw * len(wins), R, model) / launches_per_step
             ach = b / (per_launch_ms * 1e-3) / 1e9
@@ -490,7 +513,11 @@ def run_ours(args):
             traffic = None if cnt is None or model != "strict" else cnt["dram_bytes_per_event"] * events_per_launch
             obj = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                    "traffic": traffic, "kernel": dom,
-                   "launch_ms": per_launch_ms, "bytes_per_launch": b, "launches_per_step": launches_per_step,
+                   "launch_ms": per_launch_ms, "launch_ms_events": ms / nl, "share_of_kernel_time": share,
+                   "bytes_per_launch": b, "launches_per_step": launches_per_step,
+                   "step_bytes_strict": kernel_bytes_step(batch.events, hw * len(wins), R),
+                   "step_frac_strict": kernel_bytes_step(batch.events, hw * len(wins), R) / (ms_per_step * 1e-3)
+                   / 1e9 / peak,
                    "overlap": overlap, "peak_kind": f"{peak_kind} hbm_gbs"}
             if model == "strict":
                 roof = obj
@@ -509,8 +536,7 @@ def run_ours(args):
                        "frac": ach / pk, "kernel": dom, "requests_per_launch": rd + rq,
                        "read_requests_per_event": cnt["l2_read_requests_per_event"],
                        "red_requests_per_event": cnt["l2_red_requests_per_event"],
-                       "measured_red_per_s": l2[0], "measured_load_per_s": l2[1], "overlap": overlap,
-                       "frac_times_overlap": ach / pk * overlap,
+                       "measured_red_per_s": l2[0], "measured_load_per_s": l2[1],
                        "peak_kind": "measured by cm_measure_l2_rates on this GPU before the timed region"}
 
     # ---- plain per-window comparison (a stream sync after every window) ----
@@ -561,16 +587,11 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": "Mev/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD if args.events == "iid" else WORKLOAD + "_motion",
-                       "events": "iid (gradient-sampled pixels, uniform times)" if args.events == "iid"
-                       else "motion-consistent, flow input with the true flow (contention stress variant)",
-                       "windows": len(wins), "events_per_step": batch.events,
-                       "sensor": "640x480", "bins": wins[0].nbins, "refs": R, "splat": "atomic",
-                       "backward": "stored warps" if args.store_warps else "recompute",
-                       "path": "batched plan replayed from a CUDA graph",
-                       "schedule": {"chains": schedule[0], "windows_per_kernel": schedule[1],
-                                    "grouping": GROUPING[schedule[2]]},
-                       "l2": "per-step IWE working set %.2f GB > L2 (no flush needed)" % (len(wins) * R * hw * 16 / 1e9)},
+            "config": workload_config(wins, args.events, batch.events),
+            "plan": {"splat": "atomic", "backward": "stored warps" if args.store_warps else "recompute",
+                     "path": "batched plan replayed from a CUDA graph",
+                     "schedule": {"chains": schedule[0], "windows_per_kernel": schedule[1],
+                                  "grouping": GROUPING[schedule[2]]}},
             "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
             "plain": plain, "splat_compare": splat_cmp, "roofline": roof, "roofline_iwe": roof_iwe,
             "roofline_l2": roof_l2, "other_kernels": others, "cpu_baseline": cpu,

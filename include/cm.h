@@ -443,16 +443,22 @@ int cm_server_destroy(cm_server* server);
  *   - The fixed array holds CM_STATIC_SCRATCH_BYTES; a window whose images of
  *     warped events and reduction buffers need more (about R x W x H x 16 bytes,
  *     e.g. 346x260 with 11 references fits, 640x480 with 11 does not) is rejected
- *     with CM_ENOMEM before anything is enqueued.  Every GPU that loads the
- *     library's module keeps the array reserved until the process exits.
+ *     with CM_ENOMEM before anything is enqueued.
  *   - The call makes no cudaMalloc, cudaFree or other allocating call.  The
  *     first call on each device looks up the array's device address (once, with
- *     that device current); make that first call before any stream capture.
+ *     that device current), and that first lookup is where the device reserves
+ *     the array (the library's module is loaded lazily, on first use): it fails
+ *     with CM_ENOMEM when the device has no room for it.  The device then keeps
+ *     the array until the process exits.  Make a first call at set-up time, on
+ *     every device used (a window of n = 0 events does), before any stream
+ *     capture and before the loop that must not fail.
  *   - All calls share the array and it keeps the last call's contents; each
  *     call clears what must start at zero.  Calls whose work overlaps on the
  *     GPU race on the array: order them on one stream or synchronise between them.
  *   - cfg->splat must be CM_SPLAT_AUTO or CM_SPLAT_ATOMIC.
- * Errors: CM_EINVAL, CM_ENOMEM (window too large for the array), CM_ECUDA. */
+ * Errors: CM_EINVAL (the checks of cm_loss_forward, plus store_warps = 1 or the
+ * sort splat), CM_ENOMEM (window too large for the array, or no room for the
+ * array on the first call on a device), CM_ECUDA. */
 #define CM_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
 int cm_loss_grad_static(const cm_camera* cam, const cm_events* ev, const float* flow, int32_t n_flow_bins,
                         const cm_loss_cfg* cfg, const float* dloss, float* loss_out, float* dflow_out,

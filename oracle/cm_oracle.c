@@ -39,16 +39,25 @@
  *   - pixel centres at integers, image interval closed: 0 <= x <= W-1
  *   - flow sampled with clamped corner indices (the clamped corner always has
  *     weight zero inside the closed image)
- *   - positions: either FP64 throughout (pos_f32 = 0; the plain definition) or
- *     in FP32 with the fixed sequence of correctly rounded operations of the
- *     GPU kernels (pos_f32 = 1).  The floor of a position decides the cell, the
- *     support and the mask, and the eps-regularised ratio makes the loss and
- *     its gradient sensitive to sub-ULP position changes, so parity against an
- *     FP32 kernel takes those decisions in FP32 (the kernel's precision).  All
- *     other arithmetic is FP64 in both modes.
+ *   - every operation is FP64: positions, weights, sums, the loss and the
+ *     gradient.  The oracle shares no arithmetic with the FP32 GPU path.
  *
- * Build: gcc -O2 -std=c11 -ffp-contract=off -fPIC -shared (no fast-math; the
- * FP32 position path relies on IEEE single precision with no contraction).
+ * Straddles (how an FP32 result is judged against this FP64 definition).  The
+ * floor of a trajectory position decides the flow cell, the pixels a splat
+ * touches and whether a corner carries weight (so which pixels are non-empty
+ * and N_nz); the image border decides the mask; floor(tau B) decides the bin.
+ * The loss jumps where such a decision changes (a pixel reached by a tiny
+ * weight counts fully in N_nz and in the sum of T^2), and the gradient jumps
+ * too (kinks of the bilinear weights).  orc_cm_bounds bounds, coordinate by
+ * coordinate, how far an FP32 evaluation of the trajectory can be from the
+ * FP64 one (a forward error bound from the magnitudes of the quantities
+ * involved), flags every decision within that distance of its threshold, and
+ * returns the interval of N_nz and of the loss over every outcome of the
+ * flagged decisions.  An FP32 result passes when its N_nz lies in the interval
+ * and its loss within the stated tolerance of it; gradients are compared on the
+ * events no decision of which is flagged.
+ *
+ * Build: gcc -O2 -std=c11 -ffp-contract=off -fPIC -shared (no fast-math).
  */
 #include <math.h>
 #include <stdint.h>
@@ -93,45 +102,6 @@ void orc_flow_from_depth(int32_t W, int32_t H, double fx, double fy, double cx, 
             const double ydot = r * (-vy + yn * vz) + (1.0 + yn * yn) * wx - xn * yn * wy - xn * wz;
             flow[2 * ((int64_t)v * W + u) + 0] = dt * fx * xdot;
             flow[2 * ((int64_t)v * W + u) + 1] = dt * fy * ydot;
-        }
-    }
-}
-
-/*
- * The same motion field in FP32, with the operation sequence that decides the
- * positions of the FP32 trajectory (pos_f32 = 1).  Every operation is one
- * correctly rounded IEEE single operation; fmaf is the fused multiply-add.
- *   ifx = 1/fx, ify = 1/fy, sx = dt*fx, sy = dt*fy
- *   xn = (u - cx) * ifx,  yn = (v - cy) * ify,  xy = xn * yn
- *   xd = rho * fma(xn, vz, -vx);  xd = fma(xy, wx, xd);
- *   xd = fma(-fma(xn, xn, 1), wy, xd);  xd = fma(yn, wz, xd)
- *   yd = rho * fma(yn, vz, -vy);  yd = fma(fma(yn, yn, 1), wx, yd);
- *   yd = fma(-xy, wy, yd);  yd = fma(-xn, wz, yd)
- *   flow = (sx * xd, sy * yd)
- */
-void orc_flow_from_depth_f32(int32_t W, int32_t H, float fx, float fy, float cx, float cy,
-                             const float* rho, const float* ego, float dt, float* flow)
-{
-    const float vx = ego[0], vy = ego[1], vz = ego[2];
-    const float wx = ego[3], wy = ego[4], wz = ego[5];
-    const float ifx = 1.0f / fx, ify = 1.0f / fy;
-    const float sx = dt * fx, sy = dt * fy;
-    for (int32_t v = 0; v < H; ++v) {
-        for (int32_t u = 0; u < W; ++u) {
-            const float xn = ((float)u - cx) * ifx;
-            const float yn = ((float)v - cy) * ify;
-            const float r = rho[(int64_t)v * W + u];
-            const float xy = xn * yn;
-            float xd = r * fmaf(xn, vz, -vx);
-            xd = fmaf(xy, wx, xd);
-            xd = fmaf(-fmaf(xn, xn, 1.0f), wy, xd);
-            xd = fmaf(yn, wz, xd);
-            float yd = r * fmaf(yn, vz, -vy);
-            yd = fmaf(fmaf(yn, yn, 1.0f), wx, yd);
-            yd = fmaf(-xy, wy, yd);
-            yd = fmaf(-xn, wz, yd);
-            flow[2 * ((int64_t)v * W + u) + 0] = sx * xd;
-            flow[2 * ((int64_t)v * W + u) + 1] = sy * yd;
         }
     }
 }
@@ -227,107 +197,6 @@ void orc_flow_eq2_bins(int32_t W, int32_t H, double fx, double fy, double cx, do
         double* f = flow + 2 * HW * i;
         orc_flow_eq2(W, H, fx, fy, cx, cy, rho, ego + 6 * i, dt_bin, f);
         for (int64_t q = 0; q < 2 * HW; ++q) f[q] *= scale;
-    }
-}
-
-/*
- * The same in FP32 with the operation sequence of the GPU kernels, which
- * decides the positions of the FP32 trajectory when these flows drive it
- * (every operation one correctly rounded IEEE single operation, fmaf fused):
- *   per bin:  k = -(w * dt), t = -(v * dt) (componentwise);
- *             kxx = kx*kx, kyy = ky*ky, kzz = kz*kz, kxy = kx*ky, kxz = kx*kz, kyz = ky*kz
- *             s = (kxx + kyy) + kzz
- *             a = sin(th)/th and b = (1 - cos th)/th^2 as their Taylor series in s
- *                 (terms up to s^9, Horner from the highest term: c = fma(c, s, c_n))
- *             R00 = fma(b, -(kyy + kzz), 1)   R01 = fma(b, kxy, -(a*kz))   R02 = fma(b, kxz, a*ky)
- *             R10 = fma(b, kxy, a*kz)         R11 = fma(b, -(kxx + kzz), 1) R12 = fma(b, kyz, -(a*kx))
- *             R20 = fma(b, kxz, -(a*ky))      R21 = fma(b, kyz, a*kx)      R22 = fma(b, -(kxx + kyy), 1)
- *             Ad_i = b * -(...) (the diagonal of R - I, the same sums as R_ii)
- *   per pixel: xn = (u - cx) * (1/fx), yn = (v - cy) * (1/fy), Z = 1/rho,
- *             the displacement d of disp_f32 below; flow = (scale * d.x, scale * d.y)
- * The displacement is fx (P0/P2 - xn), the same quantity as fx P0/P2 + cx - u.
- */
-static const double ORC_SIN_SERIES[10] = {1.0, -1.0 / 6.0, 1.0 / 120.0, -1.0 / 5040.0, 1.0 / 362880.0,
-                                          -1.0 / 39916800.0, 1.0 / 6227020800.0, -1.0 / 1307674368000.0,
-                                          1.0 / 355687428096000.0, -1.0 / 121645100408832000.0};
-static const double ORC_COS_SERIES[10] = {1.0 / 2.0, -1.0 / 24.0, 1.0 / 720.0, -1.0 / 40320.0, 1.0 / 3628800.0,
-                                          -1.0 / 479001600.0, 1.0 / 87178291200.0, -1.0 / 20922789888000.0,
-                                          1.0 / 6402373705728000.0, -1.0 / 2432902008176640000.0};
-
-static void rot_f32(const float* e, float dt, float Rm[9], float tv[3], float Ad[3])
-{
-    const float kx = -(e[3] * dt), ky = -(e[4] * dt), kz = -(e[5] * dt);
-    tv[0] = -(e[0] * dt);
-    tv[1] = -(e[1] * dt);
-    tv[2] = -(e[2] * dt);
-    const float kxx = kx * kx, kyy = ky * ky, kzz = kz * kz;
-    const float kxy = kx * ky, kxz = kx * kz, kyz = ky * kz;
-    const float s = (kxx + kyy) + kzz;
-    float a = (float)ORC_SIN_SERIES[9], b = (float)ORC_COS_SERIES[9];
-    for (int n = 8; n >= 0; --n) {
-        a = fmaf(a, s, (float)ORC_SIN_SERIES[n]);
-        b = fmaf(b, s, (float)ORC_COS_SERIES[n]);
-    }
-    Ad[0] = b * -(kyy + kzz);
-    Ad[1] = b * -(kxx + kzz);
-    Ad[2] = b * -(kxx + kyy);
-    Rm[0] = fmaf(b, -(kyy + kzz), 1.0f);
-    Rm[1] = fmaf(b, kxy, -(a * kz));
-    Rm[2] = fmaf(b, kxz, a * ky);
-    Rm[3] = fmaf(b, kxy, a * kz);
-    Rm[4] = fmaf(b, -(kxx + kzz), 1.0f);
-    Rm[5] = fmaf(b, kyz, -(a * kx));
-    Rm[6] = fmaf(b, kxz, -(a * ky));
-    Rm[7] = fmaf(b, kyz, a * kx);
-    Rm[8] = fmaf(b, -(kxx + kyy), 1.0f);
-}
-
-/* The displacement of pixel (u, v) in FP32 (the sequence of the kernels):
- * with m = (xn, yn, 1) and A = R - I (its diagonal built directly),
- *   c_0j = fma(-xn, A_2j, A_0j), c_1j = fma(-yn, A_2j, A_1j)      (j = 0, 1, 2)
- *   s0 = fma(c_00, xn, fma(c_01, yn, c_02)),  s1 = fma(c_10, xn, fma(c_11, yn, c_12))
- *   e0 = fma(Z, s0, fma(-xn, t2, t0)),        e1 = fma(Z, s1, fma(-yn, t2, t1))
- *   P2 = fma(Z, fma(R20, xn, fma(R21, yn, R22)), t2),  iz = 1 / P2
- *   d = (fx * (e0 * iz), fy * (e1 * iz))
- * e0 = P0 - xn P2 taken in this form is exactly 0 for a camera at rest and
- * never cancels two large terms. */
-static void disp_f32(const float Rm[9], const float tv[3], const float Ad[3], float xn, float yn, float Z, float fx,
-                     float fy, float* dx, float* dy, float* P2out)
-{
-    const float A00 = Ad[0], A11 = Ad[1], A22 = Ad[2];
-    const float c00 = fmaf(-xn, Rm[6], A00), c01 = fmaf(-xn, Rm[7], Rm[1]), c02 = fmaf(-xn, A22, Rm[2]);
-    const float c10 = fmaf(-yn, Rm[6], Rm[3]), c11 = fmaf(-yn, Rm[7], A11), c12 = fmaf(-yn, A22, Rm[5]);
-    const float s0 = fmaf(c00, xn, fmaf(c01, yn, c02));
-    const float s1 = fmaf(c10, xn, fmaf(c11, yn, c12));
-    const float e0 = fmaf(Z, s0, fmaf(-xn, tv[2], tv[0]));
-    const float e1 = fmaf(Z, s1, fmaf(-yn, tv[2], tv[1]));
-    const float P2 = fmaf(Z, fmaf(Rm[6], xn, fmaf(Rm[7], yn, Rm[8])), tv[2]);
-    const float iz = 1.0f / P2;
-    *dx = fx * (e0 * iz);
-    *dy = fy * (e1 * iz);
-    *P2out = P2;
-}
-
-void orc_flow_eq2_bins_f32(int32_t W, int32_t H, float fx, float fy, float cx, float cy, const float* rho,
-                           const float* ego, int32_t nb, float dt_bin, float scale, float* flow)
-{
-    const int64_t HW = (int64_t)W * H;
-    const float ifx = 1.0f / fx, ify = 1.0f / fy;
-    for (int32_t i = 0; i < nb; ++i) {
-        float Rm[9], tv[3], Ad[3];
-        rot_f32(ego + 6 * i, dt_bin, Rm, tv, Ad);
-        for (int32_t v = 0; v < H; ++v) {
-            for (int32_t u = 0; u < W; ++u) {
-                const int64_t q = (int64_t)v * W + u;
-                const float xn = ((float)u - cx) * ifx;
-                const float yn = ((float)v - cy) * ify;
-                const float Z = 1.0f / rho[q];
-                float dx, dy, P2;
-                disp_f32(Rm, tv, Ad, xn, yn, Z, fx, fy, &dx, &dy, &P2);
-                flow[2 * (HW * i + q) + 0] = scale * dx;
-                flow[2 * (HW * i + q) + 1] = scale * dy;
-            }
-        }
     }
 }
 
@@ -437,133 +306,361 @@ void orc_flow_eq2_grad(int32_t W, int32_t H, double fx, double fy, double cx, do
     }
 }
 
+/* ------------------------------------------------------------------------- */
+/* Error bounds of an FP32 evaluation (used to flag straddles)               */
+/* ------------------------------------------------------------------------- */
+
+#define ORC_U 5.9604644775390625e-08 /* 2^-24: unit roundoff of IEEE single precision */
+
+/*
+ * Bound on |flow32 - flow| per pixel for the motion field of S1 evaluated in
+ * FP32 (any evaluation order): each of the products and sums that make up
+ * d(xn)/dt and d(yn)/dt is rounded once, and xn, yn carry the rounding of
+ * (u - cx) / fx, so the error is at most c u M, where M is the sum of the
+ * magnitudes of the terms, u = 2^-24 and c = 20 (the rounded operations on the
+ * longest path, with a margin); the product with dt f adds 2u of the result.
+ * eb[H][W] is the bound of the larger of the two components.
+ */
+void orc_flow_error_bound(int32_t W, int32_t H, double fx, double fy, double cx, double cy, const double* rho,
+                          const double* ego, double dt, double* eb)
+{
+    const double vx = fabs(ego[0]), vy = fabs(ego[1]), vz = fabs(ego[2]);
+    const double wx = fabs(ego[3]), wy = fabs(ego[4]), wz = fabs(ego[5]);
+    for (int32_t v = 0; v < H; ++v) {
+        for (int32_t u = 0; u < W; ++u) {
+            const double xn = fabs(((double)u - cx) / fx), yn = fabs(((double)v - cy) / fy);
+            const double r = fabs(rho[(int64_t)v * W + u]);
+            const double Mx = r * (vx + xn * vz) + xn * yn * wx + (1.0 + xn * xn) * wy + yn * wz;
+            const double My = r * (vy + yn * vz) + (1.0 + yn * yn) * wx + xn * yn * wy + xn * wz;
+            const double bx = 22.0 * ORC_U * dt * fx * Mx, by = 22.0 * ORC_U * dt * fy * My;
+            eb[(int64_t)v * W + u] = bx > by ? bx : by;
+        }
+    }
+}
+
+/* |R - I| bounded entrywise by |a K| + |b K^2| (R = I + a K + b K^2 of
+ * Rodrigues' formula; a ~ 1, b ~ 1/2) */
+static void rot_abs(const double k[3], double Aabs[3][3])
+{
+    const double th = sqrt(k[0] * k[0] + k[1] * k[1] + k[2] * k[2]);
+    double a, b;
+    if (th < 1e-12) { a = 1.0; b = 0.5; }
+    else { a = sin(th) / th; b = (1.0 - cos(th)) / (th * th); }
+    const double K[3][3] = {{0, -k[2], k[1]}, {k[2], 0, -k[0]}, {-k[1], k[0], 0}};
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double K2 = 0;
+            for (int l = 0; l < 3; ++l) K2 += K[i][l] * K[l][j];
+            Aabs[i][j] = fabs(a * K[i][j]) + fabs(b * K2);
+        }
+}
+
+/*
+ * Bound on the FP32 error of the Eq. 2 displacement of one pixel,
+ * d = f (P0/P2 - xn) (and likewise y), for an evaluation in the form
+ * P0/P2 - xn = (Z s0 + t0 - xn t2) / P2, s0 = ((R - I) m)_0 - xn ((R - I) m)_2,
+ * m = (xn, yn, 1), that never subtracts two large terms: the numerator and P2
+ * are sums of terms of magnitudes Me and Mp2, each rounded a bounded number of
+ * times (c u M with c = 16, covering also the rounding of xn, yn, Z = 1/rho and
+ * of the rotation's entries), and the quotient adds the error of P2 and two
+ * roundings.  e0, e1: the exact numerators; P2: the exact depth.
+ */
+static void eq2_bound(const double Aabs[3][3], const double t[3], double xn, double yn, double Z, double P2,
+                      double e0, double e1, double fx, double fy, double* ebx, double* eby, double* ebp2)
+{
+    const double m[3] = {fabs(xn), fabs(yn), 1.0};
+    double Am[3];
+    for (int i = 0; i < 3; ++i) Am[i] = Aabs[i][0] * m[0] + Aabs[i][1] * m[1] + Aabs[i][2] * m[2];
+    const double Za = fabs(Z);
+    const double Me0 = Za * (Am[0] + m[0] * Am[2]) + fabs(t[0]) + m[0] * fabs(t[2]);
+    const double Me1 = Za * (Am[1] + m[1] * Am[2]) + fabs(t[1]) + m[1] * fabs(t[2]);
+    const double Mp2 = Za * (1.0 + Am[2]) + fabs(t[2]);
+    const double c = 16.0 * ORC_U;
+    const double eP2 = c * Mp2, aP2 = fabs(P2);
+    *ebx = fx * (c * Me0 / aP2 + fabs(e0) * eP2 / (aP2 * aP2) + 3.0 * ORC_U * fabs(e0) / aP2);
+    *eby = fy * (c * Me1 / aP2 + fabs(e1) * eP2 / (aP2 * aP2) + 3.0 * ORC_U * fabs(e1) / aP2);
+    *ebp2 = eP2;
+}
+
+/*
+ * Bound on |flow32 - flow| per bin and pixel for orc_flow_eq2_bins evaluated
+ * in FP32 (eq2_bound; the product with `scale` adds 2u of the result).
+ * eb[nb][H][W]: the larger of the two components.
+ */
+void orc_flow_eq2_error_bound(int32_t W, int32_t H, double fx, double fy, double cx, double cy, const double* rho,
+                              const double* ego, int32_t nb, double dt_bin, double scale, double* eb)
+{
+    const int64_t HW = (int64_t)W * H;
+    for (int32_t i = 0; i < nb; ++i) {
+        const double* e = ego + 6 * i;
+        const double k[3] = {-e[3] * dt_bin, -e[4] * dt_bin, -e[5] * dt_bin};
+        const double t[3] = {-e[0] * dt_bin, -e[1] * dt_bin, -e[2] * dt_bin};
+        double Rm[3][3], Aabs[3][3];
+        rodrigues(k, Rm);
+        rot_abs(k, Aabs);
+        for (int32_t v = 0; v < H; ++v) {
+            for (int32_t u = 0; u < W; ++u) {
+                const int64_t q = (int64_t)v * W + u;
+                const double xn = ((double)u - cx) / fx, yn = ((double)v - cy) / fy;
+                const double Z = 1.0 / rho[q];
+                double P[3];
+                for (int a = 0; a < 3; ++a) P[a] = Z * (Rm[a][0] * xn + Rm[a][1] * yn + Rm[a][2]) + t[a];
+                const double e0 = P[0] - xn * P[2], e1 = P[1] - yn * P[2];
+                double bx, by, bp;
+                eq2_bound(Aabs, t, xn, yn, Z, P[2], e0, e1, fx, fy, &bx, &by, &bp);
+                bx = fabs(scale) * bx + 2.0 * ORC_U * fabs(scale * fx * e0 / P[2]);
+                by = fabs(scale) * by + 2.0 * ORC_U * fabs(scale * fy * e1 / P[2]);
+                eb[HW * i + q] = bx > by ? bx : by;
+            }
+        }
+    }
+}
+
 /*
  * Geometry-consistency loss (Sec. 3.2, Eq. 3), read as in the consistency loss
  * the paper cites: every pixel x of view 0 with depth D0 = 1/rho0 is moved by
  * the camera motion between the two views (the rigid transform of Eq. 2:
  * P = R X + t, R = Rodrigues(-w dt), t = -v dt); its forward-projected depth
- * is a = P2, its projection x' lands in view 1, where the interpolated depth b
- * is the bilinear sample of D1 = 1/rho1 at x' (corner indices clamped).  Valid
- * pixels V: P2 > 0 and x' inside the closed image box.
+ * is a = P2, its projection x' = (fx P0/P2 + cx, fy P1/P2 + cy) lands in view
+ * 1, where the interpolated depth b is the bilinear sample of D1 = 1/rho1 at
+ * x' (corner indices clamped).  Valid pixels V: P2 > 0 and x' inside the
+ * closed image box.
  *   L_geo = (1 / |V|) sum_{x in V} |a - b| / (a + b)
- * The projection decides integers (valid or not, the sample's cell, the sign
- * of a - b), so the decisions are taken in the kernels' FP32 sequence
- * (orc_geo_proj_f32) and the loss in FP64 on those decisions; the gradient is
- * that of the branch the decisions select (sign 0 when a = b in FP32).
+ * FP64 throughout.  The gradient is that of the branch the decisions select
+ * (valid set, sample cell, sign of a - b; sign 0 where a = b).
+ * dec: NULL, or per pixel the decisions (cell [HW][2], valid [HW], sign [HW])
+ * to record (mode 1) or to replay with FP64 positions (mode 2, frozen-branch
+ * differences).
  */
-/* The decisions in FP32: the projection, the valid flag, and the sign of
- * a - b (the branch of |a - b|), with
- *   ax = x' - floor(x'), bx = 1 - ax (likewise y), w00 = bx*by, w10 = ax*by,
- *   w01 = bx*ay, w11 = ax*ay, D_c = 1/rho1_c,
- *   b = fma(w11, D11, fma(w01, D01, fma(w10, D10, w00*D00))),  a = P2. */
-void orc_geo_proj_f32(int32_t W, int32_t H, float fx, float fy, float cx, float cy, const float* rho0,
-                      const float* rho1, const float* ego, float dt, float* proj, uint8_t* ok, int8_t* sgn)
+typedef struct {
+    int32_t mode;   /* 0: decide; 1: decide and record; 2: replay */
+    int32_t pad_;
+    int32_t* cell;  /* [HW][2] */
+    uint8_t* ok;    /* [HW] */
+    int8_t* sgn;    /* [HW] */
+} orc_geo_dec;
+
+/* the projection of pixel (u, v) of view 0: x', y', the depth a = P2, and the
+ * quantities the error bound needs */
+typedef struct {
+    double xn, yn, Z, X[3], P[3], xp, yp;
+} geo_proj;
+
+static void geo_project(double Rm[3][3], const double t[3], double fx, double fy, double cx, double cy, int u, int v,
+                        double rho0, geo_proj* g)
 {
-    float Rm[9], tv[3], Ad[3];
-    rot_f32(ego, dt, Rm, tv, Ad);
-    const float ifx = 1.0f / fx, ify = 1.0f / fy;
-    const float W1 = (float)(W - 1), H1 = (float)(H - 1);
-    for (int32_t v = 0; v < H; ++v) {
-        for (int32_t u = 0; u < W; ++u) {
-            const int64_t q = (int64_t)v * W + u;
-            const float xn = ((float)u - cx) * ifx;
-            const float yn = ((float)v - cy) * ify;
-            const float Z = 1.0f / rho0[q];
-            float dx, dy, P2;
-            disp_f32(Rm, tv, Ad, xn, yn, Z, fx, fy, &dx, &dy, &P2);
-            const float xp = (float)u + dx;
-            const float yp = (float)v + dy;
-            proj[2 * q] = xp;
-            proj[2 * q + 1] = yp;
-            ok[q] = P2 > 0.0f && xp >= 0.0f && xp <= W1 && yp >= 0.0f && yp <= H1;
-            sgn[q] = 0;
-            if (!ok[q]) continue;
-            const float fx0 = floorf(xp), fy0 = floorf(yp);
-            const int ix = (int)fx0, iy = (int)fy0;
-            const int ix1 = ix + 1 < W ? ix + 1 : W - 1, iy1 = iy + 1 < H ? iy + 1 : H - 1;
-            const float ax = xp - fx0, ay = yp - fy0, bx = 1.0f - ax, by = 1.0f - ay;
-            const float w00 = bx * by, w10 = ax * by, w01 = bx * ay, w11 = ax * ay;
-            const float D00 = 1.0f / rho1[(int64_t)iy * W + ix], D10 = 1.0f / rho1[(int64_t)iy * W + ix1];
-            const float D01 = 1.0f / rho1[(int64_t)iy1 * W + ix], D11 = 1.0f / rho1[(int64_t)iy1 * W + ix1];
-            const float b = fmaf(w11, D11, fmaf(w01, D01, fmaf(w10, D10, w00 * D00)));
-            sgn[q] = P2 > b ? 1 : (P2 < b ? -1 : 0);
-        }
-    }
+    g->xn = ((double)u - cx) / fx;
+    g->yn = ((double)v - cy) / fy;
+    g->Z = 1.0 / rho0;
+    g->X[0] = g->Z * g->xn;
+    g->X[1] = g->Z * g->yn;
+    g->X[2] = g->Z;
+    for (int r = 0; r < 3; ++r) g->P[r] = Rm[r][0] * g->X[0] + Rm[r][1] * g->X[1] + Rm[r][2] * g->X[2] + t[r];
+    /* x' = fx P0/P2 + cx written as the pixel plus its displacement
+     * fx (P0 - xn P2) / P2 (the same value; exactly the pixel at rest) */
+    g->xp = (double)u + fx * (g->P[0] - g->xn * g->P[2]) / g->P[2];
+    g->yp = (double)v + fy * (g->P[1] - g->yn * g->P[2]) / g->P[2];
+}
+
+static int geo_inside(double xp, double yp, int W, int H)
+{
+    return xp >= 0.0 && xp <= (double)(W - 1) && yp >= 0.0 && yp <= (double)(H - 1);
+}
+
+/* b = bilinear sample of 1/rho1 at (xp, yp) in cell (ix, iy), its gradient
+ * with respect to (xp, yp), the four weights and corner indices */
+static double geo_sample(const double* rho1, int W, int H, double xp, double yp, int ix, int iy, double* dbx,
+                         double* dby, double w[4], int64_t c[4], double D[4])
+{
+    const int ix1 = ix + 1 < W ? ix + 1 : W - 1, iy1 = iy + 1 < H ? iy + 1 : H - 1;
+    const double ax = xp - ix, ay = yp - iy;
+    c[0] = (int64_t)iy * W + ix;
+    c[1] = (int64_t)iy * W + ix1;
+    c[2] = (int64_t)iy1 * W + ix;
+    c[3] = (int64_t)iy1 * W + ix1;
+    for (int q = 0; q < 4; ++q) D[q] = 1.0 / rho1[c[q]];
+    w[0] = (1 - ax) * (1 - ay);
+    w[1] = ax * (1 - ay);
+    w[2] = (1 - ax) * ay;
+    w[3] = ax * ay;
+    *dbx = (1 - ay) * (D[1] - D[0]) + ay * (D[3] - D[2]);
+    *dby = (1 - ax) * (D[2] - D[0]) + ax * (D[3] - D[1]);
+    return w[0] * D[0] + w[1] * D[1] + w[2] * D[2] + w[3] * D[3];
 }
 
 double orc_geo(int32_t W, int32_t H, double fx, double fy, double cx, double cy, const double* rho0,
-               const double* rho1, const double* ego, double dt, const float* proj, const uint8_t* ok,
-               const int8_t* sgn, double dloss, int64_t* count, double* drho0, double* drho1, double* dego)
+               const double* rho1, const double* ego, double dt, const orc_geo_dec* dec, double dloss,
+               int64_t* count, double* drho0, double* drho1, double* dego)
 {
     const int64_t HW = (int64_t)W * H;
     const double k[3] = {-ego[3] * dt, -ego[4] * dt, -ego[5] * dt};
     const double t[3] = {-ego[0] * dt, -ego[1] * dt, -ego[2] * dt};
+    const int mode = dec ? dec->mode : 0;
     double Rm[3][3];
     rodrigues(k, Rm);
+    /* the decisions of every pixel */
+    uint8_t* ok = (uint8_t*)malloc((size_t)HW);
+    int32_t* cell = (int32_t*)malloc(sizeof(int32_t) * 2 * (size_t)HW);
+    int8_t* sgn = (int8_t*)malloc((size_t)HW);
+    if (!ok || !cell || !sgn) { free(ok); free(cell); free(sgn); return NAN; }
     int64_t nv = 0;
-    for (int64_t q = 0; q < HW; ++q) nv += ok[q] != 0;
+    for (int32_t v = 0; v < H; ++v) {
+        for (int32_t u = 0; u < W; ++u) {
+            const int64_t q = (int64_t)v * W + u;
+            if (mode == 2) {
+                ok[q] = dec->ok[q];
+                cell[2 * q] = dec->cell[2 * q];
+                cell[2 * q + 1] = dec->cell[2 * q + 1];
+                sgn[q] = dec->sgn[q];
+            } else {
+                geo_proj g;
+                geo_project(Rm, t, fx, fy, cx, cy, u, v, rho0[q], &g);
+                ok[q] = g.P[2] > 0.0 && geo_inside(g.xp, g.yp, W, H);
+                cell[2 * q] = ok[q] ? (int32_t)floor(g.xp) : 0;
+                cell[2 * q + 1] = ok[q] ? (int32_t)floor(g.yp) : 0;
+                sgn[q] = 0;
+                if (ok[q]) {
+                    double dbx, dby, w[4], D[4];
+                    int64_t c[4];
+                    const double b = geo_sample(rho1, W, H, g.xp, g.yp, cell[2 * q], cell[2 * q + 1], &dbx, &dby, w,
+                                                c, D);
+                    sgn[q] = g.P[2] > b ? 1 : (g.P[2] < b ? -1 : 0);
+                }
+                if (mode == 1) {
+                    dec->ok[q] = ok[q];
+                    dec->cell[2 * q] = cell[2 * q];
+                    dec->cell[2 * q + 1] = cell[2 * q + 1];
+                    dec->sgn[q] = sgn[q];
+                }
+            }
+            nv += ok[q] != 0;
+        }
+    }
     *count = nv;
     if (drho0)
         for (int64_t q = 0; q < HW; ++q) drho0[q] = drho1[q] = 0.0;
     double gt[3] = {0, 0, 0}, M[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
     double sum = 0.0;
-    const double g = nv > 0 ? dloss / (double)nv : 0.0;
+    const double gs = nv > 0 ? dloss / (double)nv : 0.0;
     for (int32_t v = 0; v < H; ++v) {
         for (int32_t u = 0; u < W; ++u) {
             const int64_t q = (int64_t)v * W + u;
             if (!ok[q]) continue;
-            const double xn = ((double)u - cx) / fx, yn = ((double)v - cy) / fy;
-            const double Z = 1.0 / rho0[q];
-            const double X[3] = {Z * xn, Z * yn, Z};
-            double P[3];
-            for (int r = 0; r < 3; ++r) P[r] = Rm[r][0] * X[0] + Rm[r][1] * X[1] + Rm[r][2] * X[2] + t[r];
-            const double xp = fx * P[0] / P[2] + cx, yp = fy * P[1] / P[2] + cy;
-            /* the decided cell; the weights from the FP64 position */
-            const int ix = (int)floorf(proj[2 * q]), iy = (int)floorf(proj[2 * q + 1]);
-            const int ix1 = ix + 1 < W ? ix + 1 : W - 1, iy1 = iy + 1 < H ? iy + 1 : H - 1;
-            const double ax = xp - ix, ay = yp - iy;
-            const int64_t c00 = (int64_t)iy * W + ix, c10 = (int64_t)iy * W + ix1;
-            const int64_t c01 = (int64_t)iy1 * W + ix, c11 = (int64_t)iy1 * W + ix1;
-            const double D00 = 1.0 / rho1[c00], D10 = 1.0 / rho1[c10], D01 = 1.0 / rho1[c01], D11 = 1.0 / rho1[c11];
-            const double w00 = (1 - ax) * (1 - ay), w10 = ax * (1 - ay), w01 = (1 - ax) * ay, w11 = ax * ay;
-            const double a = P[2];
-            const double b = w00 * D00 + w10 * D10 + w01 * D01 + w11 * D11;
-            const double sg = (double)sgn[q]; /* the branch of |a - b| decided in FP32 */
-            sum += (sg != 0.0 ? sg * (a - b) : fabs(a - b)) / (a + b);
+            geo_proj g;
+            geo_project(Rm, t, fx, fy, cx, cy, u, v, rho0[q], &g);
+            double dbx, dby, w[4], D[4];
+            int64_t c[4];
+            const double a = g.P[2];
+            const double b = geo_sample(rho1, W, H, g.xp, g.yp, cell[2 * q], cell[2 * q + 1], &dbx, &dby, w, c, D);
+            /* |a - b| on the recorded branch when replaying, else its value */
+            const double sg = (double)sgn[q];
+            sum += (mode == 2 ? sg * (a - b) : fabs(a - b)) / (a + b);
             if (!drho0) continue;
-            const double dfa = g * sg * 2.0 * b / ((a + b) * (a + b));
-            const double dfb = -g * sg * 2.0 * a / ((a + b) * (a + b));
-            const double dbx = (1 - ay) * (D10 - D00) + ay * (D11 - D01);
-            const double dby = (1 - ax) * (D01 - D00) + ax * (D11 - D10);
+            const double dfa = gs * sg * 2.0 * b / ((a + b) * (a + b));
+            const double dfb = -gs * sg * 2.0 * a / ((a + b) * (a + b));
             /* x' = fx P0/P2 + cx, y' = fy P1/P2 + cy */
-            const double dP[3] = {dfb * dbx * fx / P[2], dfb * dby * fy / P[2],
-                                  dfa - dfb * (dbx * fx * P[0] + dby * fy * P[1]) / (P[2] * P[2])};
+            const double P2 = g.P[2];
+            const double dP[3] = {dfb * dbx * fx / P2, dfb * dby * fy / P2,
+                                  dfa - dfb * (dbx * fx * g.P[0] + dby * fy * g.P[1]) / (P2 * P2)};
             for (int r = 0; r < 3; ++r) {
                 gt[r] += dP[r];
-                for (int c = 0; c < 3; ++c) M[r][c] += dP[r] * X[c];
+                for (int cc = 0; cc < 3; ++cc) M[r][cc] += dP[r] * g.X[cc];
             }
             double dX[3];
-            for (int c = 0; c < 3; ++c) dX[c] = Rm[0][c] * dP[0] + Rm[1][c] * dP[1] + Rm[2][c] * dP[2];
-            drho0[q] += -Z * Z * (dX[0] * xn + dX[1] * yn + dX[2]);
+            for (int cc = 0; cc < 3; ++cc) dX[cc] = Rm[0][cc] * dP[0] + Rm[1][cc] * dP[1] + Rm[2][cc] * dP[2];
+            drho0[q] += -g.Z * g.Z * (dX[0] * g.xn + dX[1] * g.yn + dX[2]);
             /* b = sum_c w_c / rho1_c */
-            drho1[c00] -= dfb * w00 * D00 * D00;
-            drho1[c10] -= dfb * w10 * D10 * D10;
-            drho1[c01] -= dfb * w01 * D01 * D01;
-            drho1[c11] -= dfb * w11 * D11 * D11;
+            for (int cc = 0; cc < 4; ++cc) drho1[c[cc]] -= dfb * w[cc] * D[cc] * D[cc];
         }
     }
     if (drho0) {
         double dR[3][3][3];
         rodrigues_grad(k, dR);
-        for (int c = 0; c < 3; ++c) {
+        for (int cc = 0; cc < 3; ++cc) {
             double dk = 0.0;
             for (int r = 0; r < 3; ++r)
-                for (int s2 = 0; s2 < 3; ++s2) dk += M[r][s2] * dR[c][r][s2];
-            dego[c] = -dt * gt[c];
-            dego[3 + c] = -dt * dk;
+                for (int s2 = 0; s2 < 3; ++s2) dk += M[r][s2] * dR[cc][r][s2];
+            dego[cc] = -dt * gt[cc];
+            dego[3 + cc] = -dt * dk;
         }
     }
+    free(ok);
+    free(cell);
+    free(sgn);
     return nv > 0 ? sum / (double)nv : 0.0;
+}
+
+/*
+ * Straddles of the geometry-consistency loss for an FP32 evaluation that keeps
+ * the projection as the pixel plus the FP32 displacement (eq2_bound): per
+ * pixel, with margins safety x the error bound of x', y', a and b,
+ *   bit 0: x' or y' within its margin of an integer (the sample cell; a kink
+ *          of the gradient, the loss is continuous there),
+ *   bit 1: x' or y' within its margin of the border, or P2 within its margin
+ *          of 0 (the valid set: the loss jumps),
+ *   bit 2: |a - b| within the margin of a - b (the branch of |a - b|: a kink).
+ * count_lo/hi: the valid count over every outcome of the bit-1 decisions;
+ * loss_lo/hi: the loss over those outcomes (a pixel's term |a-b|/(a+b) lies in
+ * [0, 1] for positive depths).  Returns the number of flagged pixels.
+ */
+int64_t orc_geo_bounds(int32_t W, int32_t H, double fx, double fy, double cx, double cy, const double* rho0,
+                       const double* rho1, const double* ego, double dt, double safety, uint8_t* flags,
+                       int64_t* count_lo, int64_t* count_hi, double* loss_lo, double* loss_hi)
+{
+    const double k[3] = {-ego[3] * dt, -ego[4] * dt, -ego[5] * dt};
+    const double t[3] = {-ego[0] * dt, -ego[1] * dt, -ego[2] * dt};
+    double Rm[3][3], Aabs[3][3];
+    rodrigues(k, Rm);
+    rot_abs(k, Aabs);
+    int64_t nsure = 0, nmaybe = 0, nflag = 0;
+    double ssure = 0.0;
+    for (int32_t v = 0; v < H; ++v) {
+        for (int32_t u = 0; u < W; ++u) {
+            const int64_t q = (int64_t)v * W + u;
+            geo_proj g;
+            geo_project(Rm, t, fx, fy, cx, cy, u, v, rho0[q], &g);
+            const double e0 = g.P[0] - g.xn * g.P[2], e1 = g.P[1] - g.yn * g.P[2];
+            double ebx, eby, ebp;
+            eq2_bound(Aabs, t, g.xn, g.yn, g.Z, g.P[2], e0, e1, fx, fy, &ebx, &eby, &ebp);
+            /* the displacement is added to the integer pixel: no further rounding of x'
+             * (an exact displacement, error bound 0, decides exactly: margin 0) */
+            const double mx = ebx > 0.0 ? safety * (ebx + ORC_U) : 0.0;
+            const double my = eby > 0.0 ? safety * (eby + ORC_U) : 0.0, mp = safety * ebp;
+            uint8_t f = 0;
+            const double W1 = (double)(W - 1), H1 = (double)(H - 1);
+            if (fabs(g.P[2]) <= mp || (mx > 0.0 && (fabs(g.xp) <= mx || fabs(g.xp - W1) <= mx)) ||
+                (my > 0.0 && (fabs(g.yp) <= my || fabs(g.yp - H1) <= my)))
+                f |= 2;
+            const int valid = g.P[2] > 0.0 && geo_inside(g.xp, g.yp, W, H);
+            if (valid) {
+                if ((mx > 0.0 && fabs(g.xp - floor(g.xp + 0.5)) <= mx) ||
+                    (my > 0.0 && fabs(g.yp - floor(g.yp + 0.5)) <= my))
+                    f |= 1;
+                double dbx, dby, w[4], D[4];
+                int64_t c[4];
+                const double b = geo_sample(rho1, W, H, g.xp, g.yp, (int)floor(g.xp), (int)floor(g.yp), &dbx, &dby,
+                                            w, c, D);
+                /* b: weights from x' (its error times the slope) and 1/rho1 (two roundings each) */
+                const double Dmax = fmax(fmax(fabs(D[0]), fabs(D[1])), fmax(fabs(D[2]), fabs(D[3])));
+                const double eb = fabs(dbx) * (ebx + ORC_U) + fabs(dby) * (eby + ORC_U) + 8.0 * ORC_U * Dmax;
+                if (fabs(g.P[2] - b) <= safety * (ebp + eb)) f |= 4;
+                if (f & 2) nmaybe += 1;
+                else {
+                    nsure += 1;
+                    ssure += fabs(g.P[2] - b) / (g.P[2] + b);
+                }
+            } else if (f & 2) {
+                nmaybe += 1;
+            }
+            if (flags) flags[q] = f;
+            nflag += f != 0;
+        }
+    }
+    *count_lo = nsure;
+    *count_hi = nsure + nmaybe;
+    *loss_lo = nsure + nmaybe > 0 ? ssure / (double)(nsure + nmaybe) : 0.0;
+    *loss_hi = nsure > 0 ? (ssure + (double)nmaybe) / (double)nsure : (nmaybe > 0 ? 1.0 : 0.0);
+    return nflag;
 }
 
 /*
@@ -592,9 +689,7 @@ typedef struct {
     int32_t nbins;           /* B >= 1 */
     int32_t ref_mode;        /* ORC_REF_END or ORC_REF_ALL */
     int32_t n_flow_bins;     /* 1 (one field for every bin) or B (one per bin) */
-    int32_t pos_f32;         /* 1: positions in FP32 (kernel precision); 0: FP64 */
     int32_t branch_mode;     /* 0: decide; 1: decide and record; 2: replay record */
-    int32_t pad_;
     int64_t n;               /* number of events */
     const int16_t* x;        /* [n] pixel column */
     const int16_t* y;        /* [n] pixel row */
@@ -604,7 +699,6 @@ typedef struct {
     double eps;              /* regulariser of both ratios */
     double dloss;            /* upstream gradient dOut/dL for the backward */
     const double* flow;      /* [nfb][H][W][2], FP64 values */
-    const float* flow32;     /* [nfb][H][W][2], FP32 flow for pos_f32 = 1 */
     /* branch record, [n] and [n][B+1]: used when branch_mode != 0 */
     int32_t* br_cell;        /* [n][B+1][2] floor of each computed position */
     uint8_t* br_supp;        /* [n][B+1] bit c: corner c carries a nonzero weight */
@@ -631,11 +725,6 @@ typedef struct {
 static const double* field64(const orc_cm_args* a, int j)
 {
     return a->flow + (a->n_flow_bins == 1 ? 0 : (int64_t)j * a->W * a->H * 2);
-}
-
-static const float* field32(const orc_cm_args* a, int j)
-{
-    return a->flow32 + (a->n_flow_bins == 1 ? 0 : (int64_t)j * a->W * a->H * 2);
 }
 
 /* bilinear sample of one field at (px, py) in cell (ix, iy), FP64; also the
@@ -665,40 +754,9 @@ static void sample64(const double* U, int W, int H, double px, double py, int ix
     }
 }
 
-/* FP32 bilinear sample with the fixed operation order of the kernels:
- *   ax = px - floor(px), bx = 1 - ax (same in y)
- *   w00 = bx*by, w10 = ax*by, w01 = bx*ay, w11 = ax*ay
- *   u = w00*u00;  u = fma(w10, u10, u);  u = fma(w01, u01, u);  u = fma(w11, u11, u) */
-static void sample32(const float* U, int W, int H, float px, float py, float u[2])
-{
-    const float fx0 = floorf(px), fy0 = floorf(py);
-    const float ax = px - fx0, ay = py - fy0;
-    const float bx = 1.0f - ax, by = 1.0f - ay;
-    const float w00 = bx * by, w10 = ax * by, w01 = bx * ay, w11 = ax * ay;
-    const int ix = (int)fx0, iy = (int)fy0;
-    const int ix1 = ix + 1 < W ? ix + 1 : W - 1;
-    const int iy1 = iy + 1 < H ? iy + 1 : H - 1;
-    const float* p00 = U + 2 * ((int64_t)iy * W + ix);
-    const float* p10 = U + 2 * ((int64_t)iy * W + ix1);
-    const float* p01 = U + 2 * ((int64_t)iy1 * W + ix);
-    const float* p11 = U + 2 * ((int64_t)iy1 * W + ix1);
-    for (int d = 0; d < 2; ++d) {
-        float s = w00 * p00[d];
-        s = fmaf(w10, p10[d], s);
-        s = fmaf(w01, p01[d], s);
-        s = fmaf(w11, p11[d], s);
-        u[d] = s;
-    }
-}
-
 static int inside64(double px, double py, int W, int H)
 {
     return px >= 0.0 && px <= (double)(W - 1) && py >= 0.0 && py <= (double)(H - 1);
-}
-
-static int inside32(float px, float py, int W, int H)
-{
-    return px >= 0.0f && px <= (float)(W - 1) && py >= 0.0f && py <= (float)(H - 1);
 }
 
 /* support bits of the four corners at position (px, py) in cell (ix, iy): a
@@ -715,17 +773,13 @@ static uint8_t support_bits(double px, double py, int ix, int iy, int W, int H)
     return s;
 }
 
-/* Bin index of normalised time tau: b = min(floor(tau * B), B - 1), clamped
- * below at 0.  In the FP32 mode tau = (t - t0) / (t1 - t0) and tau * B are
- * single-precision operations, as in the kernels. */
-static int bin_of(const orc_cm_args* a, int B, int64_t k, double* tau64, float* tau32)
+/* Bin index of normalised time tau = (t - t0) / (t1 - t0):
+ * b = min(floor(tau * B), B - 1), clamped below at 0. */
+static int bin_of(const orc_cm_args* a, int B, int64_t k, double* tau64)
 {
     const double tau = ((double)a->t[k] - a->t0) / (a->t1 - a->t0);
-    const float t0f = (float)a->t0, t1f = (float)a->t1;
-    const float tf = (a->t[k] - t0f) / (t1f - t0f);
     *tau64 = tau;
-    *tau32 = tf;
-    double q = a->pos_f32 ? (double)floorf(tf * (float)B) : floor(tau * (double)B);
+    const double q = floor(tau * (double)B);
     int b = (int)(q < 0 ? 0 : q);
     if (b > B - 1) b = B - 1;
     return b;
@@ -747,59 +801,12 @@ static int trajectory(const orc_cm_args* a, const orc_setup* s, int64_t k, int* 
     const int W = a->W, H = a->H, B = s->B;
     const int xk = a->x[k], yk = a->y[k];
     double tau;
-    float tau32;
-    int b = bin_of(a, B, k, &tau, &tau32);
+    int b = bin_of(a, B, k, &tau);
     *tau_out = tau;
     if (a->branch_mode == 2) b = a->br_bin[k];
     *bin_out = b;
     if (xk < 0 || xk > W - 1 || yk < 0 || yk > H - 1) return 0;
     const int replay = a->branch_mode == 2;
-    int ok = 1;
-    if (a->pos_f32 && !replay) {
-        /* FP32 trajectory with the kernels' operation order:
-         *   tau_j = j / B, h = 1 / B (single-precision divisions)
-         *   forward:  x = fma(tau_{b+1} - tau, u_b(x_k), x_k), then x = fma(h, u_j(x), x)
-         *   backward: x = fma(-(tau - tau_b), u_b(x_k), x_k), then x = fma(-h, u_{j-1}(x), x) */
-        const float Bf = (float)B, h = 1.0f / Bf;
-        float p32[ORC_MAX_BINS + 1][2];
-        float u0[2];
-        sample32(field32(a, b), W, H, (float)xk, (float)yk, u0);
-        if (s->jhi > b) {
-            const float dt = (float)(b + 1) / Bf - tau32;
-            p32[b + 1][0] = fmaf(dt, u0[0], (float)xk);
-            p32[b + 1][1] = fmaf(dt, u0[1], (float)yk);
-            for (int j = b + 1; j < s->jhi; ++j) {
-                if (!inside32(p32[j][0], p32[j][1], W, H)) { ok = 0; break; }
-                float u[2];
-                sample32(field32(a, j), W, H, p32[j][0], p32[j][1], u);
-                p32[j + 1][0] = fmaf(h, u[0], p32[j][0]);
-                p32[j + 1][1] = fmaf(h, u[1], p32[j][1]);
-            }
-            if (ok && !inside32(p32[s->jhi][0], p32[s->jhi][1], W, H)) ok = 0;
-        }
-        if (ok && s->jlo <= b) {
-            const float dt = tau32 - (float)b / Bf;
-            p32[b][0] = fmaf(-dt, u0[0], (float)xk);
-            p32[b][1] = fmaf(-dt, u0[1], (float)yk);
-            for (int j = b; j > s->jlo; --j) {
-                if (!inside32(p32[j][0], p32[j][1], W, H)) { ok = 0; break; }
-                float u[2];
-                sample32(field32(a, j - 1), W, H, p32[j][0], p32[j][1], u);
-                p32[j - 1][0] = fmaf(-h, u[0], p32[j][0]);
-                p32[j - 1][1] = fmaf(-h, u[1], p32[j][1]);
-            }
-            if (ok && !inside32(p32[s->jlo][0], p32[s->jlo][1], W, H)) ok = 0;
-        }
-        if (!ok) return 0;
-        for (int j = s->jlo; j <= s->jhi; ++j) {
-            pos[j][0] = (double)p32[j][0];
-            pos[j][1] = (double)p32[j][1];
-            cell[j][0] = (int)floor(pos[j][0]);
-            cell[j][1] = (int)floor(pos[j][1]);
-            supp[j] = support_bits(pos[j][0], pos[j][1], cell[j][0], cell[j][1], W, H);
-        }
-        return 1;
-    }
 
     /* FP64 trajectory (the plain definition), or a replay of a recorded branch:
      * cells, support and validity taken from the record, positions in FP64 */
@@ -858,8 +865,7 @@ static int setup(const orc_cm_args* a, orc_setup* s)
     if (!(a->t1 > a->t0) || a->n < 0 || !(a->eps > 0)) return ORC_EINVAL;
     if (a->n_flow_bins != 1 && a->n_flow_bins != a->nbins) return ORC_EINVAL;
     if (a->ref_mode != ORC_REF_END && a->ref_mode != ORC_REF_ALL) return ORC_EINVAL;
-    if (a->pos_f32 && !a->flow32) return ORC_EINVAL;
-    if (a->branch_mode == 2 && (a->pos_f32 || !a->br_cell || !a->br_supp || !a->br_valid || !a->br_bin))
+    if (a->branch_mode == 2 && (!a->br_cell || !a->br_supp || !a->br_valid || !a->br_bin))
         return ORC_EINVAL;
     if (a->branch_mode == 1 && (!a->br_cell || !a->br_supp || !a->br_valid || !a->br_bin)) return ORC_EINVAL;
     const int B = a->nbins;
@@ -886,8 +892,7 @@ static void event_range(const orc_cm_args* a, const orc_setup* s0, int64_t k, or
     *s = *s0;
     if (a->ref_mode == ORC_REF_END) {
         double t64;
-        float t32;
-        const int b = a->branch_mode == 2 ? a->br_bin[k] : bin_of(a, s0->B, k, &t64, &t32);
+        const int b = a->branch_mode == 2 ? a->br_bin[k] : bin_of(a, s0->B, k, &t64);
         s->jlo = b + 1;
     }
 }
@@ -1090,4 +1095,361 @@ int orc_cm(orc_cm_args* a)
     return ORC_OK;
 }
 
-int orc_abi_version(void) { return 1; }
+/* ------------------------------------------------------------------------- */
+/* Straddles of an FP32 evaluation: flags and the interval of the loss       */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+    double safety;          /* margin of a decision = safety x (error bound + u); 0 error -> 0 margin */
+    int32_t pad_;
+    int32_t pad2_;
+    const double* eflow;    /* [nfb][H][W] bound on |flow32 - flow| per pixel, or NULL: the flow values
+                             * are FP32 numbers given to both evaluations exactly */
+    /* outputs; NULL = not wanted */
+    uint8_t* flags;         /* [n]: bit 0 a point within its margin of an integer coordinate (cell and
+                             * support decisions), bit 1 within its margin of the image border (the mask),
+                             * bit 2 tau B within its margin of an interior bin edge (the bin) */
+    double* err;            /* [n][B+1][2] error bound of each computed point (NaN elsewhere) */
+    double* loss_lo;        /* [1] */
+    double* loss_hi;        /* [1] */
+    double* loss_r_lo;      /* [R] */
+    double* loss_r_hi;      /* [R] */
+    int64_t* nnz_lo;        /* [R] */
+    int64_t* nnz_hi;        /* [R] */
+    int64_t counts[4];      /* events with bit 0, bit 1, bit 2, any bit */
+} orc_bounds;
+
+/* largest change of each flow component between neighbouring pixels along x
+ * (L[d][0]) and along y (L[d][1]) over rows iy-1..iy+2 and columns ix-1..ix+2
+ * (clamped): a Lipschitz constant of the bilinear interpolant within one pixel
+ * of cell (ix, iy) */
+static void lipschitz(const double* U, int W, int H, int ix, int iy, double L[2][2])
+{
+    L[0][0] = L[0][1] = L[1][0] = L[1][1] = 0.0;
+    for (int yy = iy - 1; yy <= iy + 2; ++yy) {
+        const int y0 = yy < 0 ? 0 : (yy > H - 1 ? H - 1 : yy);
+        for (int xx = ix - 1; xx <= ix + 2; ++xx) {
+            const int x0 = xx < 0 ? 0 : (xx > W - 1 ? W - 1 : xx);
+            const int x1 = x0 + 1 < W ? x0 + 1 : W - 1, y1 = y0 + 1 < H ? y0 + 1 : H - 1;
+            const double* p = U + 2 * ((int64_t)y0 * W + x0);
+            const double* px = U + 2 * ((int64_t)y0 * W + x1);
+            const double* py = U + 2 * ((int64_t)y1 * W + x0);
+            for (int d = 0; d < 2; ++d) {
+                const double gx = fabs(px[d] - p[d]), gy = fabs(py[d] - p[d]);
+                if (gx > L[d][0]) L[d][0] = gx;
+                if (gy > L[d][1]) L[d][1] = gy;
+            }
+        }
+    }
+}
+
+static double clampd(double v, double lo, double hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+/* flags of one point from its position and error bound; returns 0 when the
+ * point lies outside the image beyond its margin (outside in any evaluation) */
+static int point_flags(const double p[2], const double e[2], double safety, int W, int H, double m[2],
+                       uint8_t* flag)
+{
+    const double ext[2] = {(double)(W - 1), (double)(H - 1)};
+    for (int d = 0; d < 2; ++d) {
+        m[d] = e[d] > 0.0 ? safety * (e[d] + ORC_U) : 0.0;
+        if (p[d] < -m[d] || p[d] > ext[d] + m[d]) return 0;
+        if (m[d] > 0.0) {
+            if (fabs(p[d]) <= m[d] || fabs(p[d] - ext[d]) <= m[d]) *flag |= 2;
+            if (fabs(p[d] - floor(p[d] + 0.5)) <= m[d]) *flag |= 1;
+        }
+    }
+    return 1;
+}
+
+/*
+ * The FP64 trajectory of event k with a bound on the error of an FP32
+ * evaluation of every point, and the event's flags.  The bound assumes the
+ * evaluation keeps each point as the event's pixel plus an FP32 offset (so a
+ * rounding costs u times the offset, not u times the coordinate) and follows
+ * each push x' = x + hs u(x):
+ *   e' = e + |hs| (L e + 8 u max|u_c| + max eflow_c) + u |hs u| + u |x' - x_k|
+ * (L: Lipschitz constants of the sampled field near x, u_c / eflow_c: the
+ * corner values and their bounds); the first push of a chain adds the error
+ * of tau and of tau_j to its time step.  A point outside the image by less
+ * than its margin is carried on (the flow sampled at the nearest image point)
+ * and makes the event's validity uncertain (flag bit 1).
+ * Returns 0 for an event that is outside the image (or the sensor) in any
+ * evaluation, 1 for a valid one, 2 for one whose validity is uncertain.
+ */
+static int traj_bound(const orc_cm_args* a, const orc_setup* s, const double* eflow, double safety, int64_t k,
+                      int* bin_out, double* tau_out, double pos[][2], double err[][2], double mar[][2],
+                      uint8_t* flag)
+{
+    const int W = a->W, H = a->H, B = s->B;
+    const int64_t HW = (int64_t)W * H;
+    const int xk = a->x[k], yk = a->y[k];
+    double tau;
+    const int b = bin_of(a, B, k, &tau);
+    *tau_out = tau;
+    *bin_out = b;
+    *flag = 0;
+    if (xk < 0 || xk > W - 1 || yk < 0 || yk > H - 1) return 0;
+    const double etau = 4.0 * ORC_U * fabs(tau);
+    {
+        const double q = tau * (double)B, qr = floor(q + 0.5);
+        const double mq = safety * ((double)B * etau + 2.0 * ORC_U * fabs(q));
+        if (qr >= 1.0 && qr <= (double)(B - 1) && fabs(q - qr) <= mq && mq > 0.0) *flag |= 4;
+    }
+    const double h = 1.0 / (double)B;
+    int status = 1;
+    const double* U0 = field64(a, b);
+    const double* E0 = eflow ? eflow + (a->n_flow_bins == 1 ? 0 : (int64_t)b * HW) : NULL;
+    const int64_t i0 = (int64_t)yk * W + xk;
+    const double u0[2] = {U0[2 * i0], U0[2 * i0 + 1]};
+    const double e0 = E0 ? E0[i0] : 0.0;
+    for (int dir = 0; dir < 2; ++dir) {
+        /* dir 0: forward chain b+1 .. jhi; dir 1: backward chain b .. jlo */
+        if (dir == 0 && !(s->jhi > b)) continue;
+        if (dir == 1 && !(s->jlo <= b)) continue;
+        const int jfirst = dir == 0 ? b + 1 : b;
+        const double dt = dir == 0 ? s->tau_edge[b + 1] - tau : -(tau - s->tau_edge[b]);
+        const double edt = etau + ORC_U * s->tau_edge[dir == 0 ? b + 1 : b] + ORC_U * fabs(dt);
+        for (int d = 0; d < 2; ++d) {
+            const double disp = dt * u0[d];
+            pos[jfirst][d] = (double)(d == 0 ? xk : yk) + disp;
+            err[jfirst][d] = (u0[d] != 0.0 || e0 > 0.0) ? fabs(u0[d]) * edt + fabs(dt) * e0 + ORC_U * fabs(disp)
+                                                         : 0.0;
+        }
+        if (!point_flags(pos[jfirst], err[jfirst], safety, W, H, mar[jfirst], flag)) return 0;
+        if (!inside64(pos[jfirst][0], pos[jfirst][1], W, H)) status = 2;
+        const int jend = dir == 0 ? s->jhi : s->jlo;
+        const int step = dir == 0 ? 1 : -1;
+        const double hs = dir == 0 ? h : -h;
+        for (int j = jfirst; j != jend; j += step) {
+            const int field = dir == 0 ? j : j - 1;
+            const int jn = j + step;
+            /* sample at the point, moved into the image when it lies just outside */
+            const double px = clampd(pos[j][0], 0.0, (double)(W - 1)), py = clampd(pos[j][1], 0.0, (double)(H - 1));
+            const int ix = (int)floor(px), iy = (int)floor(py);
+            double u[2], J[2][2], w[4];
+            int64_t idx[4];
+            const double* U = field64(a, field);
+            sample64(U, W, H, px, py, ix, iy, u, J, w, idx);
+            double L[2][2];
+            lipschitz(U, W, H, ix, iy, L);
+            double umax[2] = {0, 0}, emax = 0.0;
+            const double* E = eflow ? eflow + (a->n_flow_bins == 1 ? 0 : (int64_t)field * HW) : NULL;
+            for (int c = 0; c < 4; ++c) {
+                for (int d = 0; d < 2; ++d)
+                    if (fabs(U[2 * idx[c] + d]) > umax[d]) umax[d] = fabs(U[2 * idx[c] + d]);
+                if (E && E[idx[c]] > emax) emax = E[idx[c]];
+            }
+            for (int d = 0; d < 2; ++d) {
+                const double inc = hs * u[d];
+                pos[jn][d] = pos[j][d] + inc;
+                const double off = pos[jn][d] - (double)(d == 0 ? xk : yk);
+                const int exact = err[j][0] == 0.0 && err[j][1] == 0.0 && emax == 0.0 && umax[d] == 0.0;
+                err[jn][d] = exact ? err[j][d]
+                                   : err[j][d] + fabs(hs) * (L[d][0] * err[j][0] + L[d][1] * err[j][1] +
+                                                             8.0 * ORC_U * umax[d] + emax) +
+                                         ORC_U * fabs(inc) + ORC_U * fabs(off);
+            }
+            if (!point_flags(pos[jn], err[jn], safety, W, H, mar[jn], flag)) return 0;
+            if (!inside64(pos[jn][0], pos[jn][1], W, H)) status = 2;
+        }
+    }
+    if (*flag & 2) status = 2;
+    return status;
+}
+
+/* one maybe contribution: weight in [0, wmax] of average timestamp tbar to
+ * polarity pol of pixel pix at reference r */
+typedef struct {
+    int64_t key;   /* (r * HW + pix) * 2 + pol */
+    double wmax, tbar;
+} orc_maybe;
+
+static int cmp_maybe(const void* x, const void* y)
+{
+    const int64_t a = ((const orc_maybe*)x)->key, b = ((const orc_maybe*)y)->key;
+    return a < b ? -1 : (a > b);
+}
+
+/* range of T = (S + sum w_i t_i) / (C + sum w_i + eps) over w_i in [0, wmax_i]:
+ * a linear-fractional function of the w_i, extreme at a vertex of the box */
+static void t_range(double C, double S, const orc_maybe* m, int k, double eps, double* lo, double* hi)
+{
+    if (k > 12) {
+        double sw = 0, swt = 0;
+        for (int i = 0; i < k; ++i) {
+            sw += m[i].wmax;
+            swt += m[i].wmax * m[i].tbar;
+        }
+        *lo = S / (C + sw + eps);
+        *hi = (S + swt) / (C + eps);
+        return;
+    }
+    double tl = INFINITY, th = -INFINITY;
+    for (int v = 0; v < (1 << k); ++v) {
+        double c = C, sm = S;
+        for (int i = 0; i < k; ++i)
+            if (v >> i & 1) {
+                c += m[i].wmax;
+                sm += m[i].wmax * m[i].tbar;
+            }
+        const double T = sm / (c + eps);
+        if (T < tl) tl = T;
+        if (T > th) th = T;
+    }
+    *lo = tl;
+    *hi = th;
+}
+
+/*
+ * Flags and the loss interval (see the header).  Per reference and pixel the
+ * splat is split into sure contributions (both axis factors of the corner away
+ * from a flagged decision, event surely valid) and maybe contributions (weight
+ * anywhere in [0, its bound]): a corner whose factor is within the margin of 0
+ * on the near side of an integer, the mirror corner on the far side (where an
+ * FP32 floor on the other side of the integer would put the small weight), and
+ * every corner of an event of uncertain validity.  N_nz(r) lies between the
+ * pixels with a sure contribution and those plus the pixels with only maybe
+ * ones; the sum of T^2 between the sums of each pixel's extremes; L_r and L
+ * between the ratios of those bounds.
+ */
+int orc_cm_bounds(const orc_cm_args* a, orc_bounds* o)
+{
+    orc_setup s0;
+    int st = setup(a, &s0);
+    if (st) return st;
+    if (a->branch_mode != 0 || !(o->safety >= 0)) return ORC_EINVAL;
+    const int W = a->W, H = a->H, B = s0.B, R = s0.R;
+    const int64_t HW = (int64_t)W * H;
+    double* iwe = (double*)calloc((size_t)(R * HW * 4), sizeof(double));
+    uint8_t* hit = (uint8_t*)calloc((size_t)(R * HW), 1);
+    size_t mcap = 1024, mn = 0;
+    orc_maybe* mb = (orc_maybe*)malloc(sizeof(orc_maybe) * mcap);
+    if (!iwe || !hit || !mb) { free(iwe); free(hit); free(mb); return ORC_ENOMEM; }
+    double pos[ORC_MAX_BINS + 1][2], err[ORC_MAX_BINS + 1][2], mar[ORC_MAX_BINS + 1][2];
+    for (int q = 0; q < 4; ++q) o->counts[q] = 0;
+    for (int64_t k = 0; k < a->n; ++k) {
+        orc_setup s;
+        int b;
+        double tau;
+        uint8_t flag = 0;
+        event_range(a, &s0, k, &s);
+        for (int j = 0; j <= B; ++j) err[j][0] = err[j][1] = NAN;
+        const int status = traj_bound(a, &s, o->eflow, o->safety, k, &b, &tau, pos, err, mar, &flag);
+        if (o->flags) o->flags[k] = flag;
+        if (o->err)
+            for (int j = 0; j <= B; ++j) {
+                const int have = status && j >= s.jlo && j <= s.jhi;
+                o->err[2 * (k * (B + 1) + j) + 0] = have ? err[j][0] : NAN;
+                o->err[2 * (k * (B + 1) + j) + 1] = have ? err[j][1] : NAN;
+            }
+        for (int q = 0; q < 3; ++q) o->counts[q] += (flag >> q) & 1;
+        o->counts[3] += flag != 0;
+        if (!status) continue;
+        const int pol = a->p[k] > 0 ? 0 : 1;
+        for (int r = 0; r < R; ++r) {
+            const int j = s.ref_edge[r];
+            const double tbar = 1.0 - fabs(s.tau_edge[j] - tau);
+            /* per axis: up to three columns / rows, each with a factor, a bound
+             * on it and whether it is sure */
+            int cix[2][3], ncand[2];
+            double fac[2][3], fmax[2][3];
+            int sure[2][3];
+            for (int d = 0; d < 2; ++d) {
+                const double x = pos[j][d], m = mar[j][d];
+                const int x0 = (int)floor(x);
+                const double f = x - x0;
+                int n = 0;
+                if (m > 0.0 && f <= m) {
+                    cix[d][n] = x0; fac[d][n] = 1 - f; fmax[d][n] = 1 - f + m; sure[d][n++] = 1;
+                    cix[d][n] = x0 + 1; fac[d][n] = f; fmax[d][n] = f + m; sure[d][n++] = 0;
+                    cix[d][n] = x0 - 1; fac[d][n] = 0; fmax[d][n] = m - f; sure[d][n++] = 0;
+                } else if (m > 0.0 && 1 - f <= m) {
+                    cix[d][n] = x0 + 1; fac[d][n] = f; fmax[d][n] = f + m; sure[d][n++] = 1;
+                    cix[d][n] = x0; fac[d][n] = 1 - f; fmax[d][n] = 1 - f + m; sure[d][n++] = 0;
+                    cix[d][n] = x0 + 2; fac[d][n] = 0; fmax[d][n] = m - (1 - f); sure[d][n++] = 0;
+                } else {
+                    cix[d][n] = x0; fac[d][n] = 1 - f; fmax[d][n] = 1 - f + m; sure[d][n++] = 1;
+                    cix[d][n] = x0 + 1; fac[d][n] = f; fmax[d][n] = f + m; sure[d][n++] = 1;
+                }
+                ncand[d] = n;
+            }
+            for (int cy = 0; cy < ncand[1]; ++cy) {
+                for (int cx = 0; cx < ncand[0]; ++cx) {
+                    const int X = cix[0][cx], Y = cix[1][cy];
+                    if (X < 0 || X > W - 1 || Y < 0 || Y > H - 1) continue;
+                    const int64_t pix = (int64_t)Y * W + X;
+                    const int is_sure = status == 1 && sure[0][cx] && sure[1][cy];
+                    if (is_sure) {
+                        const double wgt = fac[0][cx] * fac[1][cy];
+                        if (wgt <= 0.0) continue;
+                        double* q = iwe + 4 * (r * HW + pix) + 2 * pol;
+                        q[0] += wgt;
+                        q[1] += wgt * tbar;
+                        hit[r * HW + pix] = 1;
+                    } else {
+                        const double wmax = (sure[0][cx] && status == 1 ? fac[0][cx] : fmax[0][cx]) *
+                                            (sure[1][cy] && status == 1 ? fac[1][cy] : fmax[1][cy]);
+                        if (!(wmax > 0.0)) continue;
+                        if (mn == mcap) {
+                            mcap *= 2;
+                            orc_maybe* nb = (orc_maybe*)realloc(mb, sizeof(orc_maybe) * mcap);
+                            if (!nb) { free(iwe); free(hit); free(mb); return ORC_ENOMEM; }
+                            mb = nb;
+                        }
+                        mb[mn].key = (r * HW + pix) * 2 + pol;
+                        mb[mn].wmax = wmax;
+                        mb[mn].tbar = tbar;
+                        mn += 1;
+                    }
+                }
+            }
+        }
+    }
+    qsort(mb, mn, sizeof(orc_maybe), cmp_maybe);
+    /* per reference: sums over the pixels without maybe contributions, then
+     * the pixels with some */
+    double Llo = 0.0, Lhi = 0.0;
+    size_t mi = 0;
+    for (int r = 0; r < R; ++r) {
+        double slo = 0.0, shi = 0.0;
+        int64_t nlo = 0, nmaybe = 0;
+        for (int64_t i = 0; i < HW; ++i) {
+            const double* q = iwe + 4 * (r * HW + i);
+            const int64_t kp = (r * HW + i) * 2;
+            double tlo[2], thi[2];
+            int any_maybe = 0;
+            for (int p = 0; p < 2; ++p) {
+                size_t m0 = mi;
+                while (mi < mn && mb[mi].key == kp + p) ++mi;
+                const int km = (int)(mi - m0);
+                any_maybe |= km > 0;
+                if (km == 0) {
+                    tlo[p] = thi[p] = q[2 * p + 1] / (q[2 * p] + a->eps);
+                } else {
+                    t_range(q[2 * p], q[2 * p + 1], mb + m0, km, a->eps, &tlo[p], &thi[p]);
+                }
+            }
+            slo += tlo[0] * tlo[0] + tlo[1] * tlo[1];
+            shi += thi[0] * thi[0] + thi[1] * thi[1];
+            if (hit[r * HW + i]) nlo += 1;
+            else if (any_maybe) nmaybe += 1;
+        }
+        const double lo = slo / ((double)(nlo + nmaybe) + a->eps);
+        const double hi = shi / ((double)nlo + a->eps);
+        if (o->loss_r_lo) o->loss_r_lo[r] = lo;
+        if (o->loss_r_hi) o->loss_r_hi[r] = hi;
+        if (o->nnz_lo) o->nnz_lo[r] = nlo;
+        if (o->nnz_hi) o->nnz_hi[r] = nlo + nmaybe;
+        Llo += lo;
+        Lhi += hi;
+    }
+    if (o->loss_lo) o->loss_lo[0] = Llo / (double)R;
+    if (o->loss_hi) o->loss_hi[0] = Lhi / (double)R;
+    free(iwe);
+    free(hit);
+    free(mb);
+    return ORC_OK;
+}
+
+int orc_abi_version(void) { return 2; }

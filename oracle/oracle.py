@@ -5,7 +5,10 @@ the CPU-baseline / reference legs of bench.py.  The CUDA product path never
 imports this module.
 
 Each function cites the part of the paper it follows; the C file states the
-readings taken where the paper is silent.
+readings taken where the paper is silent.  Every value is computed in FP64.
+The *_bounds functions flag the decisions (cells, supports, mask, bins, the
+valid set and branch of Eq. 3) that an FP32 evaluation could take the other
+way, and give the interval of the loss over those outcomes.
 """
 from __future__ import annotations
 
@@ -23,6 +26,7 @@ CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-s
 
 REF_END = 0
 REF_ALL = 1
+SAFETY = 4.0  # margin of a flagged decision: SAFETY x the FP32 error bound of its input
 
 _lock = threading.Lock()
 _lib = None
@@ -40,17 +44,32 @@ def build(force: bool = False) -> str:
 class _Args(ctypes.Structure):
     _fields_ = [
         ("W", ctypes.c_int32), ("H", ctypes.c_int32), ("nbins", ctypes.c_int32),
-        ("ref_mode", ctypes.c_int32), ("n_flow_bins", ctypes.c_int32), ("pos_f32", ctypes.c_int32),
-        ("branch_mode", ctypes.c_int32), ("pad_", ctypes.c_int32),
+        ("ref_mode", ctypes.c_int32), ("n_flow_bins", ctypes.c_int32), ("branch_mode", ctypes.c_int32),
         ("n", ctypes.c_int64),
         ("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("t", ctypes.c_void_p), ("p", ctypes.c_void_p),
         ("t0", ctypes.c_double), ("t1", ctypes.c_double), ("eps", ctypes.c_double), ("dloss", ctypes.c_double),
-        ("flow", ctypes.c_void_p), ("flow32", ctypes.c_void_p),
+        ("flow", ctypes.c_void_p),
         ("br_cell", ctypes.c_void_p), ("br_supp", ctypes.c_void_p), ("br_valid", ctypes.c_void_p),
         ("br_bin", ctypes.c_void_p),
         ("loss", ctypes.c_void_p), ("loss_r", ctypes.c_void_p), ("nnz_r", ctypes.c_void_p),
         ("iwe", ctypes.c_void_p), ("dflow", ctypes.c_void_p), ("valid", ctypes.c_void_p), ("pos", ctypes.c_void_p),
     ]
+
+
+class _Bounds(ctypes.Structure):
+    _fields_ = [
+        ("safety", ctypes.c_double), ("pad_", ctypes.c_int32), ("pad2_", ctypes.c_int32),
+        ("eflow", ctypes.c_void_p), ("flags", ctypes.c_void_p), ("err", ctypes.c_void_p),
+        ("loss_lo", ctypes.c_void_p), ("loss_hi", ctypes.c_void_p),
+        ("loss_r_lo", ctypes.c_void_p), ("loss_r_hi", ctypes.c_void_p),
+        ("nnz_lo", ctypes.c_void_p), ("nnz_hi", ctypes.c_void_p),
+        ("counts", ctypes.c_int64 * 4),
+    ]
+
+
+class _GeoDec(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("pad_", ctypes.c_int32), ("cell", ctypes.c_void_p),
+                ("ok", ctypes.c_void_p), ("sgn", ctypes.c_void_p)]
 
 
 def lib():
@@ -60,18 +79,21 @@ def lib():
             l = ctypes.CDLL(build())
             d, i, f, vp = ctypes.c_double, ctypes.c_int32, ctypes.c_float, ctypes.c_void_p
             l.orc_flow_from_depth.argtypes = [i, i, d, d, d, d, vp, vp, d, vp]
-            l.orc_flow_from_depth_f32.argtypes = [i, i, f, f, f, f, vp, vp, f, vp]
+            l.orc_flow_error_bound.argtypes = [i, i, d, d, d, d, vp, vp, d, vp]
             l.orc_depth_ego_grad.argtypes = [i, i, d, d, d, d, vp, vp, d, vp, vp, vp]
             l.orc_flow_eq2.argtypes = [i, i, d, d, d, d, vp, vp, d, vp]
             l.orc_flow_eq2_bins.argtypes = [i, i, d, d, d, d, vp, vp, i, d, d, vp]
-            l.orc_flow_eq2_bins_f32.argtypes = [i, i, f, f, f, f, vp, vp, i, f, f, vp]
+            l.orc_flow_eq2_error_bound.argtypes = [i, i, d, d, d, d, vp, vp, i, d, d, vp]
             l.orc_flow_eq2_grad.argtypes = [i, i, d, d, d, d, vp, vp, i, d, d, vp, vp, vp]
             l.orc_event_frame.argtypes = [i, i, ctypes.c_int64, vp, vp, vp, vp]
-            l.orc_geo_proj_f32.argtypes = [i, i, f, f, f, f, vp, vp, vp, f, vp, vp, vp]
-            l.orc_geo.argtypes = [i, i, d, d, d, d, vp, vp, vp, d, vp, vp, vp, d, vp, vp, vp, vp]
+            l.orc_geo.argtypes = [i, i, d, d, d, d, vp, vp, vp, d, ctypes.POINTER(_GeoDec), d, vp, vp, vp, vp]
             l.orc_geo.restype = d
+            l.orc_geo_bounds.argtypes = [i, i, d, d, d, d, vp, vp, vp, d, d, vp, vp, vp, vp, vp]
+            l.orc_geo_bounds.restype = ctypes.c_int64
             l.orc_cm.argtypes = [ctypes.POINTER(_Args)]
             l.orc_cm.restype = ctypes.c_int
+            l.orc_cm_bounds.argtypes = [ctypes.POINTER(_Args), ctypes.POINTER(_Bounds)]
+            l.orc_cm_bounds.restype = ctypes.c_int
             _lib = l
     return _lib
 
@@ -98,14 +120,14 @@ def flow_from_depth(cam, inv_depth, ego, dt):
     return out
 
 
-def flow_from_depth_f32(cam, inv_depth, ego, dt):
-    """The same motion field in FP32 with the kernels' operation order; it
-    feeds the FP32 trajectory that takes the floor/mask/support decisions."""
-    rho = _c(inv_depth, np.float32)
-    e = _c(ego, np.float32)
-    out = np.empty((cam.height, cam.width, 2), np.float32)
-    lib().orc_flow_from_depth_f32(cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy, _p(rho), _p(e),
-                                  float(np.float32(dt)), _p(out))
+def flow_error_bound(cam, inv_depth, ego, dt):
+    """Bound on |FP32 flow - flow| per pixel [H, W] for the motion field
+    evaluated in single precision (the larger of the two components)."""
+    rho = _c(inv_depth, np.float64)
+    e = _c(ego, np.float64)
+    out = np.empty((cam.height, cam.width), np.float64)
+    lib().orc_flow_error_bound(cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy, _p(rho), _p(e), float(dt),
+                               _p(out))
     return out
 
 
@@ -131,15 +153,15 @@ def flow_eq2_bins(cam, inv_depth, ego, dt_bin, scale):
     return out
 
 
-def flow_eq2_bins_f32(cam, inv_depth, ego, dt_bin, scale):
-    """The same in FP32 with the kernels' operation sequence (the values that
-    decide the FP32 trajectory when these flows drive it)."""
-    rho = _c(inv_depth, np.float32)
-    e = _c(ego, np.float32).reshape(-1, 6)
+def flow_eq2_error_bound(cam, inv_depth, ego, dt_bin, scale):
+    """Bound on |FP32 flow - flow| per bin and pixel [nb, H, W] for
+    flow_eq2_bins evaluated in single precision without cancellation."""
+    rho = _c(inv_depth, np.float64)
+    e = _c(ego, np.float64).reshape(-1, 6)
     nb = e.shape[0]
-    out = np.empty((nb, cam.height, cam.width, 2), np.float32)
-    lib().orc_flow_eq2_bins_f32(cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy, _p(rho), _p(e), nb,
-                                float(dt_bin), float(scale), _p(out))
+    out = np.empty((nb, cam.height, cam.width), np.float64)
+    lib().orc_flow_eq2_error_bound(cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy, _p(rho), _p(e), nb,
+                                   float(dt_bin), float(scale), _p(out))
     return out
 
 
@@ -156,31 +178,21 @@ def flow_eq2_grad(cam, inv_depth, ego, dt_bin, scale, dflow):
     return drho, dego
 
 
-def geo_proj_f32(cam, inv_depth0, inv_depth1, ego, dt):
-    """The decisions of the geometry-consistency loss in the kernels' FP32
-    sequence: the projection of every pixel of view 0 into view 1 [H, W, 2],
-    the valid flags [H, W] and the sign of a - b [H, W]."""
-    r0, r1 = _c(inv_depth0, np.float32), _c(inv_depth1, np.float32)
-    e = _c(ego, np.float32)
-    proj = np.empty((cam.height, cam.width, 2), np.float32)
-    ok = np.empty((cam.height, cam.width), np.uint8)
-    sgn = np.empty((cam.height, cam.width), np.int8)
-    lib().orc_geo_proj_f32(cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy, _p(r0), _p(r1), _p(e), float(dt),
-                           _p(proj), _p(ok), _p(sgn))
-    return proj, ok, sgn
-
-
-def geo(cam, inv_depth0, inv_depth1, ego, dt, *, decisions=None, grad=False, dloss=1.0):
+def geo(cam, inv_depth0, inv_depth1, ego, dt, *, grad=False, dloss=1.0, record=False, replay=None):
     """Geometry-consistency loss (Eq. 3) between the depth of view 0 moved by
-    the camera motion (v, w) over dt and the depth of view 1, FP64 on the
-    FP32 decisions (computed here unless given).  Returns loss, count (valid pixels) and, with grad, dL/d
-    inv_depth0 [H, W], dL/d inv_depth1 [H, W], dL/d ego [6] for dloss.
-    decisions: (proj, ok, sign) of geo_proj_f32."""
-    if decisions is None:
-        decisions = geo_proj_f32(cam, inv_depth0, inv_depth1, ego, dt)
-    proj, ok, sgn = decisions
+    the camera motion (v, w) over dt and the depth of view 1, FP64.  Returns
+    loss, count (valid pixels) and, with grad, dL/d inv_depth0 [H, W], dL/d
+    inv_depth1 [H, W], dL/d ego [6] for dloss.  record: also return the
+    decisions (cells, valid flags, signs of a - b); replay: such decisions,
+    frozen (positions FP64), for differences on one branch."""
     r0, r1 = _c(inv_depth0, np.float64), _c(inv_depth1, np.float64)
     e = _c(ego, np.float64)
+    HW = cam.width * cam.height
+    dec = None
+    if record or replay is not None:
+        rec = replay if replay is not None else {"cell": np.zeros((HW, 2), np.int32), "ok": np.zeros(HW, np.uint8),
+                                                 "sgn": np.zeros(HW, np.int8)}
+        dec = _GeoDec(2 if replay is not None else 1, 0, _p(rec["cell"]), _p(rec["ok"]), _p(rec["sgn"]))
     cnt = ctypes.c_int64()
     out = {}
     if grad:
@@ -191,11 +203,29 @@ def geo(cam, inv_depth0, inv_depth1, ego, dt, *, decisions=None, grad=False, dlo
     else:
         g0 = g1 = ge = None
     out["loss"] = lib().orc_geo(cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy, _p(r0), _p(r1), _p(e),
-                                float(dt), _p(_c(proj, np.float32)), _p(_c(ok, np.uint8)), _p(_c(sgn, np.int8)),
-                                float(dloss),
+                                float(dt), ctypes.byref(dec) if dec is not None else None, float(dloss),
                                 ctypes.byref(cnt), g0, g1, ge)
     out["count"] = cnt.value
+    if record:
+        out["decisions"] = rec
     return out
+
+
+def geo_bounds(cam, inv_depth0, inv_depth1, ego, dt, *, safety=SAFETY):
+    """Straddles of the geometry-consistency loss for an FP32 evaluation:
+    flags [H, W] (bit 0 sample cell, bit 1 valid set, bit 2 branch of
+    |a - b|), and the valid count and loss over every outcome of the bit-1
+    decisions (count_lo/hi, loss_lo/hi)."""
+    r0, r1 = _c(inv_depth0, np.float64), _c(inv_depth1, np.float64)
+    e = _c(ego, np.float64)
+    flags = np.zeros((cam.height, cam.width), np.uint8)
+    clo, chi = ctypes.c_int64(), ctypes.c_int64()
+    llo, lhi = ctypes.c_double(), ctypes.c_double()
+    nf = lib().orc_geo_bounds(cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy, _p(r0), _p(r1), _p(e),
+                              float(dt), float(safety), _p(flags), ctypes.byref(clo), ctypes.byref(chi),
+                              ctypes.byref(llo), ctypes.byref(lhi))
+    return {"flags": flags, "flagged": int(nf), "count_lo": clo.value, "count_hi": chi.value,
+            "loss_lo": llo.value, "loss_hi": lhi.value}
 
 
 def event_frame(events, width, height):
@@ -207,15 +237,23 @@ def event_frame(events, width, height):
     return out
 
 
-def rsat(events, flow, *, width, height, nbins, ref_mode, eps=1e-9, flow32=None):
+def rsat(events, flow, *, width, height, nbins, ref_mode, eps=1e-9, bounds=False, eflow=None):
     """Ratio of squared average timestamps: the CM loss with `flow` over the CM
     loss with zero flow (the unwarped events), same references; 0 when the
-    zero-flow loss is 0 (no event in the image)."""
+    zero-flow loss is 0 (no event in the image).  With bounds, returns
+    (value, lo, hi): the interval over the flagged decisions of the numerator
+    (the zero-flow positions are exact integers, so its loss has none)."""
     fl = np.asarray(flow, np.float64)
-    a = cm(events, fl, width=width, height=height, nbins=nbins, ref_mode=ref_mode, eps=eps, flow32=flow32)["loss"]
-    b = cm(events, np.zeros((height, width, 2)), width=width, height=height, nbins=nbins, ref_mode=ref_mode,
-           eps=eps)["loss"]
-    return a / b if b > 0 else 0.0
+    kw = dict(width=width, height=height, nbins=nbins, ref_mode=ref_mode, eps=eps)
+    a = cm(events, fl, **kw)["loss"]
+    b = cm(events, np.zeros((height, width, 2)), **kw)["loss"]
+    v = a / b if b > 0 else 0.0
+    if not bounds:
+        return v
+    bo = cm_bounds(events, fl, eflow=eflow, **kw)
+    if b <= 0:
+        return v, 0.0, 0.0
+    return v, bo["loss_lo"] / b, bo["loss_hi"] / b
 
 
 def depth_ego_grad(cam, inv_depth, ego, dt, dflow):
@@ -238,15 +276,25 @@ def n_refs(nbins, ref_mode):
     return 1 if ref_mode == REF_END else nbins + 1
 
 
-def cm(events, flow, *, width, height, nbins, ref_mode, eps=1e-9, positions="f32", flow32=None,
-       grad=False, dloss=1.0, want_iwe=False, want_pos=False, record=False, replay=None):
-    """Contrast-maximisation loss of one window (and its flow gradient).
+def _args(events, fl, W, H, nbins, ref_mode, eps, dloss):
+    a = _Args()
+    nfb = fl.shape[0]
+    a.W, a.H, a.nbins, a.ref_mode, a.n_flow_bins = W, H, int(nbins), int(ref_mode), nfb
+    arrs = (_c(events.x, np.int16), _c(events.y, np.int16), _c(events.t, np.float32), _c(events.p, np.int8))
+    a.n = events.n
+    a.x, a.y, a.t, a.p = (_p(v) for v in arrs)
+    a.t0, a.t1 = float(np.float32(events.t0)), float(np.float32(events.t1))
+    a.eps, a.dloss = float(eps), float(dloss)
+    a.flow = _p(fl)
+    return a, arrs
+
+
+def cm(events, flow, *, width, height, nbins, ref_mode, eps=1e-9, grad=False, dloss=1.0, want_iwe=False,
+       want_pos=False, record=False, replay=None):
+    """Contrast-maximisation loss of one window (and its flow gradient), FP64.
 
     events: synth.Events (x, y int16; t float32; p int8; t0, t1)
     flow:   [nfb, H, W, 2] or [H, W, 2] values (nfb = 1 or nbins), px per window
-    positions: "f32" takes the trajectory in the kernels' FP32 arithmetic (the
-        floor / mask / support decisions), "f64" is the plain FP64 definition
-    flow32: the FP32 flow driving the FP32 trajectory (default: flow cast to FP32)
     record: return the branch (bins, cells, supports, validity) for replay
     replay: a recorded branch; positions are then FP64 with those decisions frozen
     Returns a dict with loss, loss_r [R], nnz_r [R], valid [n] and optionally
@@ -258,26 +306,11 @@ def cm(events, flow, *, width, height, nbins, ref_mode, eps=1e-9, positions="f32
     fl = fl.reshape(nfb, H, W, 2)
     R = n_refs(nbins, ref_mode)
     n = events.n
-    x = _c(events.x, np.int16)
-    y = _c(events.y, np.int16)
-    t = _c(events.t, np.float32)
-    p = _c(events.p, np.int8)
-    f32 = None
-    pos_f32 = positions == "f32" and replay is None
-    if pos_f32:
-        f32 = _c(flow32 if flow32 is not None else fl, np.float32).reshape(nfb, H, W, 2)
     out = {
         "loss": np.zeros(1), "loss_r": np.zeros(R), "nnz_r": np.zeros(R, np.int64),
         "valid": np.zeros(n, np.uint8),
     }
-    a = _Args()
-    a.W, a.H, a.nbins, a.ref_mode, a.n_flow_bins = W, H, int(nbins), int(ref_mode), nfb
-    a.pos_f32 = 1 if pos_f32 else 0
-    a.n = n
-    a.x, a.y, a.t, a.p = _p(x), _p(y), _p(t), _p(p)
-    a.t0, a.t1 = float(np.float32(events.t0)), float(np.float32(events.t1))
-    a.eps, a.dloss = float(eps), float(dloss)
-    a.flow, a.flow32 = _p(fl), _p(f32)
+    a, _keep = _args(events, fl, W, H, nbins, ref_mode, eps, dloss)
     br = None
     if record or replay is not None:
         if replay is not None:
@@ -309,24 +342,70 @@ def cm(events, flow, *, width, height, nbins, ref_mode, eps=1e-9, positions="f32
     return out
 
 
-def cm_depth(events, cam, inv_depth, ego, dt, *, nbins, ref_mode, eps=1e-9, positions="f32", grad=False,
-             dloss=1.0, **kw):
-    """Loss of one window whose flow comes from inverse depth and ego-motion
-    (Sec. 3.2 then Sec. 3.1); with grad, also dL/d(inv_depth) and dL/d(ego)."""
-    f64 = flow_from_depth(cam, inv_depth, ego, dt)
-    f32 = flow_from_depth_f32(cam, inv_depth, ego, dt) if positions == "f32" else None
-    out = cm(events, f64, width=cam.width, height=cam.height, nbins=nbins, ref_mode=ref_mode, eps=eps,
-             positions=positions, flow32=f32, grad=grad, dloss=dloss, **kw)
-    out["flow"] = f64
-    if grad:
-        out["dinv_depth"], out["dego"] = depth_ego_grad(cam, inv_depth, ego, dt, out["dflow"])
+def cm_bounds(events, flow, *, width, height, nbins, ref_mode, eps=1e-9, eflow=None, safety=SAFETY,
+              want_err=False):
+    """Straddles of an FP32 evaluation of the window (orc_cm_bounds): flags [n]
+    (bit 0 cell / support, bit 1 mask, bit 2 bin), counts of flagged events,
+    and the interval of N_nz(r) (nnz_lo/hi), of L_r (loss_r_lo/hi) and of the
+    loss (loss_lo/hi) over every outcome of the flagged decisions.  eflow:
+    bound on the FP32 error of the flow per pixel ([nfb, H, W]; None: the flow
+    values are FP32 numbers both sides use exactly).  want_err: the error bound
+    of every trajectory point [n, B+1, 2]."""
+    W, H = int(width), int(height)
+    fl = _c(flow, np.float64)
+    nfb = 1 if fl.ndim == 3 else fl.shape[0]
+    fl = fl.reshape(nfb, H, W, 2)
+    R = n_refs(nbins, ref_mode)
+    n = events.n
+    a, _keep = _args(events, fl, W, H, nbins, ref_mode, eps, 1.0)
+    ef = None if eflow is None else _c(eflow, np.float64).reshape(nfb, H, W)
+    out = {"flags": np.zeros(n, np.uint8), "loss_lo": np.zeros(1), "loss_hi": np.zeros(1),
+           "loss_r_lo": np.zeros(R), "loss_r_hi": np.zeros(R), "nnz_lo": np.zeros(R, np.int64),
+           "nnz_hi": np.zeros(R, np.int64)}
+    b = _Bounds()
+    b.safety = float(safety)
+    b.eflow = _p(ef)
+    b.flags = _p(out["flags"])
+    for k in ("loss_lo", "loss_hi", "loss_r_lo", "loss_r_hi", "nnz_lo", "nnz_hi"):
+        setattr(b, k, _p(out[k]))
+    if want_err:
+        out["err"] = np.zeros((n, nbins + 1, 2))
+        b.err = _p(out["err"])
+    st = lib().orc_cm_bounds(ctypes.byref(a), ctypes.byref(b))
+    if st != 0:
+        raise ValueError(f"oracle rejected the arguments (status {st})")
+    out["loss_lo"] = float(out["loss_lo"][0])
+    out["loss_hi"] = float(out["loss_hi"][0])
+    out["counts"] = tuple(int(c) for c in b.counts)
     return out
 
 
-def cm_window(win, **kw):
-    """Oracle on a synth.Window (flow input or depth + ego input)."""
+def cm_depth(events, cam, inv_depth, ego, dt, *, nbins, ref_mode, eps=1e-9, grad=False, dloss=1.0, bounds=False,
+             **kw):
+    """Loss of one window whose flow comes from inverse depth and ego-motion
+    (Sec. 3.2 then Sec. 3.1); with grad, also dL/d(inv_depth) and dL/d(ego);
+    with bounds, also the straddle analysis (cm_bounds) under "bounds"."""
+    f64 = flow_from_depth(cam, inv_depth, ego, dt)
+    out = cm(events, f64, width=cam.width, height=cam.height, nbins=nbins, ref_mode=ref_mode, eps=eps, grad=grad,
+             dloss=dloss, **kw)
+    out["flow"] = f64
+    if grad:
+        out["dinv_depth"], out["dego"] = depth_ego_grad(cam, inv_depth, ego, dt, out["dflow"])
+    if bounds:
+        out["bounds"] = cm_bounds(events, f64, width=cam.width, height=cam.height, nbins=nbins, ref_mode=ref_mode,
+                                  eps=eps, eflow=flow_error_bound(cam, inv_depth, ego, dt)[None])
+    return out
+
+
+def cm_window(win, bounds=False, **kw):
+    """Oracle on a synth.Window (flow input or depth + ego input); with
+    bounds, the straddle analysis under "bounds" (cm_bounds)."""
     if win.flow is not None:
-        return cm(win.events, win.flow, width=win.cam.width, height=win.cam.height, nbins=win.nbins,
-                  ref_mode=win.ref_mode, **kw)
-    return cm_depth(win.events, win.cam, win.inv_depth, win.ego, win.dt, nbins=win.nbins,
-                    ref_mode=win.ref_mode, **kw)
+        out = cm(win.events, win.flow, width=win.cam.width, height=win.cam.height, nbins=win.nbins,
+                 ref_mode=win.ref_mode, **kw)
+        if bounds:
+            out["bounds"] = cm_bounds(win.events, win.flow, width=win.cam.width, height=win.cam.height,
+                                      nbins=win.nbins, ref_mode=win.ref_mode, eps=kw.get("eps", 1e-9))
+        return out
+    return cm_depth(win.events, win.cam, win.inv_depth, win.ego, win.dt, nbins=win.nbins, ref_mode=win.ref_mode,
+                    bounds=bounds, **kw)

@@ -40,28 +40,7 @@ struct cm_workspace {
     bool fwd_warp;           // the last forward stored its trajectory points in `warp`
 };
 
-namespace {
-
-constexpr size_t kAlign = 256;
-
-size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
-
-int n_refs(const cm_loss_cfg& c) { return c.ref_mode == CM_REF_END ? 1 : c.nbins + 1; }
-
-int tiles_for(size_t hw, int cap)
-{
-    size_t t = (hw + 2047) / 2048;
-    if (t < 1) t = 1;
-    if (t > (size_t)cap) t = cap;
-    return (int)t;
-}
-
-struct Layout {
-    size_t iwe, flow, dflow, loss_part, norm, loss_r, nnz_r, dego_part, warp, scal, total;
-    size_t ka, kb, va, vb, pay, hist, part, start;  // sort path (CM_SPLAT_SORT only)
-    int R, loss_tiles, pix_tiles;
-    bool sort;
-};
+namespace cmk {
 
 bool finite_pos(float v) { return std::isfinite(v) && v > 0.0f; }
 
@@ -85,8 +64,6 @@ int check_cfg(const cm_loss_cfg* cfg)
     return CM_OK;
 }
 
-float eps_of(const cm_loss_cfg& c) { return c.eps > 0.0f ? c.eps : 1e-9f; }
-
 int check_events(const cm_events* ev)
 {
     if (!ev || ev->n < 0) return CM_EINVAL;
@@ -96,6 +73,37 @@ int check_events(const cm_events* ev)
     if (!(span > 0.0f) || !std::isfinite(span)) return CM_EINVAL;
     return CM_OK;
 }
+
+}  // namespace cmk
+
+namespace {
+
+using cmk::check_camera;
+using cmk::check_cfg;
+using cmk::check_events;
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+int n_refs(const cm_loss_cfg& c) { return c.ref_mode == CM_REF_END ? 1 : c.nbins + 1; }
+
+int tiles_for(size_t hw, int cap)
+{
+    size_t t = (hw + 2047) / 2048;
+    if (t < 1) t = 1;
+    if (t > (size_t)cap) t = cap;
+    return (int)t;
+}
+
+struct Layout {
+    size_t iwe, flow, dflow, loss_part, norm, loss_r, nnz_r, dego_part, warp, scal, total;
+    size_t ka, kb, va, vb, pay, hist, part, start;  // sort path (CM_SPLAT_SORT only)
+    int R, loss_tiles, pix_tiles;
+    bool sort;
+};
+
+float eps_of(const cm_loss_cfg& c) { return c.eps > 0.0f ? c.eps : 1e-9f; }
 
 Layout layout(const cm_camera& cam, const cm_loss_cfg& cfg, int32_t nfb, int64_t max_events)
 {

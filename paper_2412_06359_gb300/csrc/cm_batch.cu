@@ -367,10 +367,16 @@ __device__ __forceinline__ void use_grouped(Win& d)
     }
 }
 
+// the event kernels keep their trajectory points in shared memory up to 20
+// bins (the static 48 KB a block may declare), in registers beyond
 template <int MAXB>
-__global__ void __launch_bounds__(kEventThreads) k_splat_batch(const BatchHdr* h, const Win* tab,
+constexpr bool kPointsSmem = MAXB <= 20;
+
+template <int MAXB>
+__global__ void __launch_bounds__(kEventThreads, MAXB <= 10 ? 4 : 2) k_splat_batch(const BatchHdr* h, const Win* tab,
                                                                 const long long* cstart, int w0, int w1)
 {
+    __shared__ float pts[kPointsSmem<MAXB> ? 2 * (MAXB + 1) * kEventThreads : 1];
     w1 = clamp_end(h, w1);
     if (w0 >= w1) return;
     const long long cb = cstart[w0], ce = cstart[w1];
@@ -379,14 +385,17 @@ __global__ void __launch_bounds__(kEventThreads) k_splat_batch(const BatchHdr* h
         Win d = tab[w];
         use_grouped(d);
         const long long k = (c - cstart[w]) * kEventThreads + threadIdx.x;
-        if (k < d.n) splat_event<MAXB>(d, k);
+        if (k >= d.n) continue;
+        if (kPointsSmem<MAXB>) splat_event_smem<MAXB>(d, k, pts);
+        else splat_event<MAXB>(d, k);
     }
 }
 
 template <int MAXB>
-__global__ void __launch_bounds__(kEventThreads, MAXB <= 10 ? 3 : 2) k_adjoint_batch(const BatchHdr* h, const Win* tab,
+__global__ void __launch_bounds__(kEventThreads, MAXB <= 10 ? 4 : 2) k_adjoint_batch(const BatchHdr* h, const Win* tab,
                                                                   const long long* cstart, int w0, int w1)
 {
+    __shared__ float pts[kPointsSmem<MAXB> ? 2 * (MAXB + 1) * kEventThreads : 1];
     w1 = clamp_end(h, w1);
     if (w0 >= w1) return;
     const long long cb = cstart[w0], ce = cstart[w1];
@@ -395,7 +404,10 @@ __global__ void __launch_bounds__(kEventThreads, MAXB <= 10 ? 3 : 2) k_adjoint_b
         Win d = tab[w];
         use_grouped(d);
         const long long k = (c - cstart[w]) * kEventThreads + threadIdx.x;
-        if (k < d.n) adjoint_event<MAXB, RedSink, true>(d, k, __ldg(d.dloss));  // polarity-plane images
+        if (k >= d.n) continue;
+        // polarity-plane images
+        if (kPointsSmem<MAXB>) adjoint_event_smem<MAXB, RedSink, true>(d, k, __ldg(d.dloss), pts);
+        else adjoint_event<MAXB, RedSink, true>(d, k, __ldg(d.dloss));
     }
 }
 

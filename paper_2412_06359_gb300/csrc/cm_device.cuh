@@ -2,23 +2,28 @@
 // kernels: the window descriptor, the FP32 trajectory arithmetic and the
 // bilinear sample / splat primitives.
 //
-// FP32 arithmetic contract.  The floor of a trajectory position decides the
-// flow cell that is sampled, the pixels a splat touches, whether a corner has a
+// Position precision.  The floor of a trajectory position decides the flow
+// cell that is sampled, the pixels a splat touches, whether a corner has a
 // nonzero weight and whether the event stays inside the image; the
-// eps-regularised ratio of Eq. 1 makes the loss sensitive to those decisions.
-// Every operation that produces a position is therefore written as an explicit
-// correctly rounded single-precision intrinsic (__fadd_rn, __fmul_rn,
-// __fmaf_rn, __fdiv_rn), so that the compiler cannot contract or reorder it
-// and the positions are a fixed function of the inputs:
+// eps-regularised ratio of Eq. 1 makes the loss sensitive to those decisions,
+// and the second derivative of the bilinear weights makes every gradient term
+// sensitive to the position itself.  A trajectory point is therefore kept as
+// the event's own pixel (xk, yk), an exact integer, plus an FP32 offset
+// (dx, dy) from it: the offset is at most the distance the event travels in a
+// window (tens of pixels), so its rounding unit is 30-100x finer than that of
+// the absolute coordinate of a 346- or 640-pixel sensor.  The cell is
+// xk + floor(dx) and the fractional part dx - floor(dx).  The steps
+// (Sec. 3.1 iterative warp with bilinearly sampled flow; Sec. 3.3):
 //   tau     = (t - t0) / span                      span = t1 - t0
 //   b       = clamp(floor(tau * B), 0, B - 1)
 //   tau_j   = j / B,  h = 1 / B
-//   forward:  x_{b+1} = fma(tau_{b+1} - tau, u_b[x_k], x_k),   x_{j+1} = fma(h, u_j(x_j), x_j)
-//   backward: x_b     = fma(-(tau - tau_b), u_b[x_k], x_k),    x_{j-1} = fma(-h, u_{j-1}(x_j), x_j)
-//   sample u(x): a = x - floor(x), c = 1 - a (per axis),
-//                w00 = cx*cy, w10 = ax*cy, w01 = cx*ay, w11 = ax*ay,
-//                u = w00*u00;  u = fma(w10, u10, u);  u = fma(w01, u01, u);  u = fma(w11, u11, u)
-// (Sec. 3.1 iterative warp with bilinearly sampled flow; Sec. 3.3.)
+//   forward:  d_{b+1} = (tau_{b+1} - tau) u_b[x_k],   d_{j+1} = d_j + h u_j(x_k + d_j)
+//   backward: d_b     = -(tau - tau_b) u_b[x_k],      d_{j-1} = d_j - h u_{j-1}(x_k + d_j)
+//   u(x): bilinear sample of the flow in the cell of x, corner indices clamped
+// The operations are written as explicit correctly rounded single-precision
+// intrinsics (__fadd_rn, __fmul_rn, __fmaf_rn, __fdiv_rn) so that the compiler
+// cannot contract or reorder them: the points are a fixed function of the
+// inputs, the same in every kernel that recomputes them.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -141,9 +146,11 @@ __device__ __forceinline__ float tbar_of(int j, int B, float tau)
     return __fsub_rn(1.0f, fabsf(__fsub_rn(edge_tau(j, B), tau)));
 }
 
-__device__ __forceinline__ bool inside(float px, float py, float W1, float H1)
+// the point (xk + dx, yk + dy) lies in the closed image box [0, W-1] x [0, H-1]
+// (the bounds -xk and W-1-xk are exact in FP32)
+__device__ __forceinline__ bool inside(int xk, int yk, float dx, float dy, int W, int H)
 {
-    return px >= 0.0f && px <= W1 && py >= 0.0f && py <= H1;
+    return dx >= (float)(-xk) && dx <= (float)(W - 1 - xk) && dy >= (float)(-yk) && dy <= (float)(H - 1 - yk);
 }
 
 // Bilinear cell, fractional parts and the four weights of a point.
@@ -153,16 +160,39 @@ struct Bil {
     float w00, w10, w01, w11;
 };
 
-__device__ __forceinline__ Bil bil(float px, float py)
+// cell and weights of the point (xk + dx, yk + dy).  The fractional part
+// dx - floor(dx) is exact except for -1 < dx < 0, where it can round up to 1;
+// it is capped at the largest float below 1 (a change of at most 2^-24 px), so
+// that 0 <= a < 1 always holds and the cell is always xk + floor(dx).
+__device__ __forceinline__ Bil bil(int xk, int yk, float dx, float dy)
 {
+    constexpr float kBelowOne = 0x1.fffffep-1f;
     Bil s;
-    const float fx0 = floorf(px), fy0 = floorf(py);
-    s.ix = (int)fx0;
-    s.iy = (int)fy0;
-    s.ax = __fsub_rn(px, fx0);
-    s.ay = __fsub_rn(py, fy0);
+    const float fx0 = floorf(dx), fy0 = floorf(dy);
+    s.ix = xk + (int)fx0;
+    s.iy = yk + (int)fy0;
+    s.ax = fminf(__fsub_rn(dx, fx0), kBelowOne);
+    s.ay = fminf(__fsub_rn(dy, fy0), kBelowOne);
     s.bx = __fsub_rn(1.0f, s.ax);
     s.by = __fsub_rn(1.0f, s.ay);
+    s.w00 = __fmul_rn(s.bx, s.by);
+    s.w10 = __fmul_rn(s.ax, s.by);
+    s.w01 = __fmul_rn(s.bx, s.ay);
+    s.w11 = __fmul_rn(s.ax, s.ay);
+    return s;
+}
+
+// the same for a point given by its fractional parts in a known cell
+// (0 <= ax, ay < 1; the sort path's payload)
+__device__ __forceinline__ Bil bil_frac(float ax, float ay)
+{
+    Bil s;
+    s.ix = 0;
+    s.iy = 0;
+    s.ax = ax;
+    s.ay = ay;
+    s.bx = __fsub_rn(1.0f, ax);
+    s.by = __fsub_rn(1.0f, ay);
     s.w00 = __fmul_rn(s.bx, s.by);
     s.w10 = __fmul_rn(s.ax, s.by);
     s.w01 = __fmul_rn(s.bx, s.ay);
@@ -199,14 +229,29 @@ __device__ __forceinline__ float2 interp(const Bil& s, const Quad& q)
     return make_float2(ux, uy);
 }
 
-// Trajectory points at the computed edges (registers; indices are compile-time
-// after unrolling).
+// Trajectory points at the computed edges, as offsets from the event's pixel.
+// Traj keeps them in registers (indices are compile-time after unrolling);
+// SmemTraj in the block's shared memory, [edge][thread] (consecutive threads
+// in consecutive banks), for the adjoint, which keeps every point live through
+// its reverse sweeps while it waits on its gathers: registers it does not spend
+// on the points are occupancy.
 template <int MAXB>
 struct Traj {
-    float x[MAXB + 1];
-    float y[MAXB + 1];
+    float x_[MAXB + 1];
+    float y_[MAXB + 1];
     float ex, ey;  // the point at the window end (edge B), kept in scalars so that
                    // selecting it never needs a run-time array index
+    __device__ __forceinline__ float& x(int j) { return x_[j]; }
+    __device__ __forceinline__ float& y(int j) { return y_[j]; }
+};
+
+template <int MAXB>
+struct SmemTraj {
+    float* xs;  // this thread's column of a [MAXB + 1][kEventThreads] array
+    float* ys;
+    float ex, ey;
+    __device__ __forceinline__ float& x(int j) { return xs[j * kEventThreads]; }
+    __device__ __forceinline__ float& y(int j) { return ys[j * kEventThreads]; }
 };
 
 // Per-event quantities shared by the forward and backward kernels.
@@ -258,34 +303,32 @@ __device__ __forceinline__ float2 flow_at_pixel(const Win& d, int j, int x, int 
 // S2 + S3: the trajectory of one event through all computed edges (forward
 // chain b+1..B; with all edges as references also the backward chain b..0)
 // and the global mask.  Returns false when any computed point leaves the image.
-template <int MAXB>
-__device__ __forceinline__ bool trajectory(const Win& d, const EventAt& e, Traj<MAXB>& P)
+template <int MAXB, class TR>
+__device__ __forceinline__ bool trajectory(const Win& d, const EventAt& e, TR& P)
 {
-    const int W = d.W, H = d.H, B = d.B, b = e.b;
-    const float W1 = (float)(W - 1), H1 = (float)(H - 1);
+    const int W = d.W, H = d.H, B = d.B, b = e.b, xk = e.xk, yk = e.yk;
     const float h = __fdiv_rn(1.0f, (float)B);
-    const float2 u0 = flow_at_pixel(d, b, e.xk, e.yk);
-    const float fxk = (float)e.xk, fyk = (float)e.yk;
+    const float2 u0 = flow_at_pixel(d, b, xk, yk);
     bool ok = true;
     const float dtf = __fsub_rn(edge_tau(b + 1, B), e.tau);
 #pragma unroll
     for (int j = 1; j <= MAXB; ++j) {
         if (j <= B && j > b) {
             if (j == b + 1) {
-                P.x[j] = __fmaf_rn(dtf, u0.x, fxk);
-                P.y[j] = __fmaf_rn(dtf, u0.y, fyk);
+                P.x(j) = __fmul_rn(dtf, u0.x);
+                P.y(j) = __fmul_rn(dtf, u0.y);
             } else if (ok) {
-                const Bil s = bil(P.x[j - 1], P.y[j - 1]);
+                const Bil s = bil(xk, yk, P.x(j - 1), P.y(j - 1));
                 const float2 u = interp(s, quad_at(d, j - 1, s));
-                P.x[j] = __fmaf_rn(h, u.x, P.x[j - 1]);
-                P.y[j] = __fmaf_rn(h, u.y, P.y[j - 1]);
+                P.x(j) = __fmaf_rn(h, u.x, P.x(j - 1));
+                P.y(j) = __fmaf_rn(h, u.y, P.y(j - 1));
             } else {
-                P.x[j] = P.x[j - 1];
-                P.y[j] = P.y[j - 1];
+                P.x(j) = P.x(j - 1);
+                P.y(j) = P.y(j - 1);
             }
-            ok = ok && inside(P.x[j], P.y[j], W1, H1);
-            P.ex = P.x[j];
-            P.ey = P.y[j];
+            ok = ok && inside(xk, yk, P.x(j), P.y(j), W, H);
+            P.ex = P.x(j);
+            P.ey = P.y(j);
         }
     }
     if (d.ref_mode == kRefAll) {
@@ -294,18 +337,18 @@ __device__ __forceinline__ bool trajectory(const Win& d, const EventAt& e, Traj<
         for (int j = MAXB - 1; j >= 0; --j) {
             if (j <= b) {
                 if (j == b) {
-                    P.x[j] = __fmaf_rn(-dtb, u0.x, fxk);
-                    P.y[j] = __fmaf_rn(-dtb, u0.y, fyk);
+                    P.x(j) = __fmul_rn(-dtb, u0.x);
+                    P.y(j) = __fmul_rn(-dtb, u0.y);
                 } else if (ok) {
-                    const Bil s = bil(P.x[j + 1], P.y[j + 1]);
+                    const Bil s = bil(xk, yk, P.x(j + 1), P.y(j + 1));
                     const float2 u = interp(s, quad_at(d, j, s));
-                    P.x[j] = __fmaf_rn(-h, u.x, P.x[j + 1]);
-                    P.y[j] = __fmaf_rn(-h, u.y, P.y[j + 1]);
+                    P.x(j) = __fmaf_rn(-h, u.x, P.x(j + 1));
+                    P.y(j) = __fmaf_rn(-h, u.y, P.y(j + 1));
                 } else {
-                    P.x[j] = P.x[j + 1];
-                    P.y[j] = P.y[j + 1];
+                    P.x(j) = P.x(j + 1);
+                    P.y(j) = P.y(j + 1);
                 }
-                ok = ok && inside(P.x[j], P.y[j], W1, H1);
+                ok = ok && inside(xk, yk, P.x(j), P.y(j), W, H);
             }
         }
     }
@@ -349,9 +392,8 @@ __device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float 
 // S4: bilinear splat of one point (weight w to C_p, w * tbar to S_p) into one
 // IWE plane; corners with a zero weight are skipped (they lie outside the
 // image or carry nothing).
-__device__ __forceinline__ void splat_point(float4* plane, int W, float px, float py, float tbar, int pol2)
+__device__ __forceinline__ void splat_point(float4* plane, int W, const Bil& s, float tbar, int pol2)
 {
-    const Bil s = bil(px, py);
     float* q = reinterpret_cast<float*>(plane + (size_t)s.iy * W + s.ix) + pol2;
     red_add_v2(q, s.w00, __fmul_rn(s.w00, tbar));
     if (s.ax > 0.0f) red_add_v2(q + 4, s.w10, __fmul_rn(s.w10, tbar));
@@ -375,9 +417,8 @@ __device__ __forceinline__ void splat_row(float2* img, size_t gi, bool two, floa
 }
 
 // S4 into the polarity-plane layout: plane 2r + polarity
-__device__ __forceinline__ void splat_point_split(const Win& d, int r, float px, float py, float tbar, int pol2)
+__device__ __forceinline__ void splat_point_split(const Win& d, int r, const Bil& s, float tbar, int pol2)
 {
-    const Bil s = bil(px, py);
     const size_t gi = (size_t)(2 * r + (pol2 >> 1)) * plane_size(d) + (size_t)s.iy * d.W + s.ix;
     float2* img = reinterpret_cast<float2*>(d.iwe);
     const bool two = s.ax > 0.0f;
@@ -390,19 +431,19 @@ __device__ __forceinline__ void splat_point_split(const Win& d, int r, float px,
 // RedSink adds into the IWE / dL/dflow with 8-byte vector reductions (the order
 // of the additions is not fixed).  EmitSink writes one entry per splat point or
 // push instead: a key (plane * HW + the cell of the point's top-left corner) and
-// the payload (x, y, a, b); entry k * stride + slot belongs to event k, so the
+// the payload (ax, ay, a, b), the point's fractional parts in that cell and two
+// values; entry k * stride + slot belongs to event k, so the
 // entries have a fixed order.  The sort path orders them by key (stable) and a
 // per-pixel gather sums each pixel's entries in that order: bit-reproducible.
 struct RedSink {
-    __device__ __forceinline__ void splat(const Win& d, int r, float px, float py, float tbar, int pol2,
-                                          int64_t) const
+    __device__ __forceinline__ void splat(const Win& d, int r, const Bil& s, float tbar, int pol2, int64_t) const
     {
-        if (d.iwe_split) splat_point_split(d, r, px, py, tbar, pol2);
-        else splat_point(d.iwe + (size_t)r * plane_size(d), d.W, px, py, tbar, pol2);
+        if (d.iwe_split) splat_point_split(d, r, s, tbar, pol2);
+        else splat_point(d.iwe + (size_t)r * plane_size(d), d.W, s, tbar, pol2);
     }
-    // a push sampled at (px, py) in cell s: hs * w_c * lambda to the four corners
-    __device__ __forceinline__ void scatter(const Win& d, int field, int, const Bil& s, float, float, float hx,
-                                            float hy, int64_t) const
+    // a push sampled in cell s: hs * w_c * lambda to the four corners
+    __device__ __forceinline__ void scatter(const Win& d, int field, int, const Bil& s, float hx, float hy,
+                                            int64_t) const
     {
         const int W = d.W;
         if (d.dq) {
@@ -434,27 +475,25 @@ struct EmitSink {
     float4* pay;
     int32_t stride;  // entries per event: R for the splat, B + 1 for the adjoint (one per edge)
 
-    __device__ __forceinline__ void splat(const Win& d, int r, float px, float py, float tbar, int pol2,
-                                          int64_t k) const
+    __device__ __forceinline__ void splat(const Win& d, int r, const Bil& s, float tbar, int pol2, int64_t k) const
     {
-        const Bil s = bil(px, py);
         const int64_t e = k * stride + r;
         key[e] = (uint32_t)((size_t)(2 * r + (pol2 >> 1)) * plane_size(d) + (size_t)s.iy * d.W + s.ix);
-        pay[e] = make_float4(px, py, 1.0f, tbar);
+        pay[e] = make_float4(s.ax, s.ay, 1.0f, tbar);
     }
-    __device__ __forceinline__ void scatter(const Win& d, int field, int edge, const Bil& s, float px, float py,
-                                            float hx, float hy, int64_t k) const
+    __device__ __forceinline__ void scatter(const Win& d, int field, int edge, const Bil& s, float hx, float hy,
+                                            int64_t k) const
     {
         const int64_t e = k * stride + edge;
         key[e] = (uint32_t)(plane_of(d, field) * plane_size(d) + (size_t)s.iy * d.W + s.ix);
-        pay[e] = make_float4(px, py, hx, hy);
+        pay[e] = make_float4(s.ax, s.ay, hx, hy);
     }
     __device__ __forceinline__ void point(const Win& d, int field, int edge, int xk, int yk, float vx, float vy,
                                           int64_t k) const
     {
         const int64_t e = k * stride + edge;
         key[e] = (uint32_t)(plane_of(d, field) * plane_size(d) + (size_t)yk * d.W + xk);
-        pay[e] = make_float4((float)xk, (float)yk, vx, vy);
+        pay[e] = make_float4(0.0f, 0.0f, vx, vy);
     }
 };
 
@@ -465,31 +504,31 @@ __device__ __forceinline__ bool computed_edge(const Win& d, int j, int b)
     return j <= d.B && (j > b || d.ref_mode == kRefAll);
 }
 
-// Stored warps: the splat writes every computed point of event k to
-// d.warp[j][k] (coalesced across a warp); the adjoint reads them back instead
+// Stored warps: the splat writes every computed point of event k (its offset
+// from the event's pixel) to d.warp[j][k] (coalesced across a warp); the
+// adjoint reads them back instead
 // of recomputing the trajectory, and takes the mask from them (a point outside
 // the image stays outside in every later point of its chain, so the test over
 // all stored points repeats the decision of the trajectory exactly).
-template <int MAXB>
-__device__ __forceinline__ void store_traj(const Win& d, const EventAt& e, const Traj<MAXB>& P, int64_t k)
+template <int MAXB, class TR>
+__device__ __forceinline__ void store_traj(const Win& d, const EventAt& e, TR& P, int64_t k)
 {
 #pragma unroll
     for (int j = 0; j <= MAXB; ++j)
-        if (computed_edge(d, j, e.b)) d.warp[(size_t)j * d.n + k] = make_float2(P.x[j], P.y[j]);
+        if (computed_edge(d, j, e.b)) d.warp[(size_t)j * d.n + k] = make_float2(P.x(j), P.y(j));
 }
 
-template <int MAXB>
-__device__ __forceinline__ bool load_traj(const Win& d, const EventAt& e, Traj<MAXB>& P, int64_t k)
+template <int MAXB, class TR>
+__device__ __forceinline__ bool load_traj(const Win& d, const EventAt& e, TR& P, int64_t k)
 {
-    const float W1 = (float)(d.W - 1), H1 = (float)(d.H - 1);
     bool ok = true;
 #pragma unroll
     for (int j = 0; j <= MAXB; ++j) {
         if (computed_edge(d, j, e.b)) {
             const float2 q = __ldg(d.warp + (size_t)j * d.n + k);
-            P.x[j] = q.x;
-            P.y[j] = q.y;
-            ok = ok && inside(q.x, q.y, W1, H1);
+            P.x(j) = q.x;
+            P.y(j) = q.y;
+            ok = ok && inside(e.xk, e.yk, q.x, q.y, d.W, d.H);
             if (j == d.B) {
                 P.ex = q.x;
                 P.ey = q.y;
@@ -499,22 +538,39 @@ __device__ __forceinline__ bool load_traj(const Win& d, const EventAt& e, Traj<M
     return ok;
 }
 
-template <int MAXB, class Sink = RedSink>
-__device__ __forceinline__ void splat_event(const Win& d, int64_t k, const Sink& sink = Sink())
+template <int MAXB, class Sink, class TR>
+__device__ __forceinline__ void splat_points(const Win& d, int64_t k, const Sink& sink, TR& P)
 {
     EventAt e;
     if (!load_event(d, k, e)) return;
-    Traj<MAXB> P;
     const bool ok = trajectory<MAXB>(d, e, P);
     if (d.warp) store_traj<MAXB>(d, e, P, k);
     if (!ok) return;
     if (d.ref_mode == kRefAll) {
 #pragma unroll
         for (int j = 0; j <= MAXB; ++j)
-            if (j <= d.B) sink.splat(d, j, P.x[j], P.y[j], tbar_of(j, d.B, e.tau), e.pol2, k);
+            if (j <= d.B) sink.splat(d, j, bil(e.xk, e.yk, P.x(j), P.y(j)), tbar_of(j, d.B, e.tau), e.pol2, k);
     } else {
-        sink.splat(d, 0, P.ex, P.ey, tbar_of(d.B, d.B, e.tau), e.pol2, k);
+        sink.splat(d, 0, bil(e.xk, e.yk, P.ex, P.ey), tbar_of(d.B, d.B, e.tau), e.pol2, k);
     }
+}
+
+template <int MAXB, class Sink = RedSink>
+__device__ __forceinline__ void splat_event(const Win& d, int64_t k, const Sink& sink = Sink())
+{
+    Traj<MAXB> P;
+    splat_points<MAXB>(d, k, sink, P);
+}
+
+// the same with the points in shared memory: smem is the block's
+// [2][MAXB + 1][kEventThreads] float array
+template <int MAXB, class Sink = RedSink>
+__device__ __forceinline__ void splat_event_smem(const Win& d, int64_t k, float* smem, const Sink& sink = Sink())
+{
+    SmemTraj<MAXB> P;
+    P.xs = smem + threadIdx.x;
+    P.ys = smem + (MAXB + 1) * kEventThreads + threadIdx.x;
+    splat_points<MAXB>(d, k, sink, P);
 }
 
 // dL/dw_c of one corner from its count and timestamp sum, with the loss
@@ -551,15 +607,13 @@ __device__ __forceinline__ void phi_row(const float2* img, size_t gi, bool two, 
 // layout (Win::iwe_split == 1), a compile-time choice so that the event kernels
 // carry the code of one layout only.
 template <bool SPLIT>
-__device__ __forceinline__ float2 ref_adjoint(const Win& d, int r, int j, float px, float py, float tau, int pol2,
-                                              float dl)
+__device__ __forceinline__ float2 ref_adjoint(const Win& d, int r, int j, const Bil& s, float tau, int pol2, float dl)
 {
     const size_t HW = plane_size(d);
     const int W = d.W, H = d.H;
     const float kap = dl * __ldg(d.norm + r);
     const float tb = tbar_of(j, d.B, tau);
     const float eps = d.eps;
-    const Bil s = bil(px, py);
     const size_t i00 = (size_t)s.iy * W + s.ix;
     const bool inx = s.ix + 1 <= W - 1, iny = s.iy + 1 <= H - 1;
     float p00, p10 = 0.0f, p01 = 0.0f, p11 = 0.0f;
@@ -586,17 +640,16 @@ __device__ __forceinline__ float2 ref_adjoint(const Win& d, int r, int j, float 
     return a;
 }
 
-// One push of the adjoint back across a step x' = x + hs u(x) sampled at x
-// (hs = +h forward chain, -h backward chain): scatter hs w_c lambda into the
-// gradient of field `field` and return lambda + hs J(x)^T lambda.
+// One push of the adjoint back across a step x' = x + hs u(x) sampled at x,
+// in cell s (hs = +h forward chain, -h backward chain): scatter hs w_c lambda
+// into the gradient of field `field` and return lambda + hs J(x)^T lambda.
 template <class Sink>
-__device__ __forceinline__ float2 push_back(const Win& d, const Sink& sink, int field, int edge, float px, float py,
+__device__ __forceinline__ float2 push_back(const Win& d, const Sink& sink, int field, int edge, const Bil& s,
                                             float hs, float2 lam, int64_t k)
 {
-    const Bil s = bil(px, py);
     const Quad q = quad_at(d, field, s);
     const float hx = hs * lam.x, hy = hs * lam.y;
-    sink.scatter(d, field, edge, s, px, py, hx, hy, k);
+    sink.scatter(d, field, edge, s, hx, hy, k);
     const float jxx = s.by * (q.u10.x - q.u00.x) + s.ay * (q.u11.x - q.u01.x);
     const float jxy = s.bx * (q.u01.x - q.u00.x) + s.ax * (q.u11.x - q.u10.x);
     const float jyx = s.by * (q.u10.y - q.u00.y) + s.ay * (q.u11.y - q.u01.y);
@@ -610,13 +663,14 @@ __device__ __forceinline__ float2 push_back(const Win& d, const Sink& sink, int 
 // S6: per-event adjoint.  The trajectory is recomputed (or read back when the
 // splat stored it); the position adjoint of each reference point comes from
 // the (C, S) pairs gathered at its corners (phi_of), and the adjoint is
-// carried back along both chains of pushes, scattering dL/dflow.
-template <int MAXB, class Sink = RedSink, bool SPLIT = false>
-__device__ __forceinline__ void adjoint_event(const Win& d, int64_t k, float dl, const Sink& sink = Sink())
+// carried back along both chains of pushes, scattering dL/dflow.  The points
+// live in registers (Traj) or, given a block's [2][MAXB + 1][kEventThreads]
+// shared array `smem`, in shared memory (SmemTraj).
+template <int MAXB, bool SPLIT, class Sink, class TR>
+__device__ __forceinline__ void adjoint_points(const Win& d, int64_t k, float dl, const Sink& sink, TR& P)
 {
     EventAt e;
     if (!load_event(d, k, e)) return;
-    Traj<MAXB> P;
     if (!(d.warp ? load_traj<MAXB>(d, e, P, k) : trajectory<MAXB>(d, e, P))) return;
     const int B = d.B, b = e.b;
     const float h = __fdiv_rn(1.0f, (float)B);
@@ -627,12 +681,13 @@ __device__ __forceinline__ void adjoint_event(const Win& d, int64_t k, float dl,
     for (int j = MAXB; j >= 1; --j) {
         if (j <= B && j > b) {
             if (all || j == B) {
-                const float2 a = ref_adjoint<SPLIT>(d, all ? j : 0, j, P.x[j], P.y[j], e.tau, e.pol2, dl);
+                const float2 a =
+                    ref_adjoint<SPLIT>(d, all ? j : 0, j, bil(e.xk, e.yk, P.x(j), P.y(j)), e.tau, e.pol2, dl);
                 lam.x += a.x;
                 lam.y += a.y;
             }
             if (j > b + 1) {
-                lam = push_back(d, sink, j - 1, j, P.x[j - 1], P.y[j - 1], h, lam, k);
+                lam = push_back(d, sink, j - 1, j, bil(e.xk, e.yk, P.x(j - 1), P.y(j - 1)), h, lam, k);
             } else {
                 const float dtf = __fsub_rn(edge_tau(b + 1, B), e.tau);
                 sink.point(d, b, j, e.xk, e.yk, dtf * lam.x, dtf * lam.y, k);
@@ -645,17 +700,36 @@ __device__ __forceinline__ void adjoint_event(const Win& d, int64_t k, float dl,
 #pragma unroll
     for (int j = 0; j <= MAXB - 1; ++j) {
         if (j <= b) {
-            const float2 a = ref_adjoint<SPLIT>(d, j, j, P.x[j], P.y[j], e.tau, e.pol2, dl);
+            const float2 a = ref_adjoint<SPLIT>(d, j, j, bil(e.xk, e.yk, P.x(j), P.y(j)), e.tau, e.pol2, dl);
             lam.x += a.x;
             lam.y += a.y;
             if (j < b) {
-                lam = push_back(d, sink, j, j, P.x[j + 1], P.y[j + 1], -h, lam, k);
+                lam = push_back(d, sink, j, j, bil(e.xk, e.yk, P.x(j + 1), P.y(j + 1)), -h, lam, k);
             } else {
                 const float dtb = __fsub_rn(e.tau, edge_tau(b, B));
                 sink.point(d, b, j, e.xk, e.yk, -dtb * lam.x, -dtb * lam.y, k);
             }
         }
     }
+}
+
+template <int MAXB, class Sink = RedSink, bool SPLIT = false>
+__device__ __forceinline__ void adjoint_event(const Win& d, int64_t k, float dl, const Sink& sink = Sink())
+{
+    Traj<MAXB> P;
+    adjoint_points<MAXB, SPLIT>(d, k, dl, sink, P);
+}
+
+// the same with the points in shared memory: smem is the block's
+// [2][MAXB + 1][kEventThreads] float array
+template <int MAXB, class Sink = RedSink, bool SPLIT = false>
+__device__ __forceinline__ void adjoint_event_smem(const Win& d, int64_t k, float dl, float* smem,
+                                                   const Sink& sink = Sink())
+{
+    SmemTraj<MAXB> P;
+    P.xs = smem + threadIdx.x;
+    P.ys = smem + (MAXB + 1) * kEventThreads + threadIdx.x;
+    adjoint_points<MAXB, SPLIT>(d, k, dl, sink, P);
 }
 
 // warp-level sum (fixed shuffle tree: deterministic)

@@ -7,11 +7,12 @@
 // lands in view 1, where the interpolated depth b is the bilinear sample of
 // 1/rho1 at x' (corner indices clamped).  Valid pixels: P2 > 0 and x' inside
 // the closed image box.  L_geo = (1/|V|) sum_V |a - b| / (a + b).
-// The projection and the valid flags follow the FP32 sequence of
-// cm_pose.cuh (x' = u + d.x, y' = v + d.y, correctly rounded), and b and the
-// sign of a - b a fixed FP32 sequence too (geo_pixel), so the valid set, the
-// sample cells and the branch of |a - b| are fixed functions of the inputs;
-// sums are fixed-order (per-tile partials, FP64 final).
+// The projection is kept as the pixel plus the FP32 displacement of
+// cm_pose.cuh (cell u + floor(d.x), fractional part d.x - floor(d.x)), and b
+// and the sign of a - b are computed with correctly rounded operations
+// (geo_pixel), so the valid set, the sample cells and the branch of |a - b|
+// are fixed functions of the inputs; sums are fixed-order (per-tile partials,
+// FP64 final).
 #include <cmath>
 #include <cstdint>
 
@@ -68,18 +69,21 @@ __device__ __forceinline__ GeoPixel geo_pixel(const GeoArgs& g, const Pose& p, c
     GeoPixel r;
     float P2;
     const float2 d = displacement(p, q, g.fx, g.fy, P2);
-    const float xp = __fadd_rn((float)u, d.x), yp = __fadd_rn((float)v, d.y);
-    r.valid = P2 > 0.0f && xp >= 0.0f && xp <= (float)(g.W - 1) && yp >= 0.0f && yp <= (float)(g.H - 1);
+    // x' = (u + d.x, v + d.y) kept as the pixel plus the offset d: the cell is
+    // u + floor(d.x) and the fractional part d.x - floor(d.x) (capped below 1),
+    // without rounding x' to the coarser grid of its absolute coordinate
+    r.valid = P2 > 0.0f && d.x >= (float)(-u) && d.x <= (float)(g.W - 1 - u) && d.y >= (float)(-v) &&
+              d.y <= (float)(g.H - 1 - v);
     if (!r.valid) return r;
-    const float fx0 = floorf(xp), fy0 = floorf(yp);
-    r.ix = (int)fx0;
-    r.iy = (int)fy0;
+    constexpr float kBelowOne = 0x1.fffffep-1f;
+    const float fx0 = floorf(d.x), fy0 = floorf(d.y);
+    r.ix = u + (int)fx0;
+    r.iy = v + (int)fy0;
     r.ix1 = min(r.ix + 1, g.W - 1);
     r.iy1 = min(r.iy + 1, g.H - 1);
-    // b and the sign of a - b in a fixed FP32 sequence (the sign is the
-    // branch of |a - b|, decided the same way by the CPU oracle)
-    r.ax = __fsub_rn(xp, fx0);
-    r.ay = __fsub_rn(yp, fy0);
+    // b and the sign of a - b (the branch of |a - b|)
+    r.ax = fminf(__fsub_rn(d.x, fx0), kBelowOne);
+    r.ay = fminf(__fsub_rn(d.y, fy0), kBelowOne);
     r.D00 = __frcp_rn(__ldg(g.rho1 + (size_t)r.iy * g.W + r.ix));
     r.D10 = __frcp_rn(__ldg(g.rho1 + (size_t)r.iy * g.W + r.ix1));
     r.D01 = __frcp_rn(__ldg(g.rho1 + (size_t)r.iy1 * g.W + r.ix));

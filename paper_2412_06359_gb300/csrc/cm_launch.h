@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include "../../include/cm.h"
 #include "cm_device.cuh"
 
 namespace cmk {
@@ -16,6 +17,11 @@ cudaError_t launch_depth_ego(const Win& d, cudaStream_t st);
 
 // number of SMs of the current device (cached per device)
 int sm_count_current();
+
+// argument checks of the C ABI (cm_api.cu): CM_OK or CM_EINVAL
+int check_camera(const cm_camera* cam);  // sizes 2..32767, finite fx, fy > 0, finite cx, cy
+int check_cfg(const cm_loss_cfg* cfg);   // bins, reference mode, splat, store_warps, finite eps
+int check_events(const cm_events* ev);   // n >= 0, arrays given when n > 0, finite t0 < t1 with a finite span
 
 // Tracing scope around one kernel launch: counts the launch and, when
 // profiling is on and the stream is not being captured, brackets it with CUDA

@@ -201,9 +201,8 @@ struct cm_server {
     }
 
     // make the stream's resident state fit request q; false when memory is short now
-    bool ensure_state(StreamState& s, const cm_request& q, bool* one_time_init)
+    bool ensure_state(StreamState& s, const cm_request& q)
     {
-        *one_time_init = false;
         if (s.fixed_off != Pool::kNone && (s.W != q.cam.width || s.H != q.cam.height)) {
             pool.release(s.fixed_off, s.fixed_bytes);
             s.fixed_off = Pool::kNone;
@@ -216,7 +215,6 @@ struct cm_server {
             s.fixed_bytes = b;
             s.W = q.cam.width;
             s.H = q.cam.height;
-            *one_time_init = true;
         }
         if (s.ev_off == Pool::kNone || s.ev_cap < (size_t)q.n) {
             if (s.ev_off != Pool::kNone) pool.release(s.ev_off, s.ev_bytes);
@@ -242,7 +240,6 @@ struct cm_server {
         char* fixed;
         char* ev;
         size_t cap, o_scratch, o_rho, o_drho, o_small;
-        bool init;
     };
 
     // enqueue copies in, the plan, copies out for one batch on a lane reserved
@@ -264,10 +261,10 @@ struct cm_server {
             float* small = reinterpret_cast<float*>(it.fixed + it.o_small);  // ego[6], dego[6], loss, dloss
             const size_t HW = (size_t)q.cam.width * q.cam.height;
             bool ok = true;
-            if (it.init) {
-                static const float one = 1.0f;
-                ok = ok && cudaMemcpyAsync(small + 13, &one, 4, cudaMemcpyHostToDevice, L.s) == cudaSuccess;
-            }
+            // the upstream gradient dL/dloss = 1, written on every launch: the fixed
+            // block may have been (re)allocated from pool memory that held anything
+            static const float one = 1.0f;
+            ok = ok && cudaMemcpyAsync(small + 13, &one, 4, cudaMemcpyHostToDevice, L.s) == cudaSuccess;
             if (q.n > 0) {
                 ok = ok && cudaMemcpyAsync(dx, q.x, 2 * q.n, cudaMemcpyHostToDevice, L.s) == cudaSuccess;
                 ok = ok && cudaMemcpyAsync(dy, q.y, 2 * q.n, cudaMemcpyHostToDevice, L.s) == cudaSuccess;
@@ -350,8 +347,7 @@ struct cm_server {
                 StreamState& s = streams[R.r.stream_id];
                 s.id = R.r.stream_id;
                 bool blocked = s.busy || seen.count(s.id) != 0;
-                bool init = false;
-                if (!blocked && !ensure_state(s, R.r, &init)) {
+                if (!blocked && !ensure_state(s, R.r)) {
                     blocked = true;
                     st.memory_waits += 1;
                 }
@@ -363,7 +359,7 @@ struct cm_server {
                 s.busy = true;
                 batch.push_back(tk);
                 items.push_back(Item{R.r, at(s.fixed_off), at(s.ev_off), s.ev_cap, s.o_scratch, s.o_rho, s.o_drho,
-                                     s.o_small, init});
+                                     s.o_small});
             }
             // the requests passed over go back to the front, in their order
             for (auto it = rest.rbegin(); it != rest.rend(); ++it) queue.push_front(*it);

@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(kRsThreads) k_cell_gather(const uint32_t* star
             const uint32_t i0 = st[cell], i1 = st[cell + 1];
             for (uint32_t i = i0; i < i1; ++i) {
                 const float4 v = pay[vals[i]];
-                const Bil s = bil(v.x, v.y);
+                const Bil s = bil_frac(v.x, v.y);
                 const float wgt = c == 0 ? s.w00 : (c == 1 ? s.w10 : (c == 2 ? s.w01 : s.w11));
                 a = __fadd_rn(a, __fmul_rn(wgt, v.z));
                 b = __fadd_rn(b, __fmul_rn(wgt, v.w));

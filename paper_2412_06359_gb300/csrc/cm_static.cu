@@ -11,9 +11,9 @@
 // up front.  The regular entry points need a caller-provided workspace;
 // this one needs none.
 //
-// The scratch array below is CM_STATIC_SCRATCH_BYTES (32 MiB).  Every GPU that
-// loads this library's module keeps that much memory reserved until the process
-// exits.  All calls share the one array and it keeps whatever the last call left
+// The scratch array below is CM_STATIC_SCRATCH_BYTES (32 MiB).  The first call
+// on each device reserves it there (see scratch_address) and the device keeps it
+// until the process exits.  All calls share the one array and it keeps whatever the last call left
 // in it; each call clears the part that must start at zero (the images of warped
 // events) before using it.  Two calls whose work overlaps on the GPU (different
 // streams, no ordering between them) race on the array and give wrong results:
@@ -36,6 +36,10 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_addr[kMaxDevices] = {nullptr};
 
+// The first lookup on a device is also where the array is reserved: with
+// CUDA's lazy module loading this module (it holds no kernels, only the array)
+// is loaded on that device when its symbol is first asked for, so a device
+// without 32 MiB free fails here, with CM_ENOMEM.
 int scratch_address(void** out)
 {
     int dev = -1;
@@ -43,7 +47,12 @@ int scratch_address(void** out)
     std::lock_guard<std::mutex> lk(g_mu);
     if (!g_addr[dev]) {
         void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) return CM_ECUDA;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e == cudaErrorMemoryAllocation) {
+            (void)cudaGetLastError();
+            return CM_ENOMEM;
+        }
+        if (e != cudaSuccess || !p) return CM_ECUDA;
         g_addr[dev] = p;
     }
     *out = g_addr[dev];
@@ -52,19 +61,17 @@ int scratch_address(void** out)
 
 size_t up256(size_t v) { return (v + 255) / 256 * 256; }
 
+// the checks of the workspace entry points, then what this entry point does
+// not support (stored warps, the sort path)
 bool valid_args(const cm_camera* cam, const cm_events* ev, const float* flow, int32_t nfb, const cm_loss_cfg* cfg,
                 const float* dloss, const float* loss_out, const float* dflow_out)
 {
-    if (!cam || !ev || !cfg || !flow || !dloss || !loss_out || !dflow_out) return false;
-    if (cam->width < 2 || cam->height < 2 || cam->width > 32767 || cam->height > 32767) return false;
-    if (!(cam->fx > 0.0f) || !(cam->fy > 0.0f) || !std::isfinite(cam->fx) || !std::isfinite(cam->fy)) return false;
-    if (cfg->nbins < 1 || cfg->nbins > CM_MAX_BINS) return false;
-    if (cfg->ref_mode != CM_REF_END && cfg->ref_mode != CM_REF_ALL_EDGES) return false;
-    if (cfg->store_warps != 0 || !std::isfinite(cfg->eps)) return false;
+    if (cmk::check_camera(cam) != CM_OK || cmk::check_cfg(cfg) != CM_OK || cmk::check_events(ev) != CM_OK)
+        return false;
+    if (!flow || !dloss || !loss_out || !dflow_out) return false;
+    if (cfg->store_warps != 0) return false;
     if (cfg->splat != CM_SPLAT_AUTO && cfg->splat != CM_SPLAT_ATOMIC) return false;
     if (nfb != 1 && nfb != cfg->nbins) return false;
-    if (ev->n < 0 || (ev->n > 0 && (!ev->x || !ev->y || !ev->t || !ev->p))) return false;
-    if (!std::isfinite(ev->t0) || !std::isfinite(ev->t1) || !(ev->t1 - ev->t0 > 0.0f)) return false;
     return true;
 }
 

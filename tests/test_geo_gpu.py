@@ -1,7 +1,12 @@
 """GPU parity of the geometry-consistency loss (Eq. 3) and of its gradient to
-both inverse depths and the camera motion, against the oracle (FP64 on the
-same FP32 projection decisions), and its composition into the total loss of
-Eq. 4 through autograd."""
+both inverse depths and the camera motion, against the FP64 oracle, and its
+composition into the total loss of Eq. 4 through autograd.  The oracle's
+straddle analysis (oracle.geo_bounds) flags the pixels whose valid flag,
+sample cell or branch of |a - b| an FP32 evaluation could decide the other
+way: the loss must lie within 1e-5 of its interval; with the flagged pixels
+made invalid in both views' input (a negative inverse depth puts the point
+behind the camera, far from every threshold) the loss must match within 1e-5
+and every gradient within 1e-4 relative L2."""
 import numpy as np
 import pytest
 
@@ -30,9 +35,20 @@ def test_geo_loss_and_gradients_match_oracle(W, H, seed, dt):
     r1 = torch.from_numpy(rho1).cuda().requires_grad_(True)
     e = torch.from_numpy(ego).cuda().requires_grad_(True)
     loss = cm.geo_loss(cam, r0, r1, e, dt)
-    (2.5 * loss).backward()
-    o = O.geo(cam, rho0, rho1, ego, dt, grad=True, dloss=2.5)
+    o = O.geo(cam, rho0, rho1, ego, dt)
+    b = O.geo_bounds(cam, rho0, rho1, ego, dt)
     assert 0 < o["count"] < W * H  # some pixels leave the image
+    assert b["count_lo"] <= o["count"] <= b["count_hi"] and b["loss_lo"] <= o["loss"] <= b["loss_hi"]
+    assert b["loss_lo"] - LOSS_RTOL * o["loss"] <= loss.item() <= b["loss_hi"] + LOSS_RTOL * o["loss"]
+    assert b["flagged"] < 3e-3 * W * H
+    # the flagged pixels moved behind the camera in view 0: no decision in doubt
+    rho0f = rho0.copy()
+    rho0f[b["flags"] != 0] = -1.0
+    assert O.geo_bounds(cam, rho0f, rho1, ego, dt)["flagged"] == 0
+    r0 = torch.from_numpy(rho0f).cuda().requires_grad_(True)
+    loss = cm.geo_loss(cam, r0, r1, e, dt)
+    (2.5 * loss).backward()
+    o = O.geo(cam, rho0f, rho1, ego, dt, grad=True, dloss=2.5)
     assert abs(loss.item() - o["loss"]) <= LOSS_RTOL * abs(o["loss"])
     assert rel_l2(r0.grad.cpu().numpy(), o["dinv_depth0"]) <= GRAD_RTOL_L2
     assert rel_l2(r1.grad.cpu().numpy(), o["dinv_depth1"]) <= GRAD_RTOL_L2

@@ -75,7 +75,30 @@ def test_pan_closed_form():
     np.testing.assert_allclose(f[..., 1], cam.fy * Yp / Zp + cam.cy - v, atol=1e-11)
 
 
-def test_fp32_sequence_tracks_fp64():
+def _eq2_float32(cam, rho, e, dt, scale):
+    """Eq. 2 displacement in numpy float32 arithmetic, written in the
+    cancellation-free form (Z s0 + t0 - xn t2) / P2 with s0 = ((R - I) m)_0 -
+    xn ((R - I) m)_2, m = (xn, yn, 1), and the rotation's coefficients in the
+    stable forms sin(th)/th and 2 sin^2(th/2)/th^2."""
+    f = np.float32
+    k = (-e[3:] * f(dt)).astype(np.float32)
+    t = (-e[:3] * f(dt)).astype(np.float32)
+    th = np.sqrt((k * k).sum(dtype=np.float32))
+    a = np.sin(th) / th if th > 0 else f(1)
+    b = f(2) * np.sin(th / f(2)) ** 2 / (th * th) if th > 0 else f(0.5)
+    K = np.array([[0, -k[2], k[1]], [k[2], 0, -k[0]], [-k[1], k[0], 0]], np.float32)
+    A = (a * K + b * (K @ K)).astype(np.float32)  # R - I
+    v, u = np.mgrid[0:cam.height, 0:cam.width].astype(np.float32)
+    xn, yn = (u - f(cam.cx)) / f(cam.fx), (v - f(cam.cy)) / f(cam.fy)
+    Z = f(1) / rho.astype(np.float32)
+    Am = [A[i, 0] * xn + A[i, 1] * yn + A[i, 2] for i in range(3)]
+    P2 = Z * (f(1) + Am[2]) + t[2]
+    e0 = Z * (Am[0] - xn * Am[2]) + (t[0] - xn * t[2])
+    e1 = Z * (Am[1] - yn * Am[2]) + (t[1] - yn * t[2])
+    return np.stack([f(scale) * (f(cam.fx) * (e0 / P2)), f(scale) * (f(cam.fy) * (e1 / P2))], -1)
+
+
+def test_error_bound_covers_a_single_precision_evaluation():
     cam = synth.camera_for(346, 260)
     rng = synth.rng_for(2)
     rho = synth.inv_depth_map(rng, 346, 260)
@@ -83,15 +106,12 @@ def test_fp32_sequence_tracks_fp64():
     ego[3, 3:] *= 40.0  # a large rotation angle (about 0.5 rad over the bin)
     scale = 4.0
     f64 = O.flow_eq2_bins(cam, rho, ego, 0.01, scale)
-    f32 = O.flow_eq2_bins_f32(cam, rho, ego, 0.01, scale)
-    # FP32 bound: the displacement fx (P0 - xn P2) / P2 inherits a few ulps of
-    # the camera-frame point (|X| <= Zmax (1 + max |xn|)), times fx and scale
-    zmax = 1.0 / float(rho.min())
-    xmax = max(cam.cx, cam.width - cam.cx) / cam.fx
-    bound = 8 * scale * max(cam.fx, cam.fy) * zmax * (1 + xmax) * 2.0 ** -24
+    eb = O.flow_eq2_error_bound(cam, rho, ego, 0.01, scale)
     for i in range(4):
-        err = np.abs(f64[i] - f32[i]).max()
-        assert err < bound, (i, err, bound)
+        f32 = _eq2_float32(cam, rho, ego[i].astype(np.float32), 0.01, scale)
+        d = np.abs(f32.astype(np.float64) - f64[i]).max(axis=-1)
+        assert np.all(d <= eb[i]), (i, (d / eb[i]).max())
+        assert eb[i].max() < 1e-5 * np.abs(f64[i]).max() + 1e-5  # FP32-tight
 
 
 def _loss(cam, rho, ego, dt, scale, g):

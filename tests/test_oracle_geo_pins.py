@@ -1,9 +1,10 @@
 """Pins of the oracle's geometry-consistency loss (Eq. 3): closed forms for a
 camera at rest (equal and uniformly scaled depth), for forward motion over a
 fronto-parallel plane (consistent depths give zero loss; the valid count from
-the closed-form projection), for a pan over a plane, and central differences
-of the loss on frozen decisions for every inverse-depth pixel of both views
-and every pose component."""
+the closed-form projection), for a pan over a plane, central differences of
+the loss on frozen decisions for every inverse-depth pixel of both views and
+every pose component, and the straddle analysis (flags, the interval of the
+valid count and of the loss) against perturbed evaluations."""
 import numpy as np
 import pytest
 
@@ -45,18 +46,21 @@ def test_pan_over_a_plane():
     rho = np.full((cam.height, cam.width), 1 / Z0)
     ego = np.array([0, 0, 0, 0, wy, 0])
     r = O.geo(cam, rho, rho, ego, dt)
-    proj, ok, _ = O.geo_proj_f32(cam, rho, rho, ego, dt)
     th = -wy * dt
     v, u = np.mgrid[0:cam.height, 0:cam.width]
     xn = (u - cam.cx) / cam.fx
     a = Z0 * (-np.sin(th) * xn + np.cos(th))  # depth of the rotated point; view 1 sees the plane at Z0
     f = np.abs(a - Z0) / (a + Z0)
+    # the projection of the rotated plane point, in closed form
+    xp = cam.fx * (np.cos(th) * xn + np.sin(th)) / (-np.sin(th) * xn + np.cos(th)) + cam.cx
+    yp = cam.fy * ((v - cam.cy) / cam.fy) / (-np.sin(th) * xn + np.cos(th)) + cam.cy
+    ok = (xp >= 0) & (xp <= cam.width - 1) & (yp >= 0) & (yp <= cam.height - 1) & (a > 0)
     assert r["count"] == int(ok.sum()) > 0
-    assert r["loss"] == pytest.approx(f[ok.astype(bool)].mean(), rel=1e-12)
+    assert r["loss"] == pytest.approx(f[ok].mean(), rel=1e-12)
 
 
 def _loss(cam, r0, r1, e, dt, dec):
-    return O.geo(cam, r0, r1, e, dt, decisions=dec)["loss"]
+    return O.geo(cam, r0, r1, e, dt, replay=dec)["loss"]
 
 
 def test_gradient_matches_central_differences_on_frozen_decisions():
@@ -66,9 +70,11 @@ def test_gradient_matches_central_differences_on_frozen_decisions():
     r1 = r0 * rng.uniform(0.8, 1.2, r0.shape)
     e = np.array([0.3, -0.2, 0.8, 0.4, -0.6, 0.2])
     dt = 0.05
-    dec = O.geo_proj_f32(cam, r0, r1, e, dt)
-    assert 0 < dec[1].sum() < r0.size  # some pixels leave the image
-    g = O.geo(cam, r0, r1, e, dt, decisions=dec, grad=True, dloss=1.7)
+    base = O.geo(cam, r0, r1, e, dt, record=True)
+    dec = base["decisions"]
+    assert 0 < dec["ok"].sum() < r0.size  # some pixels leave the image
+    g = O.geo(cam, r0, r1, e, dt, replay=dec, grad=True, dloss=1.7)
+    assert g["loss"] == pytest.approx(base["loss"], rel=1e-14)
     for name, x in (("dinv_depth0", r0), ("dinv_depth1", r1)):
         fd = np.empty_like(x)
         for q in range(x.size):
@@ -88,3 +94,37 @@ def test_gradient_matches_central_differences_on_frozen_decisions():
         em[q] -= h
         fde[q] = 1.7 * (_loss(cam, r0, r1, ep, dt, dec) - _loss(cam, r0, r1, em, dt, dec)) / (2 * h)
     np.testing.assert_allclose(g["dego"], fde, rtol=1e-5, atol=1e-6 * np.abs(fde).max())
+
+
+def test_bounds_contain_the_loss_and_every_perturbed_evaluation():
+    # a sideways translation over a fronto-parallel plane moves every pixel by
+    # exactly -3 px, so every projection lies on an integer and column 3 lands
+    # on the border x' = 0: every pixel is flagged (cell), column 3 also in the
+    # valid set.  Inverse depths perturbed by 1e-7 relative (x' moves by 3e-7 px,
+    # inside the margins) move column 3 in and out of the image: every
+    # perturbed count and loss lies in the interval
+    cam = _cam(40, 30, 30.0)
+    dt, rho0 = 0.05, 0.8
+    vx = 3.0 / (cam.fx * dt * rho0)
+    e = np.array([vx, 0, 0, 0, 0, 0])
+    r0 = np.full((cam.height, cam.width), rho0)
+    r1 = r0 * np.random.default_rng(11).uniform(0.9, 1.1, r0.shape)
+    base = O.geo(cam, r0, r1, e, dt)
+    b = O.geo_bounds(cam, r0, r1, e, dt, safety=100.0)
+    f = b["flags"]
+    # every cell in doubt along x (y' = v is exact: no rows in doubt), column 3
+    # also valid or not; columns 0-2 land beyond the margin: invalid in any evaluation
+    assert np.all(f[:, 3:] & 1) and np.all(f[:, 3] & 2) and not np.any(f[:, 4:] & 2)
+    assert not np.any(f[:, :3])
+    assert b["count_hi"] - b["count_lo"] == cam.height
+    assert b["count_lo"] <= base["count"] <= b["count_hi"]
+    assert b["loss_lo"] <= base["loss"] <= b["loss_hi"]
+    counts = set()
+    for s in range(8):
+        g = np.random.default_rng(50 + s)
+        p0 = r0 * (1 + 1e-7 * g.uniform(-1, 1, r0.shape))
+        pr = O.geo(cam, p0, r1, e, dt)
+        assert b["count_lo"] <= pr["count"] <= b["count_hi"]
+        assert b["loss_lo"] <= pr["loss"] <= b["loss_hi"]
+        counts.add(pr["count"])
+    assert len(counts) > 1  # the perturbations did move pixels across the border

@@ -8,7 +8,7 @@ import pytest
 
 from paper_2412_06359_gb300 import _capi as C
 from paper_2412_06359_gb300 import synth
-from tests.gpu_util import GRAD_RTOL_L2, LOSS_RTOL, gpu_lib, rel_l2, run_oracle
+from tests.gpu_util import GRAD_EPS, GRAD_RTOL_L2, LOSS_RTOL, gpu_lib, rel_l2, run_oracle, unflagged
 
 pytestmark = pytest.mark.gpu
 
@@ -34,6 +34,31 @@ def _server(budget=2 << 30, **kw):
     return Server(budget, **kw)
 
 
+def check_served(reqs):
+    """Served results against the FP64 oracle: each request's loss within
+    LOSS_RTOL of the oracle's straddle interval; the windows without their
+    flagged events served again (a server at eps = GRAD_EPS, where the
+    gradient is well-conditioned) against the oracle strictly: loss within
+    LOSS_RTOL, dL/d(inv depth) and dL/d(ego) within GRAD_RTOL_L2."""
+    from paper_2412_06359_gb300.serve import HostRequest
+    subs = []
+    for r in reqs:
+        o = run_oracle(r.window, grad=False, bounds=True)
+        b, L = o["bounds"], float(r.loss[0])
+        assert b["loss_lo"] - LOSS_RTOL * o["loss"] <= L <= b["loss_hi"] + LOSS_RTOL * o["loss"], (L, b)
+        subs.append(unflagged(r.window, b["flags"]))
+    srv = _server(eps=GRAD_EPS, max_batch=4, lanes=2)
+    sreqs = [HostRequest.from_window(i, w) for i, w in enumerate(subs)]
+    for t in [srv.submit(q) for q in sreqs]:
+        assert srv.wait(t, 120).status == 0
+    srv.close()
+    for q in sreqs:
+        o = run_oracle(q.window, eps=GRAD_EPS)
+        assert abs(float(q.loss[0]) - o["loss"]) <= LOSS_RTOL * o["loss"]
+        assert rel_l2(q.drho, o["dinv_depth"]) <= GRAD_RTOL_L2
+        assert rel_l2(q.dego, o["dego"]) <= GRAD_RTOL_L2
+
+
 def _snapshot(req):
     return float(req.loss[0]), req.drho.copy(), req.dego.copy()
 
@@ -57,17 +82,14 @@ def test_results_alone_equal_results_in_the_mix():
         assert rel_l2(rm, ra) <= GRAD_RTOL_L2
         assert rel_l2(em, ea) <= GRAD_RTOL_L2
     # and against the oracle
-    for r in reqs[:3]:
-        o = run_oracle(r.window)
-        assert abs(float(r.loss[0]) - o["loss"]) <= LOSS_RTOL * o["loss"]
-        assert rel_l2(r.drho, o["dinv_depth"]) <= GRAD_RTOL_L2
-        assert rel_l2(r.dego, o["dego"]) <= GRAD_RTOL_L2
+    check_served(reqs[:3])
     st = srv.stats()
     assert st.completed == 2 * len(reqs) and st.queued == 0
     srv.close()
 
 
 def test_budget_admission_and_eviction():
+    from paper_2412_06359_gb300.serve import HostRequest
     # a budget that holds the plans and about two streams' state: the server evicts
     # idle streams and makes requests wait for memory, and every result is right
     reqs = _requests(10, 5, seed=8)
@@ -81,9 +103,25 @@ def test_budget_admission_and_eviction():
     st = srv.stats()
     assert st.evictions > 0
     assert st.pool_peak <= st.pool_bytes
-    for r in reqs[:4]:
-        o = run_oracle(r.window)
-        assert abs(float(r.loss[0]) - o["loss"]) <= LOSS_RTOL * o["loss"]
+    srv.close()
+    # every result right under memory pressure, gradients included (the upstream
+    # gradient must be set however the stream's state was (re)allocated): the
+    # same requests at eps = GRAD_EPS through a server of the same small budget
+    srv = _server(budget=budget, max_batch=4, lanes=2, eps=GRAD_EPS)
+    subs = []
+    for r in reqs:
+        o = run_oracle(r.window, grad=False, bounds=True)
+        b = o["bounds"]
+        assert b["loss_lo"] - LOSS_RTOL * o["loss"] <= float(r.loss[0]) <= b["loss_hi"] + LOSS_RTOL * o["loss"]
+        subs.append(HostRequest.from_window(r.stream_id, unflagged(r.window, b["flags"])))
+    results = [srv.wait(t, 120) for t in [srv.submit(q) for q in subs]]
+    assert all(res.status == 0 for res in results)
+    assert srv.stats().evictions > 0
+    for q in subs:
+        o = run_oracle(q.window, eps=GRAD_EPS)
+        assert abs(float(q.loss[0]) - o["loss"]) <= LOSS_RTOL * o["loss"]
+        assert rel_l2(q.drho, o["dinv_depth"]) <= GRAD_RTOL_L2
+        assert rel_l2(q.dego, o["dego"]) <= GRAD_RTOL_L2
     srv.close()
 
 

@@ -1,11 +1,12 @@
-"""The deterministic sort-by-pixel path (CM_SPLAT_SORT): parity with the
-oracle at the same tolerances as the atomic path, and bit-reproducibility run
-to run of the images of warped events, the loss and every gradient."""
+"""The deterministic sort-by-pixel path (CM_SPLAT_SORT): parity with the FP64
+oracle by the same checks as the atomic path (tests/gpu_util.py), and
+bit-reproducibility run to run of the images of warped events, the loss and
+every gradient."""
 import numpy as np
 import pytest
 
 from paper_2412_06359_gb300 import synth
-from tests.gpu_util import assert_parity, gpu_lib, rel_l2, run_gpu, run_oracle
+from tests.gpu_util import check_window, gpu_lib, plain, rel_l2, run_gpu, run_oracle, unflagged
 from tests.test_parity_gpu import small_depth_window, small_flow_window
 
 pytestmark = pytest.mark.gpu
@@ -19,26 +20,25 @@ def sort_mode():
 
 def test_sort_flow_window_128():
     win = synth.flow_window()
-    assert_parity(run_gpu(win, splat=sort_mode()), run_oracle(win))
+    check_window(win, plain(splat=sort_mode()))
 
 
 def test_sort_davis_window_346():
     win = synth.davis_window()
-    assert_parity(run_gpu(win, splat=sort_mode()), run_oracle(win))
+    check_window(win, plain(splat=sort_mode()))
 
 
 @pytest.mark.parametrize("B,ref_mode,nfb", [(4, ALL, 4), (5, END, 1), (3, ALL, 1), (20, ALL, 1)])
 def test_sort_bins_refs_and_per_bin_flows(B, ref_mode, nfb):
     win = small_flow_window(70, 50, 5000, B, ref_mode, nfb=nfb, seed=B * 7 + nfb)
-    assert_parity(run_gpu(win, splat=sort_mode()), run_oracle(win))
+    check_window(win, plain(splat=sort_mode()))
 
 
 @pytest.mark.parametrize("n", [1, 255, 2049, 4097])
 def test_sort_ragged_event_counts(n):
     # entry counts below, at and across the sort's 2048-entry tiles
     win = small_depth_window(64, 48, n, 10, seed=n + 1)
-    assert_parity(run_gpu(win, splat=sort_mode(), grad=False), run_oracle(win, grad=False), grad=False)
-    assert_parity(run_gpu(win, splat=sort_mode(), eps=1e-2), run_oracle(win, eps=1e-2))
+    check_window(win, plain(splat=sort_mode()))
 
 
 def test_sort_empty_and_all_masked():
@@ -53,6 +53,7 @@ def test_sort_empty_and_all_masked():
 
 def test_sort_iwe_matches_oracle_elementwise():
     win = small_depth_window(120, 90, 9000, 10, seed=4)
+    win = unflagged(win, run_oracle(win, grad=False, bounds=True)["bounds"]["flags"])
     g = run_gpu(win, splat=sort_mode(), grad=False, want_iwe=True)
     o = run_oracle(win, grad=False, want_iwe=True)
     assert np.array_equal(g["iwe"] != 0, o["iwe"] != 0)

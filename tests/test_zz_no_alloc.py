@@ -4,12 +4,14 @@ real-time loops, plug-ins inside a framework that owns the memory pool, code
 with a fixed up-front budget).  Its output must equal the workspace path's
 (cm_loss_forward + cm_loss_backward) within the parity tolerances, on two
 calls in a row, whether this file runs alone in a fresh process or after the
-other tests.  Kept in its own file, collected last."""
+other tests; its loss must lie within the FP64 oracle's interval; and after a
+first call the calls must leave the device's free memory and torch's
+allocation count unchanged.  Kept in its own file, collected last."""
 import numpy as np
 import pytest
 
 from paper_2412_06359_gb300 import synth
-from tests.gpu_util import GRAD_RTOL_L2, LOSS_RTOL, gpu_lib, rel_l2
+from tests.gpu_util import GRAD_RTOL_L2, LOSS_RTOL, gpu_lib, rel_l2, run_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -66,6 +68,39 @@ def test_static_entry_matches_workspace_path_two_calls():
             loss, g = _static_call(cm, win, flow, ev, dloss)
             assert abs(loss - ref_loss) <= LOSS_RTOL * abs(ref_loss), (loss, ref_loss)
             assert rel_l2(g, ref_g) <= GRAD_RTOL_L2
+        # and against the FP64 oracle's interval over FP32-sensitive decisions
+        o = run_oracle(win, grad=False, bounds=True)
+        b = o["bounds"]
+        assert b["loss_lo"] - LOSS_RTOL * o["loss"] <= loss <= b["loss_hi"] + LOSS_RTOL * o["loss"]
+
+
+def test_static_entry_allocates_nothing():
+    import torch
+    from paper_2412_06359_gb300 import _capi as C
+    cm = gpu_lib()
+    win = synth.flow_window()
+    ev = cm.DeviceEvents.from_host(win.events)
+    flow = torch.from_numpy(np.ascontiguousarray(win.flow[0], np.float32)).cuda()
+    dloss = torch.ones(1, device="cuda")
+    loss = torch.empty(1, device="cuda")
+    dflow = torch.empty_like(flow)
+    cfg = cm.loss_cfg(win.nbins, win.ref_mode, cm.SPLAT_ATOMIC)
+    # the set-up call (an empty window): reserves the array on this device
+    empty = cm.DeviceEvents.from_host(win.events.take(np.arange(0)))
+    C.cm_loss_grad_static(cm.camera(win.cam), empty.c(), flow.data_ptr(), 1, cfg, dloss.data_ptr(),
+                          loss.data_ptr(), dflow.data_ptr(), cm.stream_handle())
+    torch.cuda.synchronize()
+    assert float(loss.cpu()[0]) == 0.0
+    free0, _ = torch.cuda.mem_get_info()
+    allocs0 = torch.cuda.memory_stats().get("allocation.all.allocated", 0)
+    for _ in range(5):
+        C.cm_loss_grad_static(cm.camera(win.cam), ev.c(), flow.data_ptr(), 1, cfg, dloss.data_ptr(),
+                              loss.data_ptr(), dflow.data_ptr(), cm.stream_handle())
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert torch.cuda.memory_stats().get("allocation.all.allocated", 0) == allocs0
+    assert float(loss.cpu()[0]) > 0.0
 
 
 def test_static_entry_rejects_windows_beyond_its_array():
