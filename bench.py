@@ -46,14 +46,16 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="bound of the CPU oracle sample")
     ap.add_argument("--schedule", default="auto",
-                    help="batch schedule 'chains,windows_per_kernel,grouping' (grouping 0: given order, 1: 32x32 "
-                         "tiles, 2: 32-row bands; e.g. 6,2,2), or 'auto' to autotune")
+                    help="batch schedule 'chains,windows_per_kernel,grouping[,persist]' (grouping 0: given order, "
+                         "1: 32x32 tiles, 2: 32-row bands, 3: tiles in shared memory; persist k > 0: one persistent "
+                         "kernel staggering the windows by k phases, with 1,0,g; e.g. 6,2,2 or 1,0,2,2), or 'auto'")
     ap.add_argument("--events", default="iid", choices=["iid", "motion"],
                     help="iid: the headline workload; motion: motion-consistent events with their true flow "
                          "(flow input, many events per pixel after the warp: the contention stress variant)")
     ap.add_argument("--store-warps", type=int, default=0, choices=[0, 1],
                     help="1: the forward stores the trajectory points for the backward (no recompute)")
     ap.add_argument("--serve", action="store_true", help="run the serving workload instead (one line per rate)")
+    ap.add_argument("--no-serve", action="store_true", help="skip the short serving leg of the default line")
     ap.add_argument("--latency", action="store_true",
                     help="single-window latency of the parity workloads (128x128 flow, 346x260 and 1280x720 depth)")
     ap.add_argument("--reps", type=int, default=200, help="repetitions per workload of --latency")
@@ -204,7 +206,7 @@ def workload_config(wins, events_kind: str, events_per_step: int) -> dict:
 
 
 # the batch schedule's event grouping modes (cm_batch_schedule.bin)
-GROUPING = ("given order", "32x32 tiles", "32-row bands")
+GROUPING = ("given order", "32x32 tiles", "32-row bands", "32x32 tiles, shared-memory accumulation")
 
 
 def measured_peak():
@@ -217,11 +219,11 @@ def measured_peak():
 
 
 def kernel_source_hash() -> str:
-    """Hash of the sources of the batched plan's kernels (device code and the
-    batch translation unit): recorded ncu counters hold while it is unchanged."""
+    """Hash of the device sources of the batched plan's kernels: recorded ncu
+    counters hold while it is unchanged."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2412_06359_gb300", "csrc")
-    for f in ("cm_device.cuh", "cm_launch.h", "cm_batch.cu"):
+    for f in ("cm_device.cuh", "cm_bands.cuh", "cm_batch_kernels.cuh"):
         h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -554,10 +556,30 @@ def run_ours(args):
         plain = {"value": batch.events / el / 1e6, "unit": "Mev/s", "p50_ms": float(np.percentile(lat, 50)),
                  "p99_ms": float(np.percentile(lat, 99)), "windows": len(wins)}
 
-    # ---- the two splat strategies through the single-window calls ----
-    splat_cmp = None
+    # ---- the splat strategies: single-window calls (atomic, sort) and the
+    # batched plan (direct reductions, shared-memory tiles) on the bench's
+    # windows and on motion-consistent windows (many events per pixel) ----
+    splat_cmp = sched_cmp = None
     if not args.no_plain:
         splat_cmp = compare_splats(batch, min(4, len(wins)))
+        c, g = schedule[0], schedule[1]
+        splat_cmp["batched_iid"] = compare_batched_splats(
+            batch, {"direct_bands": (c, g, 2), "direct_given_order": (c, g, 0), "smem_tiles": (c, g, 3)})
+        batch.plan.set_schedule(*schedule)
+        from paper_2412_06359_gb300 import synth as _synth
+        mot = Batch(_synth.batch_windows_motion(8), dev)
+        splat_cmp["batched_motion"] = compare_batched_splats(
+            mot, {"direct_given_order": (2, 1, 0), "direct_bands": (2, 1, 2), "smem_tiles": (2, 1, 3)})
+        splat_cmp["batched_motion"]["windows"] = 8
+        splat_cmp["batched_motion"]["events"] = mot.events
+        del mot
+        # the graph of per-phase kernels against the persistent step (device work queue)
+        sched_cmp = compare_batched_splats(batch, {
+            "graph_6x2_bands": (6, 2, 2, 0), "graph_8x2_bands": (8, 2, 2, 0),
+            "persistent_bands_stagger1": (1, 0, 2, 1), "persistent_bands_stagger2": (1, 0, 2, 2),
+            "persistent_bands_stagger3": (1, 0, 2, 3), "persistent_bands_stagger7": (1, 0, 2, 7),
+            "persistent_given_order_stagger2": (1, 0, 0, 2)})
+        batch.plan.set_schedule(*schedule)
 
     # ---- the kernels beside the CM path (discrete flow, geometry loss, event frame) ----
     others = None
@@ -568,6 +590,11 @@ def run_ours(args):
     e2e = None
     if not args.no_e2e and not batch.flow_input:
         e2e = run_e2e(batch, args, stream, schedule)
+
+    # ---- a short serving leg (32 streams, 0.5x and 1x the arrival rate, 3 runs each) ----
+    serve = None
+    if rank == 0 and world == 1 and not args.no_serve:
+        serve = serve_leg([0.5, 1.0], 2.0, 3, args.serve_lanes, args.serve_batch)
 
     # ---- CPU oracle baseline (rank 0 at N = 1 only) ----
     cpu = cpu_all = None
@@ -591,11 +618,13 @@ def run_ours(args):
             "plan": {"splat": "atomic", "backward": "stored warps" if args.store_warps else "recompute",
                      "path": "batched plan replayed from a CUDA graph",
                      "schedule": {"chains": schedule[0], "windows_per_kernel": schedule[1],
-                                  "grouping": GROUPING[schedule[2]]}},
+                                  "grouping": GROUPING[schedule[2]],
+                                  "persistent": schedule[3] > 0, "stagger": schedule[3]}},
             "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
-            "plain": plain, "splat_compare": splat_cmp, "roofline": roof, "roofline_iwe": roof_iwe,
+            "plain": plain, "splat_compare": splat_cmp, "schedule_compare": sched_cmp, "roofline": roof,
+            "roofline_iwe": roof_iwe,
             "roofline_l2": roof_l2, "other_kernels": others, "cpu_baseline": cpu,
-            "cpu_baseline_all_cores": cpu_all, "e2e": e2e,
+            "cpu_baseline_all_cores": cpu_all, "e2e": e2e, "serve": serve,
             "clocks": clocks, "gpu_launches": int(launches),
             "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])},
         }
@@ -710,6 +739,27 @@ def compare_splats(batch, nwin: int):
     return out
 
 
+def compare_batched_splats(batch, schedules, reps: int = 5):
+    """The batched plan's splat strategies on the same windows: device time of
+    `reps` replays (CUDA events) per schedule, in Mev/s.  schedules: name ->
+    (chains, windows per kernel, grouping); grouping 3 is the shared-memory
+    tile strategy, the others reduce straight into the images."""
+    import torch
+    out = {}
+    for name, sched in schedules.items():
+        batch.plan.set_schedule(*sched)
+        batch.plan.run()
+        torch.cuda.synchronize()
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            batch.plan.run()
+        z.record()
+        z.synchronize()
+        out[name] = {"schedule": list(sched), "mev_s": batch.events * reps / (a.elapsed_time(z) * 1e-3) / 1e6}
+    return out
+
+
 def run_e2e(batch, args, stream, schedule):
     """Same metric through the public API with host buffers.  The inputs of all
     windows (events, inverse depth, ego-motion) sit back to back in one pinned
@@ -798,6 +848,108 @@ def run_e2e(batch, args, stream, schedule):
                         "steps' compute (two input arenas, two plans)"}
 
 
+SERVE_STREAMS = 32
+
+
+def serve_pools(pool: int):
+    """Pre-generated requests of the serving workload: 32 streams (resolutions
+    cycling 346x260 / 640x480 / 1280x720), `pool` windows per stream, event
+    counts log-uniform in [10k, 2M], 10 bins, in pinned host memory."""
+    import torch
+
+    from paper_2412_06359_gb300 import synth
+    from paper_2412_06359_gb300.serve import HostRequest
+
+    def pinned(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+
+    pools = []
+    for s in range(SERVE_STREAMS):
+        rng = synth.rng_for(5, s)
+        W, H = synth.SERVE_RESOLUTIONS[s % len(synth.SERVE_RESOLUTIONS)]
+        reqs = []
+        for _ in range(pool):
+            win = synth.depth_window(rng, W, H, synth.log_uniform_count(rng, 1e4, 2e6), nbins=10)
+            r = HostRequest.from_window(s, win)
+            for f in ("x", "y", "t", "p", "rho", "ego", "loss", "drho", "dego"):
+                setattr(r, f, pinned(getattr(r, f)))
+            reqs.append(r)
+        pools.append(reqs)
+    return pools
+
+
+def serve_arrivals(scale: float, seconds: float, pool: int, seed: int = 77):
+    """Poisson arrivals at 100 Hz x scale per stream over `seconds`: sorted
+    (time, stream, pool index)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for s in range(SERVE_STREAMS):
+        t = rng.exponential(1.0 / (100.0 * scale))
+        k = 0
+        while t < seconds:
+            out.append((t, s, k % pool))
+            k += 1
+            t += rng.exponential(1.0 / (100.0 * scale))
+    return sorted(out)
+
+
+def serve_replay(srv, pools, arr):
+    """Submit the arrivals at their times (host clock), wait for all; latency
+    of a request = its completion - its submission (the server's clocks)."""
+    from paper_2412_06359_gb300 import _capi as C
+    # warm up: one request per stream (allocates its state, captures the graphs)
+    for s in range(SERVE_STREAMS):
+        srv.wait(srv.submit(pools[s][0]), 120)
+    t0 = time.perf_counter()
+    tickets = []
+    for ta, s, k in arr:
+        dt = t0 + ta - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        while True:
+            try:
+                tickets.append((srv.submit(pools[s][k]), pools[s][k].x.shape[0]))
+                break
+            except C.CMError as e:
+                if e.status != C.CM_EBUSY:
+                    raise
+                time.sleep(1e-4)
+    res = [(srv.wait(t, 600), n) for t, n in tickets]
+    lat = np.array([1e3 * (r.t_done - r.t_submit) for r, _ in res])
+    first = min(r.t_submit for r, _ in res)
+    last = max(r.t_done for r, _ in res)
+    ev = sum(n for _, n in res)
+    sizes = [r.batch_size for r, _ in res]
+    return {"requests": len(res), "events": int(ev), "throughput": ev / (last - first) / 1e6,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_batch": float(np.mean(sizes)), "offered_mev_s": ev / arr[-1][0] / 1e6 if arr else 0.0,
+            "stats": {k: int(getattr(srv.stats(), k)) for k in ("batches", "evictions", "memory_waits",
+                                                                 "pool_peak")}}
+
+
+def serve_leg(scales, seconds: float, reps: int, lanes: int, batch: int, pool: int = 2):
+    """The serving workload at each rate scale, `reps` runs each (a fresh
+    server per run): Mev/s served and p50 / p99 request latency per run, with
+    the p99 spread over the runs."""
+    from paper_2412_06359_gb300.serve import Server
+    pools = serve_pools(pool)
+    out = {"workload": "serve32_mixed_res_poisson100hz", "seconds": seconds, "streams": SERVE_STREAMS,
+           "lanes": lanes, "max_batch": batch, "hbm_budget_gb": 40, "runs": reps, "unit": "Mev/s", "scales": {}}
+    for scale in scales:
+        arr = serve_arrivals(scale, seconds, pool)
+        runs = []
+        for _ in range(reps):
+            srv = Server(40 << 30, max_batch=batch, lanes=lanes)
+            runs.append(serve_replay(srv, pools, arr))
+            srv.close()
+        p99 = [r["p99_ms"] for r in runs]
+        out["scales"][str(scale)] = {
+            "offered_mev_s": runs[0]["offered_mev_s"], "requests": runs[0]["requests"],
+            "served_mev_s": [r["throughput"] for r in runs], "p50_ms": [r["p50_ms"] for r in runs],
+            "p99_ms": p99, "p99_spread_ms": [min(p99), max(p99)], "mean_batch": [r["mean_batch"] for r in runs]}
+    return out
+
+
 def run_serve(args):
     """Serving workload: 32 streams (resolutions cycling 346x260 / 640x480 /
     1280x720), Poisson arrivals at 100 Hz per stream scaled by --serve-scales,
@@ -808,88 +960,30 @@ def run_serve(args):
     import torch
 
     from paper_2412_06359_gb300 import _capi as C
-    from paper_2412_06359_gb300 import build, synth
-    from paper_2412_06359_gb300.serve import HostRequest, Server
+    from paper_2412_06359_gb300 import build
+    from paper_2412_06359_gb300.serve import Server
     build.build()
     C.lib()
     torch.cuda.init()
-
-    def pinned(a):
-        return torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
-
-    streams = 32
-    pools = []
-    for s in range(streams):
-        rng = synth.rng_for(5, s)
-        W, H = synth.SERVE_RESOLUTIONS[s % len(synth.SERVE_RESOLUTIONS)]
-        reqs = []
-        for _ in range(args.serve_pool):
-            win = synth.depth_window(rng, W, H, synth.log_uniform_count(rng, 1e4, 2e6), nbins=10)
-            r = HostRequest.from_window(s, win)
-            for f in ("x", "y", "t", "p", "rho", "ego", "loss", "drho", "dego"):
-                setattr(r, f, pinned(getattr(r, f)))
-            reqs.append(r)
-        pools.append(reqs)
-
-    def arrivals(scale, seconds, seed=77):
-        rng = np.random.default_rng(seed)
-        out = []
-        for s in range(streams):
-            t = rng.exponential(1.0 / (100.0 * scale))
-            k = 0
-            while t < seconds:
-                out.append((t, s, k % args.serve_pool))
-                k += 1
-                t += rng.exponential(1.0 / (100.0 * scale))
-        return sorted(out)
-
-    def replay(srv, arr):
-        # warm up: one request per stream (allocates its state, captures the graphs)
-        for s in range(streams):
-            srv.wait(srv.submit(pools[s][0]), 120)
-        t0 = time.perf_counter()
-        tickets = []
-        for ta, s, k in arr:
-            dt = t0 + ta - time.perf_counter()
-            if dt > 0:
-                time.sleep(dt)
-            while True:
-                try:
-                    tickets.append((srv.submit(pools[s][k]), pools[s][k].x.shape[0]))
-                    break
-                except C.CMError as e:
-                    if e.status != C.CM_EBUSY:
-                        raise
-                    time.sleep(1e-4)
-        res = [(srv.wait(t, 600), n) for t, n in tickets]
-        lat = np.array([1e3 * (r.t_done - r.t_submit) for r, _ in res])
-        first = min(r.t_submit for r, _ in res)
-        last = max(r.t_done for r, _ in res)
-        ev = sum(n for _, n in res)
-        sizes = [r.batch_size for r, _ in res]
-        return {"requests": len(res), "events": int(ev), "throughput": ev / (last - first) / 1e6,
-                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                "mean_batch": float(np.mean(sizes)), "offered_mev_s": ev / arr[-1][0] / 1e6 if arr else 0.0,
-                "stats": {k: int(getattr(srv.stats(), k)) for k in ("batches", "evictions", "memory_waits",
-                                                                     "pool_peak")}}
-
+    pools = serve_pools(args.serve_pool)
     budget = 40 << 30
     for scale in [float(x) for x in args.serve_scales.split(",")]:
-        arr = arrivals(scale, args.serve_seconds)
+        arr = serve_arrivals(scale, args.serve_seconds, args.serve_pool)
         srv = Server(budget, max_batch=args.serve_batch, lanes=args.serve_lanes)
-        batched = replay(srv, arr)
+        batched = serve_replay(srv, pools, arr)
         srv.close()
         plain = None
         if not args.no_plain:
             srv = Server(budget, max_batch=1, lanes=1)
-            plain = replay(srv, arr)
+            plain = serve_replay(srv, pools, arr)
             srv.close()
         line = {"metric": "serving: CM loss+grad Mev/s and p50/p99 request latency", "unit": "Mev/s",
                 "value": batched["throughput"], "p50_ms": batched["p50_ms"], "p99_ms": batched["p99_ms"],
                 "higher_is_better": True, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": "serve32_mixed_res_poisson100hz", "rate_scale": scale,
-                           "seconds": args.serve_seconds, "streams": streams, "pool_per_stream": args.serve_pool,
-                           "max_batch": args.serve_batch, "lanes": args.serve_lanes, "hbm_budget_gb": 40},
+                           "seconds": args.serve_seconds, "streams": SERVE_STREAMS,
+                           "pool_per_stream": args.serve_pool, "max_batch": args.serve_batch,
+                           "lanes": args.serve_lanes, "hbm_budget_gb": 40},
                 "batched": batched, "plain": plain}
         print(json.dumps(line), flush=True)
 

@@ -75,6 +75,9 @@ extern "C" {
 #define CM_SPLAT_AUTO 0     /* pick by the autotuner's cached choice (atomic until tuned) */
 #define CM_SPLAT_ATOMIC 1   /* FP32 vector atomics into the IWE (order of additions not fixed) */
 #define CM_SPLAT_SORT 2     /* deterministic: sort contributions by pixel, segmented sums */
+#define CM_SPLAT_TILES 3    /* batched plans only: accumulate each 32x32 tile in shared memory, flush once
+                               (warp-aggregated shared-memory atomics; schedule bin 3).  The single-window
+                               entry points refuse it (CM_EINVAL) */
 
 #define CM_MAX_BINS 32      /* largest supported number of bins B */
 
@@ -167,7 +170,12 @@ int cm_warp_splat(const cm_camera* cam, const cm_events* ev, const float* flow, 
  * inv_depth (device [H][W]) + ego6 (device [6]) + dt_window, from which the
  * flow is computed into the workspace (n_flow_bins must then be 1).
  * The workspace keeps what the backward needs; the per-reference losses and
- * non-empty counts can be read with cm_workspace_stats.
+ * non-empty counts can be read with cm_workspace_stats.  With one flow field
+ * and the atomic splat the workspace holds the images as polarity planes of
+ * (C, S) pairs and the flow as 32-byte cell quads (the batched plan's layout:
+ * 16-byte splat reductions and gathers, one load per bilinear sample); with
+ * per-bin flows or the sort splat, [R][H][W] float4 images and the flow as
+ * given.  The results are the same either way (within the parity tolerances).
  * Errors: CM_EINVAL, CM_ENOMEM (workspace too small for n), CM_ECUDA.
  */
 int cm_loss_forward(const cm_camera* cam, const cm_events* ev, const float* flow, int32_t n_flow_bins,
@@ -182,7 +190,8 @@ int cm_loss_forward(const cm_camera* cam, const cm_events* ev, const float* flow
  *   dflow       device float [n_flow_bins][H][W][2]   dL/dflow
  *   dinv_depth  device float [H][W]                    dL/d(inverse depth)  (depth input only)
  *   dego6       device float [6]                       dL/d(ego-motion)     (depth input only)
- * Outputs are overwritten, not accumulated.  Errors: CM_EINVAL, CM_ESTATE, CM_ECUDA.
+ * Outputs are overwritten, not accumulated; the backward may be called again
+ * after the same forward.  Errors: CM_EINVAL, CM_ESTATE, CM_ECUDA.
  */
 int cm_loss_backward(const cm_camera* cam, const cm_events* ev, const float* flow, int32_t n_flow_bins,
                      const float* inv_depth, const float* ego6, float dt_window, const cm_loss_cfg* cfg,
@@ -330,13 +339,31 @@ int cm_batch_run(cm_batch* plan, void* stream);
  * events of a warp then share their bin).  Either way the events in flight touch a
  * compact region of the flow and of the images.  Windows that do not fit the
  * plan's grouping memory (sized for the windows it was created with), and
- * sensors taller than 4096 rows in bin 2, stay ungrouped.  Every schedule gives
- * the same results up to the order of the floating-point reductions.
- * Default: chains 2, group 1, bin 0. */
+ * sensors taller than 4096 rows in bin 2, stay ungrouped.  bin 3 groups by tile
+ * as bin 1 and runs the splat and the adjoint one block per tile: the block
+ * accumulates the (C, S) pairs of the points landing in its tile (the first 12
+ * references; 16 KB of shared memory each) and its pushes into the tile's cell
+ * records of dL/dflow, with warp-aggregated shared-memory atomics, and flushes
+ * each tile once with 16-byte reductions; points and pushes outside the tile go
+ * straight to the images and records.  Every schedule gives the same results
+ * up to the order of the floating-point reductions.
+ * persist > 0 replaces the graph's kernels by one persistent kernel: its blocks
+ * take work items (a pixel tile, a super-chunk, a chunk of 256 events or a
+ * loss tile of one phase of one window) from a device queue in which window
+ * w + 1's first phase comes `persist` phases after window w's, and before an
+ * item a block waits (bounded) on the window's per-phase completion counters
+ * for the phases it depends on; the graph holds a memset of the queue and the
+ * kernel.  A few windows are then in flight, with no launch or graph edge
+ * between a window's phases.
+ * Default: chains 2, group 1, bin 0, persist 0 (bin 3 when the plan's
+ * cfg->splat is CM_SPLAT_TILES). */
 typedef struct {
     int32_t chains;  /* 1..8 */
     int32_t group;   /* windows per kernel; 0 = all */
-    int32_t bin;     /* 0: events in their given order; 1: grouped by tile; 2: by row band, stable */
+    int32_t bin;     /* 0: events in their given order; 1: grouped by tile; 2: by row band, stable;
+                        3: grouped by tile, splat and adjoint pushes accumulated per tile in shared memory */
+    int32_t persist; /* 0: the graph of per-phase kernels above; 1..8: one persistent kernel (chains 1,
+                        group 0, bin 0 or 2) whose device work queue staggers the windows by this many phases */
 } cm_batch_schedule;
 int cm_batch_set_schedule(cm_batch* plan, const cm_batch_schedule* schedule);
 int cm_batch_get_schedule(const cm_batch* plan, cm_batch_schedule* schedule);

@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(PKG, "libcm.so")
 
 CM_OK, CM_EINVAL, CM_ENOMEM, CM_EBUSY, CM_ETIMEOUT, CM_ECUDA, CM_ENOTFOUND, CM_ESTATE = range(8)
 CM_REF_END, CM_REF_ALL_EDGES = 0, 1
-CM_SPLAT_AUTO, CM_SPLAT_ATOMIC, CM_SPLAT_SORT = 0, 1, 2
+CM_SPLAT_AUTO, CM_SPLAT_ATOMIC, CM_SPLAT_SORT, CM_SPLAT_TILES = 0, 1, 2, 3
 CM_MAX_BINS = 32
 CM_STATIC_SCRATCH_BYTES = 32 * 1024 * 1024
 
@@ -50,7 +50,8 @@ class cm_window(ctypes.Structure):
 
 
 class cm_batch_schedule(ctypes.Structure):
-    _fields_ = [("chains", ctypes.c_int32), ("group", ctypes.c_int32), ("bin", ctypes.c_int32)]
+    _fields_ = [("chains", ctypes.c_int32), ("group", ctypes.c_int32), ("bin", ctypes.c_int32),
+                ("persist", ctypes.c_int32)]
 
 
 class cm_server_cfg(ctypes.Structure):
@@ -253,21 +254,21 @@ def cm_batch_run(plan: int, stream: int) -> None:
     _check(lib().cm_batch_run(plan, stream), "cm_batch_run")
 
 
-def cm_batch_set_schedule(plan: int, chains: int, group: int, bin: int = 0) -> None:
-    s = cm_batch_schedule(chains, group, bin)
+def cm_batch_set_schedule(plan: int, chains: int, group: int, bin: int = 0, persist: int = 0) -> None:
+    s = cm_batch_schedule(chains, group, bin, persist)
     _check(lib().cm_batch_set_schedule(plan, ctypes.byref(s)), "cm_batch_set_schedule")
 
 
-def cm_batch_get_schedule(plan: int) -> tuple[int, int, int]:
+def cm_batch_get_schedule(plan: int) -> tuple[int, int, int, int]:
     s = cm_batch_schedule()
     _check(lib().cm_batch_get_schedule(plan, ctypes.byref(s)), "cm_batch_get_schedule")
-    return s.chains, s.group, s.bin
+    return s.chains, s.group, s.bin, s.persist
 
 
-def cm_batch_autotune(plan: int, stream: int) -> tuple[int, int, int]:
+def cm_batch_autotune(plan: int, stream: int) -> tuple[int, int, int, int]:
     s = cm_batch_schedule()
     _check(lib().cm_batch_autotune(plan, stream, ctypes.byref(s)), "cm_batch_autotune")
-    return s.chains, s.group, s.bin
+    return s.chains, s.group, s.bin, s.persist
 
 
 def cm_batch_stats(plan: int, window: int) -> tuple[int, int]:

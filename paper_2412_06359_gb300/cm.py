@@ -16,7 +16,8 @@ from . import _capi as C
 
 REF_END = C.CM_REF_END
 REF_ALL = C.CM_REF_ALL_EDGES
-SPLAT_AUTO, SPLAT_ATOMIC, SPLAT_SORT = C.CM_SPLAT_AUTO, C.CM_SPLAT_ATOMIC, C.CM_SPLAT_SORT
+SPLAT_AUTO, SPLAT_ATOMIC, SPLAT_SORT, SPLAT_TILES = (C.CM_SPLAT_AUTO, C.CM_SPLAT_ATOMIC, C.CM_SPLAT_SORT,
+                                                   C.CM_SPLAT_TILES)
 
 
 def _require_cuda(t: torch.Tensor, name: str, dtype=None):
@@ -413,17 +414,20 @@ class BatchPlan:
     def run(self):
         C.cm_batch_run(self.handle, stream_handle(self.buf.device))
 
-    def set_schedule(self, chains: int, group: int, bin: int = 0):
+    def set_schedule(self, chains: int, group: int, bin: int = 0, persist: int = 0):
         """chains: concurrent kernel chains; group: windows per kernel (0: one
         kernel over every window); bin: 1 to group each window's events by
         32x32 pixel tile before the splat, 2 by band of 32 rows keeping the
-        order of 4096-event super-chunks within a band."""
-        C.cm_batch_set_schedule(self.handle, chains, group, bin)
+        order of 4096-event super-chunks within a band, 3 by tile with the
+        splat and the adjoint's pushes accumulated per tile in shared memory;
+        persist > 0: one persistent kernel with a device work queue that
+        staggers the windows by that many phases (chains 1, group 0, bin 0 or 2)."""
+        C.cm_batch_set_schedule(self.handle, chains, group, bin, persist)
 
-    def schedule(self) -> tuple[int, int, int]:
+    def schedule(self) -> tuple[int, int, int, int]:
         return C.cm_batch_get_schedule(self.handle)
 
-    def autotune(self) -> tuple[int, int, int]:
+    def autotune(self) -> tuple[int, int, int, int]:
         """Pick the fastest schedule for these windows (runs the plan several times)."""
         return C.cm_batch_autotune(self.handle, stream_handle(self.buf.device))
 

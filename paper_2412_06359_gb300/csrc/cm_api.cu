@@ -7,6 +7,7 @@
 #include <new>
 
 #include "../../include/cm.h"
+#include "cm_bands.cuh"
 #include "cm_launch.h"
 #include "cm_sort.h"
 
@@ -30,6 +31,16 @@ struct cm_workspace {
     int32_t* nnz_r;
     float* dego_part;
     float2* warp;            // [B+1][max_events] stored trajectory points (store_warps), else nullptr
+    cmk::FQ* fq;             // [H][W] flow quads and
+    cmk::FQ* dq;             // [H][W] quad accumulators of dL/dflow: the plane layout (below), else nullptr
+    int32_t bands;           // > 0: events grouped by band of rows on the plane layout (below)
+    int32_t* band_tab;       // [bands][super-chunks of max_events]
+    int32_t* sync;           // [4] completion counters (zeroed by the first forward)
+    int16_t* gx;             // [max_events] the events grouped by band
+    int16_t* gy;
+    float* gt;
+    int8_t* gp;
+    bool sync_zeroed;
     float* scal;             // [4] device scalars of cm_rsat
     bool has_sort;           // buffers of the deterministic sort path are laid out
     cmk::SortBufs sb;
@@ -38,6 +49,9 @@ struct cm_workspace {
     const void* fwd_events;  // event x pointer of the last forward
     int64_t fwd_n;
     bool fwd_warp;           // the last forward stored its trajectory points in `warp`
+    bool fwd_planes;         // the last forward used the plane layout
+    bool fwd_grouped;        // the last forward grouped its events by band
+    bool dq_dirty;           // the quad accumulators hold a backward's sums (else zero, as the prep pass left them)
 };
 
 namespace cmk {
@@ -97,11 +111,32 @@ int tiles_for(size_t hw, int cap)
 }
 
 struct Layout {
-    size_t iwe, flow, dflow, loss_part, norm, loss_r, nnz_r, dego_part, warp, scal, total;
+    size_t iwe, flow, dflow, loss_part, norm, loss_r, nnz_r, dego_part, warp, scal, fq, dq, total;
+    size_t band_tab, sync, gx, gy, gt, gp;
+    int bands;
     size_t ka, kb, va, vb, pay, hist, part, start;  // sort path (CM_SPLAT_SORT only)
     int R, loss_tiles, pix_tiles;
-    bool sort;
+    bool sort, planes;
 };
+
+// The atomic path of a window with one flow field keeps the batched plan's
+// layout: the images as polarity planes of (C, S) pairs (a splat row's two
+// corners in one 16-byte reduction, the adjoint's gathers in 16-byte loads),
+// the flow as 32-byte quads (one load per bilinear sample) and dL/dflow in
+// per-cell quad accumulators.  cm_warp_splat, the sort path and per-bin flows
+// keep the [R][H][W] float4 images and the flow as given.
+bool plane_layout(const cm_loss_cfg& cfg, int32_t nfb) { return cfg.splat != CM_SPLAT_SORT && nfb == 1; }
+
+// On the plane layout, windows whose images exceed about 3/4 of the 129 MB L2
+// group their events by band of 32 rows first (their time order kept within a
+// band): the events in flight then touch one strip of the images.  Returns the
+// number of bands, or 0.
+int band_count_for(const cm_camera& cam, int R)
+{
+    const size_t img = (size_t)R * cam.width * cam.height * sizeof(float4);
+    const int nb = (cam.height + cmk::kBandRows - 1) / cmk::kBandRows;
+    return img > ((size_t)96 << 20) && nb <= cmk::kMaxBands ? nb : 0;
+}
 
 float eps_of(const cm_loss_cfg& c) { return c.eps > 0.0f ? c.eps : 1e-9f; }
 
@@ -133,6 +168,30 @@ Layout layout(const cm_camera& cam, const cm_loss_cfg& cfg, int32_t nfb, int64_t
     if (cfg.store_warps) off = align_up(off + (size_t)(cfg.nbins + 1) * max_events * sizeof(float2));
     L.scal = off;
     off = align_up(off + 4 * sizeof(float));
+    L.planes = plane_layout(cfg, nfb);
+    L.bands = 0;
+    if (L.planes) {
+        L.fq = off;
+        off = align_up(off + HW * sizeof(cmk::FQ));
+        L.dq = off;
+        off = align_up(off + HW * sizeof(cmk::FQ));
+        L.bands = max_events > 0 ? band_count_for(cam, L.R) : 0;
+        if (L.bands) {
+            const size_t nsc = (size_t)((max_events + cmk::kSuperChunk - 1) / cmk::kSuperChunk);
+            L.band_tab = off;
+            off = align_up(off + (size_t)L.bands * nsc * sizeof(int32_t));
+            L.sync = off;
+            off = align_up(off + 4 * sizeof(int32_t));
+            L.gx = off;
+            off = align_up(off + (size_t)max_events * sizeof(int16_t));
+            L.gy = off;
+            off = align_up(off + (size_t)max_events * sizeof(int16_t));
+            L.gt = off;
+            off = align_up(off + (size_t)max_events * sizeof(float));
+            L.gp = off;
+            off = align_up(off + (size_t)max_events);
+        }
+    }
     L.sort = cfg.splat == CM_SPLAT_SORT;
     if (L.sort) {
         const cmk::SortSizes z = cmk::sort_sizes(max_events, L.R, cfg.nbins, nfb, HW);
@@ -290,6 +349,17 @@ int cm_workspace_create(void* dev_mem, size_t bytes, const cm_camera* cam, const
     ws->dego_part = reinterpret_cast<float*>(b + L.dego_part);
     ws->warp = cfg->store_warps ? reinterpret_cast<float2*>(b + L.warp) : nullptr;
     ws->scal = reinterpret_cast<float*>(b + L.scal);
+    ws->fq = L.planes ? reinterpret_cast<cmk::FQ*>(b + L.fq) : nullptr;
+    ws->dq = L.planes ? reinterpret_cast<cmk::FQ*>(b + L.dq) : nullptr;
+    ws->bands = L.bands;
+    if (L.bands) {
+        ws->band_tab = reinterpret_cast<int32_t*>(b + L.band_tab);
+        ws->sync = reinterpret_cast<int32_t*>(b + L.sync);
+        ws->gx = reinterpret_cast<int16_t*>(b + L.gx);
+        ws->gy = reinterpret_cast<int16_t*>(b + L.gy);
+        ws->gt = reinterpret_cast<float*>(b + L.gt);
+        ws->gp = reinterpret_cast<int8_t*>(b + L.gp);
+    }
     ws->has_sort = L.sort;
     if (L.sort) {
         ws->sb.ka = reinterpret_cast<uint32_t*>(b + L.ka);
@@ -374,6 +444,53 @@ int cm_loss_forward(const cm_camera* cam, const cm_events* ev, const float* flow
     attach_ws(d, ws);
     d.loss = loss_out;
     d.warp = warp_of(ws, *cfg);
+    if (ws->fq && plane_layout(*cfg, n_flow_bins)) {
+        // the plane layout: quads built (from the flow or the motion field) by the prep pass
+        d.iwe_split = 1;
+        d.fq = ws->fq;
+        d.dq = ws->dq;
+        if (depth) {
+            d.rho = inv_depth;
+            d.ego = ego6;
+            d.dt = dt_window;
+        } else {
+            d.flow = reinterpret_cast<const float2*>(flow);
+        }
+        const int sms = cmk::sm_count_current();
+        const bool grouped = ws->bands > 0 && ev->n >= cmk::kSuperChunk;
+        if (grouped) {
+            if (!ws->sync_zeroed) {
+                if ((st = cuda_status(cudaMemsetAsync(ws->sync, 0, 4 * sizeof(int32_t), s)))) return st;
+                ws->sync_zeroed = true;
+            }
+            Win g = d;
+            g.tile_cnt = ws->band_tab;
+            g.sync = ws->sync;
+            g.rx = ws->gx;
+            g.ry = ws->gy;
+            g.rt = ws->gt;
+            g.rp = ws->gp;
+            g.ntx = 1;
+            g.nty = ws->bands;
+            g.band_rows = cmk::kBandRows;
+            if ((st = cuda_status(cmk::launch_bands(g, sms, s)))) return st;
+            d.x = ws->gx;
+            d.y = ws->gy;
+            d.t = ws->gt;
+            d.p = ws->gp;
+        }
+        if ((st = cuda_status(cmk::launch_prep(d, sms, s)))) return st;
+        if ((st = cuda_status(cmk::launch_splat(d, sms, s)))) return st;
+        if ((st = cuda_status(cmk::launch_loss_planes(d, s)))) return st;
+        ws->fwd_mode = depth ? 2 : 1;
+        ws->fwd_events = ev->x;
+        ws->fwd_n = ev->n;
+        ws->fwd_warp = d.warp != nullptr;
+        ws->fwd_planes = true;
+        ws->fwd_grouped = grouped;
+        ws->dq_dirty = false;
+        return CM_OK;
+    }
     if (depth) {
         d.rho = inv_depth;
         d.ego = ego6;
@@ -396,6 +513,7 @@ int cm_loss_forward(const cm_camera* cam, const cm_events* ev, const float* flow
     ws->fwd_events = ev->x;
     ws->fwd_n = ev->n;
     ws->fwd_warp = d.warp != nullptr;
+    ws->fwd_planes = false;
     return CM_OK;
 }
 
@@ -418,6 +536,40 @@ int cm_loss_backward(const cm_camera* cam, const cm_events* ev, const float* flo
     attach_ws(d, ws);
     d.dloss = dloss;
     d.warp = ws->fwd_warp ? ws->warp : nullptr;  // read back whenever the forward stored them
+    if (ws->fwd_planes) {
+        // the plane layout: pushes into the quad accumulators (zeroed by the
+        // forward's prep pass), then folded per pixel
+        d.iwe_split = 1;
+        d.fq = ws->fq;
+        d.dq = ws->dq;
+        d.flow = depth ? nullptr : reinterpret_cast<const float2*>(flow);
+        d.dflow = dflow ? reinterpret_cast<float2*>(dflow) : nullptr;
+        if (ws->fwd_grouped) {  // the forward's grouped copy of the events, in the same order
+            d.x = ws->gx;
+            d.y = ws->gy;
+            d.t = ws->gt;
+            d.p = ws->gp;
+        }
+        if (!depth && !dflow) return CM_OK;
+        if (ws->dq_dirty &&
+            (st = cuda_status(cudaMemsetAsync(ws->dq, 0, (size_t)cam->width * cam->height * sizeof(cmk::FQ), s))))
+            return st;
+        if ((st = cuda_status(cmk::launch_adjoint(d, cmk::sm_count_current(), s)))) return st;
+        ws->dq_dirty = true;
+        if (depth) {
+            if (!dinv_depth && !dego6) {
+                if (d.dflow) return cuda_status(cmk::launch_fold(d, s));
+                return CM_OK;
+            }
+            d.rho = inv_depth;
+            d.ego = ego6;
+            d.dt = dt_window;
+            d.drho = dinv_depth;
+            d.dego = dego6;
+            return cuda_status(cmk::launch_depth_ego(d, s));  // folds the accumulators (and stores dL/dflow)
+        }
+        return cuda_status(cmk::launch_fold(d, s));
+    }
     d.flow = depth ? ws->flow : reinterpret_cast<const float2*>(flow);
     d.dflow = dflow ? reinterpret_cast<float2*>(dflow) : ws->dflow;
     if (!depth && !dflow) return CM_OK;

@@ -27,6 +27,7 @@
 // cm_batch_set_windows rewrites the staging copy and the next cm_batch_run
 // uploads it before the replay.  With group 0 the graph stays valid for any
 // windows that fit the plan; otherwise it is captured again for the new set.
+#include <algorithm>
 #include <climits>
 #include <cmath>
 #include <cstdint>
@@ -35,431 +36,10 @@
 #include <vector>
 
 #include "../../include/cm.h"
+#include "cm_bands.cuh"
+#include "cm_batch_kernels.cuh"
 #include "cm_launch.h"
 
-namespace cmk {
-
-struct BatchHdr {
-    int32_t nwin;
-    int32_t pad;
-    long long total_chunks;  // event chunks of kEventThreads events
-    int32_t total_ltiles;    // loss / gradient tiles (loss_tiles per window)
-    int32_t total_ptiles;    // pixel tiles (pix_tiles per window)
-};
-
-// largest w in [lo, hi) with s[w] <= c (s non-decreasing; empty windows skipped)
-__device__ __forceinline__ int find_ll(const long long* s, int lo, int hi, long long c)
-{
-    hi -= 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (__ldg(s + mid) <= c) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
-
-__device__ __forceinline__ int find_i(const int* s, int lo, int hi, int c)
-{
-    hi -= 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (__ldg(s + mid) <= c) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
-
-__device__ __forceinline__ int clamp_end(const BatchHdr* h, int w1) { return w1 < h->nwin ? w1 : h->nwin; }
-
-// Each kernel covers windows [w0, w1) of the table (clamped to the windows in
-// use).  Pixel passes walk per-window tiles, event passes chunks of 256 events.
-
-__device__ __forceinline__ int tile_of(const Win& d, int x, int y)
-{
-    const int tx = min(max(x, 0), d.W - 1) / kBinTile, ty = min(max(y, 0), d.H - 1) / kBinTile;
-    return ty * d.ntx + tx;
-}
-
-// block-wide exclusive scan (any blockDim multiple of 32 up to 1024); returns
-// the block total through *total
-__device__ __forceinline__ int block_scan_excl(int v, int* total)
-{
-    __shared__ int ws[32];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    int x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) ws[w] = x;
-    __syncthreads();
-    if (w == 0) {
-        int t = lane < nw ? ws[lane] : 0;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, t, o);
-            if (lane >= o) t += y;
-        }
-        ws[lane] = t;
-    }
-    __syncthreads();
-    const int before = (w > 0 ? ws[w - 1] : 0) + x - v;
-    *total = ws[nw - 1];
-    __syncthreads();
-    return before;
-}
-
-// Binning works on super-chunks of kSuperChunk events of one window: a block
-// counts its super-chunk's events per tile in shared memory and touches the
-// global counters once per tile, not once per event.
-constexpr int kSuperChunk = 4096;
-constexpr int kMaxBinTiles = 2048;  // windows with more tiles are not grouped
-constexpr int kBandRows = 32;       // rows per band of the stable band grouping
-constexpr int kMaxBands = 128;      // windows with more bands (H > 4096) are not grouped
-
-__device__ __forceinline__ void count_tiles(const Win& d, long long e0, long long e1, int* hist)
-{
-    const int nt = d.ntx * d.nty;
-    for (int i = threadIdx.x; i < nt; i += blockDim.x) hist[i] = 0;
-    __syncthreads();
-    for (long long k = e0 + threadIdx.x; k < e1; k += blockDim.x) atomicAdd(hist + tile_of(d, d.x[k], d.y[k]), 1);
-    __syncthreads();
-}
-
-__device__ __forceinline__ int band_of(const Win& d, int y) { return min(max(y, 0), d.H - 1) / d.band_rows; }
-
-__device__ __forceinline__ int super_chunks(const Win& d) { return (int)((d.n + kSuperChunk - 1) / kSuperChunk); }
-
-constexpr int kRounds = kSuperChunk / kEventThreads;  // 256-event rounds of a super-chunk
-static_assert(kRounds * kEventThreads == kSuperChunk, "a super-chunk is whole rounds of a block");
-
-// band grouping, pass 1 for super-chunk sc = [e0, e1): its events per band,
-// column sc of the band-major [band][super-chunk] table (warp-aggregated
-// shared-memory counts; the rows of all rounds are loaded first, so the block
-// waits on memory once).  The block completing a window's last super-chunk
-// scans the whole table in band-major order: entry (b, sc) becomes the first
-// slot of super-chunk sc's events of band b, so the bands keep the order of
-// the super-chunks.
-__device__ __forceinline__ void band_count(const Win& d, int sc, long long e0, long long e1, int* hist)
-{
-    const int nb = d.nty, nsc = super_chunks(d), lane = threadIdx.x & 31;
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) hist[i] = 0;
-    int16_t yr[kRounds];
-#pragma unroll
-    for (int r = 0; r < kRounds; ++r) {
-        const long long k = e0 + r * kEventThreads + threadIdx.x;
-        yr[r] = k < e1 ? d.y[k] : (int16_t)0;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < kRounds; ++r) {
-        const long long k = e0 + r * kEventThreads + threadIdx.x;
-        const int b = k < e1 ? band_of(d, yr[r]) : -1;
-        const unsigned peers = __match_any_sync(0xffffffffu, b);
-        if (b >= 0 && lane == __ffs(peers) - 1) atomicAdd(hist + b, __popc(peers));
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) d.tile_cnt[(size_t)i * nsc + sc] = hist[i];
-    if (last_tile_done(d.sync + 2, nsc)) {
-        const int total = nb * nsc;
-        int carry = 0;
-        for (int base = 0; base < total; base += blockDim.x) {
-            const int i = base + threadIdx.x;
-            const int v = i < total ? __ldcg(d.tile_cnt + i) : 0;  // other blocks' columns, from L2
-            int tot = 0;
-            const int ex = block_scan_excl(v, &tot);
-            if (i < total) d.tile_cnt[i] = carry + ex;
-            carry += tot;
-        }
-        __syncthreads();
-    }
-}
-
-// band grouping, pass 2 for super-chunk sc: its events (all rounds loaded
-// first) go to the slots of their band that the count pass reserved for this
-// super-chunk, so the bands keep the order of the super-chunks; within one
-// super-chunk's share of a band (4096 consecutive events, a small part of the
-// window's time span) a warp takes a run of slots per band through one
-// shared-memory atomic (lanes in order), the warps and rounds in any order
-__device__ __forceinline__ void band_scatter(const Win& d, int sc, long long e0, long long e1)
-{
-    __shared__ int cur[kMaxBands];
-    const int nb = d.nty, nsc = super_chunks(d), lane = threadIdx.x & 31;
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) cur[i] = d.tile_cnt[(size_t)i * nsc + sc];
-    int16_t xr[kRounds], yr[kRounds];
-    float tr[kRounds];
-    int8_t pr[kRounds];
-#pragma unroll
-    for (int r = 0; r < kRounds; ++r) {
-        const long long k = e0 + r * kEventThreads + threadIdx.x;
-        const bool ok = k < e1;
-        xr[r] = ok ? d.x[k] : (int16_t)0;
-        yr[r] = ok ? d.y[k] : (int16_t)0;
-        tr[r] = ok ? __ldg(d.t + k) : 0.0f;
-        pr[r] = ok ? d.p[k] : (int8_t)0;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < kRounds; ++r) {
-        const long long k = e0 + r * kEventThreads + threadIdx.x;
-        const bool ok = k < e1;
-        const int b = ok ? band_of(d, yr[r]) : -1;
-        const unsigned peers = __match_any_sync(0xffffffffu, b);
-        const int leader = __ffs(peers) - 1;
-        int first = 0;
-        if (ok && lane == leader) first = atomicAdd(cur + b, __popc(peers));
-        first = __shfl_sync(0xffffffffu, first, leader);
-        if (ok) {
-            const int pos = first + __popc(peers & ((1u << lane) - 1u));
-            d.rx[pos] = xr[r];
-            d.ry[pos] = yr[r];
-            d.rt[pos] = tr[r];
-            d.rp[pos] = pr[r];
-        }
-    }
-    __syncthreads();
-}
-
-// zero the images of warped events and the quad accumulators of dL/dflow,
-// build the flow quads (the motion field for depth input), reset the
-// completion counters.  With `bands`, the blocks first run pass 1 of the band
-// grouping (the count per band and super-chunk); it needs no zeroed state (the
-// table's columns are written whole and its completion counter returns to zero
-// when the last block has scanned the table), so it is not reset here.
-__global__ void __launch_bounds__(kEventThreads) k_prep_batch(const BatchHdr* h, const Win* tab, const int* pstart,
-                                                              const long long* sstart, int bands, int w0, int w1)
-{
-    __shared__ int hist[kMaxBands];
-    w1 = clamp_end(h, w1);
-    if (w0 >= w1) return;
-    if (bands) {
-        const long long cb = sstart[w0], ce = sstart[w1];
-        for (long long c = cb + blockIdx.x; c < ce; c += gridDim.x) {
-            const int w = find_ll(sstart, w0, w1, c);
-            const Win d = tab[w];
-            if (!d.tile_cnt || !d.band_rows) continue;
-            const long long e0 = (c - sstart[w]) * kSuperChunk;
-            const long long e1 = e0 + kSuperChunk < d.n ? e0 + kSuperChunk : d.n;
-            band_count(d, (int)(c - sstart[w]), e0, e1, hist);
-        }
-    }
-    const int tb = pstart[w0], te = pstart[w1];
-    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int tile = tb + blockIdx.x; tile < te; tile += gridDim.x) {
-        const int w = find_i(pstart, w0, w1, tile);
-        const Win d = tab[w];
-        const int ti = tile - pstart[w];
-        if (ti == 0 && threadIdx.x < (d.band_rows ? 2 : 3)) d.sync[threadIdx.x] = 0;
-        const size_t HW = plane_size(d);
-        const size_t stride = (size_t)d.pix_tiles * blockDim.x;
-        // the window's images as one flat run of 32-byte chunks (the slab is 32-byte aligned)
-        const size_t nf4 = (size_t)d.R * HW, n32 = nf4 / 2;
-        for (size_t c = (size_t)ti * blockDim.x + threadIdx.x; c < n32; c += stride) st_v8(d.iwe + 2 * c, z4, z4);
-        if ((nf4 & 1) && ti == 0 && threadIdx.x == 0) d.iwe[nf4 - 1] = z4;
-        for (size_t i = (size_t)ti * blockDim.x + threadIdx.x; i < HW; i += stride) {
-            st_v8(d.dq + i, z4, z4);
-            int u, v;
-            pixel_uv(i, d.W, u, v);
-            build_quad(d, u, v);
-        }
-        if (d.tile_cnt && !d.band_rows) {
-            const int nt = d.ntx * d.nty;
-            for (int i = ti * blockDim.x + threadIdx.x; i <= nt; i += (int)stride) {
-                d.tile_cnt[i] = 0;
-                if (i < nt) d.tile_cur[i] = 0;
-            }
-        }
-    }
-}
-
-// binning, pass 1: events per tile (or per band and super-chunk); the block
-// finishing a window's last super-chunk turns the counts into tile starts and
-// the cursors (or into stable band offsets)
-__global__ void __launch_bounds__(kEventThreads) k_bin_count_batch(const BatchHdr* h, const Win* tab,
-                                                                    const long long* sstart, int w0, int w1)
-{
-    __shared__ int hist[kMaxBinTiles];
-    w1 = clamp_end(h, w1);
-    if (w0 >= w1) return;
-    const long long cb = sstart[w0], ce = sstart[w1];
-    for (long long c = cb + blockIdx.x; c < ce; c += gridDim.x) {
-        const int w = find_ll(sstart, w0, w1, c);
-        const Win d = tab[w];
-        if (!d.tile_cnt) continue;
-        const long long e0 = (c - sstart[w]) * kSuperChunk;
-        const long long e1 = e0 + kSuperChunk < d.n ? e0 + kSuperChunk : d.n;
-        if (d.band_rows) {
-            band_count(d, (int)(c - sstart[w]), e0, e1, hist);
-            continue;
-        }
-        count_tiles(d, e0, e1, hist);
-        const int nt0 = d.ntx * d.nty;
-        for (int i = threadIdx.x; i < nt0; i += blockDim.x)
-            if (hist[i]) atomicAdd(d.tile_cnt + i, hist[i]);
-        const int chunks = (int)((d.n + kSuperChunk - 1) / kSuperChunk);
-        if (last_tile_done(d.sync + 2, chunks)) {
-            const int nt = d.ntx * d.nty;
-            int carry = 0;
-            for (int base = 0; base < nt; base += blockDim.x) {
-                const int i = base + threadIdx.x;
-                const int v = i < nt ? d.tile_cnt[i] : 0;
-                int tot = 0;
-                const int ex = block_scan_excl(v, &tot);
-                if (i < nt) {
-                    d.tile_cnt[i] = carry + ex;
-                    d.tile_cur[i] = carry + ex;
-                }
-                carry += tot;
-            }
-            if (threadIdx.x == 0) d.tile_cnt[nt] = carry;
-            __syncthreads();
-        }
-    }
-}
-
-// binning, pass 2: a block reserves, per tile, one range of slots for its
-// super-chunk's events (one global atomic per tile) and places them there (or
-// places them at their stable band slots)
-__global__ void __launch_bounds__(kEventThreads) k_bin_scatter_batch(const BatchHdr* h, const Win* tab,
-                                                                      const long long* sstart, int w0, int w1)
-{
-    __shared__ int hist[kMaxBinTiles];
-    w1 = clamp_end(h, w1);
-    if (w0 >= w1) return;
-    const long long cb = sstart[w0], ce = sstart[w1];
-    for (long long c = cb + blockIdx.x; c < ce; c += gridDim.x) {
-        const int w = find_ll(sstart, w0, w1, c);
-        const Win d = tab[w];
-        if (!d.tile_cnt) continue;
-        const long long e0 = (c - sstart[w]) * kSuperChunk;
-        const long long e1 = e0 + kSuperChunk < d.n ? e0 + kSuperChunk : d.n;
-        if (d.band_rows) {
-            band_scatter(d, (int)(c - sstart[w]), e0, e1);
-            continue;
-        }
-        count_tiles(d, e0, e1, hist);
-        const int nt = d.ntx * d.nty;
-        for (int i = threadIdx.x; i < nt; i += blockDim.x)
-            if (hist[i]) hist[i] = atomicAdd(d.tile_cur + i, hist[i]);  // the block's first slot in tile i
-        __syncthreads();
-        for (long long k = e0 + threadIdx.x; k < e1; k += blockDim.x) {
-            const int16_t x = d.x[k], y = d.y[k];
-            const int pos = atomicAdd(hist + tile_of(d, x, y), 1);
-            d.rx[pos] = x;
-            d.ry[pos] = y;
-            d.rt[pos] = __ldg(d.t + k);
-            d.rp[pos] = d.p[k];
-        }
-        __syncthreads();
-    }
-}
-
-// events of a grouped window are read in tile order
-__device__ __forceinline__ void use_grouped(Win& d)
-{
-    if (d.tile_cnt) {
-        d.x = d.rx;
-        d.y = d.ry;
-        d.t = d.rt;
-        d.p = d.rp;
-    }
-}
-
-// the event kernels keep their trajectory points in shared memory up to 20
-// bins (the static 48 KB a block may declare), in registers beyond
-template <int MAXB>
-constexpr bool kPointsSmem = MAXB <= 20;
-
-template <int MAXB>
-__global__ void __launch_bounds__(kEventThreads, MAXB <= 10 ? 4 : 2) k_splat_batch(const BatchHdr* h, const Win* tab,
-                                                                const long long* cstart, int w0, int w1)
-{
-    __shared__ float pts[kPointsSmem<MAXB> ? 2 * (MAXB + 1) * kEventThreads : 1];
-    w1 = clamp_end(h, w1);
-    if (w0 >= w1) return;
-    const long long cb = cstart[w0], ce = cstart[w1];
-    for (long long c = cb + blockIdx.x; c < ce; c += gridDim.x) {
-        const int w = find_ll(cstart, w0, w1, c);
-        Win d = tab[w];
-        use_grouped(d);
-        const long long k = (c - cstart[w]) * kEventThreads + threadIdx.x;
-        if (k >= d.n) continue;
-        if (kPointsSmem<MAXB>) splat_event_smem<MAXB>(d, k, pts);
-        else splat_event<MAXB>(d, k);
-    }
-}
-
-template <int MAXB>
-__global__ void __launch_bounds__(kEventThreads, MAXB <= 10 ? 4 : 2) k_adjoint_batch(const BatchHdr* h, const Win* tab,
-                                                                  const long long* cstart, int w0, int w1)
-{
-    __shared__ float pts[kPointsSmem<MAXB> ? 2 * (MAXB + 1) * kEventThreads : 1];
-    w1 = clamp_end(h, w1);
-    if (w0 >= w1) return;
-    const long long cb = cstart[w0], ce = cstart[w1];
-    for (long long c = cb + blockIdx.x; c < ce; c += gridDim.x) {
-        const int w = find_ll(cstart, w0, w1, c);
-        Win d = tab[w];
-        use_grouped(d);
-        const long long k = (c - cstart[w]) * kEventThreads + threadIdx.x;
-        if (k >= d.n) continue;
-        // polarity-plane images
-        if (kPointsSmem<MAXB>) adjoint_event_smem<MAXB, RedSink, true>(d, k, __ldg(d.dloss), pts);
-        else adjoint_event<MAXB, RedSink, true>(d, k, __ldg(d.dloss));
-    }
-}
-
-// loss pass 1 per tile; the block completing a window's last tile runs pass 2
-__global__ void __launch_bounds__(256) k_loss_batch(const BatchHdr* h, const Win* tab, const int* lstart, int w0,
-                                                    int w1)
-{
-    w1 = clamp_end(h, w1);
-    if (w0 >= w1) return;
-    const int tb = lstart[w0], te = lstart[w1];
-    for (int tile = tb + blockIdx.x; tile < te; tile += gridDim.x) {
-        const int w = find_i(lstart, w0, w1, tile);
-        const Win d = tab[w];
-        const int ti = tile - lstart[w];
-        if (d.iwe_split) {
-            if (plane_size(d) & 1)
-                loss_tile_planes<false>(d, ti, d.loss_tiles);
-            else
-                loss_tile_planes<true>(d, ti, d.loss_tiles);
-        } else {
-            for (int r = 0; r < d.R; ++r) loss_tile(d, r, ti, d.loss_tiles, d.loss_part + (size_t)r * d.loss_tiles + ti);
-        }
-        if (last_tile_done(d.sync + 0, d.loss_tiles)) loss_final_window(d);
-    }
-}
-
-// dL/dflow folded from the quad accumulators, and the depth / ego gradient per
-// tile (the loss pass's tiles); the block completing a window's last tile
-// reduces the six ego sums
-__global__ void __launch_bounds__(256, 3) k_grad_batch(const BatchHdr* h, const Win* tab, const int* lstart, int w0,
-                                                    int w1)
-{
-    w1 = clamp_end(h, w1);
-    if (w0 >= w1) return;
-    const int tb = lstart[w0], te = lstart[w1];
-    for (int tile = tb + blockIdx.x; tile < te; tile += gridDim.x) {
-        const int w = find_i(lstart, w0, w1, tile);
-        const Win d = tab[w];
-        if (!d.rho) {
-            if (d.dq) fold_tile(d, tile - lstart[w], d.loss_tiles);  // flow input: dL/dflow only
-            continue;
-        }
-        depth_ego_tile(d, tile - lstart[w], d.loss_tiles);
-        if (last_tile_done(d.sync + 1, d.loss_tiles)) {
-            __syncthreads();
-            depth_ego_final_window(d, d.loss_tiles);
-        }
-    }
-}
-
-
-}  // namespace cmk
 
 static_assert(cmk::kMaxRefs >= CM_MAX_BINS + 1, "per-reference shared arrays hold every reference");
 
@@ -468,14 +48,32 @@ using cmk::Win;
 
 namespace {
 
-constexpr int kPhases = 7;
-const char* const kPhaseName[kPhases] = {"k_prep_batch",  "k_bin_count_batch", "k_bin_scatter_batch",
-                                         "k_splat_batch", "k_loss_batch",      "k_adjoint_batch",
-                                         "k_grad_batch"};
+constexpr int kPhases = 9;
+const char* const kPhaseName[kPhases + 1] = {"k_prep_batch",        "k_bin_count_batch", "k_bin_scatter_batch",
+                                             "k_splat_batch",       "k_loss_batch",      "k_adjoint_batch",
+                                             "k_grad_batch",        "k_splat_tiles_batch",
+                                             "k_adjoint_tiles_batch", "k_step_persistent"};
+constexpr int kPersistentPhase = kPhases;  // the name of the persistent step's node
+constexpr int kMaxPersist = 8;             // largest stagger of the persistent step's queue
+// the order of the phases in a window group's chain (the tile phases run with bin 3 only)
+constexpr int kPhaseOrder[kPhases] = {0, 1, 2, 3, 7, 4, 5, 8, 6};
 constexpr int kSyncInts = 4;  // per window: loss, gradient and binning counters (one spare)
 constexpr int kMaxChains = 8;
 
 size_t up256(size_t v) { return (v + 255) / 256 * 256; }
+
+// the persistent step's queue head, error word and per-window counters
+size_t pq_bytes(int cap) { return (2 + (size_t)cap * cmk::kPCounters) * sizeof(int32_t); }
+
+// dynamic shared memory of the tile kernels: the splat's images of the tile
+// for min(R, kTileRefs) references, the adjoint's cell records
+size_t tiles_smem(const cm_loss_cfg& cfg, int which)
+{
+    const int R = cfg.ref_mode == CM_REF_END ? 1 : cfg.nbins + 1;
+    const int rt = R < cmk::kTileRefs ? R : cmk::kTileRefs;
+    constexpr size_t T2 = (size_t)cmk::kSmemTile * cmk::kSmemTile;
+    return which == 0 ? (size_t)rt * 2 * T2 * sizeof(float2) : T2 * sizeof(cmk::FQ);
+}
 
 int tiles_for(size_t hw, size_t px_per_tile, int cap)
 {
@@ -519,7 +117,7 @@ bool cfg_ok(const cm_loss_cfg* cfg)
 {
     if (!cfg || cfg->nbins < 1 || cfg->nbins > CM_MAX_BINS) return false;
     if (cfg->ref_mode != CM_REF_END && cfg->ref_mode != CM_REF_ALL_EDGES) return false;
-    if (cfg->splat != CM_SPLAT_AUTO && cfg->splat != CM_SPLAT_ATOMIC) return false;
+    if (cfg->splat != CM_SPLAT_AUTO && cfg->splat != CM_SPLAT_ATOMIC && cfg->splat != CM_SPLAT_TILES) return false;
     return (cfg->store_warps == 0 || cfg->store_warps == 1) && std::isfinite(cfg->eps);
 }
 
@@ -549,10 +147,11 @@ Need need_of(const cm_window* wins, int32_t nwin, const cm_loss_cfg& cfg)
 // and the grouped events
 size_t bin_bytes(int W, int H, int64_t n)
 {
-    const size_t nt = (size_t)((W + cmk::kBinTile - 1) / cmk::kBinTile) * ((H + cmk::kBinTile - 1) / cmk::kBinTile);
+    // the smaller tiles of bin 3 are the most (their table also holds the work items)
+    const size_t nt = (size_t)((W + cmk::kSmemTile - 1) / cmk::kSmemTile) * ((H + cmk::kSmemTile - 1) / cmk::kSmemTile);
     const size_t nband = (size_t)((H + cmk::kBandRows - 1) / cmk::kBandRows) *
                          (size_t)((n + cmk::kSuperChunk - 1) / cmk::kSuperChunk);
-    const size_t table = 2 * nt + 1 > nband ? 2 * nt + 1 : nband;
+    const size_t table = 3 * nt + 2 > nband ? 3 * nt + 2 : nband;
     return up256(table * sizeof(int32_t)) + 2 * up256(2 * (size_t)n) + up256(4 * (size_t)n) + up256((size_t)n);
 }
 
@@ -590,7 +189,8 @@ WinScratch win_scratch(size_t HW, int R)
 }
 
 struct Layout {
-    size_t hdr, tab, cstart, sstart, lstart, pstart, table_end;  // the uploaded region [0, table_end)
+    size_t hdr, tab, cstart, sstart, lstart, pstart, pseg, table_end;  // the uploaded region [0, table_end)
+    size_t pq;  // persistent step: queue head, error word, [windows][kPCounters] counters (zeroed per run)
     size_t iwe, flow, dflow, quad, part, norm, lr, nnz, dego, sync, bins, warp, total;
 };
 
@@ -610,7 +210,11 @@ Layout layout_of(int cap, const Need& n)
     o += (size_t)(cap + 1) * sizeof(int);
     L.pstart = o;
     o += (size_t)(cap + 1) * sizeof(int);
+    L.pseg = o = (o + 15) / 16 * 16;
+    o += (size_t)cap * 7 * sizeof(cmk::PSeg);
     L.table_end = o = up256(o);
+    L.pq = o;
+    o = up256(o + pq_bytes(cap));
     L.iwe = o;
     o = up256(o + n.iwe);
     L.dflow = o;
@@ -668,7 +272,7 @@ struct cm_batch {
     std::vector<const float*> stat_lr; // per window: device L_r and N_nz of the last run
     std::vector<const int32_t*> stat_nnz;
     std::vector<cm_window> last;       // the windows of the last staging (re-staged when grouping changes)
-    int grid_events = 0, grid_tiles = 0;
+    int grid_events = 0, grid_tiles = 0, grid_tiles_smem = 0, grid_persist = 0;
     cm_batch_schedule sched{2, 1, 0};
     bool stale = true;                 // the graph must be (re)captured before the next replay
     cudaStream_t streams[kMaxChains] = {};
@@ -683,6 +287,111 @@ struct cm_batch {
 namespace {
 
 // fill the staging copy of the table for these windows; checks the capacities
+std::vector<Group> make_groups(const cm_batch* b);
+
+// The persistent step's queue: for every window its phases in order (prep,
+// the band count and scatter when its events are grouped by band, splat,
+// loss, adjoint, gradient), each a segment of work items; the segments of all
+// windows sorted by (window x stagger + phase rank, window), so window w + 1's
+// first phase comes `stagger` phases after window w's and a window's phases
+// keep their order (every dependency is queued before its dependants).
+void build_queue(int stagger, const Win* tab, int nwin, cmk::PSeg* seg, BatchHdr* h)
+{
+    struct Key {
+        long long key;
+        int w, phase, count;
+    };
+    std::vector<Key> keys;
+    for (int w = 0; w < nwin; ++w) {
+        const Win& d = tab[w];
+        const bool grouped = d.tile_cnt && d.band_rows;
+        const int chunks = (int)((d.n + cmk::kEventThreads - 1) / cmk::kEventThreads);
+        const int nsc = (int)((d.n + cmk::kSuperChunk - 1) / cmk::kSuperChunk);
+        const int order[7] = {cmk::kPPrep, cmk::kPBandCount, cmk::kPBandScatter, cmk::kPSplat,
+                              cmk::kPLoss, cmk::kPAdjoint,   cmk::kPGrad};
+        int rank = 0;
+        for (int ph : order) {
+            if (!grouped && (ph == cmk::kPBandCount || ph == cmk::kPBandScatter)) continue;
+            int count = 0;
+            switch (ph) {
+            case cmk::kPPrep: count = d.pix_tiles; break;
+            case cmk::kPBandCount:
+            case cmk::kPBandScatter: count = nsc; break;
+            case cmk::kPSplat:
+            case cmk::kPAdjoint: count = chunks; break;
+            default: count = d.loss_tiles; break;
+            }
+            if (count > 0) keys.push_back({(long long)w * stagger + rank, w, ph, count});
+            ++rank;
+        }
+    }
+    std::stable_sort(keys.begin(), keys.end(), [](const Key& a, const Key& b) {
+        return a.key != b.key ? a.key < b.key : a.w < b.w;
+    });
+    int start = 0;
+    for (size_t i = 0; i < keys.size(); ++i) {
+        seg[i] = cmk::PSeg{keys[i].w, keys[i].phase, start, keys[i].count};
+        start += keys[i].count;
+    }
+    h->p_nseg = (int)keys.size();
+    h->p_total = start;
+}
+
+// Image and quad slabs shared along a chain: the groups of one chain run one
+// after another, so the windows at the same position of its groups can use
+// one slab (the next group's prep pass zeroes it after the previous group's
+// gradient pass has read it).  Fewer slabs in flight keep the images in L2
+// between the passes, and no window's images need to reach DRAM once another
+// reuses them.  With group 0 every window is in flight: no sharing.
+// slot[i]: the slab of window i; slab offsets of the images and quads.
+struct Slabs {
+    std::vector<int> slot;
+    std::vector<size_t> iwe_off, quad_off;
+};
+
+Slabs share_slabs(const cm_batch* b, const cm_window* wins, int32_t nwin, int R)
+{
+    Slabs sl;
+    sl.slot.assign(nwin, -1);
+    std::vector<size_t> iwe_sz, quad_sz;
+    if (b->sched.group > 0) {
+        std::vector<std::vector<int>> chain_slots(kMaxChains);
+        for (const Group& g : make_groups(b)) {
+            std::vector<int>& cs = chain_slots[g.chain];
+            for (int i = g.w0; i < g.w1; ++i) {
+                if (wins[i].scratch) continue;
+                const int p = i - g.w0;
+                while ((int)cs.size() <= p) {
+                    cs.push_back((int)iwe_sz.size());
+                    iwe_sz.push_back(0);
+                    quad_sz.push_back(0);
+                }
+                const int k = cs[p];
+                const size_t HW = (size_t)wins[i].cam.width * wins[i].cam.height;
+                iwe_sz[k] = std::max(iwe_sz[k], up256((size_t)R * HW * sizeof(float4)));
+                quad_sz[k] = std::max(quad_sz[k], 2 * HW * sizeof(cmk::FQ));
+                sl.slot[i] = k;
+            }
+        }
+    } else {
+        for (int i = 0; i < nwin; ++i) {
+            if (wins[i].scratch) continue;
+            const size_t HW = (size_t)wins[i].cam.width * wins[i].cam.height;
+            sl.slot[i] = (int)iwe_sz.size();
+            iwe_sz.push_back(up256((size_t)R * HW * sizeof(float4)));
+            quad_sz.push_back(2 * HW * sizeof(cmk::FQ));
+        }
+    }
+    size_t oi = 0, oq = 0;
+    for (size_t k = 0; k < iwe_sz.size(); ++k) {
+        sl.iwe_off.push_back(oi);
+        sl.quad_off.push_back(oq);
+        oi += iwe_sz[k];
+        oq += quad_sz[k];
+    }
+    return sl;
+}
+
 int stage_windows(cm_batch* b, const cm_window* wins, int32_t nwin)
 {
     if (nwin < 1 || nwin > b->cap) return CM_EINVAL;
@@ -704,12 +413,25 @@ int stage_windows(cm_batch* b, const cm_window* wins, int32_t nwin)
     long long supers = 0;
     int* ls = reinterpret_cast<int*>(s + b->L.lstart);
     int* ps = reinterpret_cast<int*>(s + b->L.pstart);
+
     const int R = refs_of(b->cfg);
     const float eps = b->cfg.eps > 0.0f ? b->cfg.eps : 1e-9f;
-    size_t o_warp = 0, o_iwe = 0, o_dflow = 0, o_quad = 0, o_part = 0, o_stat = 0, o_dego = 0, o_bins = 0;
+    size_t o_warp = 0, o_dflow = 0, o_part = 0, o_stat = 0, o_dego = 0, o_bins = 0;
     long long chunks = 0;
     int lt_total = 0, pt_total = 0;
     char* base = b->base;
+    // the per-window work counts first: the groups (and so the shared slabs) depend on them
+    b->nwin = nwin;
+    b->chunks.assign(nwin, 0);
+    b->ltiles.assign(nwin, 0);
+    b->ptiles.assign(nwin, 0);
+    for (int i = 0; i < nwin; ++i) {
+        const size_t HW = (size_t)wins[i].cam.width * wins[i].cam.height;
+        b->chunks[i] = (wins[i].ev.n + cmk::kEventThreads - 1) / cmk::kEventThreads;
+        b->ltiles[i] = loss_tiles_for(HW);
+        b->ptiles[i] = pix_tiles_for(HW);
+    }
+    const Slabs slabs = share_slabs(b, wins, nwin, R);
     b->chunks.assign(nwin, 0);
     b->ltiles.assign(nwin, 0);
     b->ptiles.assign(nwin, 0);
@@ -759,8 +481,7 @@ int stage_windows(cm_batch* b, const cm_window* wins, int32_t nwin)
             d.dego_part = reinterpret_cast<float*>(sc + ws.dego);
             d.sync = reinterpret_cast<int32_t*>(sc + ws.sync);
         } else {
-            d.iwe = reinterpret_cast<float4*>(base + b->L.iwe + o_iwe);
-            o_iwe += up256((size_t)R * HW * sizeof(float4));
+            d.iwe = reinterpret_cast<float4*>(base + b->L.iwe + slabs.iwe_off[slabs.slot[i]]);
             d.flow = reinterpret_cast<const float2*>(w.flow);  // nullptr for depth input (the quads hold its flow)
             if (w.dflow) {
                 d.dflow = reinterpret_cast<float2*>(w.dflow);
@@ -774,10 +495,8 @@ int stage_windows(cm_batch* b, const cm_window* wins, int32_t nwin)
                 d.warp = reinterpret_cast<float2*>(base + b->L.warp + o_warp);
                 o_warp += up256((size_t)(d.B + 1) * d.n * sizeof(float2));
             }
-            d.fq = reinterpret_cast<const cmk::FQ*>(base + b->L.quad + o_quad);
-            o_quad += HW * sizeof(cmk::FQ);
-            d.dq = reinterpret_cast<cmk::FQ*>(base + b->L.quad + o_quad);
-            o_quad += HW * sizeof(cmk::FQ);
+            d.fq = reinterpret_cast<const cmk::FQ*>(base + b->L.quad + slabs.quad_off[slabs.slot[i]]);
+            d.dq = reinterpret_cast<cmk::FQ*>(base + b->L.quad + slabs.quad_off[slabs.slot[i]] + HW * sizeof(cmk::FQ));
             d.loss_part = reinterpret_cast<float2*>(base + b->L.part + o_part);
             o_part += (size_t)R * d.loss_tiles * sizeof(float2);
             d.norm = reinterpret_cast<float*>(base + b->L.norm) + o_stat;
@@ -791,8 +510,9 @@ int stage_windows(cm_batch* b, const cm_window* wins, int32_t nwin)
             // order (bin 2), while the plan's grouping memory lasts
             const size_t bb = bin_bytes(d.W, d.H, d.n);
             const bool bands = b->sched.bin == 2;
-            const int tx = bands ? 1 : (d.W + cmk::kBinTile - 1) / cmk::kBinTile;
-            const int ty = bands ? (d.H + cmk::kBandRows - 1) / cmk::kBandRows : (d.H + cmk::kBinTile - 1) / cmk::kBinTile;
+            const int tp = b->sched.bin == 3 ? cmk::kSmemTile : cmk::kBinTile;
+            const int tx = bands ? 1 : (d.W + tp - 1) / tp;
+            const int ty = bands ? (d.H + cmk::kBandRows - 1) / cmk::kBandRows : (d.H + tp - 1) / tp;
             const bool fits = bands ? ty <= cmk::kMaxBands : tx * ty <= cmk::kMaxBinTiles;
             if (b->sched.bin && d.n > 0 && fits && o_bins + bb <= b->capn.bins) {
                 char* q = base + b->L.bins + o_bins;
@@ -800,11 +520,14 @@ int stage_windows(cm_batch* b, const cm_window* wins, int32_t nwin)
                 d.ntx = tx;
                 d.nty = ty;
                 d.band_rows = bands ? cmk::kBandRows : 0;
+                d.smem_tiles = b->sched.bin == 3 ? 1 : 0;
+                d.tile_px = tp;
                 const size_t nt = (size_t)d.ntx * d.nty;
                 d.tile_cnt = reinterpret_cast<int32_t*>(q);
                 d.tile_cur = bands ? nullptr : d.tile_cnt + nt + 1;
                 const size_t nband = (size_t)ty * ((d.n + cmk::kSuperChunk - 1) / cmk::kSuperChunk);
-                const size_t table = 2 * nt + 1 > nband ? 2 * nt + 1 : nband;
+                const size_t table = 3 * nt + 2 > nband ? 3 * nt + 2 : nband;
+                d.item_start = bands ? nullptr : d.tile_cnt + 2 * nt + 1;
                 q += up256(table * sizeof(int32_t));
                 d.rx = reinterpret_cast<int16_t*>(q);
                 q += up256(2 * (size_t)d.n);
@@ -830,6 +553,7 @@ int stage_windows(cm_batch* b, const cm_window* wins, int32_t nwin)
         supers += (w.ev.n + cmk::kSuperChunk - 1) / cmk::kSuperChunk;
         ls[i] = lt_total;
         ps[i] = pt_total;
+
         b->chunks[i] = (w.ev.n + cmk::kEventThreads - 1) / cmk::kEventThreads;
         b->ltiles[i] = d.loss_tiles;
         b->ptiles[i] = d.pix_tiles;
@@ -841,14 +565,17 @@ int stage_windows(cm_batch* b, const cm_window* wins, int32_t nwin)
     ss[nwin] = supers;
     ls[nwin] = lt_total;
     ps[nwin] = pt_total;
+
     h->nwin = nwin;
     h->total_chunks = chunks;
     h->total_ltiles = lt_total;
     h->total_ptiles = pt_total;
+    if (b->sched.persist > 0) build_queue(b->sched.persist, tab, nwin, reinterpret_cast<cmk::PSeg*>(s + b->L.pseg), h);
     b->nwin = nwin;
     if (b->last.data() != wins) b->last.assign(wins, wins + nwin);
     b->dirty = true;
     if (b->sched.group > 0) b->stale = true;  // the graph's window groups depend on the windows
+    // (the persistent step reads its queue's size from the uploaded header: its graph stays valid)
     return CM_OK;
 }
 
@@ -901,6 +628,45 @@ void enqueue_event_kernel(cm_batch* b, cudaStream_t s, int which, int grid, int 
         cmk::k_splat_batch<MAXB><<<grid, cmk::kEventThreads, 0, s>>>(h, tab, cs, w0, w1);
     else
         cmk::k_adjoint_batch<MAXB><<<grid, cmk::kEventThreads, 0, s>>>(h, tab, cs, w0, w1);
+}
+
+template <int MAXB>
+void enqueue_tiles_kernel(cm_batch* b, cudaStream_t s, int which, int grid, int w0, int w1)
+{
+    const BatchHdr* h = reinterpret_cast<const BatchHdr*>(b->base + b->L.hdr);
+    const Win* tab = reinterpret_cast<const Win*>(b->base + b->L.tab);
+    if (which == 0)
+        cmk::k_splat_tiles_batch<MAXB><<<grid, cmk::kTileThreads, tiles_smem(b->cfg, 0), s>>>(h, tab, w0, w1);
+    else
+        cmk::k_adjoint_tiles_batch<MAXB><<<grid, cmk::kTileThreads, tiles_smem(b->cfg, 1), s>>>(h, tab, w0, w1);
+}
+
+void enqueue_tiles(cm_batch* b, cudaStream_t s, int which, int grid, int w0, int w1)
+{
+    const int B = b->cfg.nbins;
+    if (B <= 1) enqueue_tiles_kernel<1>(b, s, which, grid, w0, w1);
+    else if (B <= 10) enqueue_tiles_kernel<10>(b, s, which, grid, w0, w1);
+    else if (B <= 20) enqueue_tiles_kernel<20>(b, s, which, grid, w0, w1);
+    else enqueue_tiles_kernel<32>(b, s, which, grid, w0, w1);
+}
+
+template <int MAXB>
+void enqueue_persistent_kernel(cm_batch* b, cudaStream_t s)
+{
+    const BatchHdr* h = reinterpret_cast<const BatchHdr*>(b->base + b->L.hdr);
+    const Win* tab = reinterpret_cast<const Win*>(b->base + b->L.tab);
+    const cmk::PSeg* seg = reinterpret_cast<const cmk::PSeg*>(b->base + b->L.pseg);
+    int* q = reinterpret_cast<int*>(b->base + b->L.pq);
+    cmk::k_step_persistent<MAXB><<<b->grid_persist, cmk::kEventThreads, 0, s>>>(h, tab, seg, q, q + 2);
+}
+
+void enqueue_persistent(cm_batch* b, cudaStream_t s)
+{
+    const int B = b->cfg.nbins;
+    if (B <= 1) enqueue_persistent_kernel<1>(b, s);
+    else if (B <= 10) enqueue_persistent_kernel<10>(b, s);
+    else if (B <= 20) enqueue_persistent_kernel<20>(b, s);
+    else enqueue_persistent_kernel<32>(b, s);
 }
 
 void enqueue_event(cm_batch* b, cudaStream_t s, int which, int grid, int w0, int w1)
@@ -956,11 +722,26 @@ int capture(cm_batch* b)
         for (int c = 1; c < chains; ++c) ok = ok && cudaStreamWaitEvent(b->streams[c], b->fork, 0) == cudaSuccess;
     }
     const bool wide = b->sched.group <= 0;
+    if (b->sched.persist > 0) {
+        // the persistent step: zero the queue and the counters, then one kernel
+        ProfNode p{kPersistentPhase, nullptr, nullptr, nullptr, nullptr};
+        ok = cudaEventCreate(&p.ea) == cudaSuccess && cudaEventCreate(&p.eb) == cudaSuccess;
+        if (ok) {
+            b->prof.push_back(p);
+            ok = cudaMemsetAsync(b->base + b->L.pq, 0, pq_bytes(b->cap), s0) == cudaSuccess;
+            cudaEventRecordWithFlags(p.ea, s0, cudaEventRecordExternal);
+            enqueue_persistent(b, s0);
+            cudaEventRecordWithFlags(p.eb, s0, cudaEventRecordExternal);
+        }
+    }
     for (const Group& g : groups) {
+        if (b->sched.persist > 0) break;
         cudaStream_t s = b->streams[g.chain];
-        for (int ph = 0; ph < kPhases && ok; ++ph) {
+        for (int pi = 0; pi < kPhases && ok; ++pi) {
+            const int ph = kPhaseOrder[pi];
             if (!b->sched.bin && (ph == 1 || ph == 2)) continue;  // no grouping kernels
             if (b->sched.bin == 2 && ph == 1) continue;             // the band count runs inside the prep pass
+            if (b->sched.bin != 3 && (ph == 7 || ph == 8)) continue;  // shared-memory tiles with bin 3 only
             ProfNode p{ph, nullptr, nullptr, nullptr, nullptr};
             ok = cudaEventCreate(&p.ea) == cudaSuccess && cudaEventCreate(&p.eb) == cudaSuccess;
             if (!ok) break;
@@ -981,6 +762,8 @@ int capture(cm_batch* b)
             case 4: cmk::k_loss_batch<<<gl, 256, 0, s>>>(h, tab, ls, g.w0, g.w1); break;
             case 5: enqueue_event(b, s, 1, ge, g.w0, g.w1); break;
             case 6: cmk::k_grad_batch<<<gl, 256, 0, s>>>(h, tab, ls, g.w0, g.w1); break;
+            case 7: enqueue_tiles(b, s, 0, b->grid_tiles_smem, g.w0, g.w1); break;
+            case 8: enqueue_tiles(b, s, 1, b->grid_tiles_smem, g.w0, g.w1); break;
             }
             cudaEventRecordWithFlags(p.eb, s, cudaEventRecordExternal);
         }
@@ -1033,6 +816,24 @@ void destroy_batch(cm_batch* b)
     }
     if (b->staging) cudaFreeHost(b->staging);
     delete b;
+}
+
+// the tile kernels take more than the default 48 KB of dynamic shared memory
+template <int MAXB>
+bool allow_tiles_smem(const cm_loss_cfg& cfg)
+{
+    return cudaFuncSetAttribute(cmk::k_splat_tiles_batch<MAXB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)tiles_smem(cfg, 0)) == cudaSuccess &&
+           cudaFuncSetAttribute(cmk::k_adjoint_tiles_batch<MAXB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)tiles_smem(cfg, 1)) == cudaSuccess;
+}
+
+template <int MAXB>
+int occupancy_persistent()
+{
+    int a = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, cmk::k_step_persistent<MAXB>, cmk::kEventThreads, 0);
+    return a < 1 ? 1 : a;
 }
 
 template <int MAXB>
@@ -1145,6 +946,7 @@ int cm_batch_create(void* dev_mem, size_t bytes, const cm_window* wins, int32_t 
     b->capn = n;
     b->L = L;
     b->sched = nwin > 1 ? cm_batch_schedule{2, 1, 0} : cm_batch_schedule{1, 0, 0};
+    if (cfg->splat == CM_SPLAT_TILES) b->sched.bin = 3;  // the shared-memory tile strategy
     int st = CM_OK;
     if (cudaMallocHost(reinterpret_cast<void**>(&b->staging), L.table_end) != cudaSuccess) st = CM_ENOMEM;
     if (!st && cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming) != cudaSuccess) st = CM_ECUDA;
@@ -1158,11 +960,25 @@ int cm_batch_create(void* dev_mem, size_t bytes, const cm_window* wins, int32_t 
         else occ = occupancy_blocks<32>();
         b->grid_events = sms * occ;
         b->grid_tiles = sms * 4;
+        b->grid_tiles_smem = sms;  // one tile block (512 threads, up to 192 KB) per SM
+        int occp = 1;
+        if (B <= 1) occp = occupancy_persistent<1>();
+        else if (B <= 10) occp = occupancy_persistent<10>();
+        else if (B <= 20) occp = occupancy_persistent<20>();
+        else occp = occupancy_persistent<32>();
+        b->grid_persist = sms * occp;
+        bool tiles_ok = false;
+        if (B <= 1) tiles_ok = allow_tiles_smem<1>(*cfg);
+        else if (B <= 10) tiles_ok = allow_tiles_smem<10>(*cfg);
+        else if (B <= 20) tiles_ok = allow_tiles_smem<20>(*cfg);
+        else tiles_ok = allow_tiles_smem<32>(*cfg);
+        if (!tiles_ok) st = CM_ECUDA;
         st = stage_windows(b, wins, nwin);
     }
     // the completion counters start at zero (the prep kernel also resets them)
     if (!st && cudaMemset(b->base + L.sync, 0, (size_t)nwin * kSyncInts * sizeof(int32_t)) != cudaSuccess)
         st = CM_ECUDA;
+    if (!st && cudaMemset(b->base + L.pq, 0, pq_bytes(nwin)) != cudaSuccess) st = CM_ECUDA;
     if (st) {
         destroy_batch(b);
         return st;
@@ -1178,14 +994,13 @@ int cm_batch_set_windows(cm_batch* b, const cm_window* wins, int32_t nwin)
 }
 
 namespace {
-// take schedule `s`; a change of grouping re-stages the current windows, since
-// the binning buffers are assigned per window when the table is filled
+// take schedule `s` and re-stage the current windows: the binning buffers and
+// the slabs shared along a chain are assigned per window when the table is filled
 int apply_schedule(cm_batch* b, const cm_batch_schedule& s)
 {
-    const bool rebin = s.bin != b->sched.bin;
     b->sched = s;
     b->stale = true;
-    if (rebin && b->nwin > 0) {
+    if (b->nwin > 0) {
         const std::vector<cm_window> w = b->last;
         return stage_windows(b, w.data(), (int32_t)w.size());
     }
@@ -1197,7 +1012,10 @@ int cm_batch_set_schedule(cm_batch* b, const cm_batch_schedule* s)
 {
     if (!b || !s || s->chains < 1 || s->chains > kMaxChains || s->group < 0) return CM_EINVAL;
     if (s->group == 0 && s->chains != 1) return CM_EINVAL;
-    if (s->bin < 0 || s->bin > 2) return CM_EINVAL;
+    if (s->bin < 0 || s->bin > 3) return CM_EINVAL;
+    if (s->persist < 0 || s->persist > kMaxPersist) return CM_EINVAL;
+    // the persistent step: one kernel over every window, events in their order or grouped by band
+    if (s->persist > 0 && (s->chains != 1 || s->group != 0 || (s->bin != 0 && s->bin != 2))) return CM_EINVAL;
     return apply_schedule(b, *s);
 }
 
@@ -1228,11 +1046,13 @@ int cm_batch_autotune(cm_batch* b, void* stream, cm_batch_schedule* chosen)
         }
     }
     std::vector<cm_batch_schedule> cand;
-    for (int bin = 0; bin < 3; ++bin)
+    for (int bin = 0; bin < 4; ++bin)
         for (const auto& cg : {std::pair<int, int>{1, 0}, {1, 1}, {2, 1}, {3, 1}, {4, 1}, {2, 2}, {4, 2}, {6, 1},
                                {6, 2}, {8, 1}, {8, 2}})
-            cand.push_back(cm_batch_schedule{cg.first, cg.second, bin});
-    if (b->nwin == 1) cand = {{1, 0, 0}, {1, 0, 1}, {1, 0, 2}};
+            cand.push_back(cm_batch_schedule{cg.first, cg.second, bin, 0});
+    if (b->nwin == 1) cand = {{1, 0, 0, 0}, {1, 0, 1, 0}, {1, 0, 2, 0}, {1, 0, 3, 0}};
+    for (int bin : {0, 2})  // the persistent step, its queue staggered by 1, 2, 3 or 7 phases
+        for (int k : {1, 2, 3, 7}) cand.push_back(cm_batch_schedule{1, 0, bin, k});
     cudaEvent_t a = nullptr, z = nullptr;
     if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&z) != cudaSuccess) return CM_ECUDA;
     float best = 1e30f;

@@ -93,9 +93,14 @@ struct Win {
     int8_t* rp;
     int32_t ntx, nty;        // tiles per row and per column (bands: 1 and the number of bands)
     int32_t band_rows;       // 0: 32x32 tiles; else rows per band (stable grouping by band)
+    int32_t smem_tiles;      // 1: the window's events are splatted and pushed by the shared-memory tile
+                             // kernels (grouped by kSmemTile tiles), not by the per-chunk ones
+    int32_t tile_px;         // side of the grouping tiles (kBinTile or kSmemTile)
+    int32_t* item_start;     // smem_tiles: [ntiles + 1] first work item of each tile, the total last
 };
 
-constexpr int kBinTile = 32;  // px, side of the tiles events are grouped by
+constexpr int kBinTile = 32;   // px, side of the tiles events are grouped by (schedule bin 1)
+constexpr int kSmemTile = 32;  // px, side of the tiles of the shared-memory strategy (schedule bin 3)
 constexpr int kMaxRefs = 33;  // references of a window at most (B + 1), for per-reference shared arrays
 
 __device__ __forceinline__ size_t plane_size(const Win& d) { return (size_t)d.W * (size_t)d.H; }
@@ -200,19 +205,31 @@ __device__ __forceinline__ Bil bil_frac(float ax, float ay)
     return s;
 }
 
+// Loads of data that other blocks of the same kernel may write while it runs
+// (the persistent step kernel of the batched plan, NC = false) go through L2
+// (ld.global.cg); loads of data fixed for the kernel's lifetime may take the
+// non-coherent read-only path (NC = true, __ldg).
+template <bool NC, class T>
+__device__ __forceinline__ T ld_in(const T* p)
+{
+    if constexpr (NC) return __ldg(p);
+    else return __ldcg(p);
+}
+
 // The four flow values around a cell (corner indices clamped to the image).
 struct Quad {
     float2 u00, u10, u01, u11;
 };
 
+template <bool NC = true>
 __device__ __forceinline__ Quad load_quad(const float2* __restrict__ U, int W, int H, const Bil& s)
 {
     const int ix1 = min(s.ix + 1, W - 1), iy1 = min(s.iy + 1, H - 1);
     Quad q;
-    q.u00 = __ldg(U + (size_t)s.iy * W + s.ix);
-    q.u10 = __ldg(U + (size_t)s.iy * W + ix1);
-    q.u01 = __ldg(U + (size_t)iy1 * W + s.ix);
-    q.u11 = __ldg(U + (size_t)iy1 * W + ix1);
+    q.u00 = ld_in<NC>(U + (size_t)s.iy * W + s.ix);
+    q.u10 = ld_in<NC>(U + (size_t)s.iy * W + ix1);
+    q.u01 = ld_in<NC>(U + (size_t)iy1 * W + s.ix);
+    q.u11 = ld_in<NC>(U + (size_t)iy1 * W + ix1);
     return q;
 }
 
@@ -260,25 +277,35 @@ struct EventAt {
     float tau;
 };
 
+template <bool NC = true>
 __device__ __forceinline__ bool load_event(const Win& d, int64_t k, EventAt& e)
 {
-    e.xk = d.x[k];
-    e.yk = d.y[k];
+    e.xk = NC ? d.x[k] : __ldcg(d.x + k);
+    e.yk = NC ? d.y[k] : __ldcg(d.y + k);
     if ((unsigned)e.xk >= (unsigned)d.W || (unsigned)e.yk >= (unsigned)d.H) return false;
-    e.tau = tau_of(__ldg(d.t + k), d.t0, d.span);
+    e.tau = tau_of(ld_in<NC>(d.t + k), d.t0, d.span);
     e.b = bin_of(e.tau, d.B);
-    e.pol2 = d.p[k] > 0 ? 0 : 2;
+    e.pol2 = (NC ? d.p[k] : __ldcg(d.p + k)) > 0 ? 0 : 2;
     return true;
 }
 
-// one 32-byte load of a flow quad (read-only for the kernel's lifetime)
+// one 32-byte load of a flow quad (NC: read-only for the kernel's lifetime;
+// else through L2, for quads built by another block of the same kernel)
+template <bool NC = true>
 __device__ __forceinline__ Quad load_fq(const FQ* p)
 {
     Quad q;
-    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-        : "=f"(q.u00.x), "=f"(q.u00.y), "=f"(q.u10.x), "=f"(q.u10.y), "=f"(q.u01.x), "=f"(q.u01.y), "=f"(q.u11.x),
-          "=f"(q.u11.y)
-        : "l"(p));
+    if constexpr (NC) {
+        asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+            : "=f"(q.u00.x), "=f"(q.u00.y), "=f"(q.u10.x), "=f"(q.u10.y), "=f"(q.u01.x), "=f"(q.u01.y),
+              "=f"(q.u11.x), "=f"(q.u11.y)
+            : "l"(p));
+    } else {
+        asm volatile("ld.global.cg.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                     : "=f"(q.u00.x), "=f"(q.u00.y), "=f"(q.u10.x), "=f"(q.u10.y), "=f"(q.u01.x), "=f"(q.u01.y),
+                       "=f"(q.u11.x), "=f"(q.u11.y)
+                     : "l"(p));
+    }
     return q;
 }
 
@@ -288,27 +315,29 @@ __device__ __forceinline__ size_t cell_index(const Win& d, int j, int x, int y)
 }
 
 // the four flow values around a cell of field j: one quad load, else four gathers
+template <bool NC = true>
 __device__ __forceinline__ Quad quad_at(const Win& d, int j, const Bil& s)
 {
-    if (d.fq) return load_fq(d.fq + cell_index(d, j, s.ix, s.iy));
-    return load_quad(field(d, j), d.W, d.H, s);
+    if (d.fq) return load_fq<NC>(d.fq + cell_index(d, j, s.ix, s.iy));
+    return load_quad<NC>(field(d, j), d.W, d.H, s);
 }
 
+template <bool NC = true>
 __device__ __forceinline__ float2 flow_at_pixel(const Win& d, int j, int x, int y)
 {
-    if (d.fq) return __ldg(reinterpret_cast<const float2*>(d.fq + cell_index(d, j, x, y)));
-    return __ldg(field(d, j) + (size_t)y * d.W + x);
+    if (d.fq) return ld_in<NC>(reinterpret_cast<const float2*>(d.fq + cell_index(d, j, x, y)));
+    return ld_in<NC>(field(d, j) + (size_t)y * d.W + x);
 }
 
 // S2 + S3: the trajectory of one event through all computed edges (forward
 // chain b+1..B; with all edges as references also the backward chain b..0)
 // and the global mask.  Returns false when any computed point leaves the image.
-template <int MAXB, class TR>
+template <int MAXB, bool NC = true, class TR>
 __device__ __forceinline__ bool trajectory(const Win& d, const EventAt& e, TR& P)
 {
     const int W = d.W, H = d.H, B = d.B, b = e.b, xk = e.xk, yk = e.yk;
     const float h = __fdiv_rn(1.0f, (float)B);
-    const float2 u0 = flow_at_pixel(d, b, xk, yk);
+    const float2 u0 = flow_at_pixel<NC>(d, b, xk, yk);
     bool ok = true;
     const float dtf = __fsub_rn(edge_tau(b + 1, B), e.tau);
 #pragma unroll
@@ -319,7 +348,7 @@ __device__ __forceinline__ bool trajectory(const Win& d, const EventAt& e, TR& P
                 P.y(j) = __fmul_rn(dtf, u0.y);
             } else if (ok) {
                 const Bil s = bil(xk, yk, P.x(j - 1), P.y(j - 1));
-                const float2 u = interp(s, quad_at(d, j - 1, s));
+                const float2 u = interp(s, quad_at<NC>(d, j - 1, s));
                 P.x(j) = __fmaf_rn(h, u.x, P.x(j - 1));
                 P.y(j) = __fmaf_rn(h, u.y, P.y(j - 1));
             } else {
@@ -341,7 +370,7 @@ __device__ __forceinline__ bool trajectory(const Win& d, const EventAt& e, TR& P
                     P.y(j) = __fmul_rn(-dtb, u0.y);
                 } else if (ok) {
                     const Bil s = bil(xk, yk, P.x(j + 1), P.y(j + 1));
-                    const float2 u = interp(s, quad_at(d, j, s));
+                    const float2 u = interp(s, quad_at<NC>(d, j, s));
                     P.x(j) = __fmaf_rn(-h, u.x, P.x(j + 1));
                     P.y(j) = __fmaf_rn(-h, u.y, P.y(j + 1));
                 } else {
@@ -518,14 +547,14 @@ __device__ __forceinline__ void store_traj(const Win& d, const EventAt& e, TR& P
         if (computed_edge(d, j, e.b)) d.warp[(size_t)j * d.n + k] = make_float2(P.x(j), P.y(j));
 }
 
-template <int MAXB, class TR>
+template <int MAXB, bool NC = true, class TR>
 __device__ __forceinline__ bool load_traj(const Win& d, const EventAt& e, TR& P, int64_t k)
 {
     bool ok = true;
 #pragma unroll
     for (int j = 0; j <= MAXB; ++j) {
         if (computed_edge(d, j, e.b)) {
-            const float2 q = __ldg(d.warp + (size_t)j * d.n + k);
+            const float2 q = ld_in<NC>(d.warp + (size_t)j * d.n + k);
             P.x(j) = q.x;
             P.y(j) = q.y;
             ok = ok && inside(e.xk, e.yk, q.x, q.y, d.W, d.H);
@@ -538,12 +567,12 @@ __device__ __forceinline__ bool load_traj(const Win& d, const EventAt& e, TR& P,
     return ok;
 }
 
-template <int MAXB, class Sink, class TR>
+template <int MAXB, bool NC = true, class Sink, class TR>
 __device__ __forceinline__ void splat_points(const Win& d, int64_t k, const Sink& sink, TR& P)
 {
     EventAt e;
-    if (!load_event(d, k, e)) return;
-    const bool ok = trajectory<MAXB>(d, e, P);
+    if (!load_event<NC>(d, k, e)) return;
+    const bool ok = trajectory<MAXB, NC>(d, e, P);
     if (d.warp) store_traj<MAXB>(d, e, P, k);
     if (!ok) return;
     if (d.ref_mode == kRefAll) {
@@ -564,13 +593,13 @@ __device__ __forceinline__ void splat_event(const Win& d, int64_t k, const Sink&
 
 // the same with the points in shared memory: smem is the block's
 // [2][MAXB + 1][kEventThreads] float array
-template <int MAXB, class Sink = RedSink>
+template <int MAXB, bool NC = true, class Sink = RedSink>
 __device__ __forceinline__ void splat_event_smem(const Win& d, int64_t k, float* smem, const Sink& sink = Sink())
 {
     SmemTraj<MAXB> P;
     P.xs = smem + threadIdx.x;
     P.ys = smem + (MAXB + 1) * kEventThreads + threadIdx.x;
-    splat_points<MAXB>(d, k, sink, P);
+    splat_points<MAXB, NC>(d, k, sink, P);
 }
 
 // dL/dw_c of one corner from its count and timestamp sum, with the loss
@@ -589,13 +618,14 @@ __device__ __forceinline__ float phi_of(float C, float S, float eps, float kap, 
 // together, so the row costs one L2 latency (a divergent choice between the two
 // forms would serialise them).  The aligned pair never leaves the image: the
 // last float2 of the buffer has an odd index.
+template <bool NC = true>
 __device__ __forceinline__ void phi_row(const float2* img, size_t gi, bool two, float eps, float kap, float tbar,
                                         float& pl, float& pr)
 {
     const bool odd = (gi & 1) != 0;
-    const float4 g = __ldg(reinterpret_cast<const float4*>(img + (gi & ~(size_t)1)));
+    const float4 g = ld_in<NC>(reinterpret_cast<const float4*>(img + (gi & ~(size_t)1)));
     float2 h = make_float2(0.0f, 0.0f);
-    if (two && odd) h = __ldg(img + gi + 1);
+    if (two && odd) h = ld_in<NC>(img + gi + 1);
     const float2 l = odd ? make_float2(g.z, g.w) : make_float2(g.x, g.y);
     const float2 r = odd ? h : make_float2(g.z, g.w);
     pl = phi_of(l.x, l.y, eps, kap, tbar);
@@ -606,12 +636,12 @@ __device__ __forceinline__ void phi_row(const float2* img, size_t gi, bool two, 
 // outside the image have phi = 0.  SPLIT: the image is in the polarity-plane
 // layout (Win::iwe_split == 1), a compile-time choice so that the event kernels
 // carry the code of one layout only.
-template <bool SPLIT>
+template <bool SPLIT, bool NC = true>
 __device__ __forceinline__ float2 ref_adjoint(const Win& d, int r, int j, const Bil& s, float tau, int pol2, float dl)
 {
     const size_t HW = plane_size(d);
     const int W = d.W, H = d.H;
-    const float kap = dl * __ldg(d.norm + r);
+    const float kap = dl * ld_in<NC>(d.norm + r);
     const float tb = tbar_of(j, d.B, tau);
     const float eps = d.eps;
     const size_t i00 = (size_t)s.iy * W + s.ix;
@@ -620,13 +650,13 @@ __device__ __forceinline__ float2 ref_adjoint(const Win& d, int r, int j, const 
     if (SPLIT) {
         const float2* img = reinterpret_cast<const float2*>(d.iwe);
         const size_t gi = (size_t)(2 * r + (pol2 >> 1)) * HW + i00;
-        phi_row(img, gi, inx, eps, kap, tb, p00, p10);
-        phi_row(img, iny ? gi + W : gi, inx, eps, kap, tb, p01, p11);  // unconditional: both rows in flight together
+        phi_row<NC>(img, gi, inx, eps, kap, tb, p00, p10);
+        phi_row<NC>(img, iny ? gi + W : gi, inx, eps, kap, tb, p01, p11);  // unconditional: both rows in flight together
         if (!iny) p01 = p11 = 0.0f;
     } else {
         const float2* G = reinterpret_cast<const float2*>(d.iwe + (size_t)r * HW) + (pol2 >> 1);
         auto at = [&](size_t i) {
-            const float2 g = __ldg(G + 2 * i);
+            const float2 g = ld_in<NC>(G + 2 * i);
             return phi_of(g.x, g.y, eps, kap, tb);
         };
         p00 = at(i00);
@@ -643,11 +673,11 @@ __device__ __forceinline__ float2 ref_adjoint(const Win& d, int r, int j, const 
 // One push of the adjoint back across a step x' = x + hs u(x) sampled at x,
 // in cell s (hs = +h forward chain, -h backward chain): scatter hs w_c lambda
 // into the gradient of field `field` and return lambda + hs J(x)^T lambda.
-template <class Sink>
+template <bool NC = true, class Sink>
 __device__ __forceinline__ float2 push_back(const Win& d, const Sink& sink, int field, int edge, const Bil& s,
                                             float hs, float2 lam, int64_t k)
 {
-    const Quad q = quad_at(d, field, s);
+    const Quad q = quad_at<NC>(d, field, s);
     const float hx = hs * lam.x, hy = hs * lam.y;
     sink.scatter(d, field, edge, s, hx, hy, k);
     const float jxx = s.by * (q.u10.x - q.u00.x) + s.ay * (q.u11.x - q.u01.x);
@@ -666,12 +696,12 @@ __device__ __forceinline__ float2 push_back(const Win& d, const Sink& sink, int 
 // carried back along both chains of pushes, scattering dL/dflow.  The points
 // live in registers (Traj) or, given a block's [2][MAXB + 1][kEventThreads]
 // shared array `smem`, in shared memory (SmemTraj).
-template <int MAXB, bool SPLIT, class Sink, class TR>
+template <int MAXB, bool SPLIT, bool NC = true, class Sink, class TR>
 __device__ __forceinline__ void adjoint_points(const Win& d, int64_t k, float dl, const Sink& sink, TR& P)
 {
     EventAt e;
-    if (!load_event(d, k, e)) return;
-    if (!(d.warp ? load_traj<MAXB>(d, e, P, k) : trajectory<MAXB>(d, e, P))) return;
+    if (!load_event<NC>(d, k, e)) return;
+    if (!(d.warp ? load_traj<MAXB, NC>(d, e, P, k) : trajectory<MAXB, NC>(d, e, P))) return;
     const int B = d.B, b = e.b;
     const float h = __fdiv_rn(1.0f, (float)B);
     const bool all = d.ref_mode == kRefAll;
@@ -682,12 +712,12 @@ __device__ __forceinline__ void adjoint_points(const Win& d, int64_t k, float dl
         if (j <= B && j > b) {
             if (all || j == B) {
                 const float2 a =
-                    ref_adjoint<SPLIT>(d, all ? j : 0, j, bil(e.xk, e.yk, P.x(j), P.y(j)), e.tau, e.pol2, dl);
+                    ref_adjoint<SPLIT, NC>(d, all ? j : 0, j, bil(e.xk, e.yk, P.x(j), P.y(j)), e.tau, e.pol2, dl);
                 lam.x += a.x;
                 lam.y += a.y;
             }
             if (j > b + 1) {
-                lam = push_back(d, sink, j - 1, j, bil(e.xk, e.yk, P.x(j - 1), P.y(j - 1)), h, lam, k);
+                lam = push_back<NC>(d, sink, j - 1, j, bil(e.xk, e.yk, P.x(j - 1), P.y(j - 1)), h, lam, k);
             } else {
                 const float dtf = __fsub_rn(edge_tau(b + 1, B), e.tau);
                 sink.point(d, b, j, e.xk, e.yk, dtf * lam.x, dtf * lam.y, k);
@@ -700,11 +730,11 @@ __device__ __forceinline__ void adjoint_points(const Win& d, int64_t k, float dl
 #pragma unroll
     for (int j = 0; j <= MAXB - 1; ++j) {
         if (j <= b) {
-            const float2 a = ref_adjoint<SPLIT>(d, j, j, bil(e.xk, e.yk, P.x(j), P.y(j)), e.tau, e.pol2, dl);
+            const float2 a = ref_adjoint<SPLIT, NC>(d, j, j, bil(e.xk, e.yk, P.x(j), P.y(j)), e.tau, e.pol2, dl);
             lam.x += a.x;
             lam.y += a.y;
             if (j < b) {
-                lam = push_back(d, sink, j, j, bil(e.xk, e.yk, P.x(j + 1), P.y(j + 1)), -h, lam, k);
+                lam = push_back<NC>(d, sink, j, j, bil(e.xk, e.yk, P.x(j + 1), P.y(j + 1)), -h, lam, k);
             } else {
                 const float dtb = __fsub_rn(e.tau, edge_tau(b, B));
                 sink.point(d, b, j, e.xk, e.yk, -dtb * lam.x, -dtb * lam.y, k);
@@ -722,14 +752,14 @@ __device__ __forceinline__ void adjoint_event(const Win& d, int64_t k, float dl,
 
 // the same with the points in shared memory: smem is the block's
 // [2][MAXB + 1][kEventThreads] float array
-template <int MAXB, class Sink = RedSink, bool SPLIT = false>
+template <int MAXB, class Sink = RedSink, bool SPLIT = false, bool NC = true>
 __device__ __forceinline__ void adjoint_event_smem(const Win& d, int64_t k, float dl, float* smem,
                                                    const Sink& sink = Sink())
 {
     SmemTraj<MAXB> P;
     P.xs = smem + threadIdx.x;
     P.ys = smem + (MAXB + 1) * kEventThreads + threadIdx.x;
-    adjoint_points<MAXB, SPLIT>(d, k, dl, sink, P);
+    adjoint_points<MAXB, SPLIT, NC>(d, k, dl, sink, P);
 }
 
 // warp-level sum (fixed shuffle tree: deterministic)

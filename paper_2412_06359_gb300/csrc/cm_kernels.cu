@@ -1,6 +1,7 @@
 // cm_kernels.cu -- the kernels of one window: flow from depth (S1), warp +
 // splat (S2-S4), loss reduction (S5), adjoint (S6), depth / ego gradient (S7),
 // and their host-side launchers.
+#include "cm_bands.cuh"
 #include "cm_device.cuh"
 #include "cm_launch.h"
 
@@ -11,21 +12,89 @@ namespace cmk {
 __global__ void __launch_bounds__(256) k_flow(Win d) { flow_tile(d, blockIdx.x, gridDim.x); }
 
 // ---------------------------------------------------------------------------
+// the event kernels keep their trajectory points in shared memory up to 20
+// bins (the static 48 KB a block may declare), in registers beyond
+template <int MAXB>
+constexpr bool kPointsInSmem = MAXB <= 20;
+template <int MAXB>
+constexpr int kEventBlocksPerSm = MAXB <= 10 ? 4 : 2;
+
 // S2-S4: one thread per event (grid-stride)
 template <int MAXB>
-__global__ void __launch_bounds__(kEventThreads) k_splat(Win d)
+__global__ void __launch_bounds__(kEventThreads, kEventBlocksPerSm<MAXB>) k_splat(Win d)
 {
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < d.n; k += (int64_t)gridDim.x * blockDim.x)
-        splat_event<MAXB>(d, k);
+    __shared__ float pts[kPointsInSmem<MAXB> ? 2 * (MAXB + 1) * kEventThreads : 1];
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < d.n; k += (int64_t)gridDim.x * blockDim.x) {
+        if (kPointsInSmem<MAXB>) splat_event_smem<MAXB>(d, k, pts);
+        else splat_event<MAXB>(d, k);
+    }
 }
 
-// S6: one thread per event (grid-stride)
-template <int MAXB>
-__global__ void __launch_bounds__(kEventThreads) k_adjoint(Win d)
+// S6: one thread per event (grid-stride).  SPLIT: the images are polarity
+// planes (Win::iwe_split == 1)
+template <int MAXB, bool SPLIT>
+__global__ void __launch_bounds__(kEventThreads, kEventBlocksPerSm<MAXB>) k_adjoint(Win d)
 {
+    __shared__ float pts[kPointsInSmem<MAXB> ? 2 * (MAXB + 1) * kEventThreads : 1];
     const float dl = __ldg(d.dloss);
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < d.n; k += (int64_t)gridDim.x * blockDim.x)
-        adjoint_event<MAXB>(d, k, dl);
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < d.n; k += (int64_t)gridDim.x * blockDim.x) {
+        if (kPointsInSmem<MAXB>) adjoint_event_smem<MAXB, RedSink, SPLIT>(d, k, dl, pts);
+        else adjoint_event<MAXB, RedSink, SPLIT>(d, k, dl);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The plane layout of one window (the batched plan's): zero the polarity
+// planes and the quad accumulators of dL/dflow, build the flow quads (the
+// motion field for depth input).  Grid-stride over 32-byte chunks and pixels.
+__global__ void __launch_bounds__(256) k_prep(Win d)
+{
+    const size_t HW = plane_size(d);
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const size_t nf4 = (size_t)d.R * HW, n32 = nf4 / 2;
+    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n32; c += stride) st_v8(d.iwe + 2 * c, z4, z4);
+    if ((nf4 & 1) && blockIdx.x == 0 && threadIdx.x == 0) d.iwe[nf4 - 1] = z4;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < HW; i += stride) {
+        st_v8(d.dq + i, z4, z4);
+        int u, v;
+        pixel_uv(i, d.W, u, v);
+        build_quad(d, u, v);
+    }
+}
+
+// S5 pass 1 over the polarity planes: a tile is 2048 pixels of every reference
+template <bool PAIRS>
+__global__ void __launch_bounds__(256) k_loss_planes(Win d)
+{
+    loss_tile_planes<PAIRS>(d, blockIdx.x, gridDim.x);
+}
+
+// dL/dflow folded from the quad accumulators (flow input)
+__global__ void __launch_bounds__(256) k_fold(Win d) { fold_tile(d, blockIdx.x, gridDim.x); }
+
+// Band grouping of one window's events (cm_bands.cuh): pass 1 counts every
+// super-chunk's events per band (the block finishing the last super-chunk
+// turns the table into stable offsets), pass 2 places them.
+__global__ void __launch_bounds__(kEventThreads) k_band_count(Win d)
+{
+    __shared__ int hist[kMaxBands];
+    const int nsc = super_chunks(d);
+    for (int sc = blockIdx.x; sc < nsc; sc += gridDim.x) {
+        const long long e0 = (long long)sc * kSuperChunk;
+        const long long e1 = e0 + kSuperChunk < d.n ? e0 + kSuperChunk : d.n;
+        band_count(d, sc, e0, e1, hist);
+    }
+}
+
+__global__ void __launch_bounds__(kEventThreads) k_band_scatter(Win d)
+{
+    const int nsc = super_chunks(d);
+    for (int sc = blockIdx.x; sc < nsc; sc += gridDim.x) {
+        const long long e0 = (long long)sc * kSuperChunk;
+        const long long e1 = e0 + kSuperChunk < d.n ? e0 + kSuperChunk : d.n;
+        band_scatter(d, sc, e0, e1);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -73,15 +142,72 @@ cudaError_t launch_splat(const Win& d, int sm_count, cudaStream_t st)
     return cudaGetLastError();
 }
 
+template <bool SPLIT>
+static void adjoint_for(const Win& d, int g, cudaStream_t st)
+{
+    if (d.B <= 1) k_adjoint<1, SPLIT><<<g, kEventThreads, 0, st>>>(d);
+    else if (d.B <= 10) k_adjoint<10, SPLIT><<<g, kEventThreads, 0, st>>>(d);
+    else if (d.B <= 20) k_adjoint<20, SPLIT><<<g, kEventThreads, 0, st>>>(d);
+    else k_adjoint<32, SPLIT><<<g, kEventThreads, 0, st>>>(d);
+}
+
 cudaError_t launch_adjoint(const Win& d, int sm_count, cudaStream_t st)
 {
     if (d.n == 0) return cudaSuccess;
     const int g = event_grid(d.n, sm_count);
     KernelScope ks("k_adjoint", st);
-    if (d.B <= 1) k_adjoint<1><<<g, kEventThreads, 0, st>>>(d);
-    else if (d.B <= 10) k_adjoint<10><<<g, kEventThreads, 0, st>>>(d);
-    else if (d.B <= 20) k_adjoint<20><<<g, kEventThreads, 0, st>>>(d);
-    else k_adjoint<32><<<g, kEventThreads, 0, st>>>(d);
+    if (d.iwe_split) adjoint_for<true>(d, g, st);
+    else adjoint_for<false>(d, g, st);
+    return cudaGetLastError();
+}
+
+static int pixel_grid(size_t n, int cap)
+{
+    const size_t g = (n + 255) / 256;
+    return (int)(g < 1 ? 1 : (g > (size_t)cap ? cap : g));
+}
+
+cudaError_t launch_prep(const Win& d, int sm_count, cudaStream_t st)
+{
+    KernelScope ks("k_prep", st);
+    k_prep<<<pixel_grid((size_t)d.R * d.W * d.H / 2, sm_count * 8), 256, 0, st>>>(d);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_loss_planes(const Win& d, cudaStream_t st)
+{
+    {
+        KernelScope ks("k_loss_planes", st);
+        if (((size_t)d.W * d.H) & 1) k_loss_planes<false><<<d.loss_tiles, 256, 0, st>>>(d);
+        else k_loss_planes<true><<<d.loss_tiles, 256, 0, st>>>(d);
+    }
+    {
+        KernelScope ks("k_loss_final", st);
+        k_loss_final<<<1, 1024, 0, st>>>(d);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bands(const Win& d, int sm_count, cudaStream_t st)
+{
+    if (d.n == 0) return cudaSuccess;
+    const int nsc = super_chunks(d);
+    const int g = nsc < sm_count * 4 ? nsc : sm_count * 4;
+    {
+        KernelScope ks("k_band_count", st);
+        k_band_count<<<g, kEventThreads, 0, st>>>(d);
+    }
+    {
+        KernelScope ks("k_band_scatter", st);
+        k_band_scatter<<<g, kEventThreads, 0, st>>>(d);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fold(const Win& d, cudaStream_t st)
+{
+    KernelScope ks("k_fold", st);
+    k_fold<<<d.pix_tiles, 256, 0, st>>>(d);
     return cudaGetLastError();
 }
 

@@ -39,11 +39,12 @@ def _batch_result(plan, i, win=None):
 
 
 def batch_runner(B=10, ref_mode=synth.REF_ALL, schedule=None, store_warps=False, want_dflow=False, reps=1,
-                 autotune=False):
+                 autotune=False, splat=None):
     """A runner for check_windows: one batch plan over the windows."""
     def run(wins, eps):
         cm = gpu_lib()
-        plan = cm.BatchPlan(_dev_windows(cm, wins), cm.loss_cfg(B, ref_mode, cm.SPLAT_ATOMIC, eps, store_warps),
+        sp = cm.SPLAT_ATOMIC if splat is None else splat
+        plan = cm.BatchPlan(_dev_windows(cm, wins), cm.loss_cfg(B, ref_mode, sp, eps, store_warps),
                             want_dflow=want_dflow)
         if schedule is not None:
             plan.set_schedule(*schedule)
@@ -173,13 +174,14 @@ def test_batch_profiling_records_every_phase():
 
 
 @pytest.mark.parametrize("chains,group,bin", [(1, 0, 0), (1, 1, 0), (2, 1, 0), (3, 2, 0), (4, 1, 0),
-                                              (1, 0, 1), (2, 1, 1), (3, 2, 1), (1, 0, 2), (2, 1, 2), (4, 2, 2)])
+                                              (1, 0, 1), (2, 1, 1), (3, 2, 1), (1, 0, 2), (2, 1, 2), (4, 2, 2),
+                                              (1, 0, 3), (2, 1, 3), (3, 2, 3)])
 def test_every_schedule_gives_the_same_results(chains, group, bin):
     cm = gpu_lib()
     wins = _mixed_windows(7, 21)
     plan = cm.BatchPlan(_dev_windows(cm, wins), cm.loss_cfg(10, cm.REF_ALL, cm.SPLAT_ATOMIC))
     plan.set_schedule(chains, group, bin)
-    assert plan.schedule() == (chains, group, bin)
+    assert plan.schedule() == (chains, group, bin, 0)
     plan.run()
     plan.run()
     check_windows(wins, batch_runner(schedule=(chains, group, bin), reps=2), full=plan_results(plan, wins))
@@ -189,11 +191,11 @@ def test_autotune_picks_a_schedule_and_stays_correct():
     cm = gpu_lib()
     wins = synth.batch_windows(6)
     plan = cm.BatchPlan(_dev_windows(cm, wins), cm.loss_cfg(10, cm.REF_ALL, cm.SPLAT_ATOMIC))
-    chains, group, bin = plan.autotune()
-    assert 1 <= chains <= 8 and group >= 0 and bin in (0, 1, 2)
-    assert plan.autotune() == (chains, group, bin)  # cached for this shape
+    chains, group, bin, persist = plan.autotune()
+    assert 1 <= chains <= 8 and group >= 0 and bin in (0, 1, 2, 3) and 0 <= persist <= 8
+    assert plan.autotune() == (chains, group, bin, persist)  # cached for this shape
     plan.run()
-    sched = (chains, group, bin)
+    sched = (chains, group, bin, persist)
     check_windows([wins[0], wins[3]], batch_runner(schedule=sched),
                   full=[_batch_result(plan, 0), _batch_result(plan, 3)])
 
@@ -216,7 +218,7 @@ def test_batch_of_motion_consistent_windows_matches_oracle():
     cm = gpu_lib()
     wins = [synth.motion_window(np.random.default_rng(70 + i), 160, 120, 20000 + 15000 * i) for i in range(3)]
     plan = cm.BatchPlan(_dev_windows(cm, wins), cm.loss_cfg(10, cm.REF_ALL, cm.SPLAT_ATOMIC))
-    for sched in ((2, 1, 0), (1, 0, 1), (2, 1, 2)):
+    for sched in ((2, 1, 0), (1, 0, 1), (2, 1, 2), (2, 1, 3)):
         plan.set_schedule(*sched)
         plan.run()
         check_windows(wins, batch_runner(schedule=sched), full=plan_results(plan, wins))
@@ -304,17 +306,19 @@ def test_band_grouping_across_set_windows_and_schedule_changes():
         check_windows(second, batch_runner(schedule=sched), full=plan_results(plan, second), grad=sched == (1, 0, 0))
 
 
-@pytest.mark.parametrize("chains,group,bin", [(0, 1, 0), (9, 1, 0), (2, -1, 0), (2, 0, 0), (1, 1, 3), (1, 1, -1)])
-def test_invalid_schedules_are_refused_and_leave_the_plan_as_it_was(chains, group, bin):
+@pytest.mark.parametrize("chains,group,bin,persist", [(0, 1, 0, 0), (9, 1, 0, 0), (2, -1, 0, 0), (2, 0, 0, 0),
+                                                      (1, 1, 4, 0), (1, 1, -1, 0), (1, 0, 0, 9), (1, 0, 0, -1),
+                                                      (2, 1, 0, 2), (1, 0, 1, 2), (1, 0, 3, 1)])
+def test_invalid_schedules_are_refused_and_leave_the_plan_as_it_was(chains, group, bin, persist):
     from paper_2412_06359_gb300 import _capi as C
     cm = gpu_lib()
     wins = _mixed_windows(3, 61)
     plan = cm.BatchPlan(_dev_windows(cm, wins), cm.loss_cfg(10, cm.REF_ALL, cm.SPLAT_ATOMIC))
     plan.set_schedule(1, 1, 2)
     with pytest.raises(C.CMError) as e:
-        plan.set_schedule(chains, group, bin)
+        plan.set_schedule(chains, group, bin, persist)
     assert e.value.status == C.CM_EINVAL
-    assert plan.schedule() == (1, 1, 2)
+    assert plan.schedule() == (1, 1, 2, 0)
     plan.run()
     check_windows(wins, batch_runner(schedule=(1, 1, 2)), full=plan_results(plan, wins), grad=False)
 
@@ -331,3 +335,68 @@ def test_the_bench_windows_against_the_oracle():
     flagged = check_windows(sub, batch_runner(schedule=(6, 2, 2)))
     assert all(f < 0.005 * w.events.n for f, w in zip(flagged, sub))
     check_windows(sub[:2], batch_runner(autotune=True), grad=False)
+
+
+@pytest.mark.parametrize("B,ref_mode", [(10, synth.REF_ALL), (20, synth.REF_ALL), (5, synth.REF_END),
+                                        (1, synth.REF_END)])
+def test_shared_memory_tiles_strategy(B, ref_mode):
+    # CM_SPLAT_TILES: the plan starts on bin 3 (events grouped by 32x32 tile,
+    # the splat and the adjoint's pushes accumulated per tile in shared memory);
+    # 20 bins have 21 references, of which the first 12 are held in shared
+    # memory and the rest go straight to the images
+    from paper_2412_06359_gb300 import _capi as C
+    cm = gpu_lib()
+    wins = [synth.depth_window(np.random.default_rng(7300 + i), W, H, n, nbins=B, ref_mode=ref_mode)
+            for i, (W, H, n) in enumerate([(120, 90, 6000), (97, 61, 1500), (200, 150, 20000)])]
+    plan = cm.BatchPlan(_dev_windows(cm, wins), cm.loss_cfg(B, ref_mode, cm.SPLAT_TILES))
+    assert plan.schedule()[2] == 3 and plan.schedule()[3] == 0
+    plan.run()
+    check_windows(wins, batch_runner(B=B, ref_mode=ref_mode, splat=cm.SPLAT_TILES),
+                  full=plan_results(plan, wins))
+    # the single-window entry points refuse the strategy
+    cfg = cm.loss_cfg(B, ref_mode, cm.SPLAT_TILES)
+    with pytest.raises(C.CMError) as e:
+        cm.Workspace(wins[0].cam, cfg, 100)
+    assert e.value.status == C.CM_EINVAL
+
+
+def test_shared_memory_tiles_on_the_bench_windows_and_hot_spots():
+    # the 640x480 bench windows (incl. the largest) and motion-consistent windows
+    # (many events per pixel after the warp: the warp-aggregated path) under bin 3
+    cm = gpu_lib()
+    wins = synth.batch_windows(64)
+    sub = [wins[int(np.argmax([w.events.n for w in wins]))], wins[3]]
+    check_windows(sub, batch_runner(schedule=(2, 1, 3)), grad=False)
+    mot = [synth.motion_window(np.random.default_rng(80 + i), 160, 120, 40000) for i in range(2)]
+    check_windows(mot, batch_runner(schedule=(2, 1, 3)))
+
+
+@pytest.mark.parametrize("persist,bin", [(1, 0), (2, 2), (3, 2), (7, 0)])
+def test_persistent_step_matches_the_oracle(persist, bin):
+    # one persistent kernel per run: mixed windows (some empty), replayed, then
+    # new windows through set_windows (the queue's size is read from the
+    # uploaded header, so the graph stays)
+    cm = gpu_lib()
+    wins = _mixed_windows(9, 83)
+    plan = cm.BatchPlan(_dev_windows(cm, wins), cm.loss_cfg(10, cm.REF_ALL, cm.SPLAT_ATOMIC))
+    plan.set_schedule(1, 0, bin, persist)
+    assert plan.schedule() == (1, 0, bin, persist)
+    for _ in range(2):
+        plan.run()
+    check_windows(wins, batch_runner(schedule=(1, 0, bin, persist), reps=2), full=plan_results(plan, wins))
+    second = list(reversed(wins))[:6]
+    plan.set_windows(_dev_windows(cm, second))
+    plan.run()
+    check_windows(second, batch_runner(schedule=(1, 0, bin, persist)), full=plan_results(plan, second), grad=False)
+
+
+def test_persistent_step_on_the_bench_windows_with_stored_warps_and_many_bins():
+    cm = gpu_lib()
+    wins = synth.batch_windows(64)
+    sub = [wins[int(np.argmax([w.events.n for w in wins]))], wins[5], wins[9]]
+    check_windows(sub, batch_runner(schedule=(1, 0, 2, 2)))
+    mixed = _mixed_windows(5, 91)
+    check_windows(mixed, batch_runner(schedule=(1, 0, 2, 3), store_warps=True), grad=False)
+    deep = [synth.depth_window(np.random.default_rng(9400 + i), W, H, n, nbins=20)
+            for i, (W, H, n) in enumerate([(120, 90, 3000), (160, 100, 5000)])]
+    check_windows(deep, batch_runner(B=20, schedule=(1, 0, 2, 2)))

@@ -26,7 +26,7 @@ def test_strict_byte_model():
 
 
 def test_grouping_names_cover_every_schedule_mode():
-    assert len(bench.GROUPING) == 3 and bench.GROUPING[2] == "32-row bands"
+    assert len(bench.GROUPING) == 4 and bench.GROUPING[2] == "32-row bands"
 
 
 def test_oracle_on_every_core_covers_the_windows_once():
