@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--schedule", default="auto",
                     help="batch schedule 'chains,windows_per_kernel,grouping[,persist]' (grouping 0: given order, "
                          "1: 32x32 tiles, 2: 32-row bands, 3: tiles in shared memory; persist k > 0: one persistent "
-                         "kernel staggering the windows by k phases, with 1,0,g; e.g. 6,2,2 or 1,0,2,2), or 'auto'")
+                         "kernel staggering the windows by k - 1 phases, with 1,0,g; e.g. 6,2,2 or 1,0,2,2), or 'auto'")
     ap.add_argument("--events", default="iid", choices=["iid", "motion"],
                     help="iid: the headline workload; motion: motion-consistent events with their true flow "
                          "(flow input, many events per pixel after the warp: the contention stress variant)")
@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--serve-pool", type=int, default=2, help="pre-generated windows per stream")
     ap.add_argument("--serve-lanes", type=int, default=6, help="concurrent lanes of the server")
     ap.add_argument("--serve-batch", type=int, default=8, help="requests per batch of a lane")
+    ap.add_argument("--serve-group", type=int, default=16_000_000,
+                    help="events per lane batch regrouped by 32-row band before the splat (0: given order)")
     return ap.parse_args()
 
 
@@ -576,9 +578,9 @@ def run_ours(args):
         # the graph of per-phase kernels against the persistent step (device work queue)
         sched_cmp = compare_batched_splats(batch, {
             "graph_6x2_bands": (6, 2, 2, 0), "graph_8x2_bands": (8, 2, 2, 0),
-            "persistent_bands_stagger1": (1, 0, 2, 1), "persistent_bands_stagger2": (1, 0, 2, 2),
-            "persistent_bands_stagger3": (1, 0, 2, 3), "persistent_bands_stagger7": (1, 0, 2, 7),
-            "persistent_given_order_stagger2": (1, 0, 0, 2)})
+            "persistent_bands_stagger0": (1, 0, 2, 1), "persistent_bands_stagger1": (1, 0, 2, 2),
+            "persistent_bands_stagger2": (1, 0, 2, 3), "persistent_bands_stagger7": (1, 0, 2, 8),
+            "persistent_given_order_stagger1": (1, 0, 0, 2)})
         batch.plan.set_schedule(*schedule)
 
     # ---- the kernels beside the CM path (discrete flow, geometry loss, event frame) ----
@@ -594,7 +596,7 @@ def run_ours(args):
     # ---- a short serving leg (32 streams, 0.5x and 1x the arrival rate, 3 runs each) ----
     serve = None
     if rank == 0 and world == 1 and not args.no_serve:
-        serve = serve_leg([0.5, 1.0], 2.0, 3, args.serve_lanes, args.serve_batch)
+        serve = serve_leg([0.5, 1.0], 2.0, 3, args.serve_lanes, args.serve_batch, args.serve_group)
 
     # ---- CPU oracle baseline (rank 0 at N = 1 only) ----
     cpu = cpu_all = None
@@ -619,7 +621,8 @@ def run_ours(args):
                      "path": "batched plan replayed from a CUDA graph",
                      "schedule": {"chains": schedule[0], "windows_per_kernel": schedule[1],
                                   "grouping": GROUPING[schedule[2]],
-                                  "persistent": schedule[3] > 0, "stagger": schedule[3]}},
+                                  "persistent": schedule[3] > 0,
+                                  "stagger": schedule[3] - 1 if schedule[3] > 0 else None}},
             "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
             "plain": plain, "splat_compare": splat_cmp, "schedule_compare": sched_cmp, "roofline": roof,
             "roofline_iwe": roof_iwe,
@@ -927,26 +930,37 @@ def serve_replay(srv, pools, arr):
                                                                  "pool_peak")}}
 
 
-def serve_leg(scales, seconds: float, reps: int, lanes: int, batch: int, pool: int = 2):
+def serve_leg(scales, seconds: float, reps: int, lanes: int, batch: int, group: int, pool: int = 2):
     """The serving workload at each rate scale, `reps` runs each (a fresh
     server per run): Mev/s served and p50 / p99 request latency per run, with
-    the p99 spread over the runs."""
+    the p99 spread over the runs.  The lanes group up to `group` events per
+    batch by band; one more run at the last scale keeps the given order."""
     from paper_2412_06359_gb300.serve import Server
     pools = serve_pools(pool)
     out = {"workload": "serve32_mixed_res_poisson100hz", "seconds": seconds, "streams": SERVE_STREAMS,
-           "lanes": lanes, "max_batch": batch, "hbm_budget_gb": 40, "runs": reps, "unit": "Mev/s", "scales": {}}
+           "lanes": lanes, "max_batch": batch, "hbm_budget_gb": 40, "group_events": group, "runs": reps,
+           "unit": "Mev/s", "scales": {}}
+
+    def one(arr, g):
+        srv = Server(40 << 30, max_batch=batch, lanes=lanes, group_events=g)
+        try:
+            return serve_replay(srv, pools, arr)
+        finally:
+            srv.close()
+
+    arr = None
     for scale in scales:
         arr = serve_arrivals(scale, seconds, pool)
-        runs = []
-        for _ in range(reps):
-            srv = Server(40 << 30, max_batch=batch, lanes=lanes)
-            runs.append(serve_replay(srv, pools, arr))
-            srv.close()
+        runs = [one(arr, group) for _ in range(reps)]
         p99 = [r["p99_ms"] for r in runs]
         out["scales"][str(scale)] = {
             "offered_mev_s": runs[0]["offered_mev_s"], "requests": runs[0]["requests"],
             "served_mev_s": [r["throughput"] for r in runs], "p50_ms": [r["p50_ms"] for r in runs],
             "p99_ms": p99, "p99_spread_ms": [min(p99), max(p99)], "mean_batch": [r["mean_batch"] for r in runs]}
+    if arr is not None and group > 0:
+        r = one(arr, 0)
+        out["given_order_last_scale"] = {"served_mev_s": r["throughput"], "p50_ms": r["p50_ms"],
+                                         "p99_ms": r["p99_ms"]}
     return out
 
 
@@ -969,7 +983,7 @@ def run_serve(args):
     budget = 40 << 30
     for scale in [float(x) for x in args.serve_scales.split(",")]:
         arr = serve_arrivals(scale, args.serve_seconds, args.serve_pool)
-        srv = Server(budget, max_batch=args.serve_batch, lanes=args.serve_lanes)
+        srv = Server(budget, max_batch=args.serve_batch, lanes=args.serve_lanes, group_events=args.serve_group)
         batched = serve_replay(srv, pools, arr)
         srv.close()
         plain = None
@@ -983,7 +997,7 @@ def run_serve(args):
                 "config": {"workload": "serve32_mixed_res_poisson100hz", "rate_scale": scale,
                            "seconds": args.serve_seconds, "streams": SERVE_STREAMS,
                            "pool_per_stream": args.serve_pool, "max_batch": args.serve_batch,
-                           "lanes": args.serve_lanes, "hbm_budget_gb": 40},
+                           "lanes": args.serve_lanes, "hbm_budget_gb": 40, "group_events": args.serve_group},
                 "batched": batched, "plain": plain}
         print(json.dumps(line), flush=True)
 

@@ -363,7 +363,8 @@ typedef struct {
     int32_t bin;     /* 0: events in their given order; 1: grouped by tile; 2: by row band, stable;
                         3: grouped by tile, splat and adjoint pushes accumulated per tile in shared memory */
     int32_t persist; /* 0: the graph of per-phase kernels above; 1..8: one persistent kernel (chains 1,
-                        group 0, bin 0 or 2) whose device work queue staggers the windows by this many phases */
+                        group 0, bin 0 or 2) whose device work queue staggers the windows by persist - 1
+                        phases (1: each phase over all windows before the next phase) */
 } cm_batch_schedule;
 int cm_batch_set_schedule(cm_batch* plan, const cm_batch_schedule* schedule);
 int cm_batch_get_schedule(const cm_batch* plan, cm_batch_schedule* schedule);
@@ -401,6 +402,10 @@ typedef struct {
     int32_t ref_mode;   /* CM_REF_END or CM_REF_ALL_EDGES */
     float eps;          /* <= 0: 1e-9 */
     int32_t device;     /* CUDA device ordinal */
+    int64_t group_events; /* events per batch that a lane regroups by 32-row band before the splat
+                             (0: none, the events in their given order).  Each lane reserves about
+                             9 bytes per event for the grouped copy; the windows of a batch are
+                             grouped in order while that lasts, the rest run ungrouped. */
 } cm_server_cfg;
 
 /* One request: a depth + ego-motion window of stream `stream_id`.  All

@@ -57,7 +57,7 @@ class cm_batch_schedule(ctypes.Structure):
 class cm_server_cfg(ctypes.Structure):
     _fields_ = [("hbm_budget", ctypes.c_size_t), ("max_batch", ctypes.c_int32), ("lanes", ctypes.c_int32),
                 ("max_queue", ctypes.c_int32), ("nbins", ctypes.c_int32), ("ref_mode", ctypes.c_int32),
-                ("eps", ctypes.c_float), ("device", ctypes.c_int32)]
+                ("eps", ctypes.c_float), ("device", ctypes.c_int32), ("group_events", ctypes.c_int64)]
 
 
 class cm_request(ctypes.Structure):

@@ -421,7 +421,8 @@ class BatchPlan:
         order of 4096-event super-chunks within a band, 3 by tile with the
         splat and the adjoint's pushes accumulated per tile in shared memory;
         persist > 0: one persistent kernel with a device work queue that
-        staggers the windows by that many phases (chains 1, group 0, bin 0 or 2)."""
+        staggers the windows by persist - 1 phases (chains 1, group 0, bin 0
+        or 2; persist 1 runs each phase over all windows before the next)."""
         C.cm_batch_set_schedule(self.handle, chains, group, bin, persist)
 
     def schedule(self) -> tuple[int, int, int, int]:

@@ -466,6 +466,7 @@ int cm_loss_forward(const cm_camera* cam, const cm_events* ev, const float* flow
             Win g = d;
             g.tile_cnt = ws->band_tab;
             g.sync = ws->sync;
+            g.gsync = ws->sync + 2;
             g.rx = ws->gx;
             g.ry = ws->gy;
             g.rt = ws->gt;

@@ -80,7 +80,7 @@ __device__ __forceinline__ void band_count(const Win& d, int sc, long long e0, l
     }
     __syncthreads();
     for (int i = threadIdx.x; i < nb; i += blockDim.x) d.tile_cnt[(size_t)i * nsc + sc] = hist[i];
-    if (last_tile_done(d.sync + 2, nsc)) {
+    if (last_tile_done(d.gsync, nsc)) {
         const int total = nb * nsc;
         int carry = 0;
         for (int base = 0; base < total; base += blockDim.x) {

@@ -54,7 +54,7 @@ const char* const kPhaseName[kPhases + 1] = {"k_prep_batch",        "k_bin_count
                                              "k_grad_batch",        "k_splat_tiles_batch",
                                              "k_adjoint_tiles_batch", "k_step_persistent"};
 constexpr int kPersistentPhase = kPhases;  // the name of the persistent step's node
-constexpr int kMaxPersist = 8;             // largest stagger of the persistent step's queue
+constexpr int kMaxPersist = 8;             // largest persist value: a queue staggered by 7 phases
 // the order of the phases in a window group's chain (the tile phases run with bin 3 only)
 constexpr int kPhaseOrder[kPhases] = {0, 1, 2, 3, 7, 4, 5, 8, 6};
 constexpr int kSyncInts = 4;  // per window: loss, gradient and binning counters (one spare)
@@ -128,7 +128,9 @@ Need need_of(const cm_window* wins, int32_t nwin, const cm_loss_cfg& cfg)
     Need n{};
     const int R = refs_of(cfg);
     for (int i = 0; i < nwin; ++i) {
-        if (wins[i].scratch) continue;  // the window brings its own buffers
+        // the grouped copy of the events is the plan's, also for a window with its own scratch
+        n.bins += bin_bytes(wins[i].cam.width, wins[i].cam.height, wins[i].ev.n);
+        if (wins[i].scratch) continue;  // the window brings its other buffers
         const size_t HW = (size_t)wins[i].cam.width * wins[i].cam.height;
         n.iwe += up256((size_t)R * HW * sizeof(float4));
         if (!wins[i].dflow && wins[i].flow) n.dflow += HW * sizeof(float2);
@@ -136,7 +138,6 @@ Need need_of(const cm_window* wins, int32_t nwin, const cm_loss_cfg& cfg)
         n.part += (size_t)R * loss_tiles_for(HW) * sizeof(float2);
         n.stat += (size_t)R;
         n.dego += (size_t)loss_tiles_for(HW) * 6 * sizeof(float);
-        n.bins += bin_bytes(wins[i].cam.width, wins[i].cam.height, wins[i].ev.n);
         if (cfg.store_warps) n.warp += up256((size_t)(cfg.nbins + 1) * wins[i].ev.n * sizeof(float2));
     }
     return n;
@@ -293,8 +294,9 @@ std::vector<Group> make_groups(const cm_batch* b);
 // the band count and scatter when its events are grouped by band, splat,
 // loss, adjoint, gradient), each a segment of work items; the segments of all
 // windows sorted by (window x stagger + phase rank, window), so window w + 1's
-// first phase comes `stagger` phases after window w's and a window's phases
-// keep their order (every dependency is queued before its dependants).
+// first phase comes `stagger` phases after window w's (stagger 0: phase by
+// phase over all windows) and a window's phases keep their order (every
+// dependency is queued before its dependants).
 void build_queue(int stagger, const Win* tab, int nwin, cmk::PSeg* seg, BatchHdr* h)
 {
     struct Key {
@@ -506,37 +508,39 @@ int stage_windows(cm_batch* b, const cm_window* wins, int32_t nwin)
             d.dego_part = reinterpret_cast<float*>(base + b->L.dego + o_dego);
             o_dego += (size_t)d.loss_tiles * 6 * sizeof(float);
             d.sync = reinterpret_cast<int32_t*>(base + b->L.sync) + kSyncInts * i;
-            // events grouped by 32x32 tile (bin 1) or by 32-row band in their given
-            // order (bin 2), while the plan's grouping memory lasts
-            const size_t bb = bin_bytes(d.W, d.H, d.n);
-            const bool bands = b->sched.bin == 2;
-            const int tp = b->sched.bin == 3 ? cmk::kSmemTile : cmk::kBinTile;
-            const int tx = bands ? 1 : (d.W + tp - 1) / tp;
-            const int ty = bands ? (d.H + cmk::kBandRows - 1) / cmk::kBandRows : (d.H + tp - 1) / tp;
-            const bool fits = bands ? ty <= cmk::kMaxBands : tx * ty <= cmk::kMaxBinTiles;
-            if (b->sched.bin && d.n > 0 && fits && o_bins + bb <= b->capn.bins) {
-                char* q = base + b->L.bins + o_bins;
-                o_bins += bb;
-                d.ntx = tx;
-                d.nty = ty;
-                d.band_rows = bands ? cmk::kBandRows : 0;
-                d.smem_tiles = b->sched.bin == 3 ? 1 : 0;
-                d.tile_px = tp;
-                const size_t nt = (size_t)d.ntx * d.nty;
-                d.tile_cnt = reinterpret_cast<int32_t*>(q);
-                d.tile_cur = bands ? nullptr : d.tile_cnt + nt + 1;
-                const size_t nband = (size_t)ty * ((d.n + cmk::kSuperChunk - 1) / cmk::kSuperChunk);
-                const size_t table = 3 * nt + 2 > nband ? 3 * nt + 2 : nband;
-                d.item_start = bands ? nullptr : d.tile_cnt + 2 * nt + 1;
-                q += up256(table * sizeof(int32_t));
-                d.rx = reinterpret_cast<int16_t*>(q);
-                q += up256(2 * (size_t)d.n);
-                d.ry = reinterpret_cast<int16_t*>(q);
-                q += up256(2 * (size_t)d.n);
-                d.rt = reinterpret_cast<float*>(q);
-                q += up256(4 * (size_t)d.n);
-                d.rp = reinterpret_cast<int8_t*>(q);
-            }
+        }
+        // the grouping's counter is the plan's (zeroed at creation) also for a window with its own scratch
+        d.gsync = reinterpret_cast<int32_t*>(base + b->L.sync) + kSyncInts * i + 2;
+        // events grouped by 32x32 tile (bin 1) or by 32-row band in their given
+        // order (bin 2), while the plan's grouping memory lasts
+        const size_t bb = bin_bytes(d.W, d.H, d.n);
+        const bool bands = b->sched.bin == 2;
+        const int tp = b->sched.bin == 3 ? cmk::kSmemTile : cmk::kBinTile;
+        const int tx = bands ? 1 : (d.W + tp - 1) / tp;
+        const int ty = bands ? (d.H + cmk::kBandRows - 1) / cmk::kBandRows : (d.H + tp - 1) / tp;
+        const bool fits = bands ? ty <= cmk::kMaxBands : tx * ty <= cmk::kMaxBinTiles;
+        if (b->sched.bin && d.n > 0 && fits && o_bins + bb <= b->capn.bins) {
+            char* q = base + b->L.bins + o_bins;
+            o_bins += bb;
+            d.ntx = tx;
+            d.nty = ty;
+            d.band_rows = bands ? cmk::kBandRows : 0;
+            d.smem_tiles = b->sched.bin == 3 ? 1 : 0;
+            d.tile_px = tp;
+            const size_t nt = (size_t)d.ntx * d.nty;
+            d.tile_cnt = reinterpret_cast<int32_t*>(q);
+            d.tile_cur = bands ? nullptr : d.tile_cnt + nt + 1;
+            const size_t nband = (size_t)ty * ((d.n + cmk::kSuperChunk - 1) / cmk::kSuperChunk);
+            const size_t table = 3 * nt + 2 > nband ? 3 * nt + 2 : nband;
+            d.item_start = bands ? nullptr : d.tile_cnt + 2 * nt + 1;
+            q += up256(table * sizeof(int32_t));
+            d.rx = reinterpret_cast<int16_t*>(q);
+            q += up256(2 * (size_t)d.n);
+            d.ry = reinterpret_cast<int16_t*>(q);
+            q += up256(2 * (size_t)d.n);
+            d.rt = reinterpret_cast<float*>(q);
+            q += up256(4 * (size_t)d.n);
+            d.rp = reinterpret_cast<int8_t*>(q);
         }
         if (!w.flow) {
             d.rho = w.inv_depth;
@@ -570,7 +574,8 @@ int stage_windows(cm_batch* b, const cm_window* wins, int32_t nwin)
     h->total_chunks = chunks;
     h->total_ltiles = lt_total;
     h->total_ptiles = pt_total;
-    if (b->sched.persist > 0) build_queue(b->sched.persist, tab, nwin, reinterpret_cast<cmk::PSeg*>(s + b->L.pseg), h);
+    if (b->sched.persist > 0)
+        build_queue(b->sched.persist - 1, tab, nwin, reinterpret_cast<cmk::PSeg*>(s + b->L.pseg), h);
     b->nwin = nwin;
     if (b->last.data() != wins) b->last.assign(wins, wins + nwin);
     b->dirty = true;
@@ -973,7 +978,7 @@ int cm_batch_create(void* dev_mem, size_t bytes, const cm_window* wins, int32_t 
         else if (B <= 20) tiles_ok = allow_tiles_smem<20>(*cfg);
         else tiles_ok = allow_tiles_smem<32>(*cfg);
         if (!tiles_ok) st = CM_ECUDA;
-        st = stage_windows(b, wins, nwin);
+        if (!st) st = stage_windows(b, wins, nwin);
     }
     // the completion counters start at zero (the prep kernel also resets them)
     if (!st && cudaMemset(b->base + L.sync, 0, (size_t)nwin * kSyncInts * sizeof(int32_t)) != cudaSuccess)
@@ -1051,8 +1056,8 @@ int cm_batch_autotune(cm_batch* b, void* stream, cm_batch_schedule* chosen)
                                {6, 2}, {8, 1}, {8, 2}})
             cand.push_back(cm_batch_schedule{cg.first, cg.second, bin, 0});
     if (b->nwin == 1) cand = {{1, 0, 0, 0}, {1, 0, 1, 0}, {1, 0, 2, 0}, {1, 0, 3, 0}};
-    for (int bin : {0, 2})  // the persistent step, its queue staggered by 1, 2, 3 or 7 phases
-        for (int k : {1, 2, 3, 7}) cand.push_back(cm_batch_schedule{1, 0, bin, k});
+    for (int bin : {0, 2})  // the persistent step, its queue staggered by 0, 1, 2 or 7 phases
+        for (int k : {1, 2, 3, 8}) cand.push_back(cm_batch_schedule{1, 0, bin, k});
     cudaEvent_t a = nullptr, z = nullptr;
     if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&z) != cudaSuccess) return CM_ECUDA;
     float best = 1e30f;

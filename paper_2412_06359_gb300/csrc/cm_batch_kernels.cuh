@@ -81,7 +81,9 @@ __device__ __forceinline__ void count_tiles(const Win& d, long long e0, long lon
 __device__ __forceinline__ void prep_tile(const Win& d, int ti)
 {
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (ti == 0 && threadIdx.x < (d.band_rows ? 2 : 3)) d.sync[threadIdx.x] = 0;
+    if (ti == 0 && threadIdx.x < 2) d.sync[threadIdx.x] = 0;
+    // the tile grouping counts in a later kernel: its counter can be reset here
+    if (ti == 0 && threadIdx.x == 2 && d.tile_cnt && !d.band_rows) *d.gsync = 0;
     const size_t HW = plane_size(d);
     const size_t stride = (size_t)d.pix_tiles * blockDim.x;
     // the window's images as one flat run of 32-byte chunks (the slab is 32-byte aligned)
@@ -152,7 +154,7 @@ __global__ void __launch_bounds__(kEventThreads) k_bin_count_batch(const BatchHd
         for (int i = threadIdx.x; i < nt0; i += blockDim.x)
             if (hist[i]) atomicAdd(d.tile_cnt + i, hist[i]);
         const int chunks = (int)((d.n + kSuperChunk - 1) / kSuperChunk);
-        if (last_tile_done(d.sync + 2, chunks)) {
+        if (last_tile_done(d.gsync, chunks)) {
             const int nt = d.ntx * d.nty;
             int carry = 0;
             for (int base = 0; base < nt; base += blockDim.x) {

@@ -80,8 +80,9 @@ struct Win {
     float* drho;             // [H][W]
     float* dego;             // [6]
     float* dego_part;        // [gradient tiles][6] (pix_tiles; loss_tiles on the batched path)
-    int32_t* sync;           // [4] batched path: completion counters of the loss and gradient reductions and
-                             // of the binning count
+    int32_t* sync;           // [4] batched path: completion counters of the loss and gradient reductions
+    int32_t* gsync;          // completion counter of the grouping's count pass: in memory that starts at
+                             // zero (the plan's, or a workspace's zeroed once); the last block resets it
     // spatial grouping (batched path; tile_cnt == nullptr: events are used in their given order)
     int32_t* tile_cnt;       // tiles: [ntiles + 1] events per 32x32 tile, turned into tile starts by the scan;
                              // bands: [nty][super-chunks] events per band and super-chunk, turned into

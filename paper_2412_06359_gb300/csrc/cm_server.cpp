@@ -414,7 +414,8 @@ extern "C" {
 int cm_server_create(const cm_server_cfg* cfg, cm_server** out)
 {
     if (!cfg || !out || cfg->hbm_budget < (1u << 20) || cfg->max_batch < 1 || cfg->lanes < 1 || cfg->lanes > 16 ||
-        cfg->max_queue < 1 || cfg->nbins < 1 || cfg->nbins > CM_MAX_BINS ||
+        cfg->max_queue < 1 || cfg->nbins < 1 || cfg->nbins > CM_MAX_BINS || cfg->group_events < 0 ||
+        cfg->group_events > ((int64_t)1 << 36) ||
         (cfg->ref_mode != CM_REF_END && cfg->ref_mode != CM_REF_ALL_EDGES))
         return CM_EINVAL;
     cm_server* S = new (std::nothrow) cm_server;
@@ -431,11 +432,21 @@ int cm_server_create(const cm_server_cfg* cfg, cm_server** out)
     }
     S->pool.init(cfg->hbm_budget);
     // one plan per lane, sized for max_batch windows that bring their own scratch
+    // and, with group_events, for the band grouping of that many events (the
+    // prototype windows share them out; they are never run, their event
+    // pointers only need to be non-null)
     std::vector<cm_window> proto(cfg->max_batch);
+    const int64_t per = (cfg->group_events + cfg->max_batch - 1) / cfg->max_batch;
     for (cm_window& w : proto) {
         std::memset(&w, 0, sizeof(w));
-        w.cam = cm_camera{2, 2, 1.0f, 1.0f, 0.5f, 0.5f};
-        w.ev = cm_events{nullptr, nullptr, nullptr, nullptr, 0, 0.0f, 1.0f};
+        w.cam = cm_camera{per > 0 ? 1280 : 2, per > 0 ? 720 : 2, 1.0f, 1.0f, 0.5f, 0.5f};
+        w.ev = cm_events{nullptr, nullptr, nullptr, nullptr, per, 0.0f, 1.0f};
+        if (per > 0) {
+            w.ev.x = reinterpret_cast<const int16_t*>(S->dev);
+            w.ev.y = reinterpret_cast<const int16_t*>(S->dev);
+            w.ev.t = reinterpret_cast<const float*>(S->dev);
+            w.ev.p = reinterpret_cast<const int8_t*>(S->dev);
+        }
         w.flow = reinterpret_cast<const float*>(S->dev);
         w.dloss = reinterpret_cast<const float*>(S->dev);
         w.loss_out = reinterpret_cast<float*>(S->dev);
@@ -454,7 +465,8 @@ int cm_server_create(const cm_server_cfg* cfg, cm_server** out)
             break;
         }
         if ((rc = cm_batch_create(S->dev + L.plan_off, b, proto.data(), cfg->max_batch, &S->lcfg, &L.plan))) break;
-        const cm_batch_schedule wide{1, 0};  // one graph for every mix of windows
+        // one graph for every mix of windows, events grouped by band while the lane's memory lasts
+        const cm_batch_schedule wide{1, 0, cfg->group_events > 0 ? 2 : 0, 0};
         if ((rc = cm_batch_set_schedule(L.plan, &wide))) break;
         if (cudaStreamCreateWithFlags(&L.s, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming) != cudaSuccess)

@@ -46,8 +46,10 @@ class HostRequest:
 
 class Server:
     def __init__(self, hbm_budget: int, *, max_batch: int = 8, lanes: int = 2, max_queue: int = 4096,
-                 nbins: int = 10, ref_mode: int = C.CM_REF_ALL_EDGES, eps: float = 1e-9, device: int = 0):
-        cfg = C.cm_server_cfg(int(hbm_budget), max_batch, lanes, max_queue, nbins, ref_mode, eps, device)
+                 nbins: int = 10, ref_mode: int = C.CM_REF_ALL_EDGES, eps: float = 1e-9, device: int = 0,
+                 group_events: int = 0):
+        cfg = C.cm_server_cfg(int(hbm_budget), max_batch, lanes, max_queue, nbins, ref_mode, eps, device,
+                              int(group_events))
         self.handle = C.cm_server_create(cfg)
         self.live = {}
 

@@ -34,12 +34,13 @@ def _server(budget=2 << 30, **kw):
     return Server(budget, **kw)
 
 
-def check_served(reqs):
+def check_served(reqs, **server_kw):
     """Served results against the FP64 oracle: each request's loss within
     LOSS_RTOL of the oracle's straddle interval; the windows without their
     flagged events served again (a server at eps = GRAD_EPS, where the
-    gradient is well-conditioned) against the oracle strictly: loss within
-    LOSS_RTOL, dL/d(inv depth) and dL/d(ego) within GRAD_RTOL_L2."""
+    gradient is well-conditioned, configured with server_kw) against the
+    oracle strictly: loss within LOSS_RTOL, dL/d(inv depth) and dL/d(ego)
+    within GRAD_RTOL_L2."""
     from paper_2412_06359_gb300.serve import HostRequest
     subs = []
     for r in reqs:
@@ -47,7 +48,7 @@ def check_served(reqs):
         b, L = o["bounds"], float(r.loss[0])
         assert b["loss_lo"] - LOSS_RTOL * o["loss"] <= L <= b["loss_hi"] + LOSS_RTOL * o["loss"], (L, b)
         subs.append(unflagged(r.window, b["flags"]))
-    srv = _server(eps=GRAD_EPS, max_batch=4, lanes=2)
+    srv = _server(eps=GRAD_EPS, max_batch=4, lanes=2, **server_kw)
     sreqs = [HostRequest.from_window(i, w) for i, w in enumerate(subs)]
     for t in [srv.submit(q) for q in sreqs]:
         assert srv.wait(t, 120).status == 0
@@ -57,6 +58,20 @@ def check_served(reqs):
         assert abs(float(q.loss[0]) - o["loss"]) <= LOSS_RTOL * o["loss"]
         assert rel_l2(q.drho, o["dinv_depth"]) <= GRAD_RTOL_L2
         assert rel_l2(q.dego, o["dego"]) <= GRAD_RTOL_L2
+
+
+@pytest.mark.parametrize("group", [1 << 20, 30000])
+def test_band_grouped_lanes_match_the_oracle(group):
+    # the lanes regroup each batch's events by 32-row band; with 30000 only the
+    # first windows of a batch fit the lane's grouping memory, the rest run in
+    # their given order
+    reqs = _requests(12, 6, seed=21)
+    srv = _server(max_batch=6, lanes=2, group_events=group)
+    tickets = [srv.submit(r) for r in reqs]
+    results = [srv.wait(t, 60) for t in tickets]
+    srv.close()
+    assert all(res.status == 0 for res in results)
+    check_served(reqs, group_events=group)
 
 
 def _snapshot(req):
