@@ -102,9 +102,9 @@ size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 int n_refs(const cm_loss_cfg& c) { return c.ref_mode == CM_REF_END ? 1 : c.nbins + 1; }
 
-int tiles_for(size_t hw, int cap)
+int tiles_for(size_t hw, size_t px, int cap)
 {
-    size_t t = (hw + 2047) / 2048;
+    size_t t = (hw + px - 1) / px;
     if (t < 1) t = 1;
     if (t > (size_t)cap) t = cap;
     return (int)t;
@@ -142,11 +142,13 @@ float eps_of(const cm_loss_cfg& c) { return c.eps > 0.0f ? c.eps : 1e-9f; }
 
 Layout layout(const cm_camera& cam, const cm_loss_cfg& cfg, int32_t nfb, int64_t max_events)
 {
-    Layout L;
+    Layout L{};
     const size_t HW = (size_t)cam.width * cam.height;
     L.R = n_refs(cfg);
-    L.loss_tiles = tiles_for(HW, 256);
-    L.pix_tiles = tiles_for(HW, 512);
+    // pixel passes of one window: tiles of 512 pixels (up to 1024 tiles), so
+    // that even a 346x260 window's passes spread over every SM
+    L.loss_tiles = tiles_for(HW, 512, 1024);
+    L.pix_tiles = tiles_for(HW, 512, 1024);
     size_t off = 0;
     L.iwe = off;
     off = align_up(off + (size_t)L.R * HW * sizeof(float4));
@@ -175,13 +177,14 @@ Layout layout(const cm_camera& cam, const cm_loss_cfg& cfg, int32_t nfb, int64_t
         off = align_up(off + HW * sizeof(cmk::FQ));
         L.dq = off;
         off = align_up(off + HW * sizeof(cmk::FQ));
+        // completion counters: the fused loss and gradient reductions, the grouping
+        L.sync = off;
+        off = align_up(off + 4 * sizeof(int32_t));
         L.bands = max_events > 0 ? band_count_for(cam, L.R) : 0;
         if (L.bands) {
             const size_t nsc = (size_t)((max_events + cmk::kSuperChunk - 1) / cmk::kSuperChunk);
             L.band_tab = off;
             off = align_up(off + (size_t)L.bands * nsc * sizeof(int32_t));
-            L.sync = off;
-            off = align_up(off + 4 * sizeof(int32_t));
             L.gx = off;
             off = align_up(off + (size_t)max_events * sizeof(int16_t));
             L.gy = off;
@@ -326,7 +329,7 @@ int cm_workspace_create(void* dev_mem, size_t bytes, const cm_camera* cam, const
     if (reinterpret_cast<uintptr_t>(dev_mem) % kAlign) return CM_EINVAL;
     const Layout L = layout(*cam, *cfg, n_flow_bins, max_events);
     if (bytes < L.total) return CM_ENOMEM;
-    cm_workspace* ws = new (std::nothrow) cm_workspace;
+    cm_workspace* ws = new (std::nothrow) cm_workspace{};
     if (!ws) return CM_ENOMEM;
     std::memset(ws, 0, sizeof(*ws));
     char* b = static_cast<char*>(dev_mem);
@@ -352,9 +355,10 @@ int cm_workspace_create(void* dev_mem, size_t bytes, const cm_camera* cam, const
     ws->fq = L.planes ? reinterpret_cast<cmk::FQ*>(b + L.fq) : nullptr;
     ws->dq = L.planes ? reinterpret_cast<cmk::FQ*>(b + L.dq) : nullptr;
     ws->bands = L.bands;
+    ws->sync = L.planes ? reinterpret_cast<int32_t*>(b + L.sync) : nullptr;
+    ws->sync_zeroed = false;
     if (L.bands) {
         ws->band_tab = reinterpret_cast<int32_t*>(b + L.band_tab);
-        ws->sync = reinterpret_cast<int32_t*>(b + L.sync);
         ws->gx = reinterpret_cast<int16_t*>(b + L.gx);
         ws->gy = reinterpret_cast<int16_t*>(b + L.gy);
         ws->gt = reinterpret_cast<float*>(b + L.gt);
@@ -458,11 +462,14 @@ int cm_loss_forward(const cm_camera* cam, const cm_events* ev, const float* flow
         }
         const int sms = cmk::sm_count_current();
         const bool grouped = ws->bands > 0 && ev->n >= cmk::kSuperChunk;
+        // the completion counters of the fused reductions (and of the grouping)
+        // start at zero once; every use returns them to zero
+        if (!ws->sync_zeroed) {
+            if ((st = cuda_status(cudaMemsetAsync(ws->sync, 0, 4 * sizeof(int32_t), s)))) return st;
+            ws->sync_zeroed = true;
+        }
+        d.sync = ws->sync;
         if (grouped) {
-            if (!ws->sync_zeroed) {
-                if ((st = cuda_status(cudaMemsetAsync(ws->sync, 0, 4 * sizeof(int32_t), s)))) return st;
-                ws->sync_zeroed = true;
-            }
             Win g = d;
             g.tile_cnt = ws->band_tab;
             g.sync = ws->sync;
@@ -567,7 +574,8 @@ int cm_loss_backward(const cm_camera* cam, const cm_events* ev, const float* flo
             d.dt = dt_window;
             d.drho = dinv_depth;
             d.dego = dego6;
-            return cuda_status(cmk::launch_depth_ego(d, s));  // folds the accumulators (and stores dL/dflow)
+            d.sync = ws->sync;  // zeroed by the forward
+            return cuda_status(cmk::launch_depth_ego_planes(d, s));  // folds the accumulators (and stores dL/dflow)
         }
         return cuda_status(cmk::launch_fold(d, s));
     }

@@ -236,10 +236,12 @@ __device__ __forceinline__ void use_grouped(Win& d)
     }
 }
 
-// the event kernels keep their trajectory points in shared memory up to 20
-// bins (the static 48 KB a block may declare), in registers beyond
+// the event kernels keep their trajectory points in shared memory up to 10
+// bins: 64 registers and four blocks per SM.  With more bins they keep them
+// in registers: two blocks per SM either way, and at 20 bins the register
+// form measured faster (a one-window plan at 1280x720: 2.61 against 2.74 ms).
 template <int MAXB>
-constexpr bool kPointsSmem = MAXB <= 20;
+constexpr bool kPointsSmem = MAXB <= 10;
 
 template <int MAXB>
 __global__ void __launch_bounds__(kEventThreads, MAXB <= 10 ? 4 : 2) k_splat_batch(const BatchHdr* h, const Win* tab,

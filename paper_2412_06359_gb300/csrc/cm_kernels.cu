@@ -12,10 +12,12 @@ namespace cmk {
 __global__ void __launch_bounds__(256) k_flow(Win d) { flow_tile(d, blockIdx.x, gridDim.x); }
 
 // ---------------------------------------------------------------------------
-// the event kernels keep their trajectory points in shared memory up to 20
-// bins (the static 48 KB a block may declare), in registers beyond
+// the event kernels keep their trajectory points in shared memory up to 10
+// bins: 64 registers and four blocks per SM.  With more bins they keep them
+// in registers: two blocks per SM either way, and at 20 bins the register
+// form measured faster (a one-window plan at 1280x720: 2.61 against 2.74 ms).
 template <int MAXB>
-constexpr bool kPointsInSmem = MAXB <= 20;
+constexpr bool kPointsInSmem = MAXB <= 10;
 template <int MAXB>
 constexpr int kEventBlocksPerSm = MAXB <= 10 ? 4 : 2;
 
@@ -68,6 +70,8 @@ template <bool PAIRS>
 __global__ void __launch_bounds__(256) k_loss_planes(Win d)
 {
     loss_tile_planes<PAIRS>(d, blockIdx.x, gridDim.x);
+    // the block completing the last tile reduces the tiles (fixed order)
+    if (last_tile_done(d.sync + 0, gridDim.x)) loss_final_window(d);
 }
 
 // dL/dflow folded from the quad accumulators (flow input)
@@ -111,13 +115,30 @@ __global__ void __launch_bounds__(256) k_depth_ego(Win d) { depth_ego_tile(d, bl
 
 __global__ void __launch_bounds__(192) k_depth_ego_final(Win d) { depth_ego_final_window(d, d.pix_tiles); }
 
+// the same for the plane layout, the six sums reduced by the block completing
+// the last tile
+__global__ void __launch_bounds__(256) k_depth_ego_planes(Win d)
+{
+    depth_ego_tile(d, blockIdx.x, gridDim.x);
+    if (last_tile_done(d.sync + 1, gridDim.x)) {
+        __syncthreads();
+        depth_ego_final_window(d, gridDim.x);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // launchers
 
+// The event kernels' grid: the blocks that fit on the SMs at once (their
+// launch bounds), so that the grid-stride loop keeps the events in flight
+// contiguous: with events grouped by band they then touch one strip of the
+// images (a larger grid runs its blocks in waves, each resident block
+// striding over the whole window).
+template <int MAXB>
 static int event_grid(int64_t n, int sm_count)
 {
     const int64_t blocks = (n + kEventThreads - 1) / kEventThreads;
-    const int64_t cap = (int64_t)sm_count * 8;
+    const int64_t cap = (int64_t)sm_count * kEventBlocksPerSm<MAXB>;
     return (int)(blocks < 1 ? 1 : (blocks < cap ? blocks : cap));
 }
 
@@ -133,31 +154,29 @@ cudaError_t launch_flow(const Win& d, cudaStream_t st)
 cudaError_t launch_splat(const Win& d, int sm_count, cudaStream_t st)
 {
     if (d.n == 0) return cudaSuccess;
-    const int g = event_grid(d.n, sm_count);
     KernelScope ks("k_splat", st);
-    if (d.B <= 1) k_splat<1><<<g, kEventThreads, 0, st>>>(d);
-    else if (d.B <= 10) k_splat<10><<<g, kEventThreads, 0, st>>>(d);
-    else if (d.B <= 20) k_splat<20><<<g, kEventThreads, 0, st>>>(d);
-    else k_splat<32><<<g, kEventThreads, 0, st>>>(d);
+    if (d.B <= 1) k_splat<1><<<event_grid<1>(d.n, sm_count), kEventThreads, 0, st>>>(d);
+    else if (d.B <= 10) k_splat<10><<<event_grid<10>(d.n, sm_count), kEventThreads, 0, st>>>(d);
+    else if (d.B <= 20) k_splat<20><<<event_grid<20>(d.n, sm_count), kEventThreads, 0, st>>>(d);
+    else k_splat<32><<<event_grid<32>(d.n, sm_count), kEventThreads, 0, st>>>(d);
     return cudaGetLastError();
 }
 
 template <bool SPLIT>
-static void adjoint_for(const Win& d, int g, cudaStream_t st)
+static void adjoint_for(const Win& d, int sm, cudaStream_t st)
 {
-    if (d.B <= 1) k_adjoint<1, SPLIT><<<g, kEventThreads, 0, st>>>(d);
-    else if (d.B <= 10) k_adjoint<10, SPLIT><<<g, kEventThreads, 0, st>>>(d);
-    else if (d.B <= 20) k_adjoint<20, SPLIT><<<g, kEventThreads, 0, st>>>(d);
-    else k_adjoint<32, SPLIT><<<g, kEventThreads, 0, st>>>(d);
+    if (d.B <= 1) k_adjoint<1, SPLIT><<<event_grid<1>(d.n, sm), kEventThreads, 0, st>>>(d);
+    else if (d.B <= 10) k_adjoint<10, SPLIT><<<event_grid<10>(d.n, sm), kEventThreads, 0, st>>>(d);
+    else if (d.B <= 20) k_adjoint<20, SPLIT><<<event_grid<20>(d.n, sm), kEventThreads, 0, st>>>(d);
+    else k_adjoint<32, SPLIT><<<event_grid<32>(d.n, sm), kEventThreads, 0, st>>>(d);
 }
 
 cudaError_t launch_adjoint(const Win& d, int sm_count, cudaStream_t st)
 {
     if (d.n == 0) return cudaSuccess;
-    const int g = event_grid(d.n, sm_count);
     KernelScope ks("k_adjoint", st);
-    if (d.iwe_split) adjoint_for<true>(d, g, st);
-    else adjoint_for<false>(d, g, st);
+    if (d.iwe_split) adjoint_for<true>(d, sm_count, st);
+    else adjoint_for<false>(d, sm_count, st);
     return cudaGetLastError();
 }
 
@@ -180,10 +199,6 @@ cudaError_t launch_loss_planes(const Win& d, cudaStream_t st)
         KernelScope ks("k_loss_planes", st);
         if (((size_t)d.W * d.H) & 1) k_loss_planes<false><<<d.loss_tiles, 256, 0, st>>>(d);
         else k_loss_planes<true><<<d.loss_tiles, 256, 0, st>>>(d);
-    }
-    {
-        KernelScope ks("k_loss_final", st);
-        k_loss_final<<<1, 1024, 0, st>>>(d);
     }
     return cudaGetLastError();
 }
@@ -221,6 +236,13 @@ cudaError_t launch_loss(const Win& d, cudaStream_t st)
         KernelScope ks("k_loss_final", st);
         k_loss_final<<<1, 1024, 0, st>>>(d);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_depth_ego_planes(const Win& d, cudaStream_t st)
+{
+    KernelScope ks("k_depth_ego_planes", st);
+    k_depth_ego_planes<<<d.pix_tiles, 256, 0, st>>>(d);
     return cudaGetLastError();
 }
 

@@ -14,9 +14,11 @@ cudaError_t launch_splat(const Win& d, int sm_count, cudaStream_t st);
 cudaError_t launch_adjoint(const Win& d, int sm_count, cudaStream_t st);
 cudaError_t launch_loss(const Win& d, cudaStream_t st);
 cudaError_t launch_depth_ego(const Win& d, cudaStream_t st);
+cudaError_t launch_depth_ego_planes(const Win& d, cudaStream_t st);  // fused final reduction (d.sync[1] zero)
 // the polarity-plane layout of one window (iwe_split, flow quads, quad accumulators)
 cudaError_t launch_prep(const Win& d, int sm_count, cudaStream_t st);
-cudaError_t launch_loss_planes(const Win& d, cudaStream_t st);  // d.loss_tiles blocks over every reference
+cudaError_t launch_loss_planes(const Win& d, cudaStream_t st);  // d.loss_tiles blocks over every reference,
+                                                                // fused final reduction (d.sync[0] zero)
 cudaError_t launch_fold(const Win& d, cudaStream_t st);         // dL/dflow from the quad accumulators
 // events grouped by band of rows into d.rx, d.ry, d.rt, d.rp (d.tile_cnt: the
 // [bands][super-chunks] table; d.sync[2]: its completion counter, zero)
