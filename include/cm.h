@@ -325,6 +325,16 @@ int cm_batch_set_windows(cm_batch* plan, const cm_window* wins, int32_t nwin);
 /* Forward and backward of every window of the plan, stream-ordered on
  * `stream`: writes each loss_out and the requested gradients. */
 int cm_batch_run(cm_batch* plan, void* stream);
+/* Synchronises `stream`, then reports how the last run's device-side waits
+ * ended: CM_ETIMEOUT when a wait of the persistent step (schedule persist > 0)
+ * gave up after its bound (about 4 s; that run's outputs are invalid, the
+ * context stays usable), else CM_OK.  CM_ECUDA when the stream reports an error. */
+int cm_batch_status(const cm_batch* plan, void* stream);
+/* Test hook for the failure path above: window >= 0 makes the persistent
+ * step's queue leave out that window's prep pass from the next run on, so its
+ * later phases wait until their bound runs out; -1 restores the full queue.
+ * Restages the plan's windows; CM_EINVAL outside [-1, capacity). */
+int cm_batch_inject_stall(cm_batch* plan, int32_t window);
 
 /* Schedule of a plan: windows are taken `group` at a time (each kernel of the
  * graph covers one group) and the groups run on `chains` concurrent chains of

@@ -108,6 +108,8 @@ SIGNATURES = {
     "cm_batch_create": ([_vp, _sz, _P(cm_window), _i32, _P(cm_loss_cfg), _P(_vp)], ctypes.c_int),
     "cm_batch_set_windows": ([_vp, _P(cm_window), _i32], ctypes.c_int),
     "cm_batch_run": ([_vp, _vp], ctypes.c_int),
+    "cm_batch_status": ([_vp, _vp], ctypes.c_int),
+    "cm_batch_inject_stall": ([_vp, _i32], ctypes.c_int),
     "cm_batch_set_schedule": ([_vp, _P(cm_batch_schedule)], ctypes.c_int),
     "cm_batch_get_schedule": ([_vp, _P(cm_batch_schedule)], ctypes.c_int),
     "cm_batch_autotune": ([_vp, _vp, _P(cm_batch_schedule)], ctypes.c_int),
@@ -269,6 +271,19 @@ def cm_batch_autotune(plan: int, stream: int) -> tuple[int, int, int, int]:
     s = cm_batch_schedule()
     _check(lib().cm_batch_autotune(plan, stream, ctypes.byref(s)), "cm_batch_autotune")
     return s.chains, s.group, s.bin, s.persist
+
+
+def cm_batch_status(plan: int, stream: int) -> int:
+    """CM_OK, or CM_ETIMEOUT when a bounded device wait of the last run gave up
+    (other failures raise)."""
+    st = lib().cm_batch_status(plan, stream)
+    if st not in (CM_OK, CM_ETIMEOUT):
+        _check(st, "cm_batch_status")
+    return st
+
+
+def cm_batch_inject_stall(plan: int, window: int) -> None:
+    _check(lib().cm_batch_inject_stall(plan, window), "cm_batch_inject_stall")
 
 
 def cm_batch_stats(plan: int, window: int) -> tuple[int, int]:

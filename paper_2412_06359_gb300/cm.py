@@ -414,6 +414,16 @@ class BatchPlan:
     def run(self):
         C.cm_batch_run(self.handle, stream_handle(self.buf.device))
 
+    def status(self) -> int:
+        """Waits for the plan's stream; CM_OK, or CM_ETIMEOUT when a bounded
+        device wait of the last run (persistent step) gave up."""
+        return C.cm_batch_status(self.handle, stream_handle(self.buf.device))
+
+    def inject_stall(self, window: int):
+        """Test hook: the persistent step's queue leaves out `window`'s prep
+        pass from the next run on (-1 restores it)."""
+        C.cm_batch_inject_stall(self.handle, window)
+
     def set_schedule(self, chains: int, group: int, bin: int = 0, persist: int = 0):
         """chains: concurrent kernel chains; group: windows per kernel (0: one
         kernel over every window); bin: 1 to group each window's events by

@@ -275,6 +275,7 @@ struct cm_batch {
     std::vector<cm_window> last;       // the windows of the last staging (re-staged when grouping changes)
     int grid_events = 0, grid_tiles = 0, grid_tiles_smem = 0, grid_persist = 0;
     cm_batch_schedule sched{2, 1, 0};
+    int stall_window = -1;             // test hook: the persistent queue leaves out this window's prep pass
     bool stale = true;                 // the graph must be (re)captured before the next replay
     cudaStream_t streams[kMaxChains] = {};
     cudaEvent_t fork = nullptr;
@@ -297,7 +298,7 @@ std::vector<Group> make_groups(const cm_batch* b);
 // first phase comes `stagger` phases after window w's (stagger 0: phase by
 // phase over all windows) and a window's phases keep their order (every
 // dependency is queued before its dependants).
-void build_queue(int stagger, const Win* tab, int nwin, cmk::PSeg* seg, BatchHdr* h)
+void build_queue(int stagger, const Win* tab, int nwin, int stall_window, cmk::PSeg* seg, BatchHdr* h)
 {
     struct Key {
         long long key;
@@ -314,6 +315,11 @@ void build_queue(int stagger, const Win* tab, int nwin, cmk::PSeg* seg, BatchHdr
         int rank = 0;
         for (int ph : order) {
             if (!grouped && (ph == cmk::kPBandCount || ph == cmk::kPBandScatter)) continue;
+            // a stalled window (test hook) has no prep items: its later phases wait until their bound
+            if (w == stall_window && ph == cmk::kPPrep) {
+                ++rank;
+                continue;
+            }
             int count = 0;
             switch (ph) {
             case cmk::kPPrep: count = d.pix_tiles; break;
@@ -575,7 +581,7 @@ int stage_windows(cm_batch* b, const cm_window* wins, int32_t nwin)
     h->total_ltiles = lt_total;
     h->total_ptiles = pt_total;
     if (b->sched.persist > 0)
-        build_queue(b->sched.persist - 1, tab, nwin, reinterpret_cast<cmk::PSeg*>(s + b->L.pseg), h);
+        build_queue(b->sched.persist - 1, tab, nwin, b->stall_window, reinterpret_cast<cmk::PSeg*>(s + b->L.pseg), h);
     b->nwin = nwin;
     if (b->last.data() != wins) b->last.assign(wins, wins + nwin);
     b->dirty = true;
@@ -1087,6 +1093,26 @@ int cm_batch_autotune(cm_batch* b, void* stream, cm_batch_schedule* chosen)
     g_tuned.push_back({k, pick});
     if (chosen) *chosen = pick;
     return CM_OK;
+}
+
+int cm_batch_status(const cm_batch* b, void* stream)
+{
+    if (!b) return CM_EINVAL;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (b->sched.persist <= 0) return cudaStreamSynchronize(s) == cudaSuccess ? CM_OK : CM_ECUDA;
+    int32_t err = 0;  // the error word, behind the queue head
+    if (cudaMemcpyAsync(&err, b->base + b->L.pq + sizeof(int32_t), sizeof(err), cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return CM_ECUDA;
+    return err ? CM_ETIMEOUT : CM_OK;
+}
+
+int cm_batch_inject_stall(cm_batch* b, int32_t window)
+{
+    if (!b || window < -1 || window >= b->cap) return CM_EINVAL;
+    b->stall_window = window;
+    return apply_schedule(b, b->sched);
 }
 
 int cm_batch_stats(const cm_batch* b, int32_t window, const float** loss_r, const int32_t** nnz_r)

@@ -400,3 +400,28 @@ def test_persistent_step_on_the_bench_windows_with_stored_warps_and_many_bins():
     deep = [synth.depth_window(np.random.default_rng(9400 + i), W, H, n, nbins=20)
             for i, (W, H, n) in enumerate([(120, 90, 3000), (160, 100, 5000)])]
     check_windows(deep, batch_runner(B=20, schedule=(1, 0, 2, 2)))
+
+
+def test_persistent_wait_gives_up_reports_and_the_plan_recovers():
+    # failure path of the persistent step's bounded waits: a window whose prep
+    # pass is left out of the queue (test hook) blocks its later phases; the
+    # first wait to reach its bound (about 4 s) sets the error word, every
+    # other wait returns at once, the kernel ends and the run reports
+    # CM_ETIMEOUT.  With the queue restored the same plan is correct again.
+    from paper_2412_06359_gb300 import _capi as C
+    cm = gpu_lib()
+    wins = _mixed_windows(5, 97)
+    plan = cm.BatchPlan(_dev_windows(cm, wins), cm.loss_cfg(10, cm.REF_ALL, cm.SPLAT_ATOMIC))
+    plan.set_schedule(1, 0, 2, 2)
+    plan.run()
+    assert plan.status() == C.CM_OK
+    plan.inject_stall(1)
+    plan.run()
+    assert plan.status() == C.CM_ETIMEOUT
+    plan.inject_stall(-1)
+    plan.run()
+    assert plan.status() == C.CM_OK
+    check_windows(wins, batch_runner(schedule=(1, 0, 2, 2)), full=plan_results(plan, wins), grad=False)
+    plan.set_schedule(6, 1, 2, 0)  # the graph path has no device waits
+    plan.run()
+    assert plan.status() == C.CM_OK
