@@ -200,6 +200,45 @@ struct cm_server {
         }
     }
 
+    // Run every lane's plan once on an empty 2x2 window, so that each lane
+    // captures its graph now instead of inside the first requests' latency
+    // (the lanes' schedule takes every window slot in one group: the graph
+    // stays valid for any later mix of windows).
+    int warm_lanes()
+    {
+        const cm_camera cam{2, 2, 1.0f, 1.0f, 0.5f, 0.5f};
+        size_t sb = 0;
+        if (cm_window_scratch_query(&cam, &lcfg, &sb) != CM_OK) return CM_ECUDA;
+        const size_t bytes = up256(sb) + 256;
+        const size_t off = pool.alloc(bytes);
+        if (off == Pool::kNone) return CM_ENOMEM;
+        char* m = at(off);
+        float* small = reinterpret_cast<float*>(m + up256(sb));  // rho[4], ego[6], dego[6], loss, dloss
+        int rc = cudaMemsetAsync(m, 0, bytes, lanes[0].s) == cudaSuccess &&
+                         cudaStreamSynchronize(lanes[0].s) == cudaSuccess
+                     ? CM_OK
+                     : CM_ECUDA;
+        cm_window w;
+        std::memset(&w, 0, sizeof(w));
+        w.cam = cam;
+        w.ev = cm_events{nullptr, nullptr, nullptr, nullptr, 0, 0.0f, 1.0f};
+        w.inv_depth = small;
+        w.ego6 = small + 4;
+        w.dego6 = small + 10;
+        w.loss_out = small + 16;
+        w.dloss = small + 17;
+        w.dt_window = 1.0f;
+        w.scratch = m;
+        for (Lane& L : lanes) {
+            if (rc) break;
+            if ((rc = cm_batch_set_windows(L.plan, &w, 1))) break;
+            if ((rc = cm_batch_run(L.plan, L.s))) break;
+            if (cudaStreamSynchronize(L.s) != cudaSuccess) rc = CM_ECUDA;
+        }
+        pool.release(off, bytes);
+        return rc;
+    }
+
     // make the stream's resident state fit request q; false when memory is short now
     bool ensure_state(StreamState& s, const cm_request& q)
     {
@@ -472,6 +511,7 @@ int cm_server_create(const cm_server_cfg* cfg, cm_server** out)
             cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming) != cudaSuccess)
             rc = CM_ECUDA;
     }
+    if (!rc) rc = S->warm_lanes();
     if (rc) {
         cm_server_destroy(S);
         return rc;
