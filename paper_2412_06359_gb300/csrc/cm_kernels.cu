@@ -129,16 +129,17 @@ __global__ void __launch_bounds__(256) k_depth_ego_planes(Win d)
 // ---------------------------------------------------------------------------
 // launchers
 
-// The event kernels' grid: the blocks that fit on the SMs at once (their
-// launch bounds), so that the grid-stride loop keeps the events in flight
-// contiguous: with events grouped by band they then touch one strip of the
-// images (a larger grid runs its blocks in waves, each resident block
-// striding over the whole window).
-template <int MAXB>
-static int event_grid(int64_t n, int sm_count)
+// The event kernels' grids.  The adjoint runs the blocks that fit on the SMs
+// at once (their launch bounds), so that its grid-stride loop keeps the
+// events in flight contiguous: with events grouped by band they then gather
+// from one strip of the images (a larger grid runs in waves, each resident
+// block striding over the whole window; 1.64 against 1.42 ms at 1280x720 with
+// 2M events).  The splat, whose reductions need no reply, measured faster
+// with eight blocks per SM in waves (0.96 against 1.06 ms there).
+static int event_grid(int64_t n, int sm_count, int blocks_per_sm)
 {
     const int64_t blocks = (n + kEventThreads - 1) / kEventThreads;
-    const int64_t cap = (int64_t)sm_count * kEventBlocksPerSm<MAXB>;
+    const int64_t cap = (int64_t)sm_count * blocks_per_sm;
     return (int)(blocks < 1 ? 1 : (blocks < cap ? blocks : cap));
 }
 
@@ -155,20 +156,21 @@ cudaError_t launch_splat(const Win& d, int sm_count, cudaStream_t st)
 {
     if (d.n == 0) return cudaSuccess;
     KernelScope ks("k_splat", st);
-    if (d.B <= 1) k_splat<1><<<event_grid<1>(d.n, sm_count), kEventThreads, 0, st>>>(d);
-    else if (d.B <= 10) k_splat<10><<<event_grid<10>(d.n, sm_count), kEventThreads, 0, st>>>(d);
-    else if (d.B <= 20) k_splat<20><<<event_grid<20>(d.n, sm_count), kEventThreads, 0, st>>>(d);
-    else k_splat<32><<<event_grid<32>(d.n, sm_count), kEventThreads, 0, st>>>(d);
+    const int g = event_grid(d.n, sm_count, 8);
+    if (d.B <= 1) k_splat<1><<<g, kEventThreads, 0, st>>>(d);
+    else if (d.B <= 10) k_splat<10><<<g, kEventThreads, 0, st>>>(d);
+    else if (d.B <= 20) k_splat<20><<<g, kEventThreads, 0, st>>>(d);
+    else k_splat<32><<<g, kEventThreads, 0, st>>>(d);
     return cudaGetLastError();
 }
 
 template <bool SPLIT>
 static void adjoint_for(const Win& d, int sm, cudaStream_t st)
 {
-    if (d.B <= 1) k_adjoint<1, SPLIT><<<event_grid<1>(d.n, sm), kEventThreads, 0, st>>>(d);
-    else if (d.B <= 10) k_adjoint<10, SPLIT><<<event_grid<10>(d.n, sm), kEventThreads, 0, st>>>(d);
-    else if (d.B <= 20) k_adjoint<20, SPLIT><<<event_grid<20>(d.n, sm), kEventThreads, 0, st>>>(d);
-    else k_adjoint<32, SPLIT><<<event_grid<32>(d.n, sm), kEventThreads, 0, st>>>(d);
+    if (d.B <= 1) k_adjoint<1, SPLIT><<<event_grid(d.n, sm, kEventBlocksPerSm<1>), kEventThreads, 0, st>>>(d);
+    else if (d.B <= 10) k_adjoint<10, SPLIT><<<event_grid(d.n, sm, kEventBlocksPerSm<10>), kEventThreads, 0, st>>>(d);
+    else if (d.B <= 20) k_adjoint<20, SPLIT><<<event_grid(d.n, sm, kEventBlocksPerSm<20>), kEventThreads, 0, st>>>(d);
+    else k_adjoint<32, SPLIT><<<event_grid(d.n, sm, kEventBlocksPerSm<32>), kEventThreads, 0, st>>>(d);
 }
 
 cudaError_t launch_adjoint(const Win& d, int sm_count, cudaStream_t st)
