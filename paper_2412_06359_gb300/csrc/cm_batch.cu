@@ -274,6 +274,7 @@ struct cm_batch {
     std::vector<const int32_t*> stat_nnz;
     std::vector<cm_window> last;       // the windows of the last staging (re-staged when grouping changes)
     int grid_events = 0, grid_tiles = 0, grid_tiles_smem = 0, grid_persist = 0;
+    int grid_splat = 0;  // the splat: eight blocks per SM in waves (its reductions need no reply)
     cm_batch_schedule sched{2, 1, 0};
     int stall_window = -1;             // test hook: the persistent queue leaves out this window's prep pass
     bool stale = true;                 // the graph must be (re)captured before the next replay
@@ -769,7 +770,7 @@ int capture(cm_batch* b)
             case 0: cmk::k_prep_batch<<<gt, cmk::kEventThreads, 0, s>>>(h, tab, ps, ss, b->sched.bin == 2, g.w0, g.w1); break;
             case 1: cmk::k_bin_count_batch<<<gs, cmk::kEventThreads, 0, s>>>(h, tab, ss, g.w0, g.w1); break;
             case 2: cmk::k_bin_scatter_batch<<<gs, cmk::kEventThreads, 0, s>>>(h, tab, ss, g.w0, g.w1); break;
-            case 3: enqueue_event(b, s, 0, ge, g.w0, g.w1); break;
+            case 3: enqueue_event(b, s, 0, wide ? b->grid_splat : clampi(g.chunks, 1, b->grid_splat), g.w0, g.w1); break;
             case 4: cmk::k_loss_batch<<<gl, 256, 0, s>>>(h, tab, ls, g.w0, g.w1); break;
             case 5: enqueue_event(b, s, 1, ge, g.w0, g.w1); break;
             case 6: cmk::k_grad_batch<<<gl, 256, 0, s>>>(h, tab, ls, g.w0, g.w1); break;
@@ -970,6 +971,7 @@ int cm_batch_create(void* dev_mem, size_t bytes, const cm_window* wins, int32_t 
         else if (B <= 20) occ = occupancy_blocks<20>();
         else occ = occupancy_blocks<32>();
         b->grid_events = sms * occ;
+        b->grid_splat = sms * 8;
         b->grid_tiles = sms * 4;
         b->grid_tiles_smem = sms;  // one tile block (512 threads, up to 192 KB) per SM
         int occp = 1;
