@@ -190,8 +190,12 @@ __global__ void __launch_bounds__(kEventThreads) k_bin_count_batch(const BatchHd
 
 // binning, pass 2: a block reserves, per tile, one range of slots for its
 // super-chunk's events (one global atomic per tile) and places them there (or
-// places them at their stable band slots)
-__global__ void __launch_bounds__(kEventThreads) k_bin_scatter_batch(const BatchHdr* h, const Win* tab,
+// places them at their stable band slots).  The scatter and the pixel passes
+// are held to 64 registers: in the batched step their blocks share the SMs
+// with the event kernels' (64 registers, four blocks per SM), and at 128 / 80
+// registers they took the register file of two event blocks each (1267
+// against 1279-1285 Mev/s for the 64-window step at 6 x 2).
+__global__ void __launch_bounds__(kEventThreads, 4) k_bin_scatter_batch(const BatchHdr* h, const Win* tab,
                                                                       const long long* sstart, int w0, int w1)
 {
     __shared__ int hist[kMaxBinTiles];
@@ -504,7 +508,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_adjoint_tiles_batch(const B
 }
 
 // loss pass 1 per tile; the block completing a window's last tile runs pass 2
-__global__ void __launch_bounds__(256) k_loss_batch(const BatchHdr* h, const Win* tab, const int* lstart, int w0,
+__global__ void __launch_bounds__(256, 4) k_loss_batch(const BatchHdr* h, const Win* tab, const int* lstart, int w0,
                                                     int w1)
 {
     w1 = clamp_end(h, w1);
@@ -529,7 +533,7 @@ __global__ void __launch_bounds__(256) k_loss_batch(const BatchHdr* h, const Win
 // dL/dflow folded from the quad accumulators, and the depth / ego gradient per
 // tile (the loss pass's tiles); the block completing a window's last tile
 // reduces the six ego sums
-__global__ void __launch_bounds__(256, 3) k_grad_batch(const BatchHdr* h, const Win* tab, const int* lstart, int w0,
+__global__ void __launch_bounds__(256, 4) k_grad_batch(const BatchHdr* h, const Win* tab, const int* lstart, int w0,
                                                     int w1)
 {
     w1 = clamp_end(h, w1);
