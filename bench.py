@@ -408,6 +408,7 @@ class Batch:
                 self.items.append((w, ws, ev, rho, ego, out, loss))
                 dev_wins.append({"cam": w.cam, "ev": ev, "inv_depth": rho, "ego": ego, "dt": w.dt})
         self.dloss = torch.ones(1, device=device)
+        self.dev_wins = dev_wins
         self.plan = cm.BatchPlan(dev_wins, cm.loss_cfg(wins[0].nbins, wins[0].ref_mode, cm.SPLAT_ATOMIC,
                                                        store_warps=store_warps), device)
         self.events = sum(w.events.n for w in wins)
@@ -572,6 +573,7 @@ def run_ours(args):
         c, g = schedule[0], schedule[1]
         splat_cmp["batched_iid"] = compare_batched_splats(
             batch, {"direct_bands": (c, g, 2), "direct_given_order": (c, g, 0), "smem_tiles": (c, g, 3)})
+        splat_cmp["batched_iid"]["deterministic_sort"] = compare_deterministic(batch)
         batch.plan.set_schedule(*schedule)
         from paper_2412_06359_gb300 import synth as _synth
         mot = Batch(_synth.batch_windows_motion(8), dev)
@@ -765,6 +767,28 @@ def compare_batched_splats(batch, schedules, reps: int = 5):
         z.record()
         z.synchronize()
         out[name] = {"schedule": list(sched), "mev_s": batch.events * reps / (a.elapsed_time(z) * 1e-3) / 1e6}
+    return out
+
+
+def compare_deterministic(batch, reps: int = 3):
+    """The batched plan in its deterministic mode (CM_SPLAT_SORT: the windows one
+    after another through the sort path, the same bits on every run) on the
+    same windows: device time of `reps` replays, in Mev/s."""
+    import torch
+    cm = batch.cm
+    w0 = batch.wins[0]
+    plan = cm.BatchPlan(batch.dev_wins, cm.loss_cfg(w0.nbins, w0.ref_mode, cm.SPLAT_SORT), batch.dev)
+    plan.run()
+    torch.cuda.synchronize()
+    a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        plan.run()
+    z.record()
+    z.synchronize()
+    out = {"schedule": list(plan.schedule()), "mev_s": batch.events * reps / (a.elapsed_time(z) * 1e-3) / 1e6}
+    del plan
+    torch.cuda.empty_cache()
     return out
 
 

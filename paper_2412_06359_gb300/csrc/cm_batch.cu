@@ -39,6 +39,7 @@
 #include "cm_bands.cuh"
 #include "cm_batch_kernels.cuh"
 #include "cm_launch.h"
+#include "cm_sort.h"
 
 
 static_assert(cmk::kMaxRefs >= CM_MAX_BINS + 1, "per-reference shared arrays hold every reference");
@@ -95,6 +96,7 @@ int refs_of(const cm_loss_cfg& c) { return c.ref_mode == CM_REF_END ? 1 : c.nbin
 // device bytes of the per-window slabs for a list of windows
 struct Need {
     size_t iwe, flow, dflow, quad, part, stat, dego, bins, warp;
+    cmk::SortSizes sort;  // the deterministic mode's sort buffers, sized for the largest window (else zero)
 };
 
 bool window_ok(const cm_window& w)
@@ -117,7 +119,9 @@ bool cfg_ok(const cm_loss_cfg* cfg)
 {
     if (!cfg || cfg->nbins < 1 || cfg->nbins > CM_MAX_BINS) return false;
     if (cfg->ref_mode != CM_REF_END && cfg->ref_mode != CM_REF_ALL_EDGES) return false;
-    if (cfg->splat != CM_SPLAT_AUTO && cfg->splat != CM_SPLAT_ATOMIC && cfg->splat != CM_SPLAT_TILES) return false;
+    if (cfg->splat != CM_SPLAT_AUTO && cfg->splat != CM_SPLAT_ATOMIC && cfg->splat != CM_SPLAT_TILES &&
+        cfg->splat != CM_SPLAT_SORT)
+        return false;
     return (cfg->store_warps == 0 || cfg->store_warps == 1) && std::isfinite(cfg->eps);
 }
 
@@ -139,6 +143,15 @@ Need need_of(const cm_window* wins, int32_t nwin, const cm_loss_cfg& cfg)
         n.stat += (size_t)R;
         n.dego += (size_t)loss_tiles_for(HW) * 6 * sizeof(float);
         if (cfg.store_warps) n.warp += up256((size_t)(cfg.nbins + 1) * wins[i].ev.n * sizeof(float2));
+    }
+    if (cfg.splat == CM_SPLAT_SORT) {
+        int64_t mn = 0;
+        size_t mhw = 0;
+        for (int i = 0; i < nwin; ++i) {
+            mn = std::max(mn, wins[i].ev.n);
+            mhw = std::max(mhw, (size_t)wins[i].cam.width * wins[i].cam.height);
+        }
+        n.sort = cmk::sort_sizes(mn, R, cfg.nbins, 1, mhw);
     }
     return n;
 }
@@ -192,7 +205,9 @@ WinScratch win_scratch(size_t HW, int R)
 struct Layout {
     size_t hdr, tab, cstart, sstart, lstart, pstart, pseg, table_end;  // the uploaded region [0, table_end)
     size_t pq;  // persistent step: queue head, error word, [windows][kPCounters] counters (zeroed per run)
-    size_t iwe, flow, dflow, quad, part, norm, lr, nnz, dego, sync, bins, warp, total;
+    size_t iwe, flow, dflow, quad, part, norm, lr, nnz, dego, sync, bins, warp;
+    size_t ska, skb, sva, svb, spay, shist, spart, sstart_keys;  // deterministic mode: sort buffers
+    size_t total;
 };
 
 Layout layout_of(int cap, const Need& n)
@@ -238,6 +253,23 @@ Layout layout_of(int cap, const Need& n)
     o = up256(o + n.bins);
     L.warp = o;
     o = up256(o + n.warp);
+    const cmk::SortSizes& z = n.sort;
+    L.ska = o;
+    o = up256(o + z.entries * 4);
+    L.skb = o;
+    o = up256(o + z.entries * 4);
+    L.sva = o;
+    o = up256(o + z.entries * 4);
+    L.svb = o;
+    o = up256(o + z.entries * 4);
+    L.spay = o;
+    o = up256(o + z.entries * 16);
+    L.shist = o;
+    o = up256(o + z.hist * 4);
+    L.spart = o;
+    o = up256(o + z.part * 4);
+    L.sstart_keys = o;
+    o = up256(o + z.start * 4);
     L.total = o;
     return L;
 }
@@ -277,6 +309,7 @@ struct cm_batch {
     int grid_splat = 0;  // the splat: eight blocks per SM in waves (its reductions need no reply)
     cm_batch_schedule sched{2, 1, 0};
     int stall_window = -1;             // test hook: the persistent queue leaves out this window's prep pass
+    long long graph_kernels = 0;       // kernel nodes of the captured graph
     bool stale = true;                 // the graph must be (re)captured before the next replay
     cudaStream_t streams[kMaxChains] = {};
     cudaEvent_t fork = nullptr;
@@ -411,6 +444,15 @@ int stage_windows(cm_batch* b, const cm_window* wins, int32_t nwin)
     if (n.iwe > c.iwe || n.dflow > c.dflow || n.quad > c.quad || n.part > c.part ||
         n.stat > c.stat || n.dego > c.dego || n.warp > c.warp)
         return CM_ENOMEM;
+    const bool sorted = b->cfg.splat == CM_SPLAT_SORT;
+    if (sorted) {
+        // the deterministic mode: the plan's own buffers only, sort buffers for its largest window
+        for (int i = 0; i < nwin; ++i)
+            if (wins[i].scratch) return CM_EINVAL;
+        if (n.sort.entries > c.sort.entries || n.sort.hist > c.sort.hist || n.sort.part > c.sort.part ||
+            n.sort.start > c.sort.start)
+            return CM_ENOMEM;
+    }
     // the previous upload must have left the staging buffer before it is rewritten
     if (cudaEventSynchronize(b->staged) != cudaSuccess) return CM_ECUDA;
     unsigned char* s = b->staging;
@@ -554,6 +596,22 @@ int stage_windows(cm_batch* b, const cm_window* wins, int32_t nwin)
             d.ego = w.ego6;
             d.drho = w.dinv_depth;
             d.dego = w.dego6;
+        }
+        if (sorted) {
+            // the single-window layout for the sort path: [R][H][W] float4 images in the
+            // image slab; for depth input the flow in the quad slab's first half and
+            // dL/dflow (unless the caller takes it) in its second half
+            float2* qa = reinterpret_cast<float2*>(const_cast<cmk::FQ*>(d.fq));
+            float2* qb = reinterpret_cast<float2*>(d.dq);
+            d.iwe_split = 0;
+            d.fq = nullptr;
+            d.dq = nullptr;
+            d.tile_cnt = nullptr;
+            if (!w.flow) {
+                d.flow = qa;
+                if (!d.dflow) d.dflow = qb;
+            }
+            d.pix_tiles = d.loss_tiles;  // the gradient pass's partials use the loss tiles' slab
         }
         b->stat_lr[i] = d.loss_r;
         b->stat_nnz[i] = d.nnz_r;
@@ -746,8 +804,28 @@ int capture(cm_batch* b)
             cudaEventRecordWithFlags(p.eb, s0, cudaEventRecordExternal);
         }
     }
+    const bool sorted = b->cfg.splat == CM_SPLAT_SORT;
+    if (sorted) {
+        // the deterministic mode: the windows one after another through the
+        // single-window sort path (every sum in a fixed order), on one stream
+        const Win* ht = reinterpret_cast<const Win*>(b->staging + b->L.tab);
+        cmk::SortBufs sb{reinterpret_cast<uint32_t*>(b->base + b->L.ska), reinterpret_cast<uint32_t*>(b->base + b->L.skb),
+                         reinterpret_cast<uint32_t*>(b->base + b->L.sva), reinterpret_cast<uint32_t*>(b->base + b->L.svb),
+                         reinterpret_cast<float4*>(b->base + b->L.spay), reinterpret_cast<uint32_t*>(b->base + b->L.shist),
+                         reinterpret_cast<uint32_t*>(b->base + b->L.spart),
+                         reinterpret_cast<uint32_t*>(b->base + b->L.sstart_keys)};
+        const int sms = cmk::sm_count_current();
+        for (int i = 0; i < b->nwin && ok; ++i) {
+            const Win& d = ht[i];
+            if (d.rho) ok = cmk::launch_flow(d, s0) == cudaSuccess;
+            ok = ok && cmk::sort_splat(d, sb, sms, s0) == cudaSuccess;
+            ok = ok && cmk::launch_loss(d, s0) == cudaSuccess;
+            ok = ok && cmk::sort_adjoint(d, sb, sms, s0) == cudaSuccess;
+            if (d.rho && (d.drho || d.dego)) ok = ok && cmk::launch_depth_ego(d, s0) == cudaSuccess;
+        }
+    }
     for (const Group& g : groups) {
-        if (b->sched.persist > 0) break;
+        if (b->sched.persist > 0 || sorted) break;
         cudaStream_t s = b->streams[g.chain];
         for (int pi = 0; pi < kPhases && ok; ++pi) {
             const int ph = kPhaseOrder[pi];
@@ -809,6 +887,11 @@ int capture(cm_batch* b)
     }
     for (const ProfNode& p : b->prof)
         if (!p.na || !p.nb) return CM_ECUDA;
+    b->graph_kernels = 0;
+    for (cudaGraphNode_t n : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(n, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++b->graph_kernels;
+    }
     b->stale = false;
     return CM_OK;
 }
@@ -893,7 +976,7 @@ int run_plan(cm_batch* b, cudaStream_t s)
         b->swapped = false;
     }
     if (cudaGraphLaunch(b->exec, s) != cudaSuccess) return CM_ECUDA;
-    cmk::count_launches((long long)b->prof.size());
+    cmk::count_launches(b->graph_kernels);
     if (prof)
         for (size_t i = 0; i < b->prof.size(); ++i)
             cmk::profile_push(kPhaseName[b->prof[i].phase], ev[2 * i], ev[2 * i + 1]);
@@ -959,6 +1042,7 @@ int cm_batch_create(void* dev_mem, size_t bytes, const cm_window* wins, int32_t 
     b->L = L;
     b->sched = nwin > 1 ? cm_batch_schedule{2, 1, 0} : cm_batch_schedule{1, 0, 0};
     if (cfg->splat == CM_SPLAT_TILES) b->sched.bin = 3;  // the shared-memory tile strategy
+    if (cfg->splat == CM_SPLAT_SORT) b->sched = cm_batch_schedule{1, 1, 0, 0};  // deterministic: one window at a time
     int st = CM_OK;
     if (cudaMallocHost(reinterpret_cast<void**>(&b->staging), L.table_end) != cudaSuccess) st = CM_ENOMEM;
     if (!st && cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming) != cudaSuccess) st = CM_ECUDA;
@@ -1029,6 +1113,9 @@ int cm_batch_set_schedule(cm_batch* b, const cm_batch_schedule* s)
     if (s->persist < 0 || s->persist > kMaxPersist) return CM_EINVAL;
     // the persistent step: one kernel over every window, events in their order or grouped by band
     if (s->persist > 0 && (s->chains != 1 || s->group != 0 || (s->bin != 0 && s->bin != 2))) return CM_EINVAL;
+    // the deterministic mode runs the windows one after another
+    if (b->cfg.splat == CM_SPLAT_SORT && (s->chains != 1 || s->group != 1 || s->bin != 0 || s->persist != 0))
+        return CM_EINVAL;
     return apply_schedule(b, *s);
 }
 
@@ -1048,6 +1135,10 @@ int cm_batch_run(cm_batch* b, void* stream)
 int cm_batch_autotune(cm_batch* b, void* stream, cm_batch_schedule* chosen)
 {
     if (!b) return CM_EINVAL;
+    if (b->cfg.splat == CM_SPLAT_SORT) {  // the deterministic mode has one schedule
+        if (chosen) *chosen = b->sched;
+        return CM_OK;
+    }
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const TuneKey k = key_of(b);
     for (const auto& e : g_tuned) {

@@ -425,3 +425,37 @@ def test_persistent_wait_gives_up_reports_and_the_plan_recovers():
     plan.set_schedule(6, 1, 2, 0)  # the graph path has no device waits
     plan.run()
     assert plan.status() == C.CM_OK
+
+
+def _bitwise_equal(a, b):
+    for k in a:
+        x, y = np.asarray(a[k]), np.asarray(b[k])
+        assert x.dtype == y.dtype and x.shape == y.shape and x.tobytes() == y.tobytes(), k
+
+
+@pytest.mark.parametrize("want_dflow", [False, True])
+def test_batched_deterministic_mode_is_bit_reproducible_and_matches_the_oracle(want_dflow):
+    # CM_SPLAT_SORT in a batch: the windows one after another through the sort
+    # path, every sum in a fixed order; the same bits on every replay and after
+    # the windows are set again, and the oracle's verdict on every window
+    from paper_2412_06359_gb300 import _capi as C
+    cm = gpu_lib()
+    wins = _mixed_windows(6, 101)
+    wins.append(synth.motion_window(np.random.default_rng(102), 90, 70, 4000))  # a flow-input window too
+    dev = _dev_windows(cm, wins)
+    plan = cm.BatchPlan(dev, cm.loss_cfg(10, cm.REF_ALL, cm.SPLAT_SORT), want_dflow=want_dflow)
+    assert plan.schedule() == (1, 1, 0, 0)
+    assert plan.autotune() == (1, 1, 0, 0)
+    with pytest.raises(C.CMError):
+        plan.set_schedule(6, 2, 2, 0)
+    plan.run()
+    first = plan_results(plan, wins)
+    for _ in range(2):
+        plan.run()
+    for a, b in zip(first, plan_results(plan, wins)):
+        _bitwise_equal(a, b)
+    plan.set_windows(dev)
+    plan.run()
+    for a, b in zip(first, plan_results(plan, wins)):
+        _bitwise_equal(a, b)
+    check_windows(wins, batch_runner(splat=cm.SPLAT_SORT, want_dflow=want_dflow), full=first)
