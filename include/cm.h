@@ -75,10 +75,11 @@ extern "C" {
 #define CM_SPLAT_AUTO 0     /* pick by the autotuner's cached choice (atomic until tuned) */
 #define CM_SPLAT_ATOMIC 1   /* FP32 vector atomics into the IWE (order of additions not fixed) */
 #define CM_SPLAT_SORT 2     /* deterministic: sort contributions by pixel, segmented sums.  In a batched
-                               plan the windows run one after another through this path (schedule fixed
-                               to 1 chain x 1 window; cm_batch_set_schedule refuses any other with
-                               CM_EINVAL), windows with their own scratch are refused, and the outputs are
-                               the same bits on every run */
+                               plan each window runs whole through this path, one window at a time on
+                               each of 1..8 chains (schedule {chains, 1, 0, 0}, default 8 chains; other
+                               schedules are refused with CM_EINVAL; the autotuner picks the chains),
+                               windows with their own scratch are refused, and the outputs are the same
+                               bits on every run whatever the number of chains */
 #define CM_SPLAT_TILES 3    /* batched plans only: accumulate each 32x32 tile in shared memory, flush once
                                (warp-aggregated shared-memory atomics; schedule bin 3).  The single-window
                                entry points refuse it (CM_EINVAL) */

@@ -56,6 +56,7 @@ const char* const kPhaseName[kPhases + 1] = {"k_prep_batch",        "k_bin_count
                                              "k_adjoint_tiles_batch", "k_step_persistent"};
 constexpr int kPersistentPhase = kPhases;  // the name of the persistent step's node
 constexpr int kMaxPersist = 8;             // largest persist value: a queue staggered by 7 phases
+constexpr int kSortChains = 8;             // deterministic mode: concurrent chains (one set of sort buffers each)
 // the order of the phases in a window group's chain (the tile phases run with bin 3 only)
 constexpr int kPhaseOrder[kPhases] = {0, 1, 2, 3, 7, 4, 5, 8, 6};
 constexpr int kSyncInts = 4;  // per window: loss, gradient and binning counters (one spare)
@@ -206,7 +207,8 @@ struct Layout {
     size_t hdr, tab, cstart, sstart, lstart, pstart, pseg, table_end;  // the uploaded region [0, table_end)
     size_t pq;  // persistent step: queue head, error word, [windows][kPCounters] counters (zeroed per run)
     size_t iwe, flow, dflow, quad, part, norm, lr, nnz, dego, sync, bins, warp;
-    size_t ska, skb, sva, svb, spay, shist, spart, sstart_keys;  // deterministic mode: sort buffers
+    size_t ska, skb, sva, svb, spay, shist, spart, sstart_keys;  // deterministic mode: chain 0's sort buffers
+    size_t sort_stride;                                         // bytes from one chain's set to the next
     size_t total;
 };
 
@@ -253,7 +255,9 @@ Layout layout_of(int cap, const Need& n)
     o = up256(o + n.bins);
     L.warp = o;
     o = up256(o + n.warp);
+    // the deterministic mode: one set of sort buffers per chain (kSortChains sets)
     const cmk::SortSizes& z = n.sort;
+    const size_t sort_begin = o;
     L.ska = o;
     o = up256(o + z.entries * 4);
     L.skb = o;
@@ -270,6 +274,8 @@ Layout layout_of(int cap, const Need& n)
     o = up256(o + z.part * 4);
     L.sstart_keys = o;
     o = up256(o + z.start * 4);
+    L.sort_stride = o - sort_begin;
+    o += (kSortChains - 1) * L.sort_stride;
     L.total = o;
     return L;
 }
@@ -809,19 +815,24 @@ int capture(cm_batch* b)
         // the deterministic mode: the windows one after another through the
         // single-window sort path (every sum in a fixed order), on one stream
         const Win* ht = reinterpret_cast<const Win*>(b->staging + b->L.tab);
-        cmk::SortBufs sb{reinterpret_cast<uint32_t*>(b->base + b->L.ska), reinterpret_cast<uint32_t*>(b->base + b->L.skb),
-                         reinterpret_cast<uint32_t*>(b->base + b->L.sva), reinterpret_cast<uint32_t*>(b->base + b->L.svb),
-                         reinterpret_cast<float4*>(b->base + b->L.spay), reinterpret_cast<uint32_t*>(b->base + b->L.shist),
-                         reinterpret_cast<uint32_t*>(b->base + b->L.spart),
-                         reinterpret_cast<uint32_t*>(b->base + b->L.sstart_keys)};
         const int sms = cmk::sm_count_current();
-        for (int i = 0; i < b->nwin && ok; ++i) {
-            const Win& d = ht[i];
-            if (d.rho) ok = cmk::launch_flow(d, s0) == cudaSuccess;
-            ok = ok && cmk::sort_splat(d, sb, sms, s0) == cudaSuccess;
-            ok = ok && cmk::launch_loss(d, s0) == cudaSuccess;
-            ok = ok && cmk::sort_adjoint(d, sb, sms, s0) == cudaSuccess;
-            if (d.rho && (d.drho || d.dego)) ok = ok && cmk::launch_depth_ego(d, s0) == cudaSuccess;
+        for (const Group& g : groups) {  // one window per group, the groups spread over the chains
+            if (!ok) break;
+            cudaStream_t s = b->streams[g.chain];
+            char* o = b->base + (size_t)g.chain * b->L.sort_stride;
+            cmk::SortBufs sb{reinterpret_cast<uint32_t*>(o + b->L.ska), reinterpret_cast<uint32_t*>(o + b->L.skb),
+                             reinterpret_cast<uint32_t*>(o + b->L.sva), reinterpret_cast<uint32_t*>(o + b->L.svb),
+                             reinterpret_cast<float4*>(o + b->L.spay), reinterpret_cast<uint32_t*>(o + b->L.shist),
+                             reinterpret_cast<uint32_t*>(o + b->L.spart),
+                             reinterpret_cast<uint32_t*>(o + b->L.sstart_keys)};
+            for (int i = g.w0; i < g.w1 && ok; ++i) {
+                const Win& d = ht[i];
+                if (d.rho) ok = cmk::launch_flow(d, s) == cudaSuccess;
+                ok = ok && cmk::sort_splat(d, sb, sms, s) == cudaSuccess;
+                ok = ok && cmk::launch_loss(d, s) == cudaSuccess;
+                ok = ok && cmk::sort_adjoint(d, sb, sms, s) == cudaSuccess;
+                if (d.rho && (d.drho || d.dego)) ok = ok && cmk::launch_depth_ego(d, s) == cudaSuccess;
+            }
         }
     }
     for (const Group& g : groups) {
@@ -986,7 +997,7 @@ int run_plan(cm_batch* b, cudaStream_t s)
 // autotuner cache: (window count, first window's size, references, events
 // bucket) -> schedule, for the life of the process
 struct TuneKey {
-    int nwin, W, H, R, ebucket;
+    int nwin, W, H, R, ebucket, sorted;
 };
 std::vector<std::pair<TuneKey, cm_batch_schedule>> g_tuned;
 
@@ -997,7 +1008,7 @@ TuneKey key_of(const cm_batch* b)
     int e = 0;
     while ((1LL << e) < c + 1) ++e;
     const Win* tab = reinterpret_cast<const Win*>(b->staging + b->L.tab);
-    return {b->nwin, tab[0].W, tab[0].H, refs_of(b->cfg), e};
+    return {b->nwin, tab[0].W, tab[0].H, refs_of(b->cfg), e, b->cfg.splat == CM_SPLAT_SORT ? 1 : 0};
 }
 
 }  // namespace
@@ -1042,7 +1053,8 @@ int cm_batch_create(void* dev_mem, size_t bytes, const cm_window* wins, int32_t 
     b->L = L;
     b->sched = nwin > 1 ? cm_batch_schedule{2, 1, 0} : cm_batch_schedule{1, 0, 0};
     if (cfg->splat == CM_SPLAT_TILES) b->sched.bin = 3;  // the shared-memory tile strategy
-    if (cfg->splat == CM_SPLAT_SORT) b->sched = cm_batch_schedule{1, 1, 0, 0};  // deterministic: one window at a time
+    if (cfg->splat == CM_SPLAT_SORT)  // deterministic: one window at a time on each chain
+        b->sched = cm_batch_schedule{nwin < kSortChains ? nwin : kSortChains, 1, 0, 0};
     int st = CM_OK;
     if (cudaMallocHost(reinterpret_cast<void**>(&b->staging), L.table_end) != cudaSuccess) st = CM_ENOMEM;
     if (!st && cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming) != cudaSuccess) st = CM_ECUDA;
@@ -1113,8 +1125,8 @@ int cm_batch_set_schedule(cm_batch* b, const cm_batch_schedule* s)
     if (s->persist < 0 || s->persist > kMaxPersist) return CM_EINVAL;
     // the persistent step: one kernel over every window, events in their order or grouped by band
     if (s->persist > 0 && (s->chains != 1 || s->group != 0 || (s->bin != 0 && s->bin != 2))) return CM_EINVAL;
-    // the deterministic mode runs the windows one after another
-    if (b->cfg.splat == CM_SPLAT_SORT && (s->chains != 1 || s->group != 1 || s->bin != 0 || s->persist != 0))
+    // the deterministic mode runs one window at a time on each of up to kSortChains chains
+    if (b->cfg.splat == CM_SPLAT_SORT && (s->chains > kSortChains || s->group != 1 || s->bin != 0 || s->persist != 0))
         return CM_EINVAL;
     return apply_schedule(b, *s);
 }
@@ -1135,28 +1147,29 @@ int cm_batch_run(cm_batch* b, void* stream)
 int cm_batch_autotune(cm_batch* b, void* stream, cm_batch_schedule* chosen)
 {
     if (!b) return CM_EINVAL;
-    if (b->cfg.splat == CM_SPLAT_SORT) {  // the deterministic mode has one schedule
-        if (chosen) *chosen = b->sched;
-        return CM_OK;
-    }
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const TuneKey k = key_of(b);
     for (const auto& e : g_tuned) {
         const TuneKey& q = e.first;
-        if (q.nwin == k.nwin && q.W == k.W && q.H == k.H && q.R == k.R && q.ebucket == k.ebucket) {
+        if (q.nwin == k.nwin && q.W == k.W && q.H == k.H && q.R == k.R && q.ebucket == k.ebucket &&
+            q.sorted == k.sorted) {
             const int st = apply_schedule(b, e.second);
             if (chosen) *chosen = b->sched;
             return st;
         }
     }
     std::vector<cm_batch_schedule> cand;
-    for (int bin = 0; bin < 4; ++bin)
-        for (const auto& cg : {std::pair<int, int>{1, 0}, {1, 1}, {2, 1}, {3, 1}, {4, 1}, {2, 2}, {4, 2}, {6, 1},
-                               {6, 2}, {8, 1}, {8, 2}})
-            cand.push_back(cm_batch_schedule{cg.first, cg.second, bin, 0});
-    if (b->nwin == 1) cand = {{1, 0, 0, 0}, {1, 0, 1, 0}, {1, 0, 2, 0}, {1, 0, 3, 0}};
-    for (int bin : {0, 2})  // the persistent step, its queue staggered by 0, 1, 2 or 7 phases
-        for (int k : {1, 2, 3, 8}) cand.push_back(cm_batch_schedule{1, 0, bin, k});
+    if (k.sorted) {  // the deterministic mode: 1..kSortChains chains of one window at a time
+        for (int c = 1; c <= kSortChains && c <= b->nwin; ++c) cand.push_back(cm_batch_schedule{c, 1, 0, 0});
+    } else {
+        for (int bin = 0; bin < 4; ++bin)
+            for (const auto& cg : {std::pair<int, int>{1, 0}, {1, 1}, {2, 1}, {3, 1}, {4, 1}, {2, 2}, {4, 2}, {6, 1},
+                                   {6, 2}, {8, 1}, {8, 2}})
+                cand.push_back(cm_batch_schedule{cg.first, cg.second, bin, 0});
+        if (b->nwin == 1) cand = {{1, 0, 0, 0}, {1, 0, 1, 0}, {1, 0, 2, 0}, {1, 0, 3, 0}};
+        for (int bin : {0, 2})  // the persistent step, its queue staggered by 0, 1, 2 or 7 phases
+            for (int p : {1, 2, 3, 8}) cand.push_back(cm_batch_schedule{1, 0, bin, p});
+    }
     cudaEvent_t a = nullptr, z = nullptr;
     if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&z) != cudaSuccess) return CM_ECUDA;
     float best = 1e30f;

@@ -444,17 +444,28 @@ def test_batched_deterministic_mode_is_bit_reproducible_and_matches_the_oracle(w
     wins.append(synth.motion_window(np.random.default_rng(102), 90, 70, 4000))  # a flow-input window too
     dev = _dev_windows(cm, wins)
     plan = cm.BatchPlan(dev, cm.loss_cfg(10, cm.REF_ALL, cm.SPLAT_SORT), want_dflow=want_dflow)
-    assert plan.schedule() == (1, 1, 0, 0)
-    assert plan.autotune() == (1, 1, 0, 0)
-    with pytest.raises(C.CMError):
-        plan.set_schedule(6, 2, 2, 0)
+    assert plan.schedule() == (min(len(wins), 8), 1, 0, 0)  # one window at a time on each chain
+    for bad in [(9, 1, 0, 0), (2, 2, 0, 0), (2, 1, 2, 0), (1, 0, 0, 1)]:
+        with pytest.raises(C.CMError):
+            plan.set_schedule(*bad)
     plan.run()
     first = plan_results(plan, wins)
     for _ in range(2):
         plan.run()
     for a, b in zip(first, plan_results(plan, wins)):
         _bitwise_equal(a, b)
+    # the same bits whatever the number of chains, after the windows are set again, and autotuned
+    for chains in (1, 3):
+        plan.set_schedule(chains, 1, 0, 0)
+        plan.run()
+        for a, b in zip(first, plan_results(plan, wins)):
+            _bitwise_equal(a, b)
     plan.set_windows(dev)
+    plan.run()
+    for a, b in zip(first, plan_results(plan, wins)):
+        _bitwise_equal(a, b)
+    c, g, bn, p = plan.autotune()
+    assert 1 <= c <= 8 and (g, bn, p) == (1, 0, 0)
     plan.run()
     for a, b in zip(first, plan_results(plan, wins)):
         _bitwise_equal(a, b)
