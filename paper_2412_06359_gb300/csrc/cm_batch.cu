@@ -146,12 +146,19 @@ Need need_of(const cm_window* wins, int32_t nwin, const cm_loss_cfg& cfg)
         if (cfg.store_warps) n.warp += up256((size_t)(cfg.nbins + 1) * wins[i].ev.n * sizeof(float2));
     }
     if (cfg.splat == CM_SPLAT_SORT) {
+        // the deterministic mode runs one window at a time on each of at most
+        // kSortChains chains: the windows of a chain share one image slab and
+        // one quad slab (the largest window's size), and no events are grouped
         int64_t mn = 0;
         size_t mhw = 0;
         for (int i = 0; i < nwin; ++i) {
             mn = std::max(mn, wins[i].ev.n);
             mhw = std::max(mhw, (size_t)wins[i].cam.width * wins[i].cam.height);
         }
+        const size_t slots = (size_t)std::min(nwin, kSortChains);
+        n.iwe = slots * up256((size_t)R * mhw * sizeof(float4));
+        n.quad = slots * 2 * mhw * sizeof(cmk::FQ);
+        n.bins = 0;
         n.sort = cmk::sort_sizes(mn, R, cfg.nbins, 1, mhw);
     }
     return n;
