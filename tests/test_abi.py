@@ -132,3 +132,27 @@ def test_entry_points_validate_before_launch(lib):
             C.cm_warp_splat(c, ev, fake, 2, cfg, None, fake, None)  # n_flow_bins neither 1 nor B
     finally:
         C.cm_workspace_destroy(ws)
+
+
+def test_batch_query_and_status_validate_on_the_host(lib):
+    # sizes only (no device memory is touched): the deterministic mode holds
+    # one image and quad slab per chain (at most eight), so a 64-window plan
+    # needs far less than the atomic plan's slab per window, plus its sort
+    # buffers; the status and stall-hook calls refuse a null plan
+    fake = 1 << 40
+    wins = []
+    for i in range(64):
+        ev = C.cm_events(fake, fake, fake, fake, 5000 + 1000 * i, 0.0, 0.01)
+        wins.append(C.cm_window(cam(640, 480), ev, None, fake, fake, 0.01, fake, fake, None, fake, fake, None))
+    atomic = C.cm_batch_query(wins, C.cm_loss_cfg(10, 1, 1, 0, 1e-9))
+    sort = C.cm_batch_query(wins, C.cm_loss_cfg(10, 1, 2, 0, 1e-9))
+    images = 64 * 11 * 640 * 480 * 16
+    assert atomic > images
+    assert sort < atomic / 2
+    one = C.cm_batch_query(wins[:1], C.cm_loss_cfg(10, 1, 2, 0, 1e-9))
+    assert one < sort
+    assert lib.cm_batch_status(None, None) == C.CM_EINVAL
+    assert lib.cm_batch_inject_stall(None, 0) == C.CM_EINVAL
+    with pytest.raises(C.CMError) as x:  # a splat strategy batches do not know
+        C.cm_batch_query(wins, C.cm_loss_cfg(10, 1, 7, 0, 1e-9))
+    assert x.value.status == C.CM_EINVAL
