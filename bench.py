@@ -603,7 +603,7 @@ def run_ours(args):
     # ---- a short serving leg (32 streams, 0.5x and 1x the arrival rate, 3 runs each) ----
     serve = None
     if rank == 0 and world == 1 and not args.no_serve:
-        serve = serve_leg([0.5, 1.0], 2.0, 3, args.serve_lanes, args.serve_batch, args.serve_group)
+        serve = serve_leg([0.5, 0.9, 1.0], 2.0, 3, args.serve_lanes, args.serve_batch, args.serve_group)
 
     # ---- CPU oracle baseline (rank 0 at N = 1 only) ----
     cpu = cpu_all = None

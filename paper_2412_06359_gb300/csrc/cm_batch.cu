@@ -1171,7 +1171,7 @@ int cm_batch_autotune(cm_batch* b, void* stream, cm_batch_schedule* chosen)
     } else {
         for (int bin = 0; bin < 4; ++bin)
             for (const auto& cg : {std::pair<int, int>{1, 0}, {1, 1}, {2, 1}, {3, 1}, {4, 1}, {2, 2}, {4, 2}, {6, 1},
-                                   {6, 2}, {8, 1}, {8, 2}})
+                                   {6, 2}, {7, 2}, {8, 1}, {8, 2}})
                 cand.push_back(cm_batch_schedule{cg.first, cg.second, bin, 0});
         if (b->nwin == 1) cand = {{1, 0, 0, 0}, {1, 0, 1, 0}, {1, 0, 2, 0}, {1, 0, 3, 0}};
         for (int bin : {0, 2})  // the persistent step, its queue staggered by 0, 1, 2 or 7 phases
