@@ -383,7 +383,7 @@ typedef struct {
 } cm_batch_schedule;
 int cm_batch_set_schedule(cm_batch* plan, const cm_batch_schedule* schedule);
 int cm_batch_get_schedule(const cm_batch* plan, cm_batch_schedule* schedule);
-/* Autotuner: times each candidate schedule on the plan's own windows (three
+/* Autotuner: times each candidate schedule on the plan's own windows (five
  * replays each, CUDA events on `stream`), keeps the fastest and remembers it
  * for plans of the same shape (window count, first window size, references,
  * event count to a power of two) for the life of the process.  Runs the plan

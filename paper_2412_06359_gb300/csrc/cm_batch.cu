@@ -1186,7 +1186,7 @@ int cm_batch_autotune(cm_batch* b, void* stream, cm_batch_schedule* chosen)
         if ((st = apply_schedule(b, c))) break;
         if ((st = run_plan(b, s))) break;  // capture + warm-up
         cudaEventRecord(a, s);
-        for (int r = 0; r < 3 && !st; ++r) st = run_plan(b, s);
+        for (int r = 0; r < 5 && !st; ++r) st = run_plan(b, s);
         cudaEventRecord(z, s);
         if (st || cudaEventSynchronize(z) != cudaSuccess) {
             st = st ? st : CM_ECUDA;
