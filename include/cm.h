@@ -386,7 +386,9 @@ int cm_batch_get_schedule(const cm_batch* plan, cm_batch_schedule* schedule);
 /* Autotuner: times each candidate schedule on the plan's own windows (five
  * replays each, CUDA events on `stream`), keeps the fastest and remembers it
  * for plans of the same shape (window count, first window size, references,
- * event count to a power of two) for the life of the process.  Runs the plan
+ * event count to a power of two, deterministic or not) for the life of the
+ * process.  In the deterministic mode (CM_SPLAT_SORT) the candidates are 1..8
+ * chains of one window at a time.  Runs the plan
  * several times (outputs are overwritten); synchronises `stream`. */
 int cm_batch_autotune(cm_batch* plan, void* stream, cm_batch_schedule* chosen);
 /* Device pointers to window `window`'s per-reference losses (float [R]) and
