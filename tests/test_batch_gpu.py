@@ -470,3 +470,19 @@ def test_batched_deterministic_mode_is_bit_reproducible_and_matches_the_oracle(w
     for a, b in zip(first, plan_results(plan, wins)):
         _bitwise_equal(a, b)
     check_windows(wins, batch_runner(splat=cm.SPLAT_SORT, want_dflow=want_dflow), full=first)
+
+
+def test_batched_deterministic_mode_many_bins_and_stored_warps():
+    # 20 bins (21 references) and the stored-warp backward in the deterministic
+    # mode: the same bits twice, the oracle's verdict on every window
+    cm = gpu_lib()
+    wins = [synth.depth_window(np.random.default_rng(9600 + i), W, H, n, nbins=20)
+            for i, (W, H, n) in enumerate([(120, 90, 3000), (160, 100, 5000), (64, 48, 0), (96, 72, 2500)])]
+    for sw in (False, True):
+        plan = cm.BatchPlan(_dev_windows(cm, wins), cm.loss_cfg(20, cm.REF_ALL, cm.SPLAT_SORT, store_warps=sw))
+        plan.run()
+        first = plan_results(plan, wins)
+        plan.run()
+        for a, b in zip(first, plan_results(plan, wins)):
+            _bitwise_equal(a, b)
+        check_windows(wins, batch_runner(B=20, splat=cm.SPLAT_SORT, store_warps=sw), full=first)
