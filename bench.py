@@ -985,7 +985,8 @@ def serve_leg(scales, seconds: float, reps: int, lanes: int, batch: int, group: 
         out["scales"][str(scale)] = {
             "offered_mev_s": runs[0]["offered_mev_s"], "requests": runs[0]["requests"],
             "served_mev_s": [r["throughput"] for r in runs], "p50_ms": [r["p50_ms"] for r in runs],
-            "p99_ms": p99, "p99_spread_ms": [min(p99), max(p99)], "mean_batch": [r["mean_batch"] for r in runs]}
+            "p99_ms": p99, "p99_spread_ms": [min(p99), max(p99)], "mean_batch": [r["mean_batch"] for r in runs],
+            "stats": [r["stats"] for r in runs]}
     if arr is not None and group > 0:
         r = one(arr, 0)
         out["given_order_last_scale"] = {"served_mev_s": r["throughput"], "p50_ms": r["p50_ms"],
