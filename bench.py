@@ -952,8 +952,10 @@ def serve_replay(srv, pools, arr):
     last = max(r.t_done for r, _ in res)
     ev = sum(n for _, n in res)
     sizes = [r.batch_size for r, _ in res]
+    slowest = int(np.argmax(lat))
     return {"requests": len(res), "events": int(ev), "throughput": ev / (last - first) / 1e6,
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "max_ms": float(lat[slowest]), "slowest_submitted_at_s": float(res[slowest][0].t_submit - first),
             "mean_batch": float(np.mean(sizes)), "offered_mev_s": ev / arr[-1][0] / 1e6 if arr else 0.0,
             "stats": {k: int(getattr(srv.stats(), k)) for k in ("batches", "evictions", "memory_waits",
                                                                  "pool_peak")}}
@@ -986,6 +988,7 @@ def serve_leg(scales, seconds: float, reps: int, lanes: int, batch: int, group: 
             "offered_mev_s": runs[0]["offered_mev_s"], "requests": runs[0]["requests"],
             "served_mev_s": [r["throughput"] for r in runs], "p50_ms": [r["p50_ms"] for r in runs],
             "p99_ms": p99, "p99_spread_ms": [min(p99), max(p99)], "mean_batch": [r["mean_batch"] for r in runs],
+            "max_ms": [r["max_ms"] for r in runs], "slowest_submitted_at_s": [r["slowest_submitted_at_s"] for r in runs],
             "stats": [r["stats"] for r in runs]}
     if arr is not None and group > 0:
         r = one(arr, 0)
