@@ -251,7 +251,7 @@ template <int MAXB>
 __global__ void __launch_bounds__(kEventThreads, MAXB <= 10 ? 4 : 2) k_splat_batch(const BatchHdr* h, const Win* tab,
                                                                 const long long* cstart, int w0, int w1)
 {
-    __shared__ float pts[kPointsSmem<MAXB> ? 2 * (MAXB + 1) * kEventThreads : 1];
+    __shared__ __align__(16) float pts[kPointsSmem<MAXB> ? 2 * (MAXB + 1) * kEventThreads : 1];
     w1 = clamp_end(h, w1);
     if (w0 >= w1) return;
     const long long cb = cstart[w0], ce = cstart[w1];
@@ -270,7 +270,7 @@ template <int MAXB>
 __global__ void __launch_bounds__(kEventThreads, MAXB <= 10 ? 4 : 2) k_adjoint_batch(const BatchHdr* h, const Win* tab,
                                                                   const long long* cstart, int w0, int w1)
 {
-    __shared__ float pts[kPointsSmem<MAXB> ? 2 * (MAXB + 1) * kEventThreads : 1];
+    __shared__ __align__(16) float pts[kPointsSmem<MAXB> ? 2 * (MAXB + 1) * kEventThreads : 1];
     w1 = clamp_end(h, w1);
     if (w0 >= w1) return;
     const long long cb = cstart[w0], ce = cstart[w1];
@@ -635,7 +635,7 @@ __global__ void __launch_bounds__(kEventThreads, MAXB <= 10 ? 3 : 2)
     k_step_persistent(const BatchHdr* h, const Win* tab, const PSeg* seg, int* q, int* done)
 {
     const int nseg = h->p_nseg, total = h->p_total;
-    __shared__ float pts[kPersistPointsSmem<MAXB> ? 2 * (MAXB + 1) * kEventThreads : 1];
+    __shared__ __align__(16) float pts[kPersistPointsSmem<MAXB> ? 2 * (MAXB + 1) * kEventThreads : 1];
     __shared__ int hist[kMaxBands];
     __shared__ int s_item, s_ok;
     for (;;) {

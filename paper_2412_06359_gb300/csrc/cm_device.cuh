@@ -265,11 +265,10 @@ struct Traj {
 
 template <int MAXB>
 struct SmemTraj {
-    float* xs;  // this thread's column of a [MAXB + 1][kEventThreads] array
-    float* ys;
+    float2* ps;  // this thread's column of a [MAXB + 1][kEventThreads] float2 array
     float ex, ey;
-    __device__ __forceinline__ float& x(int j) { return xs[j * kEventThreads]; }
-    __device__ __forceinline__ float& y(int j) { return ys[j * kEventThreads]; }
+    __device__ __forceinline__ float& x(int j) { return ps[j * kEventThreads].x; }
+    __device__ __forceinline__ float& y(int j) { return ps[j * kEventThreads].y; }
 };
 
 // Per-event quantities shared by the forward and backward kernels.
@@ -593,13 +592,12 @@ __device__ __forceinline__ void splat_event(const Win& d, int64_t k, const Sink&
 }
 
 // the same with the points in shared memory: smem is the block's
-// [2][MAXB + 1][kEventThreads] float array
+// [MAXB + 1][kEventThreads] float2 array (16-byte aligned)
 template <int MAXB, bool NC = true, class Sink = RedSink>
 __device__ __forceinline__ void splat_event_smem(const Win& d, int64_t k, float* smem, const Sink& sink = Sink())
 {
     SmemTraj<MAXB> P;
-    P.xs = smem + threadIdx.x;
-    P.ys = smem + (MAXB + 1) * kEventThreads + threadIdx.x;
+    P.ps = reinterpret_cast<float2*>(smem) + threadIdx.x;
     splat_points<MAXB, NC>(d, k, sink, P);
 }
 
@@ -695,7 +693,7 @@ __device__ __forceinline__ float2 push_back(const Win& d, const Sink& sink, int 
 // splat stored it); the position adjoint of each reference point comes from
 // the (C, S) pairs gathered at its corners (phi_of), and the adjoint is
 // carried back along both chains of pushes, scattering dL/dflow.  The points
-// live in registers (Traj) or, given a block's [2][MAXB + 1][kEventThreads]
+// live in registers (Traj) or, given a block's [MAXB + 1][kEventThreads] float2
 // shared array `smem`, in shared memory (SmemTraj).
 template <int MAXB, bool SPLIT, bool NC = true, class Sink, class TR>
 __device__ __forceinline__ void adjoint_points(const Win& d, int64_t k, float dl, const Sink& sink, TR& P)
@@ -752,14 +750,13 @@ __device__ __forceinline__ void adjoint_event(const Win& d, int64_t k, float dl,
 }
 
 // the same with the points in shared memory: smem is the block's
-// [2][MAXB + 1][kEventThreads] float array
+// [MAXB + 1][kEventThreads] float2 array (16-byte aligned)
 template <int MAXB, class Sink = RedSink, bool SPLIT = false, bool NC = true>
 __device__ __forceinline__ void adjoint_event_smem(const Win& d, int64_t k, float dl, float* smem,
                                                    const Sink& sink = Sink())
 {
     SmemTraj<MAXB> P;
-    P.xs = smem + threadIdx.x;
-    P.ys = smem + (MAXB + 1) * kEventThreads + threadIdx.x;
+    P.ps = reinterpret_cast<float2*>(smem) + threadIdx.x;
     adjoint_points<MAXB, SPLIT, NC>(d, k, dl, sink, P);
 }
 

@@ -25,7 +25,7 @@ constexpr int kEventBlocksPerSm = MAXB <= 10 ? 4 : 2;
 template <int MAXB>
 __global__ void __launch_bounds__(kEventThreads, kEventBlocksPerSm<MAXB>) k_splat(Win d)
 {
-    __shared__ float pts[kPointsInSmem<MAXB> ? 2 * (MAXB + 1) * kEventThreads : 1];
+    __shared__ __align__(16) float pts[kPointsInSmem<MAXB> ? 2 * (MAXB + 1) * kEventThreads : 1];
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < d.n; k += (int64_t)gridDim.x * blockDim.x) {
         if (kPointsInSmem<MAXB>) splat_event_smem<MAXB>(d, k, pts);
         else splat_event<MAXB>(d, k);
@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(kEventThreads, kEventBlocksPerSm<MAXB>) k_spla
 template <int MAXB, bool SPLIT>
 __global__ void __launch_bounds__(kEventThreads, kEventBlocksPerSm<MAXB>) k_adjoint(Win d)
 {
-    __shared__ float pts[kPointsInSmem<MAXB> ? 2 * (MAXB + 1) * kEventThreads : 1];
+    __shared__ __align__(16) float pts[kPointsInSmem<MAXB> ? 2 * (MAXB + 1) * kEventThreads : 1];
     const float dl = __ldg(d.dloss);
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < d.n; k += (int64_t)gridDim.x * blockDim.x) {
         if (kPointsInSmem<MAXB>) adjoint_event_smem<MAXB, RedSink, SPLIT>(d, k, dl, pts);
