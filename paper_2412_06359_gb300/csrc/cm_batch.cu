@@ -15,14 +15,19 @@
 //
 // Schedule.  A window's images of warped events (R x H x W x 16 bytes, 54 MB at
 // 640x480 with 11 references) are zeroed by the prep pass, reduced into by the
-// splat, read by the loss pass and gathered by the adjoint; when
-// the windows in flight exceed the 129 MB L2 those passes go to DRAM.  The
-// schedule therefore groups windows (group = windows per kernel) and runs the
-// groups on a few concurrent chains of the graph, each chain taking its groups
-// one after another: a few windows are in flight, their images stay in L2, and
-// the chains overlap each other's tails and launch gaps.  group 0 puts every window in each kernel on
-// one chain.  cm_batch_autotune times the candidates on the plan's own windows.
-//
+// splat, read by the loss pass and gathered by the adjoint.  The schedule
+// groups windows (group = windows per kernel) and runs the groups on several
+// concurrent chains of the graph, each chain taking its groups one after
+// another, so the chains overlap each other's tails and launch gaps and their
+// kernels share the SMs; group 0 puts every window in each kernel on one
+// chain.  Fewer windows in flight would keep their images in the 129 MB L2
+// but leave the GPU idle between a window's phases (measured: the 64-window
+// step is fastest with 12-14 windows in flight).  Alternatives behind the same
+// interface: a persistent kernel pulling every window's phases from a device
+// work queue (persist > 0), and the deterministic mode (CM_SPLAT_SORT: each
+// window whole through the sort path, one window at a time per chain).
+// cm_batch_autotune times the candidates on the plan's own windows.
+
 // The window table, the prefix tables and the totals live in device memory;
 // cm_batch_set_windows rewrites the staging copy and the next cm_batch_run
 // uploads it before the replay.  With group 0 the graph stays valid for any
