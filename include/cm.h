@@ -365,13 +365,16 @@ int cm_batch_inject_stall(cm_batch* plan, int32_t window);
  * persist > 0 replaces the graph's kernels by one persistent kernel: its blocks
  * take work items (a pixel tile, a super-chunk, a chunk of 256 events or a
  * loss tile of one phase of one window) from a device queue in which window
- * w + 1's first phase comes `persist` phases after window w's, and before an
+ * w + 1's first phase comes persist - 1 phases after window w's, and before an
  * item a block waits (bounded) on the window's per-phase completion counters
  * for the phases it depends on; the graph holds a memset of the queue and the
  * kernel.  A few windows are then in flight, with no launch or graph edge
  * between a window's phases.
+ * A plan whose cfg->splat is CM_SPLAT_SORT (the deterministic mode) takes
+ * only {chains 1..8, group 1, bin 0, persist 0}: each window runs whole
+ * through the sort path, one window at a time on each chain.
  * Default: chains 2, group 1, bin 0, persist 0 (bin 3 when the plan's
- * cfg->splat is CM_SPLAT_TILES). */
+ * cfg->splat is CM_SPLAT_TILES; min(windows, 8) chains for CM_SPLAT_SORT). */
 typedef struct {
     int32_t chains;  /* 1..8 */
     int32_t group;   /* windows per kernel; 0 = all */
