@@ -368,8 +368,8 @@ int cm_batch_inject_stall(cm_batch* plan, int32_t window);
  * w + 1's first phase comes persist - 1 phases after window w's, and before an
  * item a block waits (bounded) on the window's per-phase completion counters
  * for the phases it depends on; the graph holds a memset of the queue and the
- * kernel.  A few windows are then in flight, with no launch or graph edge
- * between a window's phases.
+ * kernel.  There is no launch or graph edge between a window's phases; the
+ * stagger sets how many windows are in flight at once.
  * A plan whose cfg->splat is CM_SPLAT_SORT (the deterministic mode) takes
  * only {chains 1..8, group 1, bin 0, persist 0}: each window runs whole
  * through the sort path, one window at a time on each chain.
